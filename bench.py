@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: MI pose evaluations per second on the LiDAR-shaped 120k-point pair.
+
+One step is one pass of the whole hot path on one scan pair: build A's reference state
+(voxelize A, symbols, bbox, prefix counts), then a coarse-to-fine lattice search of B
+(6 levels x 4,096 poses; each level: pose rounding, transform + voxelize + accumulate,
+symbols + joint histogram, overlap + MI, argmax).  `value` counts MI pose evaluations
+per second with both scans already in device memory; `e2e` is the same through the C
+ABI from pinned host buffers (copies inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 it runs under torchrun, one independent pair per rank (weak scaling, no
+collective on the data path).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import scangen  # noqa: E402
+
+METRIC = "MI pose evals/s on 120k-pt pair; served alignment p50/p99 ms vs plain loop"
+UNIT = "pose-evals/s"
+LEVELS = 6
+COUNTS = (8, 8, 2, 2, 2, 8)
+RANGE = np.array([2.0, 2.0, 0.25, math.radians(1.0), math.radians(1.0), math.radians(5.0)])
+# Algorithmic work of the voxel map per (point, pose) and of the accumulation per in-grid
+# (point, pose), in 32-bit lane operations (see the design notes for the count).
+OPS_MAP = 29
+OPS_ACC = 4
+SM_COUNT_NOMINAL = 152
+LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def workload_config(pair, levels):
+    X, Y, Z = pair.grid.dims
+    return {
+        "workload": "lidar-120k: 64-beam ray-cast urban pair, grid 160x160x16 @ 0.5 m, z-variance 16 symbols, "
+                    f"set_reference + {levels}-level lattice search of 4,096 poses per level",
+        "points_A": int(pair.xyzA.shape[0]),
+        "points_B": int(pair.xyzB.shape[0]),
+        "grid": f"{X}x{Y}x{Z}@{pair.grid.res_m}m",
+        "poses_per_level": int(np.prod(COUNTS)),
+        "levels": levels,
+        "lattice": "x".join(str(c) for c in COUNTS),
+        "l2": "flushed between steps (256 MiB write)",
+        "parallelism": "replicas (one independent pair per GPU)",
+    }
+
+
+# --------------------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self, t_begin=None, t_end=None):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if t_begin is not None and not (t_begin - 0.05 <= ts <= t_end + 0.05):
+                    continue
+            except ValueError:
+                pass
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def committed_traffic():
+    """Per-launch DRAM bytes of the eval kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "eval_kernel_lidar120k.md")
+    src = os.path.join(ROOT, "paper_1709_06948_gb300", "csrc", "eval.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except Exception:
+        return None
+    m_sha = re.search(r"eval\.cu sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != digest:
+        return None
+    return float(m_b.group(1))
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle (reference arm and the cpu_baseline leg)
+# --------------------------------------------------------------------------------------
+def oracle_rate(pair, n_poses, nthreads):
+    import oracle
+    G = oracle.Grid(pair.grid.origin, pair.grid.res_m, pair.grid.dims, pair.grid.feature, pair.grid.count_levels,
+                    pair.grid.var_levels)
+    symA, boxA = G.reference(pair.xyzA)
+    etas = oracle.lattice(np.zeros(6), RANGE, COUNTS)[:n_poses]
+    poses = G.round_pose(etas)
+    t0 = time.perf_counter()
+    G.eval_mi(symA, boxA, pair.xyzB, poses, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return n_poses / dt, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    pair = scangen.lidar_pair()
+    cores = oracle.host_cores()
+    sample = 128
+    for _ in range(args.warmup):
+        oracle_rate(pair, sample, cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_rate(pair, sample, cores)
+        times.append(dt)
+    total = sum(times)
+    value = sample * args.steps / total
+    desc = (f"{sample} level-0 lattice poses of the 120k-point pair per step, oracle (dense per-pose arrays, "
+            f"FP64 MI) on {cores} host threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(pair, LEVELS),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_1709_06948_gb300 import align
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    pair = scangen.lidar_pair(seed=scangen.SEED_BASE + 2 + rank)
+    spec = pair.grid
+    stream = torch.cuda.current_stream()
+    L = align.align_create_grid(spec.origin, spec.res_m, spec.dims, spec.feature, spec.count_levels,
+                                spec.var_levels, stream=stream)
+    A = torch.from_numpy(pair.xyzA).cuda()
+    B = torch.from_numpy(pair.xyzB).cuda()
+    init = np.zeros(6)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        align.align_set_reference(L, A)
+        return align.align_search(L, B, init, RANGE, levels=LEVELS)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    # in-grid point count of B at the lattice centre (for the accumulation op count)
+    ident = align.align_round_poses(spec.origin, np.zeros((1, 6)))[0]
+    acc, _ = align.align_accumulate(L, pair.xyzB, ident)
+    n_in = int(acc[:, 0].sum())
+    del acc
+
+    dev_props = torch.cuda.get_device_properties(local)
+    gpu_id = None
+    uuid = getattr(dev_props, "uuid", None)
+    if uuid is not None:
+        u = str(uuid)
+        gpu_id = u if u.startswith("GPU-") else "GPU-" + u
+    sampler = ClockSampler(gpu_id)
+    launches0 = align.align_eval_stats(L)["kernel_launches"]
+    align.align_profile(L, 1)
+    sampler.start()
+    time.sleep(0.5)  # let nvidia-smi start sampling
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_begin = time.time()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        T, mi, _ = step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_end = time.time()
+    clocks = sampler.stop(t_begin, t_end)
+    prof = align.align_profile(L, 2)
+    align.align_profile(L, 0)
+    launches = align.align_eval_stats(L)["kernel_launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    P = int(np.prod(COUNTS))
+    evals_per_step = P * LEVELS
+    value = ws * evals_per_step * args.steps / (total_ms / 1000.0)
+
+    # ---- end to end through the C ABI from pinned host buffers ----
+    A_pin = torch.from_numpy(pair.xyzA).pin_memory()
+    B_pin = torch.from_numpy(pair.xyzB).pin_memory()
+    A_h, B_h = A_pin.numpy(), B_pin.numpy()
+    e2e_steps = max(1, min(args.steps, 50))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        align.align_set_reference(L, A_h)
+        align.align_search(L, B_h, init, RANGE, levels=LEVELS)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * evals_per_step * e2e_steps / e2e_s
+    h2d = (pair.xyzA.shape[0] + pair.xyzB.shape[0]) * 12 + LEVELS * P * 48
+    d2h = 24 + LEVELS * (8 + 12 + 4)
+
+    # ---- roofline of the dominant kernel (eval) ----
+    eval_ms = prof[0] / max(prof[2], 1)
+    nB = pair.xyzB.shape[0]
+    ops_per_launch = P * (nB * OPS_MAP + n_in * OPS_ACC)
+    achieved = ops_per_launch / (eval_ms / 1000.0) / 1e12
+    sm_count = dev_props.multi_processor_count
+    peak = sm_count * LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    traffic = committed_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "eval_kernel", "eval_kernel_ms": eval_ms,
+                "ops_per_launch": ops_per_launch,
+                "peak_basis": f"{sm_count} SMs x {LANES_PER_SM} int32/fp32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz "
+                              "(nominal max SM clock; of derived peak, no measured ALU peak exists)",
+                "kernel_share_of_step": (prof[0] / total_ms) if total_ms > 0 else None}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+i32", "data": "synthetic", "config": workload_config(pair, LEVELS), "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "result_check": {"T": [float(x) for x in T], "T_true": [float(x) for x in pair.T], "mi": mi}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = oracle.host_cores()
+        n_sample = 2048
+        rate, dt = oracle_rate(pair, n_sample, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{n_sample} of the 4,096 level-0 lattice poses on the same pair, "
+                                          f"{dt:.1f} s wall on {cores} threads (MI evaluations only)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    L.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,171 @@
+/*
+ * align.h — C ABI of the GB300 library for the voxelized-feature mutual-information
+ * (MI) scan-alignment cost of Mehta, McBride & Pandey, "Robust and Fast 3D Scan
+ * Alignment using Mutual Information" (arXiv 1709.06948).
+ *
+ * The library evaluates, for large batches of candidate 6-DOF poses of scan B, the
+ * MI between the voxel feature maps of scan A and of the transformed scan B over
+ * their overlapping bounding region (Sec. III-A, Algorithm 1, Eqs. 1-5), and the
+ * pose of maximum MI.  All compute runs in hand-written CUDA kernels on one GPU;
+ * there is no CPU fallback: without a usable GPU every call fails with
+ * ALIGN_E_CUDA.
+ *
+ * Conventions (fixed here because the paper leaves them open):
+ *  - A pose eta = [tx, ty, tz, thx, thy, thz] (metres, radians) maps B's frame into
+ *    A's frame: p_A = R p_B + t with R = Rz(thz) Ry(thy) Rx(thx) (Sec. I, Eq. 1).
+ *    R is evaluated in FP64 on the host and rounded once to FP32; the translation is
+ *    stored relative to the grid origin: pose12 = [r00 r01 r02 r10 r11 r12 r20 r21
+ *    r22 t'x t'y t'z] with t' = fp32(t - origin).
+ *  - Voxel of a point (Sec. III-A, Algorithm 1 "extract voxel ids"), in FP32:
+ *      u_i = fma(r_i0, x, fma(r_i1, y, r_i2 * z));  g_i = u_i + t'_i;
+ *      k_i = floor(g_i * fp32(1/res));  inside iff 0 <= k_i < dims_i;
+ *      key = (k_z * Y + k_y) * X + k_x.
+ *    Points outside the grid are dropped.
+ *  - z-height in whole millimetres: zq = round-half-even(g_z * 1000),
+ *    dz = zq - k_z * res_mm.  Per voxel the exact integer sums n, S1 = sum dz and
+ *    S2 = sum dz^2 are kept.
+ *  - Features (Sec. III-A: "number of points in voxel", "variance of z-height";
+ *    unoccupied voxels keep the no-feature value phi = symbol 0):
+ *      count level    = #{ j : n >= count_thresh[j] }            (0 .. L_c-1)
+ *      variance level = #{ j : n*S2 - S1^2 >= var_thresh[j] * n^2 } (0 .. L_v-1)
+ *      symbol = 0 if n == 0, else
+ *        ALIGN_FEAT_COUNT:      1 + count level              (K = 1 + L_c)
+ *        ALIGN_FEAT_ZVAR:       1 + variance level           (K = 1 + L_v)
+ *        ALIGN_FEAT_COUNT_ZVAR: 1 + count level * L_v + variance level (K = 1 + L_c*L_v)
+ *    Defaults: count_thresh[j] = 2^(j+1); var_thresh[j] = floor(res_mm^2 / 2^(2 + L_v-1-j)).
+ *  - Overlap region (Algorithm 1): the inclusive voxel-index bounding boxes of the
+ *    occupied voxels of A and of transformed B, intersected (max of minima, min of
+ *    maxima).  Every voxel of the region counts, phi voxels included (Sec. III-A).
+ *    An empty region gives MI = 0.
+ *  - MI = H(X) + H(Y) - H(X,Y) (Eqs. 2-5) with p = count / N_o over the region's
+ *    N_o voxels, natural log, 0 log 0 = 0; evaluated in FP32 on the GPU.
+ *  - argmax (Eq. 1): the largest MI; ties go to the lowest pose index.
+ *
+ * Limits: dims_i in [1, 2^20], X*Y*Z < 2^31, res in whole millimetres in [1, 8000]
+ * mm, L_c, L_v >= 1 with K <= 64, point counts < 2^31, poses per call < 2^31.
+ *
+ * Threading: a grid and everything enqueued on it belong to one host thread at a
+ * time.  Errors are return codes; align_last_error() describes the last failure of
+ * the calling thread.  No function aborts or throws.
+ */
+#ifndef ALIGN_H
+#define ALIGN_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ALIGN_API_VERSION 1
+
+typedef enum {
+  ALIGN_OK = 0,
+  ALIGN_NOT_READY = 1,     /* align_poll: request still running */
+  ALIGN_E_INVALID = -1,    /* bad argument (message in align_last_error) */
+  ALIGN_E_OOM = -2,        /* device or pinned host allocation failed */
+  ALIGN_E_CUDA = -3,       /* CUDA runtime error, or no usable GPU */
+  ALIGN_E_BUSY = -4,       /* server admission refused (queue full / over budget) */
+  ALIGN_E_TIMEOUT = -5,    /* a bounded device or host wait gave up */
+  ALIGN_E_NOREF = -6,      /* align_set_reference has not been called on this grid */
+  ALIGN_E_INTERNAL = -7    /* a kernel reported a violated internal bound */
+} align_status;
+
+typedef enum { ALIGN_FEAT_COUNT = 0, ALIGN_FEAT_ZVAR = 1, ALIGN_FEAT_COUNT_ZVAR = 2 } align_feature;
+
+/* Where the buffers of a call live (bit flags).  Without ALIGN_XYZ_DEVICE the points
+   are host memory and are copied before the call returns.  With ALIGN_OUT_DEVICE the
+   outputs are device pointers and the call returns without waiting for the GPU: the
+   results are ready when the grid's stream reaches that point. */
+enum {
+  ALIGN_XYZ_DEVICE = 1,
+  ALIGN_POSES_DEVICE = 2,
+  ALIGN_OUT_DEVICE = 4
+};
+
+typedef struct {
+  float origin[3];               /* grid corner (min x, y, z) in A's frame, metres */
+  float res_m;                   /* voxel edge R_v, metres, whole millimetres */
+  int32_t dims[3];               /* X, Y, Z */
+  int32_t feature;               /* align_feature */
+  int32_t count_levels;          /* L_c (count levels of an occupied voxel) */
+  int32_t var_levels;            /* L_v (z-variance levels of an occupied voxel) */
+  const uint32_t* count_thresh;  /* L_c-1 ascending thresholds on n, or NULL */
+  const int64_t* var_thresh;     /* L_v-1 ascending thresholds in mm^2, or NULL */
+} align_grid_desc;
+
+typedef struct align_grid align_grid;     /* opaque; owns its device state */
+
+/* Create a grid (Sec. III-A: one grid of resolution R_v covering both scans).
+   cuda_stream: a cudaStream_t to enqueue all of this grid's work on (NULL = legacy
+   default stream).  The desc and its threshold arrays are copied. */
+align_status align_create_grid(const align_grid_desc* desc, void* cuda_stream, align_grid** out);
+align_status align_destroy_grid(align_grid* grid);
+
+/* K (symbols, empty included) and V (voxels) of a grid. */
+align_status align_grid_info(const align_grid* grid, int32_t* n_symbols, int64_t* n_voxels);
+
+/* Algorithm 1 initialisation: voxelize scan A (never moved), build A's feature map,
+   A's bounding box and per-symbol 3-D prefix counts.  xyzA: nA x 3 fp32 (host, or
+   device with ALIGN_XYZ_DEVICE).  The state stays resident until the next call or
+   align_destroy_grid.  nA may be 0 (every overlap is then empty and MI = 0). */
+align_status align_set_reference(align_grid* grid, const float* xyzA, int64_t nA, int flags);
+
+/* Copy A's feature map (V bytes, host) and bbox [xmin,ymin,zmin,xmax,ymax,zmax]
+   (xmin > xmax when A has no point in the grid) to the caller.  Either may be NULL. */
+align_status align_get_reference(align_grid* grid, uint8_t* symA, int32_t boxA[6]);
+
+/* Host-side pose rounding (the convention above) for a grid whose corner is `origin`:
+   eta6 P x 6 FP64 -> poses12 P x 12 FP32.  Pure host code; needs no GPU. */
+align_status align_round_poses(const float origin[3], const double* eta6, int64_t P, float* poses12);
+
+/* MI for a batch of P poses of scan B (Algorithm 1 loop body for every pose; Eqs. 1-5).
+   xyzB: nB x 3 fp32.  Poses: either poses12 (P x 12 FP32, host or device with
+   ALIGN_POSES_DEVICE) or eta6 (P x 6 FP64, host); exactly one non-NULL.
+   mi_out: P floats.  argmax_out: one int64 (may be NULL).  hist_out (may be NULL):
+   P x K x K uint32 joint histograms, row = A symbol, column = B symbol.
+   P may be 0 (nothing is written; *argmax_out = -1). */
+align_status align_eval_mi(align_grid* grid, const float* xyzB, int64_t nB, int flags,
+                           const float* poses12, const double* eta6, int64_t P,
+                           float* mi_out, int64_t* argmax_out, uint32_t* hist_out);
+
+/* Per-voxel integer sums of B under one pose, from the same kernel that serves
+   align_eval_mi: acc_out (host) V x 3 int64 rows (n, S1, S2), zero for empty voxels;
+   box_out: B's occupied bbox as above.  For parity checks of the voxel map. */
+align_status align_accumulate(align_grid* grid, const float* xyzB, int64_t nB, int flags,
+                              const float pose12[12], int64_t* acc_out, int32_t box_out[6]);
+
+/* Coarse-to-fine lattice search standing in for Algorithm 1's Nelder-Mead loop:
+   per level, counts[a] evenly spaced samples of each axis over centre +- range
+   (a single sample sits at the centre), poses ordered rotation axes outermost
+   (rx, ry, rz, tx, ty, tz; the last fastest); the best pose becomes the next
+   centre and every range halves.  T_out: final centre (eta); mi_out: its MI.
+   align_search uses counts = {8, 8, 2, 2, 2, 8} (4,096 poses per level).
+   level_best (may be NULL): each level's argmax index. */
+align_status align_search(align_grid* grid, const float* xyzB, int64_t nB, int flags,
+                          const double init[6], const double range[6], int32_t levels,
+                          double T_out[6], float* mi_out);
+align_status align_search_ex(align_grid* grid, const float* xyzB, int64_t nB, int flags,
+                             const double init[6], const double range[6], const int32_t counts[6],
+                             int32_t levels, double T_out[6], float* mi_out, int64_t* level_best);
+
+/* Counters of the last synchronising evaluation on this grid (host ints):
+   [0] key-partition passes of the hardest pose so far, [1] voxels that needed the
+   wide (64-bit) side sums, [2] hash-table slots per CTA, [3] CTAs of the last eval
+   launch, [4] kernels launched by this grid since creation. */
+align_status align_eval_stats(align_grid* grid, int64_t out[5]);
+
+/* Kernel timing with CUDA events recorded on the grid's stream around every eval
+   kernel and every compose+argmax pair.  mode 1: enable and reset the totals;
+   mode 0: disable; mode 2: only read.  out (may be NULL): [0] total eval-kernel ms,
+   [1] total compose+argmax ms, [2] eval launches timed.  Totals are gathered at
+   each synchronising call (host outputs, align_search). */
+align_status align_profile(align_grid* grid, int32_t mode, double out[3]);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* align_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,305 @@
+"""Python binding of the C ABI in include/align.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but
+check shapes, pick host/device flags and pass pointers: all of the method's work runs
+in the library's CUDA kernels.  Host inputs are numpy arrays; device inputs and
+outputs are torch CUDA tensors (torch supplies device memory and streams only).
+If the shared library cannot be loaded the calls raise: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ALIGN_OK, ALIGN_NOT_READY = 0, 1
+ALIGN_E_INVALID, ALIGN_E_OOM, ALIGN_E_CUDA, ALIGN_E_BUSY, ALIGN_E_TIMEOUT, ALIGN_E_NOREF, ALIGN_E_INTERNAL = (
+    -1, -2, -3, -4, -5, -6, -7)
+ALIGN_FEAT_COUNT, ALIGN_FEAT_ZVAR, ALIGN_FEAT_COUNT_ZVAR = 0, 1, 2
+ALIGN_XYZ_DEVICE, ALIGN_POSES_DEVICE, ALIGN_OUT_DEVICE = 1, 2, 4
+
+_STATUS_NAMES = {0: "ALIGN_OK", 1: "ALIGN_NOT_READY", -1: "ALIGN_E_INVALID", -2: "ALIGN_E_OOM", -3: "ALIGN_E_CUDA",
+                 -4: "ALIGN_E_BUSY", -5: "ALIGN_E_TIMEOUT", -6: "ALIGN_E_NOREF", -7: "ALIGN_E_INTERNAL"}
+
+# Every entry point include/align.h declares (checked by the tests against the .so).
+EXPORTS = ["align_create_grid", "align_destroy_grid", "align_grid_info", "align_set_reference",
+           "align_get_reference", "align_round_poses", "align_eval_mi", "align_accumulate", "align_search",
+           "align_search_ex", "align_eval_stats", "align_profile", "align_last_error"]
+
+
+class AlignError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("res_m", C.c_float), ("dims", C.c_int32 * 3), ("feature", C.c_int32),
+                ("count_levels", C.c_int32), ("var_levels", C.c_int32), ("count_thresh", C.c_void_p),
+                ("var_thresh", C.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the in-tree libmialign.so."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path}")
+    lib = C.CDLL(path)
+    P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "align_create_grid": [P, P, P],
+        "align_destroy_grid": [P],
+        "align_grid_info": [P, P, P],
+        "align_set_reference": [P, P, i64, C.c_int],
+        "align_get_reference": [P, P, P],
+        "align_round_poses": [P, P, i64, P],
+        "align_eval_mi": [P, P, i64, C.c_int, P, P, i64, P, P, P],
+        "align_accumulate": [P, P, i64, C.c_int, P, P, P],
+        "align_search": [P, P, i64, C.c_int, P, P, i32, P, P],
+        "align_search_ex": [P, P, i64, C.c_int, P, P, P, i32, P, P, P],
+        "align_eval_stats": [P, P],
+        "align_profile": [P, i32, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.align_last_error.argtypes = []
+    lib.align_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def align_last_error() -> str:
+    return load().align_last_error().decode()
+
+
+def _check(status: int):
+    if status != ALIGN_OK:
+        raise AlignError(status, align_last_error())
+
+
+# ---------------------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------------------
+def _is_torch_cuda(x) -> bool:
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _host(a, dtype, shape_tail=None):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if shape_tail is not None:
+        a = a.reshape(-1, *shape_tail) if a.size else a.reshape(0, *shape_tail)
+    return a
+
+
+def _points_arg(xyz):
+    """(pointer, n, flags) for a points array (numpy host or torch CUDA)."""
+    if _is_torch_cuda(xyz):
+        import torch
+        if xyz.dtype != torch.float32 or not xyz.is_contiguous() or xyz.dim() != 2 or xyz.shape[1] != 3:
+            raise ValueError("device points must be a contiguous (n, 3) float32 CUDA tensor")
+        return C.c_void_p(xyz.data_ptr()), int(xyz.shape[0]), ALIGN_XYZ_DEVICE, xyz
+    a = _host(xyz, np.float32, (3,))
+    return a.ctypes.data_as(C.c_void_p), int(a.shape[0]), 0, a
+
+
+class Grid:
+    """Owns an align_grid*.  `stream` is a torch.cuda.Stream, a raw cudaStream_t int, or None
+    (torch's current stream at creation)."""
+
+    def __init__(self, handle, desc_kw, stream_obj):
+        self._h = handle
+        self.desc = desc_kw
+        self._stream_obj = stream_obj
+        K = C.c_int32(0)
+        V = C.c_int64(0)
+        _check(load().align_grid_info(self._h, C.byref(K), C.byref(V)))
+        self.K = int(K.value)
+        self.V = int(V.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().align_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def align_create_grid(origin, res_m, dims, feature=ALIGN_FEAT_ZVAR, count_levels=7, var_levels=15,
+                      count_thresh=None, var_thresh=None, stream=None) -> Grid:
+    lib = load()
+    d = GridDesc()
+    d.origin = (C.c_float * 3)(*[float(v) for v in origin])
+    d.res_m = float(res_m)
+    d.dims = (C.c_int32 * 3)(*[int(v) for v in dims])
+    d.feature = int(feature)
+    d.count_levels = int(count_levels)
+    d.var_levels = int(var_levels)
+    ct = None if count_thresh is None else np.ascontiguousarray(count_thresh, dtype=np.uint32)
+    vt = None if var_thresh is None else np.ascontiguousarray(var_thresh, dtype=np.int64)
+    d.count_thresh = None if ct is None else ct.ctypes.data
+    d.var_thresh = None if vt is None else vt.ctypes.data
+    stream_obj = stream
+    if stream is None:
+        try:
+            import torch
+            stream_obj = torch.cuda.current_stream() if torch.cuda.is_available() else None
+        except Exception:
+            stream_obj = None
+    raw = 0
+    if stream_obj is not None:
+        raw = stream_obj if isinstance(stream_obj, int) else int(stream_obj.cuda_stream)
+    h = C.c_void_p()
+    _check(lib.align_create_grid(C.byref(d), C.c_void_p(raw), C.byref(h)))
+    return Grid(h, dict(origin=tuple(origin), res_m=res_m, dims=tuple(dims), feature=feature,
+                        count_levels=count_levels, var_levels=var_levels), stream_obj)
+
+
+def align_destroy_grid(grid: Grid):
+    grid.close()
+
+
+def align_set_reference(grid: Grid, xyzA):
+    ptr, n, flags, keep = _points_arg(xyzA)
+    _check(load().align_set_reference(grid.handle, ptr, n, flags))
+    del keep
+
+
+def align_get_reference(grid: Grid):
+    sym = np.empty(grid.V, dtype=np.uint8)
+    box = np.empty(6, dtype=np.int32)
+    _check(load().align_get_reference(grid.handle, sym.ctypes.data_as(C.c_void_p), box.ctypes.data_as(C.c_void_p)))
+    return sym, box
+
+
+def align_round_poses(origin, eta6) -> np.ndarray:
+    """FP64 eta rows -> FP32 pose12 rows for a grid with corner `origin` (host code, no GPU)."""
+    o = np.ascontiguousarray(origin, dtype=np.float32).reshape(3)
+    eta = _host(eta6, np.float64, (6,))
+    out = np.empty((eta.shape[0], 12), dtype=np.float32)
+    _check(load().align_round_poses(o.ctypes.data_as(C.c_void_p), eta.ctypes.data_as(C.c_void_p), eta.shape[0],
+                                    out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def align_eval_mi(grid: Grid, xyzB, poses12=None, eta6=None, with_hist=False, out=None):
+    """MI for a batch of poses.  Host inputs -> (mi np.float32[P], argmax int, hist or None).
+    With device tensors for `poses12` or `out=(mi, argmax, hist)`, outputs stay on the GPU
+    (returned as the given tensors, not synchronised)."""
+    lib = load()
+    pptr, n, flags, keep_pts = _points_arg(xyzB)
+    keep = [keep_pts]
+    if (poses12 is None) == (eta6 is None):
+        raise ValueError("give exactly one of poses12 and eta6")
+    if poses12 is not None:
+        if _is_torch_cuda(poses12):
+            import torch
+            if poses12.dtype != torch.float32 or not poses12.is_contiguous():
+                raise ValueError("device poses must be contiguous float32")
+            P = int(poses12.numel() // 12)
+            poses_ptr = C.c_void_p(poses12.data_ptr())
+            flags |= ALIGN_POSES_DEVICE
+        else:
+            ph = _host(poses12, np.float32, (12,))
+            keep.append(ph)
+            P = int(ph.shape[0])
+            poses_ptr = ph.ctypes.data_as(C.c_void_p)
+        eta_ptr = None
+    else:
+        eh = _host(eta6, np.float64, (6,))
+        keep.append(eh)
+        P = int(eh.shape[0])
+        poses_ptr = None
+        eta_ptr = eh.ctypes.data_as(C.c_void_p)
+    if out is not None:
+        mi_t, am_t, hist_t = out
+        flags |= ALIGN_OUT_DEVICE
+        _check(lib.align_eval_mi(grid.handle, pptr, n, flags, poses_ptr, eta_ptr, P, C.c_void_p(mi_t.data_ptr()),
+                                 None if am_t is None else C.c_void_p(am_t.data_ptr()),
+                                 None if hist_t is None else C.c_void_p(hist_t.data_ptr())))
+        return out
+    mi = np.empty(P, dtype=np.float32)
+    am = C.c_int64(-1)
+    hist = np.empty((P, grid.K, grid.K), dtype=np.uint32) if with_hist else None
+    _check(lib.align_eval_mi(grid.handle, pptr, n, flags, poses_ptr, eta_ptr, P, mi.ctypes.data_as(C.c_void_p),
+                             C.byref(am), None if hist is None else hist.ctypes.data_as(C.c_void_p)))
+    del keep
+    return mi, int(am.value), hist
+
+
+def align_accumulate(grid: Grid, xyzB, pose12):
+    """Per-voxel (n, S1, S2) int64 [V, 3] and B's occupied bbox under one pose."""
+    pptr, n, flags, keep = _points_arg(xyzB)
+    pose = _host(pose12, np.float32).reshape(12)
+    acc = np.empty((grid.V, 3), dtype=np.int64)
+    box = np.empty(6, dtype=np.int32)
+    _check(load().align_accumulate(grid.handle, pptr, n, flags, pose.ctypes.data_as(C.c_void_p),
+                                   acc.ctypes.data_as(C.c_void_p), box.ctypes.data_as(C.c_void_p)))
+    del keep
+    return acc, box
+
+
+def align_search(grid: Grid, xyzB, init, rng, levels=6, counts=None):
+    """Coarse-to-fine lattice search; returns (T eta[6], MI at T, per-level argmax)."""
+    lib = load()
+    pptr, n, flags, keep = _points_arg(xyzB)
+    init = _host(init, np.float64).reshape(6)
+    rng = _host(rng, np.float64).reshape(6)
+    T = np.zeros(6, dtype=np.float64)
+    mi = C.c_float(0.0)
+    lb = np.zeros(max(levels, 1), dtype=np.int64)
+    if counts is None:
+        _check(lib.align_search(grid.handle, pptr, n, flags, init.ctypes.data_as(C.c_void_p),
+                                rng.ctypes.data_as(C.c_void_p), int(levels), T.ctypes.data_as(C.c_void_p),
+                                C.byref(mi)))
+        del keep
+        return T, float(mi.value), None
+    cnt = np.ascontiguousarray(counts, dtype=np.int32)
+    _check(lib.align_search_ex(grid.handle, pptr, n, flags, init.ctypes.data_as(C.c_void_p),
+                               rng.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p), int(levels),
+                               T.ctypes.data_as(C.c_void_p), C.byref(mi), lb.ctypes.data_as(C.c_void_p)))
+    del keep
+    return T, float(mi.value), lb[:levels]
+
+
+def align_eval_stats(grid: Grid):
+    out = np.zeros(5, dtype=np.int64)
+    _check(load().align_eval_stats(grid.handle, out.ctypes.data_as(C.c_void_p)))
+    return {"passes": int(out[0]), "wide_voxels": int(out[1]), "table_slots": int(out[2]), "ctas": int(out[3]),
+            "kernel_launches": int(out[4])}
+
+
+def align_profile(grid: Grid, mode: int):
+    """mode 1: enable + reset, 0: disable, 2: read.  Returns (eval ms total, compose ms total,
+    eval launches timed)."""
+    out = np.zeros(3, dtype=np.float64)
+    _check(load().align_profile(grid.handle, int(mode), out.ctypes.data_as(C.c_void_p)))
+    return float(out[0]), float(out[1]), int(out[2])

@@ -1,0 +1,81 @@
+// align_internal.h — device-side conventions and launch interfaces shared by the
+// library's translation units (never by the CPU oracle).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mialign {
+
+constexpr int kMaxSymbols = 64;
+constexpr int kMaxLevels = 63;
+constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
+
+// Error bits written by kernels into the grid's error word.
+enum : uint32_t {
+  kErrDzBound = 1u,       // |dz| above the bound the 32-bit sums were sized for
+  kErrWaitTimeout = 2u,   // a bounded mbarrier wait gave up
+  kErrPassLimit = 4u,     // key partitioning could not make the table fit
+};
+
+// Grid constants passed by value to every kernel (Sec. III-A grid + feature definition).
+struct GridConst {
+  float inv_res;          // fp32(1/res)
+  int32_t res_mm;         // voxel edge in whole millimetres
+  int32_t X, Y, Z;
+  int32_t K;              // symbols including phi (0)
+  int32_t feature;        // 0 count, 1 z-variance, 2 joint
+  int32_t Lc, Lv;         // occupied levels
+  int32_t dz_bound;       // |dz| <= dz_bound for every in-grid point
+  uint32_t nlim;          // largest n whose S1, S2 fit the 32-bit table sums
+  int32_t boxA[6];        // A's occupied bbox (xmin > xmax when empty)
+  uint32_t count_thresh[kMaxLevels];
+  int64_t var_thresh[kMaxLevels];
+};
+
+// Pose-batched evaluation: per pose, per-voxel sums in a shared-memory hash table,
+// then the partial joint histogram c[a][b>=1] of the occupied B voxels inside boxA and
+// B's occupied bbox.
+struct EvalArgs {
+  const float* xyz;        // padded point buffer, n_tiles * tile_points * 3 floats
+  int32_t n_points;
+  int32_t n_tiles;
+  const float* poses;      // P x 12
+  int32_t P;
+  const uint8_t* symA;     // V
+  uint32_t* out_c;         // P x K x K (B-occupied voxels inside boxA)
+  int32_t* out_box;        // P x 6
+  uint32_t* err;           // error bits
+  uint32_t* max_passes;    // running max of key-partition passes (seed for the next launch)
+  uint32_t* wide_count;    // voxels that overflowed into the 64-bit side sums
+  unsigned long long* wide;// per CTA: table_slots x 2 (S1 as two's complement, S2)
+  int32_t table_slots;
+  int32_t passes0;         // initial key-partition passes (power of two)
+  int64_t* dump;           // optional: V x 3 (n, S1, S2) for pose 0 (parity checks)
+};
+
+struct ComposeArgs {
+  const uint32_t* c;       // P x K x K
+  const int32_t* boxB;     // P x 6
+  const int32_t* sat;      // (K-1) x (Z+1) x (Y+1) x (X+1)
+  int32_t P;
+  float* mi;               // P
+  uint32_t* hist;          // optional P x K x K full joint histogram
+  unsigned long long* best;// packed (MI, ~index) running max
+};
+
+// Launch helpers (defined in eval.cu / reference.cu).
+int eval_tile_points();
+size_t eval_smem_bytes(int K, int table_slots);
+int eval_table_slots_for(int K, size_t smem_budget);
+cudaError_t launch_eval(const GridConst& gc, const EvalArgs& a, int n_ctas, cudaStream_t s);
+cudaError_t launch_compose(const GridConst& gc, const ComposeArgs& a, cudaStream_t s);
+cudaError_t launch_argmax_finalize(const unsigned long long* best, int64_t* out, cudaStream_t s);
+
+cudaError_t launch_ref_accumulate(const GridConst& gc, const float* xyz, int64_t n, const float* pose12,
+                                  uint32_t* cnt, unsigned long long* s1, unsigned long long* s2,
+                                  cudaStream_t s);
+cudaError_t launch_ref_symbols(const GridConst& gc, const uint32_t* cnt, const unsigned long long* s1,
+                               const unsigned long long* s2, uint8_t* symA, int32_t* box, cudaStream_t s);
+cudaError_t launch_ref_sat(const GridConst& gc, const uint8_t* symA, int32_t* sat, cudaStream_t s);
+
+}  // namespace mialign

@@ -1,0 +1,144 @@
+// device_common.cuh — device-side steps of the method shared by the library's kernels:
+// the voxel-point map of one point under one pose, the feature symbol of one voxel,
+// and the inline-PTX wrappers for mbarriers and bulk (TMA) copies.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "align_internal.h"
+
+namespace mialign {
+
+// ---------------------------------------------------------------------------------
+// Voxel-point map (Sec. III-A; Algorithm 1 "transform scan B", "extract voxel ids").
+// The FP32 operation order is fixed so that every implementation of the convention
+// gets the same voxel for every point:
+//   u_i = fma(r_i0, x, fma(r_i1, y, r_i2 * z)),  g_i = u_i + t'_i,
+//   k_i = floor(g_i * inv_res),  inside iff 0 <= k_i < dims_i,
+//   zq = round-half-even(g_z * 1000),  dz = zq - k_z * res_mm.
+// Intrinsics with explicit rounding keep the compiler from contracting or reordering.
+// Returns the linear key, or kEmptyKey outside the grid.
+// ---------------------------------------------------------------------------------
+struct Pose12 {
+  float r[9];
+  float t[3];
+};
+
+__device__ __forceinline__ uint32_t voxel_key(const Pose12& P, float x, float y, float z, float inv_res,
+                                              int X, int Y, int Z, int res_mm, int* dz) {
+  const float gx = __fadd_rn(__fmaf_rn(P.r[0], x, __fmaf_rn(P.r[1], y, __fmul_rn(P.r[2], z))), P.t[0]);
+  const float gy = __fadd_rn(__fmaf_rn(P.r[3], x, __fmaf_rn(P.r[4], y, __fmul_rn(P.r[5], z))), P.t[1]);
+  const float gz = __fadd_rn(__fmaf_rn(P.r[6], x, __fmaf_rn(P.r[7], y, __fmul_rn(P.r[8], z))), P.t[2]);
+  const float fx = __fmul_rn(gx, inv_res);
+  const float fy = __fmul_rn(gy, inv_res);
+  const float fz = __fmul_rn(gz, inv_res);
+  // floor(f) in [0, D)  <=>  f in [0, D)  (NaN fails both compares)
+  const bool in = (fx >= 0.0f) & (fx < (float)X) & (fy >= 0.0f) & (fy < (float)Y) & (fz >= 0.0f) &
+                  (fz < (float)Z);
+  if (!in) return kEmptyKey;
+  const int kx = __float2int_rd(fx);
+  const int ky = __float2int_rd(fy);
+  const int kz = __float2int_rd(fz);
+  const int zq = __float2int_rn(__fmul_rn(gz, 1000.0f));
+  *dz = zq - kz * res_mm;
+  return (uint32_t)((kz * Y + ky) * X + kx);
+}
+
+// ---------------------------------------------------------------------------------
+// Feature symbol of one voxel from its exact integer sums (Sec. III-A features; phi = 0).
+// count level    = #{ j : n >= ct[j] }                     (ct ascending)
+// variance level = #{ j : n*S2 - S1^2 >= vt[j] * n^2 }      (vt ascending; exact in 128 bits)
+// Both sets are prefixes of the ascending thresholds, so a binary search finds the count.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ int count_level(const uint32_t* ct, int Lc, uint64_t n) {
+  int lo = 0, hi = Lc - 1;  // answer in [0, Lc-1]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (n >= (uint64_t)ct[mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int var_level(const int64_t* vt, int Lv, uint64_t n, int64_t s1, uint64_t s2) {
+  const __int128 spread = (__int128)n * (__int128)s2 - (__int128)s1 * (__int128)s1;  // n^2 * var
+  const __int128 n2 = (__int128)n * (__int128)n;
+  int lo = 0, hi = Lv - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (spread >= (__int128)vt[mid] * n2) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int feature_symbol(int feature, int Lc, int Lv, const uint32_t* ct, const int64_t* vt,
+                                              uint64_t n, int64_t s1, uint64_t s2) {
+  if (n == 0) return 0;
+  if (feature == 0) return 1 + count_level(ct, Lc, n);
+  if (feature == 1) return 1 + var_level(vt, Lv, n, s1, s2);
+  return 1 + count_level(ct, Lc, n) * Lv + var_level(vt, Lv, n, s1, s2);
+}
+
+// ---------------------------------------------------------------------------------
+// mbarrier / bulk-copy wrappers (sm_90+ PTX)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: false after limit_ns without completion (the caller reports an error).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_timer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// 1-D bulk copy global -> shared, completion counted on an mbarrier (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
+
+}  // namespace mialign

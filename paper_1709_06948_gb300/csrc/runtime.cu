@@ -1,0 +1,679 @@
+// runtime.cu — the C ABI of include/align.h: grids with resident reference state,
+// pose-batched MI evaluation, per-voxel sum export, lattice search, errors.
+// Host code is compiled with -ffp-contract=off so that the FP64 pose rounding and the
+// lattice offsets are evaluated exactly as written.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "align.h"
+#include "align_internal.h"
+
+using namespace mialign;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+align_status fail(align_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+align_status cuda_fail(cudaError_t e, const char* what) {
+  (void)cudaGetLastError();  // clear a sticky non-fatal error
+  if (e == cudaErrorMemoryAllocation) return fail(ALIGN_E_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(ALIGN_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                    \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, (what));  \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p != nullptr) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) cap = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+}  // namespace
+
+struct align_grid {
+  GridConst gc{};
+  float origin[3];
+  float res_m;
+  int64_t V = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n_sm = 0;
+  int table_slots = 0;
+  bool has_ref = false;
+  int32_t boxA[6];
+  DevBuf symA, sat;
+  // evaluation workspace
+  DevBuf xyz, poses, out_c, out_box, mi, hist, best, argmax, err, max_passes, wide_count, wide, dump;
+  int32_t passes_seed = 1;
+  int64_t stats[5] = {0, 0, 0, 0, 0};
+  // event timing (align_profile)
+  bool profiling = false;
+  bool ev_pending = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  double prof[3] = {0.0, 0.0, 0.0};
+};
+
+namespace {
+
+// --------------------------------------------------------------------------------------
+// Host-side conventions (the library's own implementation of the stated convention).
+// --------------------------------------------------------------------------------------
+void pose_to_fp32(const float origin[3], const double* eta, float* out12) {
+  // R = Rz(thz) Ry(thy) Rx(thx), FP64, rounded once; t' = t - origin.
+  const double cx = std::cos(eta[3]), sx = std::sin(eta[3]);
+  const double cy = std::cos(eta[4]), sy = std::sin(eta[4]);
+  const double cz = std::cos(eta[5]), sz = std::sin(eta[5]);
+  const double czsy = cz * sy;
+  const double szsy = sz * sy;
+  const double R[9] = {cz * cy, czsy * sx - sz * cx, czsy * cx + sz * sx,
+                       sz * cy, szsy * sx + cz * cx, szsy * cx - cz * sx,
+                       -sy,     cy * sx,             cy * cx};
+  for (int i = 0; i < 9; ++i) out12[i] = (float)R[i];
+  for (int i = 0; i < 3; ++i) out12[9 + i] = (float)(eta[i] - (double)origin[i]);
+}
+
+// Evenly spread samples over centre +- range (one sample: the centre itself).
+double lattice_step(double range, int32_t count, int32_t i) {
+  if (count < 2) return 0.0;
+  const double num = range * (double)(2 * i - (count - 1));
+  return num / (double)(count - 1);
+}
+
+// Rounded poses of a lattice: the FP64 rotation of each distinct (rx, ry, rz) sample is
+// evaluated once (same operations as pose_to_fp32, so the bits are identical).
+void round_lattice(const float origin[3], const std::vector<double>& eta, const int32_t m[6],
+                   std::vector<float>& poses) {
+  const int64_t P = (int64_t)(eta.size() / 6);
+  const int64_t n_trans = (int64_t)m[0] * m[1] * m[2];
+  poses.resize((size_t)P * 12);
+  for (int64_t p = 0; p < P; ++p) {
+    float* out = &poses[(size_t)p * 12];
+    if (p % n_trans == 0) {
+      pose_to_fp32(origin, &eta[(size_t)p * 6], out);
+    } else {
+      const float* first = &poses[(size_t)(p - p % n_trans) * 12];
+      for (int i = 0; i < 9; ++i) out[i] = first[i];
+      for (int i = 0; i < 3; ++i) out[9 + i] = (float)(eta[(size_t)p * 6 + i] - (double)origin[i]);
+    }
+  }
+}
+
+void build_lattice(const double c[6], const double r[6], const int32_t m[6], std::vector<double>& eta) {
+  // order: rx, ry, rz, tx, ty, tz (last fastest)
+  const int64_t P = (int64_t)m[0] * m[1] * m[2] * m[3] * m[4] * m[5];
+  eta.resize((size_t)P * 6);
+  for (int64_t idx = 0; idx < P; ++idx) {
+    int64_t rem = idx;
+    const int32_t itz = (int32_t)(rem % m[2]); rem /= m[2];
+    const int32_t ity = (int32_t)(rem % m[1]); rem /= m[1];
+    const int32_t itx = (int32_t)(rem % m[0]); rem /= m[0];
+    const int32_t irz = (int32_t)(rem % m[5]); rem /= m[5];
+    const int32_t iry = (int32_t)(rem % m[4]); rem /= m[4];
+    const int32_t irx = (int32_t)rem;
+    double* e = &eta[(size_t)idx * 6];
+    e[0] = c[0] + lattice_step(r[0], m[0], itx);
+    e[1] = c[1] + lattice_step(r[1], m[1], ity);
+    e[2] = c[2] + lattice_step(r[2], m[2], itz);
+    e[3] = c[3] + lattice_step(r[3], m[3], irx);
+    e[4] = c[4] + lattice_step(r[4], m[4], iry);
+    e[5] = c[5] + lattice_step(r[5], m[5], irz);
+  }
+}
+
+align_status validate_desc(const align_grid_desc* d, GridConst* gc) {
+  if (!d) return fail(ALIGN_E_INVALID, "desc is NULL");
+  for (int i = 0; i < 3; ++i)
+    if (d->dims[i] < 1 || d->dims[i] > (1 << 20)) return fail(ALIGN_E_INVALID, "dims[%d] out of [1, 2^20]", i);
+  const int64_t V = (int64_t)d->dims[0] * d->dims[1] * d->dims[2];
+  if (V >= INT32_MAX) return fail(ALIGN_E_INVALID, "X*Y*Z must be below 2^31");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(d->origin[i])) return fail(ALIGN_E_INVALID, "origin not finite");
+  if (!(d->res_m > 0.0f) || !std::isfinite(d->res_m)) return fail(ALIGN_E_INVALID, "res_m must be > 0");
+  const double mm = (double)d->res_m * 1000.0;
+  const int64_t res_mm = (int64_t)std::llround(mm);
+  if (res_mm < 1 || res_mm > 8000 || std::fabs(mm - (double)res_mm) > 1e-3)
+    return fail(ALIGN_E_INVALID, "res_m must be a whole number of millimetres in [1, 8000]");
+  if (d->feature < ALIGN_FEAT_COUNT || d->feature > ALIGN_FEAT_COUNT_ZVAR)
+    return fail(ALIGN_E_INVALID, "unknown feature %d", d->feature);
+  const bool use_c = d->feature != ALIGN_FEAT_ZVAR;
+  const bool use_v = d->feature != ALIGN_FEAT_COUNT;
+  const int Lc = use_c ? d->count_levels : 1;
+  const int Lv = use_v ? d->var_levels : 1;
+  if (use_c && (Lc < 1 || Lc > kMaxLevels)) return fail(ALIGN_E_INVALID, "count_levels out of [1, 63]");
+  if (use_v && (Lv < 1 || Lv > kMaxLevels)) return fail(ALIGN_E_INVALID, "var_levels out of [1, 63]");
+  int K = d->feature == ALIGN_FEAT_COUNT ? 1 + Lc : d->feature == ALIGN_FEAT_ZVAR ? 1 + Lv : 1 + Lc * Lv;
+  if (K > kMaxSymbols) return fail(ALIGN_E_INVALID, "too many symbols (%d > 64)", K);
+
+  std::memset(gc, 0, sizeof(*gc));
+  gc->inv_res = (float)(1.0 / (double)d->res_m);
+  gc->res_mm = (int32_t)res_mm;
+  gc->X = d->dims[0];
+  gc->Y = d->dims[1];
+  gc->Z = d->dims[2];
+  gc->K = K;
+  gc->feature = d->feature;
+  gc->Lc = Lc;
+  gc->Lv = Lv;
+  for (int j = 0; j < kMaxLevels; ++j) {
+    gc->count_thresh[j] = 0xFFFFFFFFu;
+    gc->var_thresh[j] = INT64_MAX;
+  }
+  for (int j = 0; j + 1 < Lc; ++j) {
+    gc->count_thresh[j] = d->count_thresh ? d->count_thresh[j] : (j + 1 < 32 ? (1u << (j + 1)) : 0xFFFFFFFFu);
+    if (j > 0 && gc->count_thresh[j] < gc->count_thresh[j - 1])
+      return fail(ALIGN_E_INVALID, "count_thresh must be ascending");
+  }
+  const int64_t r2 = res_mm * res_mm;
+  for (int j = 0; j + 1 < Lv; ++j) {
+    const int shift = 2 + (Lv - 1 - j);
+    gc->var_thresh[j] = d->var_thresh ? d->var_thresh[j] : (shift >= 63 ? 0 : (r2 >> shift));
+    if (gc->var_thresh[j] < 0) return fail(ALIGN_E_INVALID, "var_thresh must be >= 0");
+    if (j > 0 && gc->var_thresh[j] < gc->var_thresh[j - 1])
+      return fail(ALIGN_E_INVALID, "var_thresh must be ascending");
+  }
+  // |dz| bound: voxel edge, rounding to the mm, and the drift of k_z * res_mm against
+  // 1000 * k_z * res when res is not exactly a whole number of mm in binary.
+  const double drift = std::fabs(mm - (double)res_mm) * (double)gc->Z;
+  gc->dz_bound = (int32_t)(res_mm + 4 + (int64_t)std::ceil(drift));
+  const uint64_t D = (uint64_t)gc->dz_bound;
+  gc->nlim = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull / (D * D), 0x7FFFFFFFull / D);
+  for (int i = 0; i < 3; ++i) gc->boxA[i] = INT_MAX, gc->boxA[3 + i] = INT_MIN;
+  return ALIGN_OK;
+}
+
+align_status check_grid(align_grid* g) {
+  if (!g) return fail(ALIGN_E_INVALID, "grid is NULL");
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return ALIGN_OK;
+}
+
+// Upload (or copy on the device) scan B into the tile-padded point buffer.
+align_status upload_points(align_grid* g, const float* xyz, int64_t n, int flags, int32_t* n_tiles_out) {
+  if (n < 0 || n >= INT32_MAX) return fail(ALIGN_E_INVALID, "point count out of range");
+  if (n > 0 && !xyz) return fail(ALIGN_E_INVALID, "xyz is NULL");
+  const int tile = eval_tile_points();
+  const int64_t n_tiles = std::max<int64_t>(1, (n + tile - 1) / tile);
+  const size_t bytes = (size_t)n_tiles * tile * 3 * sizeof(float);
+  CU(g->xyz.ensure(bytes), "allocate point buffer");
+  if (n > 0) {
+    const cudaMemcpyKind kind = (flags & ALIGN_XYZ_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CU(cudaMemcpyAsync(g->xyz.p, xyz, (size_t)n * 3 * sizeof(float), kind, g->stream), "copy points");
+  }
+  *n_tiles_out = (int32_t)n_tiles;
+  return ALIGN_OK;
+}
+
+struct EvalOut {
+  float* mi;          // device
+  uint32_t* hist;     // device or null
+  int64_t* argmax;    // device
+  int64_t* dump;      // device or null
+};
+
+// Enqueue the eval + compose + argmax kernels for poses already on the device.
+align_status enqueue_eval(align_grid* g, int32_t n_points, int32_t n_tiles, const float* d_poses, int64_t P,
+                          const EvalOut& out) {
+  const int K = g->gc.K;
+  const size_t KK = (size_t)K * K;
+  CU(g->out_c.ensure((size_t)P * KK * sizeof(uint32_t)), "allocate histograms");
+  CU(g->out_box.ensure((size_t)P * 6 * sizeof(int32_t)), "allocate boxes");
+  CU(g->best.ensure(sizeof(unsigned long long)), "allocate argmax");
+  CU(g->err.ensure(16), "allocate error word");
+  CU(g->max_passes.ensure(16), "allocate counters");
+  CU(g->wide_count.ensure(16), "allocate counters");
+  const int n_ctas = (int)std::min<int64_t>(P, g->n_sm);
+  const size_t wide_bytes = (size_t)n_ctas * 2 * g->table_slots * sizeof(unsigned long long);
+  if (g->wide.cap < wide_bytes || g->wide.p == nullptr) {
+    CU(g->wide.ensure(wide_bytes), "allocate wide sums");
+    CU(cudaMemsetAsync(g->wide.p, 0, g->wide.cap, g->stream), "clear wide sums");
+  }
+  CU(cudaMemsetAsync(g->best.p, 0, sizeof(unsigned long long), g->stream), "reset argmax");
+
+  EvalArgs a{};
+  a.xyz = g->xyz.as<float>();
+  a.n_points = n_points;
+  a.n_tiles = n_tiles;
+  a.poses = d_poses;
+  a.P = (int32_t)P;
+  a.symA = g->symA.as<uint8_t>();
+  a.out_c = g->out_c.as<uint32_t>();
+  a.out_box = g->out_box.as<int32_t>();
+  a.err = g->err.as<uint32_t>();
+  a.max_passes = g->max_passes.as<uint32_t>();
+  a.wide_count = g->wide_count.as<uint32_t>();
+  a.wide = g->wide.as<unsigned long long>();
+  a.table_slots = g->table_slots;
+  a.passes0 = g->passes_seed;
+  a.dump = out.dump;
+  if (g->profiling) CU(cudaEventRecord(g->ev[0], g->stream), "record event");
+  CU(launch_eval(g->gc, a, n_ctas, g->stream), "launch eval kernel");
+  if (g->profiling) CU(cudaEventRecord(g->ev[1], g->stream), "record event");
+
+  ComposeArgs c{};
+  c.c = g->out_c.as<uint32_t>();
+  c.boxB = g->out_box.as<int32_t>();
+  c.sat = g->sat.as<int32_t>();
+  c.P = (int32_t)P;
+  c.mi = out.mi;
+  c.hist = out.hist;
+  c.best = g->best.as<unsigned long long>();
+  CU(launch_compose(g->gc, c, g->stream), "launch compose kernel");
+  CU(launch_argmax_finalize(g->best.as<unsigned long long>(), out.argmax, g->stream), "launch argmax");
+  if (g->profiling) {
+    CU(cudaEventRecord(g->ev[2], g->stream), "record event");
+    g->ev_pending = true;
+  }
+  g->stats[2] = g->table_slots;
+  g->stats[3] = n_ctas;
+  g->stats[4] += 3;
+  return ALIGN_OK;
+}
+
+// Read back the kernels' error word and counters (synchronises the stream).
+align_status collect_status(align_grid* g) {
+  uint32_t vals[3] = {0, 0, 0};
+  CU(cudaMemcpyAsync(&vals[0], g->err.p, 4, cudaMemcpyDeviceToHost, g->stream), "read error word");
+  CU(cudaMemcpyAsync(&vals[1], g->max_passes.p, 4, cudaMemcpyDeviceToHost, g->stream), "read counters");
+  CU(cudaMemcpyAsync(&vals[2], g->wide_count.p, 4, cudaMemcpyDeviceToHost, g->stream), "read counters");
+  CU(cudaStreamSynchronize(g->stream), "synchronize");
+  if (g->profiling && g->ev_pending) {
+    float t0 = 0.0f, t1 = 0.0f;
+    CU(cudaEventElapsedTime(&t0, g->ev[0], g->ev[1]), "event time");
+    CU(cudaEventElapsedTime(&t1, g->ev[1], g->ev[2]), "event time");
+    g->prof[0] += t0;
+    g->prof[1] += t1;
+    g->prof[2] += 1.0;
+    g->ev_pending = false;
+  }
+  CU(cudaMemsetAsync(g->err.p, 0, 4, g->stream), "reset error word");
+  CU(cudaMemsetAsync(g->wide_count.p, 0, 4, g->stream), "reset counters");
+  if (vals[1] > (uint32_t)g->passes_seed) g->passes_seed = (int32_t)vals[1];
+  g->stats[0] = vals[1];
+  g->stats[1] = vals[2];
+  if (vals[0] & kErrWaitTimeout) return fail(ALIGN_E_TIMEOUT, "a bounded device wait gave up");
+  if (vals[0] & kErrDzBound) return fail(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");
+  if (vals[0] & kErrPassLimit) return fail(ALIGN_E_INTERNAL, "key partitioning limit reached");
+  return ALIGN_OK;
+}
+
+align_status ensure_status_words(align_grid* g) {
+  CU(g->err.ensure(16), "allocate error word");
+  CU(g->max_passes.ensure(16), "allocate counters");
+  CU(g->wide_count.ensure(16), "allocate counters");
+  return ALIGN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* align_last_error(void) { return g_last_error.c_str(); }
+
+align_status align_create_grid(const align_grid_desc* desc, void* cuda_stream, align_grid** out) {
+  if (!out) return fail(ALIGN_E_INVALID, "out is NULL");
+  *out = nullptr;
+  GridConst gc;
+  align_status st = validate_desc(desc, &gc);
+  if (st != ALIGN_OK) return st;
+  int n_dev = 0;
+  cudaError_t e = cudaGetDeviceCount(&n_dev);
+  if (e != cudaSuccess || n_dev < 1) {
+    (void)cudaGetLastError();
+    return fail(ALIGN_E_CUDA, "no usable CUDA device");
+  }
+  int dev = 0;
+  CU(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaDeviceProp prop;
+  CU(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+  if (prop.major < 10) return fail(ALIGN_E_CUDA, "this library is built for sm_103a (found sm_%d%d)", prop.major, prop.minor);
+  align_grid* g = new (std::nothrow) align_grid();
+  if (!g) return fail(ALIGN_E_OOM, "host allocation failed");
+  g->gc = gc;
+  for (int i = 0; i < 3; ++i) g->origin[i] = desc->origin[i];
+  g->res_m = desc->res_m;
+  g->V = (int64_t)gc.X * gc.Y * gc.Z;
+  g->stream = (cudaStream_t)cuda_stream;
+  g->device = dev;
+  g->n_sm = prop.multiProcessorCount;
+  g->table_slots = eval_table_slots_for(gc.K, prop.sharedMemPerBlockOptin);
+  for (int i = 0; i < 6; ++i) g->boxA[i] = i < 3 ? INT_MAX : INT_MIN;
+  *out = g;
+  return ALIGN_OK;
+}
+
+align_status align_destroy_grid(align_grid* g) {
+  if (!g) return ALIGN_OK;
+  cudaSetDevice(g->device);
+  cudaStreamSynchronize(g->stream);
+  for (DevBuf* b : {&g->symA, &g->sat, &g->xyz, &g->poses, &g->out_c, &g->out_box, &g->mi, &g->hist, &g->best,
+                    &g->argmax, &g->err, &g->max_passes, &g->wide_count, &g->wide, &g->dump})
+    b->release();
+  for (cudaEvent_t& e : g->ev)
+    if (e) cudaEventDestroy(e);
+  delete g;
+  return ALIGN_OK;
+}
+
+align_status align_grid_info(const align_grid* g, int32_t* n_symbols, int64_t* n_voxels) {
+  if (!g) return fail(ALIGN_E_INVALID, "grid is NULL");
+  if (n_symbols) *n_symbols = g->gc.K;
+  if (n_voxels) *n_voxels = g->V;
+  return ALIGN_OK;
+}
+
+align_status align_round_poses(const float origin[3], const double* eta6, int64_t P, float* poses12) {
+  if (!origin) return fail(ALIGN_E_INVALID, "origin is NULL");
+  if (P < 0 || (P > 0 && (!eta6 || !poses12))) return fail(ALIGN_E_INVALID, "bad pose arrays");
+  for (int64_t p = 0; p < P; ++p) pose_to_fp32(origin, eta6 + 6 * p, poses12 + 12 * p);
+  return ALIGN_OK;
+}
+
+align_status align_set_reference(align_grid* g, const float* xyzA, int64_t nA, int flags) {
+  align_status st = check_grid(g);
+  if (st != ALIGN_OK) return st;
+  if (nA < 0 || nA >= INT32_MAX) return fail(ALIGN_E_INVALID, "nA out of range");
+  if (nA > 0 && !xyzA) return fail(ALIGN_E_INVALID, "xyzA is NULL");
+  g->has_ref = false;
+  st = ensure_status_words(g);
+  if (st != ALIGN_OK) return st;
+  const GridConst& gc = g->gc;
+  const size_t V = (size_t)g->V;
+  DevBuf pts, pose, cnt, s1, s2, box;
+  auto cleanup = [&]() {
+    pts.release();
+    pose.release();
+    cnt.release();
+    s1.release();
+    s2.release();
+    box.release();
+  };
+  align_status result = ALIGN_OK;
+  do {
+    cudaError_t e;
+#define TRY(call, what)                 \
+  if ((e = (call)) != cudaSuccess) {    \
+    result = cuda_fail(e, (what));      \
+    break;                              \
+  }
+    TRY(pts.ensure(std::max<size_t>(1, (size_t)nA) * 12), "allocate A points");
+    if (nA > 0)
+      TRY(cudaMemcpyAsync(pts.p, xyzA, (size_t)nA * 12,
+                          (flags & ALIGN_XYZ_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream),
+          "copy A points");
+    float ident[12];
+    const double eta0[6] = {0, 0, 0, 0, 0, 0};
+    pose_to_fp32(g->origin, eta0, ident);
+    TRY(pose.ensure(sizeof(ident)), "allocate pose");
+    TRY(cudaMemcpyAsync(pose.p, ident, sizeof(ident), cudaMemcpyHostToDevice, g->stream), "copy pose");
+    TRY(cnt.ensure(V * 4), "allocate A counts");
+    TRY(s1.ensure(V * 8), "allocate A sums");
+    TRY(s2.ensure(V * 8), "allocate A sums");
+    TRY(cudaMemsetAsync(cnt.p, 0, V * 4, g->stream), "clear");
+    TRY(cudaMemsetAsync(s1.p, 0, V * 8, g->stream), "clear");
+    TRY(cudaMemsetAsync(s2.p, 0, V * 8, g->stream), "clear");
+    TRY(launch_ref_accumulate(gc, pts.as<float>(), nA, pose.as<float>(), cnt.as<uint32_t>(),
+                              s1.as<unsigned long long>(), s2.as<unsigned long long>(), g->stream),
+        "launch reference accumulate");
+    TRY(g->symA.ensure(V), "allocate A symbols");
+    const int32_t box0[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+    TRY(box.ensure(sizeof(box0)), "allocate box");
+    TRY(cudaMemcpyAsync(box.p, box0, sizeof(box0), cudaMemcpyHostToDevice, g->stream), "init box");
+    TRY(launch_ref_symbols(gc, cnt.as<uint32_t>(), s1.as<unsigned long long>(), s2.as<unsigned long long>(),
+                           g->symA.as<uint8_t>(), box.as<int32_t>(), g->stream),
+        "launch reference symbols");
+    const size_t sat_elems = (size_t)(gc.K - 1) * (gc.Z + 1) * (gc.Y + 1) * (gc.X + 1);
+    TRY(g->sat.ensure(std::max<size_t>(1, sat_elems) * 4), "allocate prefix sums");
+    TRY(cudaMemsetAsync(g->sat.p, 0, std::max<size_t>(1, sat_elems) * 4, g->stream), "clear prefix sums");
+    TRY(launch_ref_sat(gc, g->symA.as<uint8_t>(), g->sat.as<int32_t>(), g->stream), "launch prefix sums");
+    int32_t hb[6];
+    TRY(cudaMemcpyAsync(hb, box.p, sizeof(hb), cudaMemcpyDeviceToHost, g->stream), "read box");
+    TRY(cudaStreamSynchronize(g->stream), "synchronize");
+    for (int i = 0; i < 6; ++i) g->boxA[i] = g->gc.boxA[i] = hb[i];
+    g->stats[4] += (nA > 0 ? 1 : 0) + 1 + (gc.K > 1 ? 3 : 0);
+#undef TRY
+  } while (0);
+  cleanup();
+  if (result != ALIGN_OK) return result;
+  g->has_ref = true;
+  return ALIGN_OK;
+}
+
+align_status align_get_reference(align_grid* g, uint8_t* symA, int32_t boxA[6]) {
+  align_status st = check_grid(g);
+  if (st != ALIGN_OK) return st;
+  if (!g->has_ref) return fail(ALIGN_E_NOREF, "no reference scan set");
+  if (symA) {
+    CU(cudaMemcpyAsync(symA, g->symA.p, (size_t)g->V, cudaMemcpyDeviceToHost, g->stream), "read symbols");
+    CU(cudaStreamSynchronize(g->stream), "synchronize");
+  }
+  if (boxA) std::memcpy(boxA, g->boxA, sizeof(g->boxA));
+  return ALIGN_OK;
+}
+
+static align_status eval_common(align_grid* g, const float* xyzB, int64_t nB, int flags, const float* poses12,
+                                const double* eta6, int64_t P, float* mi_out, int64_t* argmax_out,
+                                uint32_t* hist_out, int64_t* dump_dev, bool points_ready, int32_t n_tiles_ready) {
+  const bool out_dev = (flags & ALIGN_OUT_DEVICE) != 0;
+  int32_t n_tiles = n_tiles_ready;
+  if (!points_ready) {
+    align_status st = upload_points(g, xyzB, nB, flags, &n_tiles);
+    if (st != ALIGN_OK) return st;
+  }
+  // poses -> device fp32
+  const float* d_poses = nullptr;
+  if (poses12 && (flags & ALIGN_POSES_DEVICE)) {
+    d_poses = poses12;
+  } else {
+    CU(g->poses.ensure((size_t)P * 12 * sizeof(float)), "allocate poses");
+    if (poses12) {
+      CU(cudaMemcpyAsync(g->poses.p, poses12, (size_t)P * 48, cudaMemcpyHostToDevice, g->stream), "copy poses");
+    } else {
+      std::vector<float> tmp((size_t)P * 12);
+      for (int64_t p = 0; p < P; ++p) pose_to_fp32(g->origin, eta6 + 6 * p, &tmp[(size_t)p * 12]);
+      // a pageable source is staged before the call returns, so tmp may go away
+      CU(cudaMemcpyAsync(g->poses.p, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice, g->stream), "copy poses");
+    }
+    d_poses = g->poses.as<float>();
+  }
+  const size_t KK = (size_t)g->gc.K * g->gc.K;
+  EvalOut o{};
+  if (out_dev) {
+    o.mi = mi_out;
+    o.hist = hist_out;
+    if (argmax_out) {
+      o.argmax = argmax_out;
+    } else {
+      CU(g->argmax.ensure(8), "allocate argmax");
+      o.argmax = g->argmax.as<int64_t>();
+    }
+  } else {
+    CU(g->mi.ensure((size_t)P * 4), "allocate MI");
+    CU(g->argmax.ensure(8), "allocate argmax");
+    o.mi = g->mi.as<float>();
+    o.argmax = g->argmax.as<int64_t>();
+    if (hist_out) {
+      CU(g->hist.ensure((size_t)P * KK * 4), "allocate histograms");
+      o.hist = g->hist.as<uint32_t>();
+    }
+  }
+  o.dump = dump_dev;
+  align_status st = enqueue_eval(g, (int32_t)nB, n_tiles, d_poses, P, o);
+  if (st != ALIGN_OK) return st;
+  if (out_dev) return ALIGN_OK;
+  if (mi_out) CU(cudaMemcpyAsync(mi_out, o.mi, (size_t)P * 4, cudaMemcpyDeviceToHost, g->stream), "read MI");
+  if (argmax_out) CU(cudaMemcpyAsync(argmax_out, o.argmax, 8, cudaMemcpyDeviceToHost, g->stream), "read argmax");
+  if (hist_out)
+    CU(cudaMemcpyAsync(hist_out, o.hist, (size_t)P * KK * 4, cudaMemcpyDeviceToHost, g->stream), "read histograms");
+  return collect_status(g);
+}
+
+align_status align_eval_mi(align_grid* g, const float* xyzB, int64_t nB, int flags, const float* poses12,
+                           const double* eta6, int64_t P, float* mi_out, int64_t* argmax_out, uint32_t* hist_out) {
+  align_status st = check_grid(g);
+  if (st != ALIGN_OK) return st;
+  if (!g->has_ref) return fail(ALIGN_E_NOREF, "no reference scan set");
+  if (P < 0 || P >= INT32_MAX) return fail(ALIGN_E_INVALID, "P out of range");
+  if ((poses12 == nullptr) == (eta6 == nullptr) && P > 0)
+    return fail(ALIGN_E_INVALID, "give exactly one of poses12 and eta6");
+  if (eta6 && (flags & ALIGN_POSES_DEVICE)) return fail(ALIGN_E_INVALID, "eta6 must be host memory");
+  if (P > 0 && !mi_out) return fail(ALIGN_E_INVALID, "mi_out is NULL");
+  if (nB < 0 || nB >= INT32_MAX) return fail(ALIGN_E_INVALID, "nB out of range");
+  if (P == 0) {
+    if (argmax_out) {
+      const int64_t none = -1;
+      if (flags & ALIGN_OUT_DEVICE)
+        CU(cudaMemcpyAsync(argmax_out, &none, 8, cudaMemcpyHostToDevice, g->stream), "write argmax");
+      else
+        *argmax_out = -1;
+      if (flags & ALIGN_OUT_DEVICE) CU(cudaStreamSynchronize(g->stream), "synchronize");
+    }
+    return ALIGN_OK;
+  }
+  st = ensure_status_words(g);
+  if (st != ALIGN_OK) return st;
+  return eval_common(g, xyzB, nB, flags, poses12, eta6, P, mi_out, argmax_out, hist_out, nullptr, false, 0);
+}
+
+align_status align_accumulate(align_grid* g, const float* xyzB, int64_t nB, int flags, const float pose12[12],
+                              int64_t* acc_out, int32_t box_out[6]) {
+  align_status st = check_grid(g);
+  if (st != ALIGN_OK) return st;
+  if (!g->has_ref) return fail(ALIGN_E_NOREF, "no reference scan set");
+  if (!pose12) return fail(ALIGN_E_INVALID, "pose12 is NULL");
+  st = ensure_status_words(g);
+  if (st != ALIGN_OK) return st;
+  const size_t bytes = (size_t)g->V * 3 * sizeof(int64_t);
+  CU(g->dump.ensure(bytes), "allocate sums");
+  CU(cudaMemsetAsync(g->dump.p, 0, bytes, g->stream), "clear sums");
+  float mi = 0.0f;
+  int64_t am = 0;
+  st = eval_common(g, xyzB, nB, flags & ~(ALIGN_OUT_DEVICE | ALIGN_POSES_DEVICE), pose12, nullptr, 1, &mi, &am,
+                   nullptr, g->dump.as<int64_t>(), false, 0);
+  if (st != ALIGN_OK) return st;
+  if (acc_out) CU(cudaMemcpy(acc_out, g->dump.p, bytes, cudaMemcpyDeviceToHost), "read sums");
+  if (box_out) CU(cudaMemcpy(box_out, g->out_box.p, 6 * sizeof(int32_t), cudaMemcpyDeviceToHost), "read box");
+  return ALIGN_OK;
+}
+
+align_status align_search_ex(align_grid* g, const float* xyzB, int64_t nB, int flags, const double init[6],
+                             const double range[6], const int32_t counts[6], int32_t levels, double T_out[6],
+                             float* mi_out, int64_t* level_best) {
+  align_status st = check_grid(g);
+  if (st != ALIGN_OK) return st;
+  if (!g->has_ref) return fail(ALIGN_E_NOREF, "no reference scan set");
+  if (!init || !range || !counts || !T_out) return fail(ALIGN_E_INVALID, "NULL argument");
+  if (levels < 0) return fail(ALIGN_E_INVALID, "levels < 0");
+  int64_t P = 1;
+  for (int a = 0; a < 6; ++a) {
+    if (counts[a] < 1) return fail(ALIGN_E_INVALID, "counts must be >= 1");
+    P *= counts[a];
+    if (P >= (1 << 26)) return fail(ALIGN_E_INVALID, "lattice too large");
+  }
+  st = ensure_status_words(g);
+  if (st != ALIGN_OK) return st;
+  int32_t n_tiles = 0;
+  st = upload_points(g, xyzB, nB, flags, &n_tiles);
+  if (st != ALIGN_OK) return st;
+  double c[6], r[6];
+  std::memcpy(c, init, sizeof(c));
+  std::memcpy(r, range, sizeof(r));
+  std::vector<double> eta;
+  std::vector<float> poses;
+  float best_mi = 0.0f;
+  CU(g->mi.ensure((size_t)P * 4), "allocate MI");
+  for (int32_t l = 0; l < levels; ++l) {
+    build_lattice(c, r, counts, eta);
+    round_lattice(g->origin, eta, counts, poses);
+    int64_t am = -1;
+    // MI stays on the device; only the argmax (and its MI) come back each level
+    st = eval_common(g, xyzB, nB, ALIGN_OUT_DEVICE, poses.data(), nullptr, P, g->mi.as<float>(), nullptr,
+                     nullptr, nullptr, true, n_tiles);
+    if (st != ALIGN_OK) return st;
+    CU(cudaMemcpyAsync(&am, g->argmax.p, 8, cudaMemcpyDeviceToHost, g->stream), "read argmax");
+    st = collect_status(g);
+    if (st != ALIGN_OK) return st;
+    if (am < 0 || am >= P) return fail(ALIGN_E_INTERNAL, "argmax out of range");
+    CU(cudaMemcpy(&best_mi, g->mi.as<float>() + am, 4, cudaMemcpyDeviceToHost), "read MI");
+    if (level_best) level_best[l] = am;
+    std::memcpy(c, &eta[(size_t)am * 6], sizeof(c));
+    for (int a = 0; a < 6; ++a) r[a] = r[a] * 0.5;
+  }
+  std::memcpy(T_out, c, sizeof(c));
+  if (mi_out) *mi_out = best_mi;
+  return ALIGN_OK;
+}
+
+align_status align_search(align_grid* g, const float* xyzB, int64_t nB, int flags, const double init[6],
+                          const double range[6], int32_t levels, double T_out[6], float* mi_out) {
+  const int32_t counts[6] = {8, 8, 2, 2, 2, 8};
+  return align_search_ex(g, xyzB, nB, flags, init, range, counts, levels, T_out, mi_out, nullptr);
+}
+
+align_status align_eval_stats(align_grid* g, int64_t out[5]) {
+  if (!g || !out) return fail(ALIGN_E_INVALID, "NULL argument");
+  for (int i = 0; i < 5; ++i) out[i] = g->stats[i];
+  return ALIGN_OK;
+}
+
+align_status align_profile(align_grid* g, int32_t mode, double out[3]) {
+  align_status st = check_grid(g);
+  if (st != ALIGN_OK) return st;
+  if (mode == 1) {
+    for (cudaEvent_t& e : g->ev)
+      if (!e) CU(cudaEventCreate(&e), "create event");
+    g->profiling = true;
+    g->ev_pending = false;
+    g->prof[0] = g->prof[1] = g->prof[2] = 0.0;
+  } else if (mode == 0) {
+    g->profiling = false;
+    g->ev_pending = false;
+  } else if (mode != 2) {
+    return fail(ALIGN_E_INVALID, "mode must be 0, 1 or 2");
+  }
+  if (out)
+    for (int i = 0; i < 3; ++i) out[i] = g->prof[i];
+  return ALIGN_OK;
+}
+
+}  // extern "C"

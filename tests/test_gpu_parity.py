@@ -1,0 +1,173 @@
+"""GPU path vs the CPU oracle on the same seeded inputs, through the C ABI.
+
+Bar: voxel sums, symbols, boxes, joint histograms bit-exact; MI within 1e-5 nats of the
+oracle's FP64 MI; the argmax equal (or, on an FP32 near-tie, within the band).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scangen
+from tests.helpers import check_argmax, lib_grid, mi_tolerance, oracle_grid
+
+pytestmark = pytest.mark.gpu
+NT = oracle.host_cores()
+
+
+class Setup:
+    def __init__(self, pair):
+        from paper_1709_06948_gb300 import align
+        self.pair = pair
+        self.G = oracle_grid(pair.grid)
+        self.symA, self.boxA = self.G.reference(pair.xyzA)
+        self.L = lib_grid(pair.grid)
+        align.align_set_reference(self.L, pair.xyzA)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return Setup(scangen.tiny_pair())
+
+
+@pytest.fixture(scope="module")
+def lidar():
+    return Setup(scangen.lidar_pair())
+
+
+def _eval_both(S, etas, with_hist=True, sample=None):
+    from paper_1709_06948_gb300 import align
+    mi, am, hist = align.align_eval_mi(S.L, S.pair.xyzB, eta6=etas, with_hist=with_hist)
+    poses = S.G.round_pose(etas)
+    mo, ho, _ = S.G.eval_mi(S.symA, S.boxA, S.pair.xyzB, poses, nthreads=NT, with_hist=with_hist)
+    return mi, am, hist, mo, ho
+
+
+@pytest.mark.parametrize("which", ["tiny", "lidar"])
+def test_reference_parity(which, request):
+    from paper_1709_06948_gb300 import align
+    S = request.getfixturevalue(which)
+    sym, box = align.align_get_reference(S.L)
+    assert np.array_equal(sym, S.symA)
+    assert box.tolist() == S.boxA.tolist()
+
+
+@pytest.mark.parametrize("which", ["tiny", "lidar"])
+def test_accumulate_parity(which, request):
+    from paper_1709_06948_gb300 import align
+    S = request.getfixturevalue(which)
+    etas = [S.pair.T, np.zeros(6), np.array([0.7, -1.3, 0.05, 0.01, -0.02, 0.09])]
+    for eta in etas:
+        pose = S.G.round_pose(eta)[0]
+        acc, box = align.align_accumulate(S.L, S.pair.xyzB, pose)
+        cnt, s1, s2, obox, _ = S.G.accumulate(S.pair.xyzB, pose)
+        assert np.array_equal(acc[:, 0], cnt)
+        assert np.array_equal(acc[:, 1], s1)
+        assert np.array_equal(acc[:, 2], s2)
+        assert box.tolist() == obox.tolist()
+
+
+def test_tiny_all_poses(tiny):
+    etas = scangen.tiny_poses()
+    mi, am, hist, mo, ho = _eval_both(tiny, etas)
+    assert np.array_equal(hist, ho)
+    assert np.max(np.abs(mi.astype(np.float64) - mo)) <= mi_tolerance()
+    check_argmax(am, mo)
+
+
+def test_lidar_full_batch(lidar):
+    """The benchmark's launch: 4,096 poses on the 120k-point pair; every MI is checked, and
+    the joint histograms of every 16th pose are compared bit for bit."""
+    from paper_1709_06948_gb300 import align
+    etas = scangen.lidar_poses(center=np.zeros(6))
+    mi, am, hist = align.align_eval_mi(lidar.L, lidar.pair.xyzB, eta6=etas, with_hist=True)
+    poses = lidar.G.round_pose(etas)
+    mo, _, _ = lidar.G.eval_mi(lidar.symA, lidar.boxA, lidar.pair.xyzB, poses, nthreads=NT)
+    assert np.max(np.abs(mi.astype(np.float64) - mo)) <= mi_tolerance()
+    check_argmax(am, mo)
+    sample = np.arange(0, 4096, 16)
+    _, ho, _ = lidar.G.eval_mi(lidar.symA, lidar.boxA, lidar.pair.xyzB, poses[sample], nthreads=NT, with_hist=True)
+    assert np.array_equal(hist[sample], ho)
+    # FP64 MI recomputed from the GPU's histograms is the oracle's MI exactly
+    for i in sample[:32]:
+        assert oracle.mi_from_hist(hist[i]) == pytest.approx(mo[i], abs=1e-12)
+
+
+def test_lidar_truth_lattice(lidar):
+    etas = scangen.lidar_poses(center=lidar.pair.T, half_width=(0.5, 0.5, 0.1, 0.01, 0.01, 0.03))[::7]
+    mi, am, hist, mo, ho = _eval_both(lidar, etas)
+    assert np.array_equal(hist, ho)
+    assert np.max(np.abs(mi.astype(np.float64) - mo)) <= mi_tolerance()
+    check_argmax(am, mo)
+
+
+def test_eta_and_poses12_agree(tiny):
+    from paper_1709_06948_gb300 import align
+    etas = scangen.tiny_poses()[::5]
+    a = align.align_eval_mi(tiny.L, tiny.pair.xyzB, eta6=etas, with_hist=True)
+    b = align.align_eval_mi(tiny.L, tiny.pair.xyzB, poses12=tiny.G.round_pose(etas), with_hist=True)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1] and np.array_equal(a[2], b[2])
+
+
+def test_device_inputs_outputs(tiny):
+    import torch
+    from paper_1709_06948_gb300 import align
+    etas = scangen.tiny_poses()
+    host = align.align_eval_mi(tiny.L, tiny.pair.xyzB, eta6=etas, with_hist=True)
+    xyz = torch.from_numpy(tiny.pair.xyzB).cuda()
+    poses = torch.from_numpy(tiny.G.round_pose(etas)).cuda()
+    P = etas.shape[0]
+    mi = torch.empty(P, dtype=torch.float32, device="cuda")
+    am = torch.empty(1, dtype=torch.int64, device="cuda")
+    hist = torch.empty((P, tiny.L.K, tiny.L.K), dtype=torch.int32, device="cuda")
+    align.align_eval_mi(tiny.L, xyz, poses12=poses, out=(mi, am, hist))
+    torch.cuda.synchronize()
+    assert np.array_equal(mi.cpu().numpy(), host[0])
+    assert int(am.item()) == host[1]
+    assert np.array_equal(hist.cpu().numpy().view(np.uint32), host[2])
+
+
+def test_repeat_is_deterministic(lidar):
+    from paper_1709_06948_gb300 import align
+    etas = scangen.lidar_poses()[::3]
+    a = align.align_eval_mi(lidar.L, lidar.pair.xyzB, eta6=etas, with_hist=True)
+    b = align.align_eval_mi(lidar.L, lidar.pair.xyzB, eta6=etas, with_hist=True)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1] and np.array_equal(a[2], b[2])
+
+
+def test_permuting_poses_permutes_outputs(tiny):
+    from paper_1709_06948_gb300 import align
+    etas = scangen.tiny_poses()
+    perm = np.random.default_rng(2).permutation(len(etas))
+    a = align.align_eval_mi(tiny.L, tiny.pair.xyzB, eta6=etas, with_hist=True)
+    b = align.align_eval_mi(tiny.L, tiny.pair.xyzB, eta6=etas[perm], with_hist=True)
+    assert np.array_equal(a[0][perm], b[0]) and np.array_equal(a[2][perm], b[2])
+
+
+def test_hand_fixture_on_gpu():
+    from paper_1709_06948_gb300 import align
+    with open(os.path.join(os.path.dirname(__file__), "golden", "hand_4x4x2.json")) as f:
+        hand = json.load(f)
+    g = hand["grid"]
+    for mode in ("zvar", "count"):
+        if mode == "zvar":
+            L = align.align_create_grid(g["origin"], g["res_m"], g["dims"], align.ALIGN_FEAT_ZVAR,
+                                        var_levels=hand["zvar"]["var_levels"], var_thresh=hand["zvar"]["var_thresh"])
+        else:
+            L = align.align_create_grid(g["origin"], g["res_m"], g["dims"], align.ALIGN_FEAT_COUNT,
+                                        count_levels=hand["count"]["count_levels"])
+        align.align_set_reference(L, hand["xyzA"])
+        sym, box = align.align_get_reference(L)
+        assert {int(v): int(sym[v]) for v in np.nonzero(sym)[0]} == {int(k): v for k, v in hand[mode]["symA"].items()}
+        assert box.tolist() == hand["boxA"]
+        mi, am, hist = align.align_eval_mi(L, hand["xyzB"], eta6=[hand["eta_B"]], with_hist=True)
+        assert hist[0].tolist() == hand[mode]["hist"]
+        acc, bbox = align.align_accumulate(L, hand["xyzB"], align.align_round_poses(g["origin"], [hand["eta_B"]])[0])
+        occ = {int(v): acc[v].tolist() for v in np.nonzero(acc[:, 0])[0]}
+        assert occ == {int(k): v for k, v in hand["sumsB"].items()}
+        assert bbox.tolist() == hand["boxB"]
+        exp = oracle.mi_from_hist(np.array(hand[mode]["hist"]))
+        assert abs(mi[0] - exp) <= mi_tolerance()
