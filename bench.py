@@ -225,8 +225,17 @@ def run_ours(args):
     init = np.zeros(6)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    P = int(np.prod(COUNTS)) if args.mode == "search" else args.poses
+    etas_eval = scangen.lidar_poses()[:P] if args.mode == "eval" else None
+    poses_dev = torch.from_numpy(align.align_round_poses(spec.origin, etas_eval)).cuda() if args.mode == "eval" else None
+    mi_dev = torch.empty(max(P, 1), dtype=torch.float32, device="cuda")
+    am_dev = torch.empty(1, dtype=torch.int64, device="cuda")
+
     def step():
         align.align_set_reference(L, A)
+        if args.mode == "eval":
+            align.align_eval_mi(L, B, poses12=poses_dev, out=(mi_dev, am_dev, None))
+            return None, None, None
         return align.align_search(L, B, init, RANGE, levels=LEVELS)
 
     for _ in range(max(args.warmup, 0)):
@@ -274,15 +283,14 @@ def run_ours(args):
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    P = int(np.prod(COUNTS))
-    evals_per_step = P * LEVELS
+    evals_per_step = P * LEVELS if args.mode == "search" else P
     value = ws * evals_per_step * args.steps / (total_ms / 1000.0)
 
     # ---- end to end through the C ABI from pinned host buffers ----
     A_pin = torch.from_numpy(pair.xyzA).pin_memory()
     B_pin = torch.from_numpy(pair.xyzB).pin_memory()
     A_h, B_h = A_pin.numpy(), B_pin.numpy()
-    e2e_steps = max(1, min(args.steps, 50))
+    e2e_steps = max(1, min(args.steps, 50)) if args.mode == "search" else 0
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -295,7 +303,7 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = ws * evals_per_step * e2e_steps / e2e_s
+    e2e_value = ws * evals_per_step * e2e_steps / e2e_s if e2e_steps else None
     h2d = (pair.xyzA.shape[0] + pair.xyzB.shape[0]) * 12 + LEVELS * P * 48
     d2h = 24 + LEVELS * (8 + 12 + 4)
 
@@ -319,8 +327,15 @@ def run_ours(args):
             "dtype": "f32+i32", "data": "synthetic", "config": workload_config(pair, LEVELS), "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches), "clocks": clocks,
-            "result_check": {"T": [float(x) for x in T], "T_true": [float(x) for x in pair.T], "mi": mi}}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+            "result_check": ({"T": [float(x) for x in T], "T_true": [float(x) for x in pair.T], "mi": mi}
+                             if args.mode == "search" else {"argmax": int(am_dev.item()), "mi_max": float(mi_dev.max())})}
+    if args.mode == "eval":
+        line["config"]["workload"] = (f"lidar-120k eval: set_reference + one align_eval_mi of {P} lattice poses "
+                                      "(device-resident inputs and outputs)")
+        line["config"]["poses_per_level"] = P
+        line["config"]["levels"] = 1
+        line["e2e"] = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.mode == "search":
         import oracle
         cores = oracle.host_cores()
         n_sample = 2048
@@ -343,6 +358,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="search", choices=["search", "eval"],
+                    help="search: reference build + 6-level search per step (default); "
+                         "eval: reference build + one align_eval_mi of --poses poses per step")
+    ap.add_argument("--poses", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

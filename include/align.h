@@ -130,8 +130,9 @@ align_status align_eval_mi(align_grid* grid, const float* xyzB, int64_t nB, int 
                            float* mi_out, int64_t* argmax_out, uint32_t* hist_out);
 
 /* Per-voxel integer sums of B under one pose, from the same kernel that serves
-   align_eval_mi: acc_out (host) V x 3 int64 rows (n, S1, S2), zero for empty voxels;
-   box_out: B's occupied bbox as above.  For parity checks of the voxel map. */
+   align_eval_mi: acc_out (host) V x 3 int64 rows (n, S1, S2), zero for empty voxels
+   (S1, S2 are produced for every feature here); box_out: B's occupied bbox as above.
+   For parity checks of the voxel map. */
 align_status align_accumulate(align_grid* grid, const float* xyzB, int64_t nB, int flags,
                               const float pose12[12], int64_t* acc_out, int32_t box_out[6]);
 

@@ -50,7 +50,8 @@ struct EvalArgs {
   unsigned long long* wide;// per CTA: table_slots x 2 (S1 as two's complement, S2)
   int32_t table_slots;
   int32_t passes0;         // initial key-partition passes (power of two)
-  int64_t* dump;           // optional: V x 3 (n, S1, S2) for pose 0 (parity checks)
+  int64_t* dump;           // optional: V x 3 (n, S1, S2) for pose 0 (parity checks; S1, S2
+                           // are accumulated whenever dump is set, whatever the feature)
 };
 
 struct ComposeArgs {

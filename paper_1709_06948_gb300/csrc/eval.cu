@@ -31,7 +31,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kPPT = 2;                       // points per thread per tile
 constexpr int kTile = kThreads * kPPT;        // points per tile
 constexpr uint32_t kTileBytes = kTile * 12u;  // fp32 xyz
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kMaxPasses = 1 << 16;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
@@ -99,7 +99,8 @@ __device__ __forceinline__ void issue_tile(const EvalSmem& S, const EvalArgs& a,
 }
 
 // Find or insert `key` in the open-addressing table (linear probing, bounded by T probes).
-__device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T, uint32_t cap) {
+// A full table flags the pose for a restart with more key partitions.
+__device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T) {
   uint32_t h = __umulhi(key * 0x9E3779B1u, (uint32_t)T);
   volatile uint32_t* vkey = S.tkey;
   for (int i = 0; i < T; ++i) {
@@ -107,11 +108,7 @@ __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T
     if (k == key) return (int)h;
     if (k == kEmptyKey) {
       const uint32_t old = atomicCAS(&S.tkey[h], kEmptyKey, key);
-      if (old == kEmptyKey) {
-        if (atomicAdd(&S.flags[0], 1u) >= cap) S.flags[1] = 1u;  // too full: repartition
-        return (int)h;
-      }
-      if (old == key) return (int)h;
+      if (old == kEmptyKey || old == key) return (int)h;
     }
     h = (h + 1 == (uint32_t)T) ? 0u : h + 1;
   }
@@ -123,8 +120,7 @@ __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T
 // last lane adds the run's (n, S1, S2) into the table.
 template <bool kVar>
 __device__ __forceinline__ void commit_row(const EvalSmem& S, const GridConst& gc, const EvalArgs& a,
-                                           unsigned long long* wide, uint32_t key, int dz, int lane, int T,
-                                           uint32_t cap) {
+                                           unsigned long long* wide, uint32_t key, int dz, int lane, int T) {
   const uint32_t valid = __ballot_sync(kFull, key != kEmptyKey);
   if (valid == 0u) return;
   const uint32_t prev = __shfl_up_sync(kFull, key, 1);
@@ -148,7 +144,7 @@ __device__ __forceinline__ void commit_row(const EvalSmem& S, const GridConst& g
   }
   if (tail && key != kEmptyKey) {
     if (*(volatile uint32_t*)&S.flags[1]) return;  // pose restarts anyway
-    const int slot = table_slot(S, key, T, cap);
+    const int slot = table_slot(S, key, T);
     if (slot < 0) return;
     const uint32_t n = (uint32_t)(d + 1);
     if (kVar) {
@@ -243,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
               if (lg > 0 && ((key * 0x85EBCA77u) >> (32 - lg)) != (uint32_t)pass) key = kEmptyKey;
             }
           }
-          commit_row<kVar>(S, gc, a, wide, key, dz, lane, T, cap);
+          commit_row<kVar>(S, gc, a, wide, key, dz, lane, T);
         }
         __syncwarp();
         if (lane == 0) {
@@ -268,9 +264,11 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
       const bool overflow = S.flags[1] != 0u;
       // ---- read (and clear) the table ----
       int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX, mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
+      uint32_t occupied = 0;
       for (int s = tid; s < T; s += kThreads) {
         const uint32_t k = S.tkey[s];
         if (k == kEmptyKey) continue;
+        ++occupied;
         const uint64_t n = S.tcnt[s];
         int64_t s1 = S.ts1[s];
         uint64_t s2 = S.ts2[s];
@@ -302,6 +300,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
           a.dump[3 * (size_t)k + 2] = (int64_t)s2;
         }
       }
+      occupied = __reduce_add_sync(kFull, occupied);
+      if (lane == 0 && occupied) atomicAdd(&S.flags[0], occupied);
       mn0 = __reduce_min_sync(kFull, mn0); mn1 = __reduce_min_sync(kFull, mn1);
       mn2 = __reduce_min_sync(kFull, mn2); mx0 = __reduce_max_sync(kFull, mx0);
       mx1 = __reduce_max_sync(kFull, mx1); mx2 = __reduce_max_sync(kFull, mx2);
@@ -330,8 +330,16 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
         __syncthreads();
         continue;
       }
+      // a table filled beyond 3/4 probes slowly: sweep the following poses in more partitions
+      const bool crowded = S.flags[0] > cap;
+      __syncthreads();
       if (tid == 0) S.flags[0] = 0u;
-      ++pass;
+      if (crowded && passes < kMaxPasses) {
+        passes *= 2;
+        pass = 2 * pass + 2;  // the partitions already swept are split in two; continue after them
+      } else {
+        ++pass;
+      }
       __syncthreads();
     }
     if (aborted) break;
@@ -477,7 +485,7 @@ int eval_table_slots_for(int K, size_t smem_budget) {
 cudaError_t launch_eval(const GridConst& gc, const EvalArgs& a, int n_ctas, cudaStream_t s) {
   const size_t smem = eval_smem_bytes(gc.K, a.table_slots);
   cudaError_t e;
-  if (gc.feature == 0) {
+  if (gc.feature == 0 && a.dump == nullptr) {  // the count feature needs no z sums
     e = cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     eval_kernel<false><<<n_ctas, kThreads, smem, s>>>(gc, a);

@@ -244,6 +244,18 @@ align_status upload_points(align_grid* g, const float* xyz, int64_t n, int flags
   return ALIGN_OK;
 }
 
+// Error word and counters: allocated once per grid and zeroed (cudaMalloc memory is not).
+align_status ensure_status_words(align_grid* g) {
+  if (g->err.p && g->max_passes.p && g->wide_count.p) return ALIGN_OK;
+  CU(g->err.ensure(16), "allocate error word");
+  CU(g->max_passes.ensure(16), "allocate counters");
+  CU(g->wide_count.ensure(16), "allocate counters");
+  CU(cudaMemsetAsync(g->err.p, 0, 16, g->stream), "clear error word");
+  CU(cudaMemsetAsync(g->max_passes.p, 0, 16, g->stream), "clear counters");
+  CU(cudaMemsetAsync(g->wide_count.p, 0, 16, g->stream), "clear counters");
+  return ALIGN_OK;
+}
+
 struct EvalOut {
   float* mi;          // device
   uint32_t* hist;     // device or null
@@ -259,9 +271,8 @@ align_status enqueue_eval(align_grid* g, int32_t n_points, int32_t n_tiles, cons
   CU(g->out_c.ensure((size_t)P * KK * sizeof(uint32_t)), "allocate histograms");
   CU(g->out_box.ensure((size_t)P * 6 * sizeof(int32_t)), "allocate boxes");
   CU(g->best.ensure(sizeof(unsigned long long)), "allocate argmax");
-  CU(g->err.ensure(16), "allocate error word");
-  CU(g->max_passes.ensure(16), "allocate counters");
-  CU(g->wide_count.ensure(16), "allocate counters");
+  align_status st0 = ensure_status_words(g);
+  if (st0 != ALIGN_OK) return st0;
   const int n_ctas = (int)std::min<int64_t>(P, g->n_sm);
   const size_t wide_bytes = (size_t)n_ctas * 2 * g->table_slots * sizeof(unsigned long long);
   if (g->wide.cap < wide_bytes || g->wide.p == nullptr) {
@@ -328,7 +339,9 @@ align_status collect_status(align_grid* g) {
   }
   CU(cudaMemsetAsync(g->err.p, 0, 4, g->stream), "reset error word");
   CU(cudaMemsetAsync(g->wide_count.p, 0, 4, g->stream), "reset counters");
-  if (vals[1] > (uint32_t)g->passes_seed) g->passes_seed = (int32_t)vals[1];
+  // seed the next launch with the largest partition count a pose needed (a power of two)
+  if (vals[1] > (uint32_t)g->passes_seed && vals[1] <= (1u << 16) && (vals[1] & (vals[1] - 1)) == 0)
+    g->passes_seed = (int32_t)vals[1];
   g->stats[0] = vals[1];
   g->stats[1] = vals[2];
   if (vals[0] & kErrWaitTimeout) return fail(ALIGN_E_TIMEOUT, "a bounded device wait gave up");
@@ -337,12 +350,7 @@ align_status collect_status(align_grid* g) {
   return ALIGN_OK;
 }
 
-align_status ensure_status_words(align_grid* g) {
-  CU(g->err.ensure(16), "allocate error word");
-  CU(g->max_passes.ensure(16), "allocate counters");
-  CU(g->wide_count.ensure(16), "allocate counters");
-  return ALIGN_OK;
-}
+
 
 }  // namespace
 
