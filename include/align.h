@@ -159,8 +159,8 @@ align_status align_eval_stats(align_grid* grid, int64_t out[5]);
 /* Kernel timing with CUDA events recorded on the grid's stream around every eval
    kernel and every compose+argmax pair.  mode 1: enable and reset the totals;
    mode 0: disable; mode 2: only read.  out (may be NULL): [0] total eval-kernel ms,
-   [1] total compose+argmax ms, [2] eval launches timed.  Totals are gathered at
-   each synchronising call (host outputs, align_search). */
+   [1] total compose+argmax ms, [2] eval launches timed.  Every call of this function
+   first waits for the launches recorded so far and adds them to the totals. */
 align_status align_profile(align_grid* grid, int32_t mode, double out[3]);
 
 /* Message of the calling thread's last failure ("" if none). */

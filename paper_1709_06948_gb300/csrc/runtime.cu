@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -86,10 +87,10 @@ struct align_grid {
   DevBuf xyz, poses, out_c, out_box, mi, hist, best, argmax, err, max_passes, wide_count, wide, dump;
   int32_t passes_seed = 1;
   int64_t stats[5] = {0, 0, 0, 0, 0};
-  // event timing (align_profile)
+  // event timing (align_profile): one (before eval, after eval, after argmax) triple per
+  // launch, drained into the totals at the next synchronising call or profile read
   bool profiling = false;
-  bool ev_pending = false;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  std::vector<std::array<cudaEvent_t, 3>> ev_pending, ev_pool;
   double prof[3] = {0.0, 0.0, 0.0};
 };
 
@@ -297,9 +298,18 @@ align_status enqueue_eval(align_grid* g, int32_t n_points, int32_t n_tiles, cons
   a.table_slots = g->table_slots;
   a.passes0 = g->passes_seed;
   a.dump = out.dump;
-  if (g->profiling) CU(cudaEventRecord(g->ev[0], g->stream), "record event");
+  std::array<cudaEvent_t, 3> evs{};
+  if (g->profiling) {
+    if (g->ev_pool.empty()) {
+      for (cudaEvent_t& e : evs) CU(cudaEventCreate(&e), "create event");
+    } else {
+      evs = g->ev_pool.back();
+      g->ev_pool.pop_back();
+    }
+    CU(cudaEventRecord(evs[0], g->stream), "record event");
+  }
   CU(launch_eval(g->gc, a, n_ctas, g->stream), "launch eval kernel");
-  if (g->profiling) CU(cudaEventRecord(g->ev[1], g->stream), "record event");
+  if (g->profiling) CU(cudaEventRecord(evs[1], g->stream), "record event");
 
   ComposeArgs c{};
   c.c = g->out_c.as<uint32_t>();
@@ -312,12 +322,28 @@ align_status enqueue_eval(align_grid* g, int32_t n_points, int32_t n_tiles, cons
   CU(launch_compose(g->gc, c, g->stream), "launch compose kernel");
   CU(launch_argmax_finalize(g->best.as<unsigned long long>(), out.argmax, g->stream), "launch argmax");
   if (g->profiling) {
-    CU(cudaEventRecord(g->ev[2], g->stream), "record event");
-    g->ev_pending = true;
+    CU(cudaEventRecord(evs[2], g->stream), "record event");
+    g->ev_pending.push_back(evs);
   }
   g->stats[2] = g->table_slots;
   g->stats[3] = n_ctas;
   g->stats[4] += 3;
+  return ALIGN_OK;
+}
+
+// Add the elapsed times of all recorded event triples to the profile totals.
+align_status drain_events(align_grid* g) {
+  for (auto& evs : g->ev_pending) {
+    CU(cudaEventSynchronize(evs[2]), "synchronize event");
+    float t0 = 0.0f, t1 = 0.0f;
+    CU(cudaEventElapsedTime(&t0, evs[0], evs[1]), "event time");
+    CU(cudaEventElapsedTime(&t1, evs[1], evs[2]), "event time");
+    g->prof[0] += t0;
+    g->prof[1] += t1;
+    g->prof[2] += 1.0;
+    g->ev_pool.push_back(evs);
+  }
+  g->ev_pending.clear();
   return ALIGN_OK;
 }
 
@@ -328,14 +354,9 @@ align_status collect_status(align_grid* g) {
   CU(cudaMemcpyAsync(&vals[1], g->max_passes.p, 4, cudaMemcpyDeviceToHost, g->stream), "read counters");
   CU(cudaMemcpyAsync(&vals[2], g->wide_count.p, 4, cudaMemcpyDeviceToHost, g->stream), "read counters");
   CU(cudaStreamSynchronize(g->stream), "synchronize");
-  if (g->profiling && g->ev_pending) {
-    float t0 = 0.0f, t1 = 0.0f;
-    CU(cudaEventElapsedTime(&t0, g->ev[0], g->ev[1]), "event time");
-    CU(cudaEventElapsedTime(&t1, g->ev[1], g->ev[2]), "event time");
-    g->prof[0] += t0;
-    g->prof[1] += t1;
-    g->prof[2] += 1.0;
-    g->ev_pending = false;
+  {
+    align_status stp = drain_events(g);
+    if (stp != ALIGN_OK) return stp;
   }
   CU(cudaMemsetAsync(g->err.p, 0, 4, g->stream), "reset error word");
   CU(cudaMemsetAsync(g->wide_count.p, 0, 4, g->stream), "reset counters");
@@ -397,8 +418,9 @@ align_status align_destroy_grid(align_grid* g) {
   for (DevBuf* b : {&g->symA, &g->sat, &g->xyz, &g->poses, &g->out_c, &g->out_box, &g->mi, &g->hist, &g->best,
                     &g->argmax, &g->err, &g->max_passes, &g->wide_count, &g->wide, &g->dump})
     b->release();
-  for (cudaEvent_t& e : g->ev)
-    if (e) cudaEventDestroy(e);
+  for (auto* v : {&g->ev_pending, &g->ev_pool})
+    for (auto& evs : *v)
+      for (cudaEvent_t e : evs) cudaEventDestroy(e);
   delete g;
   return ALIGN_OK;
 }
@@ -667,17 +689,14 @@ align_status align_eval_stats(align_grid* g, int64_t out[5]) {
 align_status align_profile(align_grid* g, int32_t mode, double out[3]) {
   align_status st = check_grid(g);
   if (st != ALIGN_OK) return st;
+  if (mode != 0 && mode != 1 && mode != 2) return fail(ALIGN_E_INVALID, "mode must be 0, 1 or 2");
+  st = drain_events(g);  // waits for the recorded launches
+  if (st != ALIGN_OK) return st;
   if (mode == 1) {
-    for (cudaEvent_t& e : g->ev)
-      if (!e) CU(cudaEventCreate(&e), "create event");
     g->profiling = true;
-    g->ev_pending = false;
     g->prof[0] = g->prof[1] = g->prof[2] = 0.0;
   } else if (mode == 0) {
     g->profiling = false;
-    g->ev_pending = false;
-  } else if (mode != 2) {
-    return fail(ALIGN_E_INVALID, "mode must be 0, 1 or 2");
   }
   if (out)
     for (int i = 0; i < 3; ++i) out[i] = g->prof[i];
