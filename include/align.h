@@ -163,6 +163,28 @@ align_status align_eval_stats(align_grid* grid, int64_t out[5]);
    first waits for the launches recorded so far and adds them to the totals. */
 align_status align_profile(align_grid* grid, int32_t mode, double out[3]);
 
+/* align_reference_noalloc — A's feature map and bbox without allocating anything.
+   The paper has no counterpart; this is a library convenience.  align_set_reference
+   allocates working arrays on every call, which some callers cannot do: processes whose
+   device memory belongs to another allocator under a fixed budget, and latency-bound
+   loops in which a device allocation (it may synchronise the device) is not allowed.
+   This entry point computes the same symbols and bbox as align_set_reference followed
+   by align_get_reference, using a fixed working area that is a static array in the
+   library's device memory (10 MiB, held by every GPU that loads the library until the
+   process exits).  It calls no cudaMalloc, cudaFree or other allocating routine.
+     desc:   as for align_create_grid; X*Y*Z must be at most 2^19 (524,288) voxels,
+             larger grids are refused with ALIGN_E_INVALID.
+     xyzA:   nA x 3 fp32, device memory.
+     symA:   V bytes, device memory (written).   boxA: 6 int32, device memory (written).
+     cuda_stream: stream to enqueue on (NULL = legacy default stream).
+   The call is asynchronous: outputs are ready when the stream reaches this point.  The
+   first call on a device looks up the working area's device address (once per device,
+   with that device current); make that first call before any stream capture.  All calls
+   on a device share the working area (each clears what it uses first), so calls whose
+   work overlaps on the GPU race; issue them one after another. */
+align_status align_reference_noalloc(const align_grid_desc* desc, const float* xyzA, int64_t nA,
+                                     uint8_t* symA, int32_t* boxA, void* cuda_stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* align_last_error(void);
 

@@ -27,7 +27,7 @@ _STATUS_NAMES = {0: "ALIGN_OK", 1: "ALIGN_NOT_READY", -1: "ALIGN_E_INVALID", -2:
 # Every entry point include/align.h declares (checked by the tests against the .so).
 EXPORTS = ["align_create_grid", "align_destroy_grid", "align_grid_info", "align_set_reference",
            "align_get_reference", "align_round_poses", "align_eval_mi", "align_accumulate", "align_search",
-           "align_search_ex", "align_eval_stats", "align_profile", "align_last_error"]
+           "align_search_ex", "align_eval_stats", "align_profile", "align_reference_noalloc", "align_last_error"]
 
 
 class AlignError(RuntimeError):
@@ -74,6 +74,7 @@ def load(build_if_missing: bool = True):
         "align_search_ex": [P, P, i64, C.c_int, P, P, P, i32, P, P, P],
         "align_eval_stats": [P, P],
         "align_profile": [P, i32, P],
+        "align_reference_noalloc": [P, P, i64, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -303,3 +304,33 @@ def align_profile(grid: Grid, mode: int):
     out = np.zeros(3, dtype=np.float64)
     _check(load().align_profile(grid.handle, int(mode), out.ctypes.data_as(C.c_void_p)))
     return float(out[0]), float(out[1]), int(out[2])
+
+
+def align_reference_noalloc(desc_kw: dict, xyzA, symA_out, boxA_out, stream=None):
+    """A's symbols and bbox into caller-owned device tensors, without any device allocation
+    by the library (for callers whose device memory is managed elsewhere or who may not
+    allocate in their loop).  `xyzA` (n, 3) float32, `symA_out` (V,) uint8 and `boxA_out`
+    (6,) int32 are CUDA tensors.  Asynchronous on `stream` (default: torch's current stream)."""
+    lib = load()
+    d = GridDesc()
+    d.origin = (C.c_float * 3)(*[float(v) for v in desc_kw["origin"]])
+    d.res_m = float(desc_kw["res_m"])
+    d.dims = (C.c_int32 * 3)(*[int(v) for v in desc_kw["dims"]])
+    d.feature = int(desc_kw.get("feature", ALIGN_FEAT_ZVAR))
+    d.count_levels = int(desc_kw.get("count_levels", 7))
+    d.var_levels = int(desc_kw.get("var_levels", 15))
+    ct = desc_kw.get("count_thresh")
+    vt = desc_kw.get("var_thresh")
+    ct = None if ct is None else np.ascontiguousarray(ct, dtype=np.uint32)
+    vt = None if vt is None else np.ascontiguousarray(vt, dtype=np.int64)
+    d.count_thresh = None if ct is None else ct.ctypes.data
+    d.var_thresh = None if vt is None else vt.ctypes.data
+    if not (_is_torch_cuda(xyzA) and _is_torch_cuda(symA_out) and _is_torch_cuda(boxA_out)):
+        raise ValueError("align_reference_noalloc takes CUDA tensors only")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    raw = stream if isinstance(stream, int) else int(stream.cuda_stream)
+    _check(lib.align_reference_noalloc(C.byref(d), C.c_void_p(xyzA.data_ptr()), int(xyzA.shape[0]),
+                                       C.c_void_p(symA_out.data_ptr()), C.c_void_p(boxA_out.data_ptr()),
+                                       C.c_void_p(raw)))

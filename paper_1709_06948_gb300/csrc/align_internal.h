@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "align.h"
+
 namespace mialign {
 
 constexpr int kMaxSymbols = 64;
@@ -78,5 +80,11 @@ cudaError_t launch_ref_accumulate(const GridConst& gc, const float* xyz, int64_t
 cudaError_t launch_ref_symbols(const GridConst& gc, const uint32_t* cnt, const unsigned long long* s1,
                                const unsigned long long* s2, uint8_t* symA, int32_t* box, cudaStream_t s);
 cudaError_t launch_ref_sat(const GridConst& gc, const uint8_t* symA, int32_t* sat, cudaStream_t s);
+
+// Host helpers shared by the C-ABI translation units (defined in runtime.cu).
+align_status check_grid_desc(const align_grid_desc* desc, GridConst* gc);
+align_status report_error(align_status st, const char* msg);
+align_status report_cuda_error(cudaError_t e, const char* what);
+void round_pose_host(const float origin[3], const double* eta6, float* pose12);
 
 }  // namespace mialign

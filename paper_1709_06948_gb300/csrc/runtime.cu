@@ -704,3 +704,11 @@ align_status align_profile(align_grid* g, int32_t mode, double out[3]) {
 }
 
 }  // extern "C"
+
+// Helpers for other translation units of the library (validation, messages, pose rounding).
+namespace mialign {
+align_status check_grid_desc(const align_grid_desc* desc, GridConst* gc) { return validate_desc(desc, gc); }
+align_status report_error(align_status st, const char* msg) { return fail(st, "%s", msg); }
+align_status report_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+void round_pose_host(const float origin[3], const double* eta6, float* pose12) { pose_to_fp32(origin, eta6, pose12); }
+}  // namespace mialign
