@@ -38,22 +38,26 @@ struct GridConst {
 // then the partial joint histogram c[a][b>=1] of the occupied B voxels inside boxA and
 // B's occupied bbox.
 struct EvalArgs {
-  const float* xyz;        // padded point buffer, n_tiles * tile_points * 3 floats
-  int32_t n_points;
-  int32_t n_tiles;
-  const float* poses;      // P x 12
+  const float4* src;        // point tiles: source arrays of n_tiles * tile float4 each
+                            // (raw xyz, or xyz pre-rotated by one rotation); padding is NaN
+  size_t src_stride;        // float4 entries per source array
+  const int32_t* pose_src;  // P: source array of each pose (nullptr: all use array 0)
+  int32_t n_tiles;          // tiles per source array (>= the pipeline depth)
+  const float* poses;       // P x 12
   int32_t P;
-  const uint8_t* symA;     // V
-  uint32_t* out_c;         // P x K x K (B-occupied voxels inside boxA)
-  int32_t* out_box;        // P x 6
-  uint32_t* err;           // error bits
-  uint32_t* max_passes;    // running max of key-partition passes (seed for the next launch)
-  uint32_t* wide_count;    // voxels that overflowed into the 64-bit side sums
-  unsigned long long* wide;// per CTA: table_slots x 2 (S1 as two's complement, S2)
+  const uint8_t* symA;      // V
+  uint32_t* out_c;          // P x K x K (B-occupied voxels inside boxA)
+  int32_t* out_box;         // P x 6
+  uint32_t* err;            // error bits
+  uint32_t* max_passes;     // running max of key-partition passes (seed for the next launch)
+  uint32_t* wide_count;     // voxels that overflowed into the 64-bit side sums
+  unsigned long long* wide; // per CTA: table_slots x 2 (S1 as two's complement, S2)
+  uint32_t* redo_list;      // P: poses whose table filled up, finished by the redo kernel
+  uint32_t* redo_count;     // entries in redo_list (zeroed before every launch)
   int32_t table_slots;
-  int32_t passes0;         // initial key-partition passes (power of two)
-  int64_t* dump;           // optional: V x 3 (n, S1, S2) for pose 0 (parity checks; S1, S2
-                           // are accumulated whenever dump is set, whatever the feature)
+  int32_t passes0;          // initial key-partition passes (power of two)
+  int64_t* dump;            // optional: V x 3 (n, S1, S2) for pose 0 (parity checks; S1, S2
+                            // are accumulated whenever dump is set, whatever the feature)
 };
 
 struct ComposeArgs {
@@ -68,9 +72,16 @@ struct ComposeArgs {
 
 // Launch helpers (defined in eval.cu / reference.cu).
 int eval_tile_points();
+int eval_min_tiles();
 size_t eval_smem_bytes(int K, int table_slots);
 int eval_table_slots_for(int K, size_t smem_budget);
-cudaError_t launch_eval(const GridConst& gc, const EvalArgs& a, int n_ctas, cudaStream_t s);
+// rotate: tiles hold raw xyz (the kernel applies each pose's rotation); otherwise each
+// pose's source array already holds R p for that pose's rotation.
+cudaError_t launch_eval(const GridConst& gc, const EvalArgs& a, int n_ctas, bool rotate, cudaStream_t s);
+// xyz (n x 3 fp32) -> n_out float4 with NaN padding; with rots (n_rot x 9), one
+// pre-rotated copy u = R p per rotation (same FMA order as the voxel map).
+cudaError_t launch_pack_points(const float* xyz, int64_t n, int64_t n_out, const float* rots, int n_rot,
+                               float4* out, cudaStream_t s);
 cudaError_t launch_compose(const GridConst& gc, const ComposeArgs& a, cudaStream_t s);
 cudaError_t launch_argmax_finalize(const unsigned long long* best, int64_t* out, cudaStream_t s);
 

@@ -24,11 +24,17 @@ struct Pose12 {
   float t[3];
 };
 
-__device__ __forceinline__ uint32_t voxel_key(const Pose12& P, float x, float y, float z, float inv_res,
-                                              int X, int Y, int Z, int res_mm, int* dz) {
-  const float gx = __fadd_rn(__fmaf_rn(P.r[0], x, __fmaf_rn(P.r[1], y, __fmul_rn(P.r[2], z))), P.t[0]);
-  const float gy = __fadd_rn(__fmaf_rn(P.r[3], x, __fmaf_rn(P.r[4], y, __fmul_rn(P.r[5], z))), P.t[1]);
-  const float gz = __fadd_rn(__fmaf_rn(P.r[6], x, __fmaf_rn(P.r[7], y, __fmul_rn(P.r[8], z))), P.t[2]);
+// u = R p with the fixed FMA order (shared by every rotation of every pose).
+__device__ __forceinline__ void rotate_point(const float* r, float x, float y, float z, float& ux, float& uy,
+                                             float& uz) {
+  ux = __fmaf_rn(r[0], x, __fmaf_rn(r[1], y, __fmul_rn(r[2], z)));
+  uy = __fmaf_rn(r[3], x, __fmaf_rn(r[4], y, __fmul_rn(r[5], z)));
+  uz = __fmaf_rn(r[6], x, __fmaf_rn(r[7], y, __fmul_rn(r[8], z)));
+}
+
+// Key and dz of a transformed point g = u + t'.
+__device__ __forceinline__ uint32_t voxel_key_g(float gx, float gy, float gz, float inv_res, int X, int Y, int Z,
+                                                int res_mm, int* dz) {
   const float fx = __fmul_rn(gx, inv_res);
   const float fy = __fmul_rn(gy, inv_res);
   const float fz = __fmul_rn(gz, inv_res);
@@ -42,6 +48,14 @@ __device__ __forceinline__ uint32_t voxel_key(const Pose12& P, float x, float y,
   const int zq = __float2int_rn(__fmul_rn(gz, 1000.0f));
   *dz = zq - kz * res_mm;
   return (uint32_t)((kz * Y + ky) * X + kx);
+}
+
+__device__ __forceinline__ uint32_t voxel_key(const Pose12& P, float x, float y, float z, float inv_res,
+                                              int X, int Y, int Z, int res_mm, int* dz) {
+  float ux, uy, uz;
+  rotate_point(P.r, x, y, z, ux, uy, uz);
+  return voxel_key_g(__fadd_rn(ux, P.t[0]), __fadd_rn(uy, P.t[1]), __fadd_rn(uz, P.t[2]), inv_res, X, Y, Z, res_mm,
+                     dz);
 }
 
 // ---------------------------------------------------------------------------------

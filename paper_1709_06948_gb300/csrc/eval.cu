@@ -1,22 +1,28 @@
 // eval.cu — the pose-batched MI hot path (arXiv 1709.06948, Algorithm 1 loop body for
 // a whole batch of candidate poses; Sec. III-A features; Eqs. 1-5).
 //
-// eval_kernel: persistent, one CTA per SM, one pose at a time per CTA.  Scan B is
-// streamed through shared memory in tiles by 1-D bulk (TMA) copies on a cyclic
-// multi-stage mbarrier pipeline.  For every point and the CTA's current pose the warp
-// computes the voxel key and dz (device_common.cuh), collapses runs of equal keys
-// among its 32 consecutive points with a segmented shuffle scan, and the run's last
-// lane adds (n, S1, S2) into a shared-memory open-addressing hash table with 32-bit
-// shared atomics.  After the sweep the table holds the pose's occupied B voxels; one
-// pass over it yields the feature symbols, B's occupied bbox and the partial joint
-// histogram c[a][b >= 1] of the occupied voxels inside A's bbox.
-//  - If a pose occupies more voxels than the table holds, the pose restarts with the
-//    keys split into 2, 4, ... disjoint hash partitions swept one after another.
-//  - A voxel holding more points than the 32-bit sums allow diverts its later runs to
-//    64-bit side sums in global memory (per CTA, indexed by table slot).
-// compose_kernel: per pose, the overlap box (Algorithm 1), A's symbol counts over it
-// from per-symbol prefix sums, the phi column h[a][0], then Eqs. 2-5 in FP32 with a
-// fixed reduction order, and the packed (MI, index) maximum for Eq. 1.
+// pack_points_kernel: scan B as float4 tiles (NaN padding), either raw xyz or one
+// pre-rotated copy u = R p per distinct rotation of the batch (a search lattice has 32
+// rotations for 4,096 poses, so the 9-FMA rotation leaves the per-pose loop).
+//
+// eval_kernel: persistent, one CTA per SM, one pose at a time per CTA.  The tiles of the
+// pose's source array arrive by 1-D bulk (TMA) copies on a cyclic mbarrier ring whose
+// schedule already knows the CTA's next pose, so the copies never stall at pose
+// boundaries.  Per point and pose: voxel key and dz (device_common.cuh); runs of equal
+// keys among 32 consecutive points are summed with one warp reduction per quantity over
+// the run's lane mask; the run's last lane adds (n, S1, S2) into a shared-memory
+// open-addressing hash table with 32-bit shared atomics.  After the sweep one pass over
+// the table gives the feature symbols, B's occupied bbox and the partial joint histogram
+// c[a][b >= 1] of the occupied voxels inside A's bbox.
+//  - A pose with more occupied voxels than fit the table is handed to redo_kernel (which
+//    splits the keys into 2, 4, ... hash partitions, one sweep each); a crowded table
+//    makes the CTA sweep its following poses in twice as many partitions.
+//  - A voxel with more points than the 32-bit sums allow diverts its later runs to 64-bit
+//    side sums in global memory (per CTA, indexed by table slot).
+//
+// compose_kernel: per pose, the overlap box (Algorithm 1), A's symbol counts over it from
+// per-symbol prefix sums, the phi column h[a][0], then Eqs. 2-5 in FP32 with a fixed
+// reduction order, and the packed (MI, index) maximum for Eq. 1.
 #include <climits>
 
 #include "align_internal.h"
@@ -30,15 +36,15 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPPT = 2;                       // points per thread per tile
 constexpr int kTile = kThreads * kPPT;        // points per tile
-constexpr uint32_t kTileBytes = kTile * 12u;  // fp32 xyz
-constexpr int kStages = 4;
+constexpr uint32_t kTileBytes = kTile * 16u;  // float4 per point
+constexpr int kStages = 3;
 constexpr int kMaxPasses = 1 << 16;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
 
 struct EvalSmem {
-  float* tiles;
+  float4* tiles;
   uint32_t* tkey;
   uint32_t* tcnt;
   int32_t* ts1;
@@ -46,10 +52,11 @@ struct EvalSmem {
   uint32_t* hist;
   uint32_t* ct;
   int64_t* vt;
-  uint64_t* mbar;      // [0, kStages): full, [kStages, 2 kStages): empty
-  uint32_t* issue_cnt; // kStages
-  int32_t* box;        // 6
-  uint32_t* flags;     // fill, overflow, abort, wide
+  uint64_t* mbar;       // [0, kStages): full, [kStages, 2 kStages): empty
+  uint32_t* issue_cnt;  // kStages
+  uint32_t* sched;      // q_start, n_consume, src_cur, src_next
+  int32_t* box;         // 6
+  uint32_t* flags;      // occupied count, table full, abort, wide used
 };
 
 __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, uint8_t* base) {
@@ -70,10 +77,11 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, ui
   size_t o_vt = take(kMaxLevels * 8 + 8, 16);
   size_t o_mbar = take(2 * kStages * 8, 8);
   size_t o_issue = take(kStages * 4, 4);
+  size_t o_sched = take(4 * 4, 4);
   size_t o_box = take(6 * 4, 4);
   size_t o_flags = take(4 * 4, 4);
   if (s) {
-    s->tiles = (float*)(base + o_tiles);
+    s->tiles = (float4*)(base + o_tiles);
     s->tkey = (uint32_t*)(base + o_key);
     s->tcnt = (uint32_t*)(base + o_cnt);
     s->ts1 = (int32_t*)(base + o_s1);
@@ -83,23 +91,38 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, ui
     s->vt = (int64_t*)(base + o_vt);
     s->mbar = (uint64_t*)(base + o_mbar);
     s->issue_cnt = (uint32_t*)(base + o_issue);
+    s->sched = (uint32_t*)(base + o_sched);
     s->box = (int32_t*)(base + o_box);
     s->flags = (uint32_t*)(base + o_flags);
   }
   return off;
 }
 
-// Issue the bulk copy of consumption slot q (cyclic over the tiles).
-__device__ __forceinline__ void issue_tile(const EvalSmem& S, const EvalArgs& a, uint32_t q) {
-  const uint32_t b = q % kStages;
-  const uint32_t tile = q % (uint32_t)a.n_tiles;
-  const uint32_t full = smem_addr(&S.mbar[b]);
-  mbar_arrive_expect_tx(full, kTileBytes);
-  bulk_copy_g2s(smem_addr(S.tiles + (size_t)b * kTile * 3), a.xyz + (size_t)tile * kTile * 3, kTileBytes, full);
+__device__ __forceinline__ uint32_t pose_source(const EvalArgs& a, int p) {
+  return a.pose_src ? (uint32_t)a.pose_src[p] : 0u;
 }
 
-// Find or insert `key` in the open-addressing table (linear probing, bounded by T probes).
-// A full table flags the pose for a restart with more key partitions.
+// Issue the bulk copy for consumption index q: within the current pose's sweeps it is a
+// tile of the current source array, past them a tile of the next pose's array.
+__device__ __forceinline__ void issue_tile(const EvalSmem& S, const EvalArgs& a, uint32_t q) {
+  const uint32_t b = q % kStages;
+  const uint32_t rel = q - S.sched[0];
+  uint32_t src, tile;
+  if (rel < S.sched[1]) {
+    src = S.sched[2];
+    tile = rel % (uint32_t)a.n_tiles;
+  } else {
+    src = S.sched[3];
+    tile = (rel - S.sched[1]) % (uint32_t)a.n_tiles;
+  }
+  const uint32_t full = smem_addr(&S.mbar[b]);
+  mbar_arrive_expect_tx(full, kTileBytes);
+  bulk_copy_g2s(smem_addr(S.tiles + (size_t)b * kTile), a.src + (size_t)src * a.src_stride + (size_t)tile * kTile,
+                kTileBytes, full);
+}
+
+// Find or insert `key` in the open-addressing table (linear probing, at most T probes).
+// Returns -1 when the table is full.
 __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T) {
   uint32_t h = __umulhi(key * 0x9E3779B1u, (uint32_t)T);
   volatile uint32_t* vkey = S.tkey;
@@ -112,68 +135,145 @@ __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T
     }
     h = (h + 1 == (uint32_t)T) ? 0u : h + 1;
   }
-  S.flags[1] = 1u;
   return -1;
 }
 
-// One warp row of 32 consecutive points: collapse runs of equal keys, then the run's
-// last lane adds the run's (n, S1, S2) into the table.
+// One warp row of 32 consecutive points.  Lanes with equal adjacent keys form a run; the
+// run's sums come from one warp reduction per quantity over the run's lane mask, and the
+// run's last lane adds them to the table.
 template <bool kVar>
-__device__ __forceinline__ void commit_row(const EvalSmem& S, const GridConst& gc, const EvalArgs& a,
-                                           unsigned long long* wide, uint32_t key, int dz, int lane, int T) {
-  const uint32_t valid = __ballot_sync(kFull, key != kEmptyKey);
-  if (valid == 0u) return;
+__device__ __forceinline__ void commit_row(const EvalSmem& S, const GridConst& gc, unsigned long long* wide,
+                                           uint32_t key, int dz, int lane, int T) {
+  if (__ballot_sync(kFull, key != kEmptyKey) == 0u) return;
   const uint32_t prev = __shfl_up_sync(kFull, key, 1);
-  const bool head = (lane == 0) || (key != prev);
-  const uint32_t hm = __ballot_sync(kFull, head);
-  const bool tail = ((((hm >> 1) | 0x80000000u) >> lane) & 1u) != 0u;
-  const int hl = 31 - __clz(hm & (kFull >> (31 - lane)));
-  const int d = lane - hl;
-  int a1 = dz;
-  uint32_t a2 = (uint32_t)(dz * dz);
+  const uint32_t heads = __ballot_sync(kFull, (lane == 0) || (key != prev));
+  const uint32_t upto = kFull >> (31 - lane);  // lanes 0..lane
+  const int first = 31 - __clz(heads & upto);
+  const uint32_t later = heads & ~upto;
+  const int last = later ? (__ffs(later) - 2) : 31;
+  const uint32_t run = (kFull >> (31 - last)) & (kFull << first);
+  int s1 = 0;
+  uint32_t s2 = 0;
   if (kVar) {
-    const int maxd = (int)__reduce_max_sync(kFull, (uint32_t)d);
-    for (int off = 1; off <= maxd; off <<= 1) {
-      const int t1 = __shfl_up_sync(kFull, a1, off);
-      const uint32_t t2 = __shfl_up_sync(kFull, a2, off);
-      if (d >= off) {
-        a1 += t1;
-        a2 += t2;
-      }
-    }
+    s1 = __reduce_add_sync(run, dz);
+    s2 = __reduce_add_sync(run, (uint32_t)(dz * dz));
   }
-  if (tail && key != kEmptyKey) {
-    if (*(volatile uint32_t*)&S.flags[1]) return;  // pose restarts anyway
-    const int slot = table_slot(S, key, T);
-    if (slot < 0) return;
-    const uint32_t n = (uint32_t)(d + 1);
-    if (kVar) {
-      const uint32_t old = atomicAdd(&S.tcnt[slot], n);
-      if (old + n <= gc.nlim) {
-        atomicAdd(&S.ts1[slot], a1);
-        atomicAdd(&S.ts2[slot], a2);
-      } else {
-        atomicAdd(&wide[2 * slot], (unsigned long long)(long long)a1);
-        atomicAdd(&wide[2 * slot + 1], (unsigned long long)a2);
-        S.flags[3] = 1u;
-      }
+  if (lane != last || key == kEmptyKey) return;
+  if (*(volatile uint32_t*)&S.flags[1]) return;  // table already full: the pose is redone
+  const int slot = table_slot(S, key, T);
+  if (slot < 0) {
+    S.flags[1] = 1u;
+    return;
+  }
+  const uint32_t n = (uint32_t)(last - first + 1);
+  if (kVar) {
+    const uint32_t old = atomicAdd(&S.tcnt[slot], n);
+    if (old + n <= gc.nlim) {
+      atomicAdd(&S.ts1[slot], s1);
+      atomicAdd(&S.ts2[slot], s2);
     } else {
-      atomicAdd(&S.tcnt[slot], n);
+      atomicAdd(&wide[2 * slot], (unsigned long long)(long long)s1);
+      atomicAdd(&wide[2 * slot + 1], (unsigned long long)s2);
+      S.flags[3] = 1u;
     }
+  } else {
+    atomicAdd(&S.tcnt[slot], n);
   }
 }
 
-template <bool kVar>
-__global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, const EvalArgs a) {
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  EvalSmem S;
-  const int T = a.table_slots;
-  const int K = gc.K, KK = K * K;
-  eval_smem_layout(K, T, &S, smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t cap = (uint32_t)T - (uint32_t)T / 4u;  // 75% load factor
-  unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
+struct PoseRegs {
+  float r[9];
+  float t[3];
+};
 
+// Keys of this thread's points of one tile under the pose (key partition `part` of 2^lg).
+template <bool kRot>
+__device__ __forceinline__ void tile_keys(const GridConst& gc, const PoseRegs& P, const float4* pts, int lg,
+                                          uint32_t part, uint32_t* key, int* dz) {
+#pragma unroll
+  for (int j = 0; j < kPPT; ++j) {
+    const float4 p = pts[j * kThreads];
+    float gx, gy, gz;
+    if (kRot) {
+      float ux, uy, uz;
+      rotate_point(P.r, p.x, p.y, p.z, ux, uy, uz);
+      gx = __fadd_rn(ux, P.t[0]);
+      gy = __fadd_rn(uy, P.t[1]);
+      gz = __fadd_rn(uz, P.t[2]);
+    } else {
+      gx = __fadd_rn(p.x, P.t[0]);
+      gy = __fadd_rn(p.y, P.t[1]);
+      gz = __fadd_rn(p.z, P.t[2]);
+    }
+    dz[j] = 0;
+    key[j] = voxel_key_g(gx, gy, gz, gc.inv_res, gc.X, gc.Y, gc.Z, gc.res_mm, &dz[j]);
+    if (lg > 0 && key[j] != kEmptyKey && ((key[j] * 0x85EBCA77u) >> (32 - lg)) != part) key[j] = kEmptyKey;
+  }
+}
+
+__device__ __forceinline__ void load_pose(const EvalArgs& a, int p, PoseRegs& P) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) P.r[i] = __ldg(a.poses + 12 * (size_t)p + i);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) P.t[i] = __ldg(a.poses + 12 * (size_t)p + 9 + i);
+}
+
+// Read (and clear) the table after a sweep: symbols, bbox and histogram unless `discard`.
+// The CTA-wide occupied count is added to S.flags[0].
+template <bool kVar>
+__device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& gc, const EvalArgs& a,
+                                           unsigned long long* wide, int T, int K, int p, bool discard) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX, mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
+  uint32_t occupied = 0;
+  for (int s = tid; s < T; s += kThreads) {
+    const uint32_t k = S.tkey[s];
+    if (k == kEmptyKey) continue;
+    ++occupied;
+    const uint64_t n = S.tcnt[s];
+    int64_t s1 = S.ts1[s];
+    uint64_t s2 = S.ts2[s];
+    if (kVar && n > gc.nlim) {
+      s1 += (int64_t)wide[2 * s];
+      s2 += wide[2 * s + 1];
+      wide[2 * s] = 0ull;
+      wide[2 * s + 1] = 0ull;
+      if (!discard) atomicAdd(a.wide_count, 1u);
+    }
+    S.tkey[s] = kEmptyKey;
+    S.tcnt[s] = 0u;
+    S.ts1[s] = 0;
+    S.ts2[s] = 0u;
+    if (discard) continue;
+    const int kx = (int)(k % (uint32_t)gc.X);
+    const uint32_t r = k / (uint32_t)gc.X;
+    const int ky = (int)(r % (uint32_t)gc.Y);
+    const int kz = (int)(r / (uint32_t)gc.Y);
+    mn0 = min(mn0, kx); mn1 = min(mn1, ky); mn2 = min(mn2, kz);
+    mx0 = max(mx0, kx); mx1 = max(mx1, ky); mx2 = max(mx2, kz);
+    const int sB = feature_symbol(gc.feature, gc.Lc, gc.Lv, S.ct, S.vt, n, s1, s2);
+    if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
+        kz <= gc.boxA[5])
+      atomicAdd(&S.hist[(int)__ldg(a.symA + k) * K + sB], 1u);
+    if (a.dump != nullptr && p == 0) {
+      a.dump[3 * (size_t)k] = (int64_t)n;
+      a.dump[3 * (size_t)k + 1] = s1;
+      a.dump[3 * (size_t)k + 2] = (int64_t)s2;
+    }
+  }
+  occupied = __reduce_add_sync(kFull, occupied);
+  if (lane == 0 && occupied) atomicAdd(&S.flags[0], occupied);
+  mn0 = __reduce_min_sync(kFull, mn0); mn1 = __reduce_min_sync(kFull, mn1);
+  mn2 = __reduce_min_sync(kFull, mn2); mx0 = __reduce_max_sync(kFull, mx0);
+  mx1 = __reduce_max_sync(kFull, mx1); mx2 = __reduce_max_sync(kFull, mx2);
+  if (lane == 0 && !discard && mn0 != INT_MAX) {
+    atomicMin(&S.box[0], mn0); atomicMin(&S.box[1], mn1); atomicMin(&S.box[2], mn2);
+    atomicMax(&S.box[3], mx0); atomicMax(&S.box[4], mx1); atomicMax(&S.box[5], mx2);
+  }
+}
+
+__device__ __forceinline__ void init_smem(const EvalSmem& S, const GridConst& gc, int T, int KK) {
+  const int tid = threadIdx.x;
   for (int i = tid; i < T; i += kThreads) {
     S.tkey[i] = kEmptyKey;
     S.tcnt[i] = 0u;
@@ -186,14 +286,56 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
     S.vt[tid] = gc.var_thresh[tid];
   }
   if (tid == 0) {
+    S.box[0] = S.box[1] = S.box[2] = INT_MAX;
+    S.box[3] = S.box[4] = S.box[5] = INT_MIN;
+    S.flags[0] = S.flags[1] = S.flags[2] = S.flags[3] = 0u;
+  }
+}
+
+// Store the pose's partial histogram and bbox, then reset them for the next pose.
+__device__ __forceinline__ void emit_pose(const EvalSmem& S, const EvalArgs& a, int KK, int p) {
+  const int tid = threadIdx.x;
+  uint32_t* oc = a.out_c + (size_t)p * KK;
+  for (int i = tid; i < KK; i += kThreads) {
+    oc[i] = S.hist[i];
+    S.hist[i] = 0u;
+  }
+  if (tid < 6) a.out_box[6 * (size_t)p + tid] = S.box[tid];
+  __syncthreads();
+  if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
+}
+
+__device__ __forceinline__ void reset_pose(const EvalSmem& S, int KK) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < KK; i += kThreads) S.hist[i] = 0u;
+  if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
+}
+
+template <bool kVar, bool kRot>
+__global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, const EvalArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  EvalSmem S;
+  const int T = a.table_slots;
+  const int K = gc.K, KK = K * K;
+  eval_smem_layout(K, T, &S, smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t cap = (uint32_t)T - (uint32_t)T / 4u;  // 75% load factor
+  unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
+  const int G = gridDim.x;
+
+  init_smem(S, gc, T, KK);
+  int passes = a.passes0;
+  if (tid == 0) {
     for (int b = 0; b < kStages; ++b) {
       mbar_init(smem_addr(&S.mbar[b]), 1u);
       mbar_init(smem_addr(&S.mbar[kStages + b]), (uint32_t)kWarps);
       S.issue_cnt[b] = 0u;
     }
-    S.box[0] = S.box[1] = S.box[2] = INT_MAX;
-    S.box[3] = S.box[4] = S.box[5] = INT_MIN;
-    S.flags[0] = S.flags[1] = S.flags[2] = S.flags[3] = 0u;
+    const int p0 = blockIdx.x;
+    S.sched[0] = 0u;
+    S.sched[1] = (uint32_t)passes * (uint32_t)a.n_tiles;
+    S.sched[2] = pose_source(a, p0);
+    S.sched[3] = pose_source(a, p0 + G < a.P ? p0 + G : p0);
     fence_mbar_init();
   }
   __syncthreads();
@@ -201,20 +343,26 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
     for (int b = 0; b < kStages; ++b) issue_tile(S, a, (uint32_t)b);
 
   uint32_t q = 0;  // consumption counter, identical in every warp
-  int passes = a.passes0;
   bool aborted = false;
 
-  for (int p = blockIdx.x; p < a.P && !aborted; p += gridDim.x) {
-    Pose12 P;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) P.r[i] = __ldg(a.poses + 12 * (size_t)p + i);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) P.t[i] = __ldg(a.poses + 12 * (size_t)p + 9 + i);
-
-    int pass = 0;
-    while (pass < passes) {
-      const int lg = __ffs(passes) - 1;
-      // ---- sweep all tiles of B for this pose (and key partition) ----
+  for (int p = blockIdx.x; p < a.P && !aborted; p += G) {
+    if (p != (int)blockIdx.x) {
+      if (tid == 0) {  // the pose's sweeps start at q; every warp is past the previous pose
+        S.sched[0] = q;
+        S.sched[1] = (uint32_t)passes * (uint32_t)a.n_tiles;
+        S.sched[2] = pose_source(a, p);
+        S.sched[3] = pose_source(a, p + G < a.P ? p + G : p);
+      }
+      __syncthreads();
+    }
+    PoseRegs P;
+    load_pose(a, p, P);
+    const int pose_passes = passes;
+    const int lg = __ffs(pose_passes) - 1;
+    uint32_t max_occupied = 0;
+    bool full = false;
+    for (int pass = 0; pass < pose_passes; ++pass) {
+      // ---- sweep all tiles of the pose's source array ----
       for (int t = 0; t < a.n_tiles; ++t, ++q) {
         const uint32_t b = q % kStages;
         const uint32_t par = (q / kStages) & 1u;
@@ -224,28 +372,22 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
           S.flags[2] = 1u;
           continue;
         }
-        const float* tile = S.tiles + (size_t)b * kTile * 3;
-        const int base = t * kTile;
+        if (!full) {
+          uint32_t key[kPPT];
+          int dz[kPPT];
+          tile_keys<kRot>(gc, P, S.tiles + (size_t)b * kTile + tid, lg, (uint32_t)pass, key, dz);
 #pragma unroll
-        for (int j = 0; j < kPPT; ++j) {
-          const int li = j * kThreads + tid;
-          uint32_t key = kEmptyKey;
-          int dz = 0;
-          if (base + li < a.n_points) {
-            key = voxel_key(P, tile[3 * li], tile[3 * li + 1], tile[3 * li + 2], gc.inv_res, gc.X, gc.Y, gc.Z,
-                            gc.res_mm, &dz);
-            if (key != kEmptyKey) {
-              if ((uint32_t)(dz + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound)) atomicOr(a.err, kErrDzBound);
-              if (lg > 0 && ((key * 0x85EBCA77u) >> (32 - lg)) != (uint32_t)pass) key = kEmptyKey;
-            }
+          for (int j = 0; j < kPPT; ++j) {
+            if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
+              atomicOr(a.err, kErrDzBound);
+            commit_row<kVar>(S, gc, wide, key[j], dz[j], lane, T);
           }
-          commit_row<kVar>(S, gc, a, wide, key, dz, lane, T);
         }
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(smem_addr(&S.mbar[kStages + b]));
           const uint32_t c = atomicAdd(&S.issue_cnt[b], 1u);
-          if (c == (uint32_t)kWarps - 1u) {  // last warp done with this buffer refills it
+          if (c == (uint32_t)kWarps - 1u) {  // the last warp done with this buffer refills it
             S.issue_cnt[b] = 0u;
             if (mbar_wait_bounded(smem_addr(&S.mbar[kStages + b]), par, kWaitLimitNs)) {
               issue_tile(S, a, q + kStages);
@@ -261,97 +403,27 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
         aborted = true;
         break;
       }
-      const bool overflow = S.flags[1] != 0u;
-      // ---- read (and clear) the table ----
-      int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX, mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
-      uint32_t occupied = 0;
-      for (int s = tid; s < T; s += kThreads) {
-        const uint32_t k = S.tkey[s];
-        if (k == kEmptyKey) continue;
-        ++occupied;
-        const uint64_t n = S.tcnt[s];
-        int64_t s1 = S.ts1[s];
-        uint64_t s2 = S.ts2[s];
-        if (kVar && n > gc.nlim) {
-          s1 += (int64_t)wide[2 * s];
-          s2 += wide[2 * s + 1];
-          wide[2 * s] = 0ull;
-          wide[2 * s + 1] = 0ull;
-          if (!overflow) atomicAdd(a.wide_count, 1u);
-        }
-        S.tkey[s] = kEmptyKey;
-        S.tcnt[s] = 0u;
-        S.ts1[s] = 0;
-        S.ts2[s] = 0u;
-        if (overflow) continue;
-        const int kx = (int)(k % (uint32_t)gc.X);
-        const uint32_t r = k / (uint32_t)gc.X;
-        const int ky = (int)(r % (uint32_t)gc.Y);
-        const int kz = (int)(r / (uint32_t)gc.Y);
-        mn0 = min(mn0, kx); mn1 = min(mn1, ky); mn2 = min(mn2, kz);
-        mx0 = max(mx0, kx); mx1 = max(mx1, ky); mx2 = max(mx2, kz);
-        const int sB = feature_symbol(gc.feature, gc.Lc, gc.Lv, S.ct, S.vt, n, s1, s2);
-        if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
-            kz <= gc.boxA[5])
-          atomicAdd(&S.hist[(int)__ldg(a.symA + k) * K + sB], 1u);
-        if (a.dump != nullptr && p == 0) {
-          a.dump[3 * (size_t)k] = (int64_t)n;
-          a.dump[3 * (size_t)k + 1] = s1;
-          a.dump[3 * (size_t)k + 2] = (int64_t)s2;
-        }
-      }
-      occupied = __reduce_add_sync(kFull, occupied);
-      if (lane == 0 && occupied) atomicAdd(&S.flags[0], occupied);
-      mn0 = __reduce_min_sync(kFull, mn0); mn1 = __reduce_min_sync(kFull, mn1);
-      mn2 = __reduce_min_sync(kFull, mn2); mx0 = __reduce_max_sync(kFull, mx0);
-      mx1 = __reduce_max_sync(kFull, mx1); mx2 = __reduce_max_sync(kFull, mx2);
-      if (lane == 0 && !overflow && mn0 != INT_MAX) {
-        atomicMin(&S.box[0], mn0); atomicMin(&S.box[1], mn1); atomicMin(&S.box[2], mn2);
-        atomicMax(&S.box[3], mx0); atomicMax(&S.box[4], mx1); atomicMax(&S.box[5], mx2);
-      }
+      full = full || S.flags[1] != 0u;
+      scan_table<kVar>(S, gc, a, wide, T, K, p, full);
       __syncthreads();
-      if (overflow) {
-        // restart this pose with twice as many key partitions
-        for (int i = tid; i < KK; i += kThreads) S.hist[i] = 0u;
-        if (tid == 0) {
-          S.box[0] = S.box[1] = S.box[2] = INT_MAX;
-          S.box[3] = S.box[4] = S.box[5] = INT_MIN;
-          S.flags[0] = 0u;
-          S.flags[1] = 0u;
-        }
-        if (passes >= kMaxPasses) {
-          if (tid == 0) atomicOr(a.err, kErrPassLimit);
-          aborted = true;
-          __syncthreads();
-          break;
-        }
-        passes *= 2;
-        pass = 0;
-        __syncthreads();
-        continue;
-      }
-      // a table filled beyond 3/4 probes slowly: sweep the following poses in more partitions
-      const bool crowded = S.flags[0] > cap;
+      max_occupied = max(max_occupied, S.flags[0]);
       __syncthreads();
       if (tid == 0) S.flags[0] = 0u;
-      if (crowded && passes < kMaxPasses) {
-        passes *= 2;
-        pass = 2 * pass + 2;  // the partitions already swept are split in two; continue after them
-      } else {
-        ++pass;
-      }
-      __syncthreads();
     }
     if (aborted) break;
-    // ---- this pose's partial histogram and B bbox ----
-    uint32_t* oc = a.out_c + (size_t)p * KK;
-    for (int i = tid; i < KK; i += kThreads) {
-      oc[i] = S.hist[i];
-      S.hist[i] = 0u;
+    if (full) {
+      // the remaining sweeps of this pose were consumed without work; finish it later
+      reset_pose(S, KK);
+      if (tid == 0) {
+        S.flags[1] = 0u;
+        a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)p;
+      }
+      if (passes < kMaxPasses) passes *= 2;
+      __syncthreads();
+      continue;
     }
-    if (tid < 6) a.out_box[6 * (size_t)p + tid] = S.box[tid];
-    __syncthreads();
-    if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
+    emit_pose(S, a, KK, p);
+    if (max_occupied > cap && passes < kMaxPasses) passes *= 2;  // crowded: more partitions next
   }
 
   // Drain the prefetched tiles still in flight before the CTA's shared memory is released.
@@ -363,6 +435,94 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
       if (!mbar_wait_bounded(smem_addr(&S.mbar[qq % kStages]), (qq / kStages) & 1u, kWaitLimitNs))
         atomicOr(a.err, kErrWaitTimeout);
     }
+  }
+}
+
+// Poses whose table filled up in eval_kernel: plain loads (no prefetch ring), and on a full
+// table the pose simply restarts with twice the key partitions.
+template <bool kVar, bool kRot>
+__global__ void __launch_bounds__(kThreads, 1) redo_kernel(const GridConst gc, const EvalArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  EvalSmem S;
+  const int T = a.table_slots;
+  const int K = gc.K, KK = K * K;
+  eval_smem_layout(K, T, &S, smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31;
+  unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
+  const uint32_t n_redo = *(volatile const uint32_t*)a.redo_count;
+  if (blockIdx.x >= n_redo) return;
+  init_smem(S, gc, T, KK);
+  __syncthreads();
+  int passes = 2 * (int)*(volatile const uint32_t*)a.max_passes;
+  if (passes < 2) passes = 2;
+  if (passes > kMaxPasses) passes = kMaxPasses;
+  for (uint32_t i = blockIdx.x; i < n_redo; i += gridDim.x) {
+    const int p = (int)a.redo_list[i];
+    PoseRegs P;
+    load_pose(a, p, P);
+    const float4* src = a.src + (size_t)pose_source(a, p) * a.src_stride;
+    int pass = 0;
+    while (pass < passes) {
+      const int lg = __ffs(passes) - 1;
+      for (int t = 0; t < a.n_tiles; ++t) {
+        uint32_t key[kPPT];
+        int dz[kPPT];
+        tile_keys<kRot>(gc, P, src + (size_t)t * kTile + tid, lg, (uint32_t)pass, key, dz);
+#pragma unroll
+        for (int j = 0; j < kPPT; ++j) {
+          if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
+            atomicOr(a.err, kErrDzBound);
+          commit_row<kVar>(S, gc, wide, key[j], dz[j], lane, T);
+        }
+      }
+      __syncthreads();
+      const bool full = S.flags[1] != 0u;
+      scan_table<kVar>(S, gc, a, wide, T, K, p, full);
+      __syncthreads();
+      if (tid == 0) S.flags[0] = 0u;
+      if (full) {
+        reset_pose(S, KK);
+        if (tid == 0) S.flags[1] = 0u;
+        if (passes >= kMaxPasses) {
+          if (tid == 0) atomicOr(a.err, kErrPassLimit);
+          return;
+        }
+        passes *= 2;
+        pass = 0;
+        __syncthreads();
+        continue;
+      }
+      ++pass;
+      __syncthreads();
+    }
+    emit_pose(S, a, KK, p);
+    __syncthreads();
+  }
+  if (tid == 0) atomicMax(a.max_passes, (uint32_t)passes);
+}
+
+// xyz -> float4 tiles (NaN padding), optionally one rotated copy per rotation.
+__global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int64_t n_out,
+                                   const float* __restrict__ rots, float4* out) {
+  const int r = blockIdx.y;
+  const float nan = __int_as_float(0x7fc00000);
+  float R[9];
+  if (rots != nullptr)
+    for (int i = 0; i < 9; ++i) R[i] = rots[9 * r + i];
+  float4* o = out + (size_t)r * n_out;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_out; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 v = make_float4(nan, nan, nan, 0.0f);
+    if (i < n) {
+      const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+      if (rots != nullptr) {
+        rotate_point(R, x, y, z, v.x, v.y, v.z);
+      } else {
+        v.x = x;
+        v.y = y;
+        v.z = z;
+      }
+    }
+    o[i] = v;
   }
 }
 
@@ -463,37 +623,51 @@ __global__ void argmax_finalize_kernel(const unsigned long long* best, int64_t* 
   *out = (b == 0ull) ? -1 : (int64_t)(0xFFFFFFFFu - (uint32_t)(b & 0xFFFFFFFFull));
 }
 
+template <bool kVar, bool kRot>
+cudaError_t launch_eval_t(const GridConst& gc, const EvalArgs& a, int n_ctas, size_t smem, cudaStream_t s) {
+  cudaError_t e =
+      cudaFuncSetAttribute(eval_kernel<kVar, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(redo_kernel<kVar, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  eval_kernel<kVar, kRot><<<n_ctas, kThreads, smem, s>>>(gc, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  redo_kernel<kVar, kRot><<<n_ctas, kThreads, smem, s>>>(gc, a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int eval_tile_points() { return kTile; }
+int eval_min_tiles() { return kStages; }
 
 size_t eval_smem_bytes(int K, int table_slots) { return eval_smem_layout(K, table_slots, nullptr, nullptr); }
 
 int eval_table_slots_for(int K, size_t smem_budget) {
-  // largest multiple of 32 slots that fits the budget
-  int lo = 32, hi = 1 << 16;
-  while (lo < hi) {
-    int mid = ((lo + hi + 1) / 2) & ~31;
-    if (mid <= lo) break;
-    if (eval_smem_bytes(K, mid) <= smem_budget) lo = mid;
-    else hi = mid - 1;
-  }
-  while (eval_smem_bytes(K, lo) > smem_budget && lo > 32) lo -= 32;
+  int lo = 32;
+  while (eval_smem_bytes(K, lo + 32) <= smem_budget && lo < (1 << 16)) lo += 32;
   return lo;
 }
 
-cudaError_t launch_eval(const GridConst& gc, const EvalArgs& a, int n_ctas, cudaStream_t s) {
+cudaError_t launch_eval(const GridConst& gc, const EvalArgs& a, int n_ctas, bool rotate, cudaStream_t s) {
   const size_t smem = eval_smem_bytes(gc.K, a.table_slots);
-  cudaError_t e;
-  if (gc.feature == 0 && a.dump == nullptr) {  // the count feature needs no z sums
-    e = cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    eval_kernel<false><<<n_ctas, kThreads, smem, s>>>(gc, a);
-  } else {
-    e = cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    eval_kernel<true><<<n_ctas, kThreads, smem, s>>>(gc, a);
-  }
+  const bool var = !(gc.feature == 0 && a.dump == nullptr);  // the count feature needs no z sums
+  if (var)
+    return rotate ? launch_eval_t<true, true>(gc, a, n_ctas, smem, s)
+                  : launch_eval_t<true, false>(gc, a, n_ctas, smem, s);
+  return rotate ? launch_eval_t<false, true>(gc, a, n_ctas, smem, s)
+                : launch_eval_t<false, false>(gc, a, n_ctas, smem, s);
+}
+
+cudaError_t launch_pack_points(const float* xyz, int64_t n, int64_t n_out, const float* rots, int n_rot, float4* out,
+                               cudaStream_t s) {
+  const int threads = 256;
+  int64_t bx = (n_out + threads - 1) / threads;
+  if (bx > 2048) bx = 2048;
+  if (bx < 1) bx = 1;
+  dim3 grid((unsigned)bx, (unsigned)(rots != nullptr && n_rot > 0 ? n_rot : 1));
+  pack_points_kernel<<<grid, threads, 0, s>>>(xyz, n, n_out, rots, out);
   return cudaGetLastError();
 }
 

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "align.h"
@@ -85,6 +86,8 @@ struct align_grid {
   DevBuf symA, sat;
   // evaluation workspace
   DevBuf xyz, poses, out_c, out_box, mi, hist, best, argmax, err, max_passes, wide_count, wide, dump;
+  DevBuf pts4, pose_src, rots, redo_list, redo_count;
+  int64_t n_points = 0;  // points staged in `xyz`
   int32_t passes_seed = 1;
   int64_t stats[5] = {0, 0, 0, 0, 0};
   // event timing (align_profile): one (before eval, after eval, after argmax) triple per
@@ -229,32 +232,52 @@ align_status check_grid(align_grid* g) {
   return ALIGN_OK;
 }
 
-// Upload (or copy on the device) scan B into the tile-padded point buffer.
+// Stage scan B (n x 3 fp32) in device memory; every evaluation packs it into tiles.
 align_status upload_points(align_grid* g, const float* xyz, int64_t n, int flags, int32_t* n_tiles_out) {
   if (n < 0 || n >= INT32_MAX) return fail(ALIGN_E_INVALID, "point count out of range");
   if (n > 0 && !xyz) return fail(ALIGN_E_INVALID, "xyz is NULL");
   const int tile = eval_tile_points();
-  const int64_t n_tiles = std::max<int64_t>(1, (n + tile - 1) / tile);
-  const size_t bytes = (size_t)n_tiles * tile * 3 * sizeof(float);
-  CU(g->xyz.ensure(bytes), "allocate point buffer");
+  const int64_t n_tiles = std::max<int64_t>(eval_min_tiles(), (n + tile - 1) / tile);
+  CU(g->xyz.ensure(std::max<size_t>(1, (size_t)n) * 3 * sizeof(float)), "allocate point buffer");
   if (n > 0) {
     const cudaMemcpyKind kind = (flags & ALIGN_XYZ_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CU(cudaMemcpyAsync(g->xyz.p, xyz, (size_t)n * 3 * sizeof(float), kind, g->stream), "copy points");
   }
+  g->n_points = n;
   *n_tiles_out = (int32_t)n_tiles;
   return ALIGN_OK;
 }
 
-// Error word and counters: allocated once per grid and zeroed (cudaMalloc memory is not).
-align_status ensure_status_words(align_grid* g) {
-  if (g->err.p && g->max_passes.p && g->wide_count.p) return ALIGN_OK;
-  CU(g->err.ensure(16), "allocate error word");
-  CU(g->max_passes.ensure(16), "allocate counters");
-  CU(g->wide_count.ensure(16), "allocate counters");
-  CU(cudaMemsetAsync(g->err.p, 0, 16, g->stream), "clear error word");
-  CU(cudaMemsetAsync(g->max_passes.p, 0, 16, g->stream), "clear counters");
-  CU(cudaMemsetAsync(g->wide_count.p, 0, 16, g->stream), "clear counters");
-  return ALIGN_OK;
+// Distinct rotations of a host pose batch (bitwise equal 3x3 blocks), and each pose's index.
+struct RotKey {
+  uint32_t w[9];
+  bool operator==(const RotKey& o) const { return std::memcmp(w, o.w, sizeof(w)) == 0; }
+};
+struct RotHash {
+  size_t operator()(const RotKey& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (uint32_t v : k.w) h = (h ^ v) * 1099511628211ull;
+    return (size_t)h;
+  }
+};
+
+int group_rotations(const float* poses12, int64_t P, std::vector<float>& rots, std::vector<int32_t>& idx,
+                    int max_groups) {
+  std::unordered_map<RotKey, int32_t, RotHash> seen;
+  rots.clear();
+  idx.resize((size_t)P);
+  for (int64_t p = 0; p < P; ++p) {
+    RotKey k;
+    std::memcpy(k.w, poses12 + 12 * p, sizeof(k.w));
+    auto it = seen.find(k);
+    if (it == seen.end()) {
+      if ((int)seen.size() >= max_groups) return -1;
+      it = seen.emplace(k, (int32_t)seen.size()).first;
+      rots.insert(rots.end(), poses12 + 12 * p, poses12 + 12 * p + 9);
+    }
+    idx[(size_t)p] = it->second;
+  }
+  return (int)seen.size();
 }
 
 struct EvalOut {
@@ -264,8 +287,9 @@ struct EvalOut {
   int64_t* dump;      // device or null
 };
 
-// Enqueue the eval + compose + argmax kernels for poses already on the device.
-align_status enqueue_eval(align_grid* g, int32_t n_points, int32_t n_tiles, const float* d_poses, int64_t P,
+// Enqueue pack + eval + redo + compose + argmax for poses already on the device.
+// h_poses (may be NULL): the same poses on the host, used to find shared rotations.
+align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, const float* h_poses, int64_t P,
                           const EvalOut& out) {
   const int K = g->gc.K;
   const size_t KK = (size_t)K * K;
@@ -281,10 +305,42 @@ align_status enqueue_eval(align_grid* g, int32_t n_points, int32_t n_tiles, cons
     CU(cudaMemsetAsync(g->wide.p, 0, g->wide.cap, g->stream), "clear wide sums");
   }
   CU(cudaMemsetAsync(g->best.p, 0, sizeof(unsigned long long), g->stream), "reset argmax");
+  CU(g->redo_list.ensure((size_t)P * 4), "allocate redo list");
+  CU(g->redo_count.ensure(16), "allocate redo count");
+  CU(cudaMemsetAsync(g->redo_count.p, 0, 4, g->stream), "reset redo count");
+
+  // Pack B into float4 tiles; when many poses share a rotation, one pre-rotated copy per
+  // distinct rotation (the kernel then only translates).
+  const int64_t n_pad = (int64_t)n_tiles * eval_tile_points();
+  bool rotate = true;
+  int n_rot = 0;
+  if (h_poses != nullptr) {
+    const int max_groups = (int)std::max<int64_t>(1, P / 4);
+    const size_t budget = (size_t)512 << 20;
+    const int cap_mem = (int)std::max<int64_t>(0, (int64_t)(budget / ((size_t)n_pad * 16)));
+    std::vector<float> rots;
+    std::vector<int32_t> idx;
+    const int groups = group_rotations(h_poses, P, rots, idx, std::min(max_groups, cap_mem));
+    if (groups > 0) {
+      CU(g->rots.ensure(rots.size() * 4), "allocate rotations");
+      CU(cudaMemcpyAsync(g->rots.p, rots.data(), rots.size() * 4, cudaMemcpyHostToDevice, g->stream),
+         "copy rotations");
+      CU(g->pose_src.ensure((size_t)P * 4), "allocate pose sources");
+      CU(cudaMemcpyAsync(g->pose_src.p, idx.data(), (size_t)P * 4, cudaMemcpyHostToDevice, g->stream),
+         "copy pose sources");
+      rotate = false;
+      n_rot = groups;
+    }
+  }
+  CU(g->pts4.ensure((size_t)std::max(n_rot, 1) * (size_t)n_pad * 16), "allocate tiles");
+  CU(launch_pack_points(g->xyz.as<float>(), g->n_points, n_pad, rotate ? nullptr : g->rots.as<float>(), n_rot,
+                        g->pts4.as<float4>(), g->stream),
+     "launch pack");
 
   EvalArgs a{};
-  a.xyz = g->xyz.as<float>();
-  a.n_points = n_points;
+  a.src = g->pts4.as<float4>();
+  a.src_stride = (size_t)n_pad;
+  a.pose_src = rotate ? nullptr : g->pose_src.as<int32_t>();
   a.n_tiles = n_tiles;
   a.poses = d_poses;
   a.P = (int32_t)P;
@@ -295,6 +351,8 @@ align_status enqueue_eval(align_grid* g, int32_t n_points, int32_t n_tiles, cons
   a.max_passes = g->max_passes.as<uint32_t>();
   a.wide_count = g->wide_count.as<uint32_t>();
   a.wide = g->wide.as<unsigned long long>();
+  a.redo_list = g->redo_list.as<uint32_t>();
+  a.redo_count = g->redo_count.as<uint32_t>();
   a.table_slots = g->table_slots;
   a.passes0 = g->passes_seed;
   a.dump = out.dump;
@@ -308,7 +366,7 @@ align_status enqueue_eval(align_grid* g, int32_t n_points, int32_t n_tiles, cons
     }
     CU(cudaEventRecord(evs[0], g->stream), "record event");
   }
-  CU(launch_eval(g->gc, a, n_ctas, g->stream), "launch eval kernel");
+  CU(launch_eval(g->gc, a, n_ctas, rotate, g->stream), "launch eval kernel");
   if (g->profiling) CU(cudaEventRecord(evs[1], g->stream), "record event");
 
   ComposeArgs c{};
@@ -327,7 +385,7 @@ align_status enqueue_eval(align_grid* g, int32_t n_points, int32_t n_tiles, cons
   }
   g->stats[2] = g->table_slots;
   g->stats[3] = n_ctas;
-  g->stats[4] += 3;
+  g->stats[4] += 5;  // pack, eval, redo, compose, argmax
   return ALIGN_OK;
 }
 
@@ -416,7 +474,8 @@ align_status align_destroy_grid(align_grid* g) {
   cudaSetDevice(g->device);
   cudaStreamSynchronize(g->stream);
   for (DevBuf* b : {&g->symA, &g->sat, &g->xyz, &g->poses, &g->out_c, &g->out_box, &g->mi, &g->hist, &g->best,
-                    &g->argmax, &g->err, &g->max_passes, &g->wide_count, &g->wide, &g->dump})
+                    &g->argmax, &g->err, &g->max_passes, &g->wide_count, &g->wide, &g->dump, &g->pts4,
+                    &g->pose_src, &g->rots, &g->redo_list, &g->redo_count})
     b->release();
   for (auto* v : {&g->ev_pending, &g->ev_pool})
     for (auto& evs : *v)
@@ -530,20 +589,23 @@ static align_status eval_common(align_grid* g, const float* xyzB, int64_t nB, in
     align_status st = upload_points(g, xyzB, nB, flags, &n_tiles);
     if (st != ALIGN_OK) return st;
   }
-  // poses -> device fp32
+  // poses -> device fp32 (and a host copy, to find shared rotations)
   const float* d_poses = nullptr;
+  const float* h_poses = nullptr;
+  std::vector<float> tmp;
   if (poses12 && (flags & ALIGN_POSES_DEVICE)) {
     d_poses = poses12;
   } else {
     CU(g->poses.ensure((size_t)P * 12 * sizeof(float)), "allocate poses");
     if (poses12) {
-      CU(cudaMemcpyAsync(g->poses.p, poses12, (size_t)P * 48, cudaMemcpyHostToDevice, g->stream), "copy poses");
+      h_poses = poses12;
     } else {
-      std::vector<float> tmp((size_t)P * 12);
+      tmp.resize((size_t)P * 12);
       for (int64_t p = 0; p < P; ++p) pose_to_fp32(g->origin, eta6 + 6 * p, &tmp[(size_t)p * 12]);
-      // a pageable source is staged before the call returns, so tmp may go away
-      CU(cudaMemcpyAsync(g->poses.p, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice, g->stream), "copy poses");
+      h_poses = tmp.data();
     }
+    // a pageable source is staged before the call returns
+    CU(cudaMemcpyAsync(g->poses.p, h_poses, (size_t)P * 48, cudaMemcpyHostToDevice, g->stream), "copy poses");
     d_poses = g->poses.as<float>();
   }
   const size_t KK = (size_t)g->gc.K * g->gc.K;
@@ -568,7 +630,7 @@ static align_status eval_common(align_grid* g, const float* xyzB, int64_t nB, in
     }
   }
   o.dump = dump_dev;
-  align_status st = enqueue_eval(g, (int32_t)nB, n_tiles, d_poses, P, o);
+  align_status st = enqueue_eval(g, n_tiles, d_poses, h_poses, P, o);
   if (st != ALIGN_OK) return st;
   if (out_dev) return ALIGN_OK;
   if (mi_out) CU(cudaMemcpyAsync(mi_out, o.mi, (size_t)P * 4, cudaMemcpyDeviceToHost, g->stream), "read MI");
