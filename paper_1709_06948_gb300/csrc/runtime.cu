@@ -280,6 +280,18 @@ int group_rotations(const float* poses12, int64_t P, std::vector<float>& rots, s
   return (int)seen.size();
 }
 
+// Error word and counters: allocated once per grid and zeroed (cudaMalloc memory is not).
+align_status ensure_status_words(align_grid* g) {
+  if (g->err.p && g->max_passes.p && g->wide_count.p) return ALIGN_OK;
+  CU(g->err.ensure(16), "allocate error word");
+  CU(g->max_passes.ensure(16), "allocate counters");
+  CU(g->wide_count.ensure(16), "allocate counters");
+  CU(cudaMemsetAsync(g->err.p, 0, 16, g->stream), "clear error word");
+  CU(cudaMemsetAsync(g->max_passes.p, 0, 16, g->stream), "clear counters");
+  CU(cudaMemsetAsync(g->wide_count.p, 0, 16, g->stream), "clear counters");
+  return ALIGN_OK;
+}
+
 struct EvalOut {
   float* mi;          // device
   uint32_t* hist;     // device or null
