@@ -121,32 +121,46 @@ __device__ __forceinline__ void issue_tile(const EvalSmem& S, const EvalArgs& a,
                 kTileBytes, full);
 }
 
-// Find or insert `key` in the open-addressing table (linear probing, at most T probes).
-// Returns -1 when the table is full.
+// Find or insert `key` in the open-addressing table: buckets of 4 key slots read with one
+// 16-byte load, probed linearly; slots of a bucket fill in order, so a bucket with a free
+// slot ends the search.  Returns -1 when the probe budget is spent (table full).
 __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T) {
-  uint32_t h = __umulhi(key * 0x9E3779B1u, (uint32_t)T);
-  volatile uint32_t* vkey = S.tkey;
-  for (int i = 0; i < T; ++i) {
-    const uint32_t k = vkey[h];
-    if (k == key) return (int)h;
-    if (k == kEmptyKey) {
-      const uint32_t old = atomicCAS(&S.tkey[h], kEmptyKey, key);
-      if (old == kEmptyKey || old == key) return (int)h;
+  const uint32_t nb = (uint32_t)T >> 2;
+  uint32_t b = __umulhi(key * 0x9E3779B1u, nb);
+  for (uint32_t i = 0; i < nb + 4; ++i) {
+    uint4 k4;
+    asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(k4.x), "=r"(k4.y), "=r"(k4.z), "=r"(k4.w)
+                 : "r"(smem_addr(S.tkey + 4 * b)));
+    if (k4.x == key) return (int)(4 * b);
+    if (k4.y == key) return (int)(4 * b + 1);
+    if (k4.z == key) return (int)(4 * b + 2);
+    if (k4.w == key) return (int)(4 * b + 3);
+    const int e = (k4.x == kEmptyKey) ? 0 : (k4.y == kEmptyKey) ? 1 : (k4.z == kEmptyKey) ? 2 : (k4.w == kEmptyKey) ? 3 : -1;
+    if (e >= 0) {
+      const uint32_t old = atomicCAS(&S.tkey[4 * b + e], kEmptyKey, key);
+      if (old == kEmptyKey || old == key) return (int)(4 * b + e);
+      continue;  // another lane took that slot: read the bucket again
     }
-    h = (h + 1 == (uint32_t)T) ? 0u : h + 1;
+    b = (b + 1 == nb) ? 0u : b + 1;
   }
   return -1;
 }
 
 // One warp row of 32 consecutive points.  Lanes with equal adjacent keys form a run; the
 // run's sums come from one warp reduction per quantity over the run's lane mask, and the
-// run's last lane adds them to the table.
+// run's last lane adds them to the table.  (prev_key, prev_slot): the key and slot of the
+// previous row's last run, so a run that continues across rows needs no probe.
 template <bool kVar>
 __device__ __forceinline__ void commit_row(const EvalSmem& S, const GridConst& gc, unsigned long long* wide,
-                                           uint32_t key, int dz, int lane, int T) {
-  if (__ballot_sync(kFull, key != kEmptyKey) == 0u) return;
-  const uint32_t prev = __shfl_up_sync(kFull, key, 1);
-  const uint32_t heads = __ballot_sync(kFull, (lane == 0) || (key != prev));
+                                           uint32_t key, int dz, int lane, int T, uint32_t& prev_key,
+                                           int& prev_slot) {
+  if (__ballot_sync(kFull, key != kEmptyKey) == 0u) {
+    prev_key = kEmptyKey;
+    return;
+  }
+  const uint32_t up = __shfl_up_sync(kFull, key, 1);
+  const uint32_t heads = __ballot_sync(kFull, (lane == 0) || (key != up));
   const uint32_t upto = kFull >> (31 - lane);  // lanes 0..lane
   const int first = 31 - __clz(heads & upto);
   const uint32_t later = heads & ~upto;
@@ -158,27 +172,31 @@ __device__ __forceinline__ void commit_row(const EvalSmem& S, const GridConst& g
     s1 = __reduce_add_sync(run, dz);
     s2 = __reduce_add_sync(run, (uint32_t)(dz * dz));
   }
-  if (lane != last || key == kEmptyKey) return;
-  if (*(volatile uint32_t*)&S.flags[1]) return;  // table already full: the pose is redone
-  const int slot = table_slot(S, key, T);
-  if (slot < 0) {
-    S.flags[1] = 1u;
-    return;
-  }
-  const uint32_t n = (uint32_t)(last - first + 1);
-  if (kVar) {
-    const uint32_t old = atomicAdd(&S.tcnt[slot], n);
-    if (old + n <= gc.nlim) {
-      atomicAdd(&S.ts1[slot], s1);
-      atomicAdd(&S.ts2[slot], s2);
+  int slot = -1;
+  const bool tail = (lane == last) && key != kEmptyKey && !*(volatile uint32_t*)&S.flags[1];
+  if (tail) {
+    slot = (first == 0 && key == prev_key) ? prev_slot : table_slot(S, key, T);
+    if (slot < 0) {
+      S.flags[1] = 1u;  // table full: the pose is redone with more key partitions
     } else {
-      atomicAdd(&wide[2 * slot], (unsigned long long)(long long)s1);
-      atomicAdd(&wide[2 * slot + 1], (unsigned long long)s2);
-      S.flags[3] = 1u;
+      const uint32_t n = (uint32_t)(last - first + 1);
+      if (kVar) {
+        const uint32_t old = atomicAdd(&S.tcnt[slot], n);
+        if (old + n <= gc.nlim) {
+          atomicAdd(&S.ts1[slot], s1);
+          atomicAdd(&S.ts2[slot], s2);
+        } else {
+          atomicAdd(&wide[2 * slot], (unsigned long long)(long long)s1);
+          atomicAdd(&wide[2 * slot + 1], (unsigned long long)s2);
+          S.flags[3] = 1u;
+        }
+      } else {
+        atomicAdd(&S.tcnt[slot], n);
+      }
     }
-  } else {
-    atomicAdd(&S.tcnt[slot], n);
   }
+  prev_key = __shfl_sync(kFull, key, 31);
+  prev_slot = __shfl_sync(kFull, slot, 31);
 }
 
 struct PoseRegs {
@@ -187,12 +205,13 @@ struct PoseRegs {
 };
 
 // Keys of this thread's points of one tile under the pose (key partition `part` of 2^lg).
+// `pts` points at this warp's chunk of kPPT * 32 consecutive points plus the lane.
 template <bool kRot>
 __device__ __forceinline__ void tile_keys(const GridConst& gc, const PoseRegs& P, const float4* pts, int lg,
                                           uint32_t part, uint32_t* key, int* dz) {
 #pragma unroll
   for (int j = 0; j < kPPT; ++j) {
-    const float4 p = pts[j * kThreads];
+    const float4 p = pts[j * 32];
     float gx, gy, gz;
     if (kRot) {
       float ux, uy, uz;
@@ -319,6 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
   const int K = gc.K, KK = K * K;
   eval_smem_layout(K, T, &S, smem_raw);
   const int tid = threadIdx.x, lane = tid & 31;
+  const int chunk = (tid >> 5) * (kPPT * 32) + lane;   // warp-contiguous points of a tile
   const uint32_t cap = (uint32_t)T - (uint32_t)T / 4u;  // 75% load factor
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
   const int G = gridDim.x;
@@ -375,12 +395,14 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
         if (!full) {
           uint32_t key[kPPT];
           int dz[kPPT];
-          tile_keys<kRot>(gc, P, S.tiles + (size_t)b * kTile + tid, lg, (uint32_t)pass, key, dz);
+          tile_keys<kRot>(gc, P, S.tiles + (size_t)b * kTile + chunk, lg, (uint32_t)pass, key, dz);
+          uint32_t prev_key = kEmptyKey;
+          int prev_slot = -1;
 #pragma unroll
           for (int j = 0; j < kPPT; ++j) {
             if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
               atomicOr(a.err, kErrDzBound);
-            commit_row<kVar>(S, gc, wide, key[j], dz[j], lane, T);
+            commit_row<kVar>(S, gc, wide, key[j], dz[j], lane, T, prev_key, prev_slot);
           }
         }
         __syncwarp();
@@ -448,6 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1) redo_kernel(const GridConst gc, c
   const int K = gc.K, KK = K * K;
   eval_smem_layout(K, T, &S, smem_raw);
   const int tid = threadIdx.x, lane = tid & 31;
+  const int chunk = (tid >> 5) * (kPPT * 32) + lane;
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
   const uint32_t n_redo = *(volatile const uint32_t*)a.redo_count;
   if (blockIdx.x >= n_redo) return;
@@ -467,12 +490,14 @@ __global__ void __launch_bounds__(kThreads, 1) redo_kernel(const GridConst gc, c
       for (int t = 0; t < a.n_tiles; ++t) {
         uint32_t key[kPPT];
         int dz[kPPT];
-        tile_keys<kRot>(gc, P, src + (size_t)t * kTile + tid, lg, (uint32_t)pass, key, dz);
+        tile_keys<kRot>(gc, P, src + (size_t)t * kTile + chunk, lg, (uint32_t)pass, key, dz);
+        uint32_t prev_key = kEmptyKey;
+        int prev_slot = -1;
 #pragma unroll
         for (int j = 0; j < kPPT; ++j) {
           if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
             atomicOr(a.err, kErrDzBound);
-          commit_row<kVar>(S, gc, wide, key[j], dz[j], lane, T);
+          commit_row<kVar>(S, gc, wide, key[j], dz[j], lane, T, prev_key, prev_slot);
         }
       }
       __syncthreads();
