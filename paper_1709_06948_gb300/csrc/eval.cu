@@ -3,17 +3,20 @@
 //
 // pack_points_kernel: scan B as float4 tiles (NaN padding), either raw xyz or one
 // pre-rotated copy u = R p per distinct rotation of the batch (a search lattice has 32
-// rotations for 4,096 poses, so the 9-FMA rotation leaves the per-pose loop).
+// rotations for 4,096 poses, so the 9-FMA rotation leaves the per-pose loop).  The tiles
+// are laid out as kThreads streams: thread s of a CTA reads, tile after tile, the points
+// s*L, s*L+1, ... of B's given order (L = kPPT * tiles), so each thread walks a stretch
+// of consecutive scan points.
 //
 // eval_kernel: persistent, one CTA per SM, one pose at a time per CTA.  The tiles of the
 // pose's source array arrive by 1-D bulk (TMA) copies on a cyclic mbarrier ring whose
 // schedule already knows the CTA's next pose, so the copies never stall at pose
-// boundaries.  Per point and pose: voxel key and dz (device_common.cuh); runs of equal
-// keys among 32 consecutive points are summed with one warp reduction per quantity over
-// the run's lane mask; the run's last lane adds (n, S1, S2) into a shared-memory
-// open-addressing hash table with 32-bit shared atomics.  After the sweep one pass over
-// the table gives the feature symbols, B's occupied bbox and the partial joint histogram
-// c[a][b >= 1] of the occupied voxels inside A's bbox.
+// boundaries.  Per point and pose: voxel key and dz (device_common.cuh).  Each thread
+// keeps the run of equal keys it is walking in registers (n, S1, S2); when the key
+// changes, the finished run is added into a shared-memory open-addressing hash table
+// with 32-bit shared atomics.  After the sweep one pass over the table gives the feature
+// symbols, B's occupied bbox and the partial joint histogram c[a][b >= 1] of the occupied
+// voxels inside A's bbox.
 //  - A pose with more occupied voxels than fit the table is handed to redo_kernel (which
 //    splits the keys into 2, 4, ... hash partitions, one sweep each); a crowded table
 //    makes the CTA sweep its following poses in twice as many partitions.
@@ -147,56 +150,58 @@ __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T
   return -1;
 }
 
-// One warp row of 32 consecutive points.  Lanes with equal adjacent keys form a run; the
-// run's sums come from one warp reduction per quantity over the run's lane mask, and the
-// run's last lane adds them to the table.  (prev_key, prev_slot): the key and slot of the
-// previous row's last run, so a run that continues across rows needs no probe.
+// Add one finished run (n points of one voxel, sums s1, s2) to the table.
 template <bool kVar>
-__device__ __forceinline__ void commit_row(const EvalSmem& S, const GridConst& gc, unsigned long long* wide,
-                                           uint32_t key, int dz, int lane, int T, uint32_t& prev_key,
-                                           int& prev_slot) {
-  if (__ballot_sync(kFull, key != kEmptyKey) == 0u) {
-    prev_key = kEmptyKey;
+__device__ __forceinline__ void add_run(const EvalSmem& S, const GridConst& gc, unsigned long long* wide, uint32_t key,
+                                        uint32_t n, int s1, uint32_t s2, int T) {
+  if (*(volatile uint32_t*)&S.flags[1]) return;  // table already full: the pose is redone
+  const int slot = table_slot(S, key, T);
+  if (slot < 0) {
+    S.flags[1] = 1u;
     return;
   }
-  const uint32_t up = __shfl_up_sync(kFull, key, 1);
-  const uint32_t heads = __ballot_sync(kFull, (lane == 0) || (key != up));
-  const uint32_t upto = kFull >> (31 - lane);  // lanes 0..lane
-  const int first = 31 - __clz(heads & upto);
-  const uint32_t later = heads & ~upto;
-  const int last = later ? (__ffs(later) - 2) : 31;
-  const uint32_t run = (kFull >> (31 - last)) & (kFull << first);
-  int s1 = 0;
-  uint32_t s2 = 0;
   if (kVar) {
-    s1 = __reduce_add_sync(run, dz);
-    s2 = __reduce_add_sync(run, (uint32_t)(dz * dz));
-  }
-  int slot = -1;
-  const bool tail = (lane == last) && key != kEmptyKey && !*(volatile uint32_t*)&S.flags[1];
-  if (tail) {
-    slot = (first == 0 && key == prev_key) ? prev_slot : table_slot(S, key, T);
-    if (slot < 0) {
-      S.flags[1] = 1u;  // table full: the pose is redone with more key partitions
+    const uint32_t old = atomicAdd(&S.tcnt[slot], n);
+    if (old + n <= gc.nlim) {
+      atomicAdd(&S.ts1[slot], s1);
+      atomicAdd(&S.ts2[slot], s2);
     } else {
-      const uint32_t n = (uint32_t)(last - first + 1);
-      if (kVar) {
-        const uint32_t old = atomicAdd(&S.tcnt[slot], n);
-        if (old + n <= gc.nlim) {
-          atomicAdd(&S.ts1[slot], s1);
-          atomicAdd(&S.ts2[slot], s2);
-        } else {
-          atomicAdd(&wide[2 * slot], (unsigned long long)(long long)s1);
-          atomicAdd(&wide[2 * slot + 1], (unsigned long long)s2);
-          S.flags[3] = 1u;
-        }
-      } else {
-        atomicAdd(&S.tcnt[slot], n);
-      }
+      atomicAdd(&wide[2 * slot], (unsigned long long)(long long)s1);
+      atomicAdd(&wide[2 * slot + 1], (unsigned long long)s2);
+      S.flags[3] = 1u;
     }
+  } else {
+    atomicAdd(&S.tcnt[slot], n);
   }
-  prev_key = __shfl_sync(kFull, key, 31);
-  prev_slot = __shfl_sync(kFull, slot, 31);
+}
+
+// The run of equal keys a thread is walking.  Keys outside the current partition (and
+// points outside the grid) are skipped without ending the run.
+struct Run {
+  uint32_t key;
+  uint32_t n;
+  int s1;
+  uint32_t s2;
+};
+
+template <bool kVar>
+__device__ __forceinline__ void step_run(const EvalSmem& S, const GridConst& gc, unsigned long long* wide, Run& r,
+                                         uint32_t key, int dz, int T) {
+  if (key == kEmptyKey) return;
+  // a run stays below nlim points so that its 32-bit sums cannot overflow
+  if (key == r.key && (!kVar || r.n < gc.nlim)) {
+    r.n += 1u;
+    if (kVar) {
+      r.s1 += dz;
+      r.s2 += (uint32_t)(dz * dz);
+    }
+    return;
+  }
+  if (r.n != 0u) add_run<kVar>(S, gc, wide, r.key, r.n, r.s1, r.s2, T);
+  r.key = key;
+  r.n = 1u;
+  r.s1 = dz;
+  r.s2 = (uint32_t)(dz * dz);
 }
 
 struct PoseRegs {
@@ -205,13 +210,13 @@ struct PoseRegs {
 };
 
 // Keys of this thread's points of one tile under the pose (key partition `part` of 2^lg).
-// `pts` points at this warp's chunk of kPPT * 32 consecutive points plus the lane.
+// `pts` points at the tile plus the thread index; the thread's points are kThreads apart.
 template <bool kRot>
 __device__ __forceinline__ void tile_keys(const GridConst& gc, const PoseRegs& P, const float4* pts, int lg,
                                           uint32_t part, uint32_t* key, int* dz) {
 #pragma unroll
   for (int j = 0; j < kPPT; ++j) {
-    const float4 p = pts[j * 32];
+    const float4 p = pts[j * kThreads];
     float gx, gy, gz;
     if (kRot) {
       float ux, uy, uz;
@@ -338,7 +343,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
   const int K = gc.K, KK = K * K;
   eval_smem_layout(K, T, &S, smem_raw);
   const int tid = threadIdx.x, lane = tid & 31;
-  const int chunk = (tid >> 5) * (kPPT * 32) + lane;   // warp-contiguous points of a tile
   const uint32_t cap = (uint32_t)T - (uint32_t)T / 4u;  // 75% load factor
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
   const int G = gridDim.x;
@@ -382,6 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
     uint32_t max_occupied = 0;
     bool full = false;
     for (int pass = 0; pass < pose_passes; ++pass) {
+      Run run{kEmptyKey, 0u, 0, 0u};
       // ---- sweep all tiles of the pose's source array ----
       for (int t = 0; t < a.n_tiles; ++t, ++q) {
         const uint32_t b = q % kStages;
@@ -395,14 +400,12 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
         if (!full) {
           uint32_t key[kPPT];
           int dz[kPPT];
-          tile_keys<kRot>(gc, P, S.tiles + (size_t)b * kTile + chunk, lg, (uint32_t)pass, key, dz);
-          uint32_t prev_key = kEmptyKey;
-          int prev_slot = -1;
+          tile_keys<kRot>(gc, P, S.tiles + (size_t)b * kTile + tid, lg, (uint32_t)pass, key, dz);
 #pragma unroll
           for (int j = 0; j < kPPT; ++j) {
             if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
               atomicOr(a.err, kErrDzBound);
-            commit_row<kVar>(S, gc, wide, key[j], dz[j], lane, T, prev_key, prev_slot);
+            step_run<kVar>(S, gc, wide, run, key[j], dz[j], T);
           }
         }
         __syncwarp();
@@ -420,6 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
           }
         }
       }
+      if (run.n != 0u && !full) add_run<kVar>(S, gc, wide, run.key, run.n, run.s1, run.s2, T);
       __syncthreads();
       if (S.flags[2]) {
         aborted = true;
@@ -469,8 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1) redo_kernel(const GridConst gc, c
   const int T = a.table_slots;
   const int K = gc.K, KK = K * K;
   eval_smem_layout(K, T, &S, smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int chunk = (tid >> 5) * (kPPT * 32) + lane;
+  const int tid = threadIdx.x;
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
   const uint32_t n_redo = *(volatile const uint32_t*)a.redo_count;
   if (blockIdx.x >= n_redo) return;
@@ -487,19 +490,19 @@ __global__ void __launch_bounds__(kThreads, 1) redo_kernel(const GridConst gc, c
     int pass = 0;
     while (pass < passes) {
       const int lg = __ffs(passes) - 1;
+      Run run{kEmptyKey, 0u, 0, 0u};
       for (int t = 0; t < a.n_tiles; ++t) {
         uint32_t key[kPPT];
         int dz[kPPT];
-        tile_keys<kRot>(gc, P, src + (size_t)t * kTile + chunk, lg, (uint32_t)pass, key, dz);
-        uint32_t prev_key = kEmptyKey;
-        int prev_slot = -1;
+        tile_keys<kRot>(gc, P, src + (size_t)t * kTile + tid, lg, (uint32_t)pass, key, dz);
 #pragma unroll
         for (int j = 0; j < kPPT; ++j) {
           if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
             atomicOr(a.err, kErrDzBound);
-          commit_row<kVar>(S, gc, wide, key[j], dz[j], lane, T, prev_key, prev_slot);
+          step_run<kVar>(S, gc, wide, run, key[j], dz[j], T);
         }
       }
+      if (run.n != 0u) add_run<kVar>(S, gc, wide, run.key, run.n, run.s1, run.s2, T);
       __syncthreads();
       const bool full = S.flags[1] != 0u;
       scan_table<kVar>(S, gc, a, wide, T, K, p, full);
@@ -526,7 +529,9 @@ __global__ void __launch_bounds__(kThreads, 1) redo_kernel(const GridConst gc, c
   if (tid == 0) atomicMax(a.max_passes, (uint32_t)passes);
 }
 
-// xyz -> float4 tiles (NaN padding), optionally one rotated copy per rotation.
+// xyz -> float4 tiles (NaN padding), optionally one rotated copy per rotation.  Tile t,
+// position j*kThreads + s holds point s*L + kPPT*t + j of B (L = kPPT * tiles): stream s
+// visits consecutive points of B, kPPT per tile.
 __global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int64_t n_out,
                                    const float* __restrict__ rots, float4* out) {
   const int r = blockIdx.y;
@@ -535,10 +540,16 @@ __global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int
   if (rots != nullptr)
     for (int i = 0; i < 9; ++i) R[i] = rots[9 * r + i];
   float4* o = out + (size_t)r * n_out;
+  const int64_t L = n_out / kThreads;  // points per stream
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_out; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = i / kTile;
+    const int pos = (int)(i - t * kTile);
+    const int j = pos / kThreads;
+    const int sidx = pos - j * kThreads;
+    const int64_t src = (int64_t)sidx * L + (int64_t)kPPT * t + j;
     float4 v = make_float4(nan, nan, nan, 0.0f);
-    if (i < n) {
-      const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    if (src < n) {
+      const float x = xyz[3 * src], y = xyz[3 * src + 1], z = xyz[3 * src + 2];
       if (rots != nullptr) {
         rotate_point(R, x, y, z, v.x, v.y, v.z);
       } else {
