@@ -41,6 +41,7 @@ constexpr int kPPT = 2;                       // points per thread per tile
 constexpr int kTile = kThreads * kPPT;        // points per tile
 constexpr uint32_t kTileBytes = kTile * 16u;  // float4 per point
 constexpr int kStages = 3;
+constexpr uint32_t kQueue = 64;               // finished runs buffered per warp
 constexpr int kMaxPasses = 1 << 16;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
@@ -48,6 +49,7 @@ __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
 
 struct EvalSmem {
   float4* tiles;
+  uint4* queue;         // per warp: a ring of kQueue finished runs (key, n, S1, S2)
   uint32_t* tkey;
   uint32_t* tcnt;
   int32_t* ts1;
@@ -59,7 +61,7 @@ struct EvalSmem {
   uint32_t* issue_cnt;  // kStages
   uint32_t* sched;      // q_start, n_consume, src_cur, src_next
   int32_t* box;         // 6
-  uint32_t* flags;      // occupied count, table full, abort, wide used
+  uint32_t* flags;      // occupied count, table full, abort, sums need the exact path
 };
 
 __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, uint8_t* base) {
@@ -71,6 +73,7 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, ui
     return o;
   };
   size_t o_tiles = take((size_t)kStages * kTileBytes, 128);
+  size_t o_queue = take((size_t)kWarps * kQueue * 16, 16);
   size_t o_key = take((size_t)T * 4, 16);
   size_t o_cnt = take((size_t)T * 4, 16);
   size_t o_s1 = take((size_t)T * 4, 16);
@@ -85,6 +88,7 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, ui
   size_t o_flags = take(4 * 4, 4);
   if (s) {
     s->tiles = (float4*)(base + o_tiles);
+    s->queue = (uint4*)(base + o_queue);
     s->tkey = (uint32_t*)(base + o_key);
     s->tcnt = (uint32_t*)(base + o_cnt);
     s->ts1 = (int32_t*)(base + o_s1);
@@ -175,6 +179,51 @@ __device__ __forceinline__ void add_run(const EvalSmem& S, const GridConst& gc, 
   }
 }
 
+// Fast path: add a finished run with fire-and-forget 32-bit shared atomics.  A voxel whose
+// count ends above nlim may have wrapped its sums; the table scan sends such a pose to the
+// exact path (redo_kernel).
+template <bool kVar>
+__device__ __forceinline__ void fast_add(const EvalSmem& S, const uint4& e, int T) {
+  if (*(volatile uint32_t*)&S.flags[1]) return;
+  const int slot = table_slot(S, e.x, T);
+  if (slot < 0) {
+    S.flags[1] = 1u;
+    return;
+  }
+  atomicAdd(&S.tcnt[slot], e.y);
+  if (kVar) {
+    atomicAdd(&S.ts1[slot], (int)e.z);
+    atomicAdd(&S.ts2[slot], e.w);
+  }
+}
+
+// Per-warp ring of finished runs: lanes append what they finished at this step; once 32
+// are waiting, the whole warp adds 32 of them to the table at once.
+struct WarpQueue {
+  uint32_t head;
+  uint32_t fill;
+};
+
+template <bool kVar>
+__device__ __forceinline__ void queue_drain(const EvalSmem& S, uint4* ring, WarpQueue& wq, int lane, int T,
+                                            uint32_t count) {
+  __syncwarp();
+  if ((uint32_t)lane < count) fast_add<kVar>(S, ring[(wq.head + (uint32_t)lane) & (kQueue - 1)], T);
+  __syncwarp();
+  wq.head = (wq.head + count) & (kQueue - 1);
+  wq.fill -= count;
+}
+
+template <bool kVar>
+__device__ __forceinline__ void queue_push(const EvalSmem& S, uint4* ring, WarpQueue& wq, int lane, bool has,
+                                           const uint4& e, int T) {
+  const uint32_t m = __ballot_sync(kFull, has);
+  if (m == 0u) return;
+  if (has) ring[(wq.head + wq.fill + (uint32_t)__popc(m & ((1u << lane) - 1u))) & (kQueue - 1)] = e;
+  wq.fill += (uint32_t)__popc(m);
+  if (wq.fill >= 32u) queue_drain<kVar>(S, ring, wq, lane, T, 32u);
+}
+
 // The run of equal keys a thread is walking.  Keys outside the current partition (and
 // points outside the grid) are skipped without ending the run.
 struct Run {
@@ -184,6 +233,30 @@ struct Run {
   uint32_t s2;
 };
 
+// Advance a run by one point; returns true (and the finished run in `fin`) when the key
+// changes.  A run stays below nlim points so that its 32-bit sums cannot overflow.
+template <bool kVar>
+__device__ __forceinline__ bool advance_run(const GridConst& gc, Run& r, uint32_t key, int dz, uint4& fin) {
+  if (key == kEmptyKey) return false;
+  if (key == r.key && (!kVar || r.n < gc.nlim)) {
+    r.n += 1u;
+    if (kVar) {
+      r.s1 += dz;
+      r.s2 += (uint32_t)(dz * dz);
+    }
+    return false;
+  }
+  const bool done = r.n != 0u;
+  fin = make_uint4(r.key, r.n, (uint32_t)r.s1, r.s2);
+  r.key = key;
+  r.n = 1u;
+  r.s1 = dz;
+  r.s2 = (uint32_t)(dz * dz);
+  return done;
+}
+
+// Exact path (redo_kernel): the run goes straight to the table, with 64-bit side sums
+// for voxels beyond nlim points.
 template <bool kVar>
 __device__ __forceinline__ void step_run(const EvalSmem& S, const GridConst& gc, unsigned long long* wide, Run& r,
                                          uint32_t key, int dz, int T) {
@@ -244,7 +317,7 @@ __device__ __forceinline__ void load_pose(const EvalArgs& a, int p, PoseRegs& P)
 
 // Read (and clear) the table after a sweep: symbols, bbox and histogram unless `discard`.
 // The CTA-wide occupied count is added to S.flags[0].
-template <bool kVar>
+template <bool kVar, bool kExact>
 __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& gc, const EvalArgs& a,
                                            unsigned long long* wide, int T, int K, int p, bool discard) {
   const int tid = threadIdx.x, lane = tid & 31;
@@ -257,7 +330,8 @@ __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& g
     const uint64_t n = S.tcnt[s];
     int64_t s1 = S.ts1[s];
     uint64_t s2 = S.ts2[s];
-    if (kVar && n > gc.nlim) {
+    if (!kExact && kVar && n > gc.nlim) S.flags[3] = 1u;  // sums may have wrapped: exact path
+    if (kExact && kVar && n > gc.nlim) {
       s1 += (int64_t)wide[2 * s];
       s2 += wide[2 * s + 1];
       wide[2 * s] = 0ull;
@@ -343,7 +417,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
   const int K = gc.K, KK = K * K;
   eval_smem_layout(K, T, &S, smem_raw);
   const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t cap = (uint32_t)T - (uint32_t)T / 4u;  // 75% load factor
+  const uint32_t cap = (uint32_t)T - (uint32_t)T / 10u;  // above 90% full the table counts as crowded
+  uint4* ring = S.queue + (size_t)(tid >> 5) * kQueue;
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
   const int G = gridDim.x;
 
@@ -387,6 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
     bool full = false;
     for (int pass = 0; pass < pose_passes; ++pass) {
       Run run{kEmptyKey, 0u, 0, 0u};
+      WarpQueue wq{0u, 0u};
       // ---- sweep all tiles of the pose's source array ----
       for (int t = 0; t < a.n_tiles; ++t, ++q) {
         const uint32_t b = q % kStages;
@@ -405,7 +481,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
           for (int j = 0; j < kPPT; ++j) {
             if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
               atomicOr(a.err, kErrDzBound);
-            step_run<kVar>(S, gc, wide, run, key[j], dz[j], T);
+            uint4 fin;
+            const bool has = advance_run<kVar>(gc, run, key[j], dz[j], fin);
+            queue_push<kVar>(S, ring, wq, lane, has, fin, T);
           }
         }
         __syncwarp();
@@ -423,18 +501,25 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
           }
         }
       }
-      if (run.n != 0u && !full) add_run<kVar>(S, gc, wide, run.key, run.n, run.s1, run.s2, T);
+      if (!full) {
+        queue_push<kVar>(S, ring, wq, lane, run.n != 0u, make_uint4(run.key, run.n, (uint32_t)run.s1, run.s2), T);
+        while (wq.fill > 0u) queue_drain<kVar>(S, ring, wq, lane, T, min(wq.fill, 32u));
+      }
       __syncthreads();
       if (S.flags[2]) {
         aborted = true;
         break;
       }
       full = full || S.flags[1] != 0u;
-      scan_table<kVar>(S, gc, a, wide, T, K, p, full);
+      scan_table<kVar, false>(S, gc, a, wide, T, K, p, full);
       __syncthreads();
       max_occupied = max(max_occupied, S.flags[0]);
+      full = full || S.flags[3] != 0u;
       __syncthreads();
-      if (tid == 0) S.flags[0] = 0u;
+      if (tid == 0) {
+        S.flags[0] = 0u;
+        S.flags[3] = 0u;
+      }
     }
     if (aborted) break;
     if (full) {
@@ -505,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1) redo_kernel(const GridConst gc, c
       if (run.n != 0u) add_run<kVar>(S, gc, wide, run.key, run.n, run.s1, run.s2, T);
       __syncthreads();
       const bool full = S.flags[1] != 0u;
-      scan_table<kVar>(S, gc, a, wide, T, K, p, full);
+      scan_table<kVar, true>(S, gc, a, wide, T, K, p, full);
       __syncthreads();
       if (tid == 0) S.flags[0] = 0u;
       if (full) {
