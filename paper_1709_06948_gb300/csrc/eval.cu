@@ -35,12 +35,15 @@ namespace mialign {
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
-constexpr int kPPT = 2;                       // points per thread per tile
+constexpr int kPPT = 1;                       // points per thread per tile
 constexpr int kTile = kThreads * kPPT;        // points per tile
 constexpr uint32_t kTileBytes = kTile * 16u;  // float4 per point
 constexpr int kStages = 3;
+// Tile delivery: true = bulk (TMA) copies into a shared-memory ring; false = every thread
+// loads its own stream's points from L2 into registers, three tiles ahead.
+constexpr bool kTmaTiles = false;
 constexpr uint32_t kQueue = 64;               // finished runs buffered per warp
 constexpr int kMaxPasses = 1 << 16;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
@@ -72,7 +75,7 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, ui
     off += bytes;
     return o;
   };
-  size_t o_tiles = take((size_t)kStages * kTileBytes, 128);
+  size_t o_tiles = take(kTmaTiles ? (size_t)kStages * kTileBytes : 16, 128);
   size_t o_queue = take((size_t)kWarps * kQueue * 16, 16);
   size_t o_key = take((size_t)T * 4, 16);
   size_t o_cnt = take((size_t)T * 4, 16);
@@ -282,14 +285,14 @@ struct PoseRegs {
   float t[3];
 };
 
-// Keys of this thread's points of one tile under the pose (key partition `part` of 2^lg).
-// `pts` points at the tile plus the thread index; the thread's points are kThreads apart.
+// Keys of this thread's kPPT points (in registers) under the pose (key partition `part`
+// of 2^lg).
 template <bool kRot>
-__device__ __forceinline__ void tile_keys(const GridConst& gc, const PoseRegs& P, const float4* pts, int lg,
+__device__ __forceinline__ void regs_keys(const GridConst& gc, const PoseRegs& P, const float4* pts, int lg,
                                           uint32_t part, uint32_t* key, int* dz) {
 #pragma unroll
   for (int j = 0; j < kPPT; ++j) {
-    const float4 p = pts[j * kThreads];
+    const float4 p = pts[j];
     float gx, gy, gz;
     if (kRot) {
       float ux, uy, uz;
@@ -306,6 +309,17 @@ __device__ __forceinline__ void tile_keys(const GridConst& gc, const PoseRegs& P
     key[j] = voxel_key_g(gx, gy, gz, gc.inv_res, gc.X, gc.Y, gc.Z, gc.res_mm, &dz[j]);
     if (lg > 0 && key[j] != kEmptyKey && ((key[j] * 0x85EBCA77u) >> (32 - lg)) != part) key[j] = kEmptyKey;
   }
+}
+
+// The same for this thread's points of one tile (`pts`: the tile plus the thread index;
+// the thread's points are kThreads apart).
+template <bool kRot>
+__device__ __forceinline__ void tile_keys(const GridConst& gc, const PoseRegs& P, const float4* pts, int lg,
+                                          uint32_t part, uint32_t* key, int* dz) {
+  float4 v[kPPT];
+#pragma unroll
+  for (int j = 0; j < kPPT; ++j) v[j] = pts[j * kThreads];
+  regs_keys<kRot>(gc, P, v, lg, part, key, dz);
 }
 
 __device__ __forceinline__ void load_pose(const EvalArgs& a, int p, PoseRegs& P) {
@@ -424,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
 
   init_smem(S, gc, T, KK);
   int passes = a.passes0;
-  if (tid == 0) {
+  if (kTmaTiles && tid == 0) {
     for (int b = 0; b < kStages; ++b) {
       mbar_init(smem_addr(&S.mbar[b]), 1u);
       mbar_init(smem_addr(&S.mbar[kStages + b]), (uint32_t)kWarps);
@@ -438,14 +452,14 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0)
+  if (kTmaTiles && tid == 0)
     for (int b = 0; b < kStages; ++b) issue_tile(S, a, (uint32_t)b);
 
   uint32_t q = 0;  // consumption counter, identical in every warp
   bool aborted = false;
 
   for (int p = blockIdx.x; p < a.P && !aborted; p += G) {
-    if (p != (int)blockIdx.x) {
+    if (kTmaTiles && p != (int)blockIdx.x) {
       if (tid == 0) {  // the pose's sweeps start at q; every warp is past the previous pose
         S.sched[0] = q;
         S.sched[1] = (uint32_t)passes * (uint32_t)a.n_tiles;
@@ -464,39 +478,77 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
       Run run{kEmptyKey, 0u, 0, 0u};
       WarpQueue wq{0u, 0u};
       // ---- sweep all tiles of the pose's source array ----
-      for (int t = 0; t < a.n_tiles; ++t, ++q) {
-        const uint32_t b = q % kStages;
-        const uint32_t par = (q / kStages) & 1u;
-        if (*(volatile uint32_t*)&S.flags[2]) continue;  // aborting: no more waits
-        if (!mbar_wait_bounded(smem_addr(&S.mbar[b]), par, kWaitLimitNs)) {
-          atomicOr(a.err, kErrWaitTimeout);
-          S.flags[2] = 1u;
-          continue;
-        }
-        if (!full) {
-          uint32_t key[kPPT];
-          int dz[kPPT];
-          tile_keys<kRot>(gc, P, S.tiles + (size_t)b * kTile + tid, lg, (uint32_t)pass, key, dz);
-#pragma unroll
-          for (int j = 0; j < kPPT; ++j) {
-            if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
-              atomicOr(a.err, kErrDzBound);
-            uint4 fin;
-            const bool has = advance_run<kVar>(gc, run, key[j], dz[j], fin);
-            queue_push<kVar>(S, ring, wq, lane, has, fin, T);
+      if constexpr (kTmaTiles) {
+        for (int t = 0; t < a.n_tiles; ++t, ++q) {
+          const uint32_t b = q % kStages;
+          const uint32_t par = (q / kStages) & 1u;
+          if (*(volatile uint32_t*)&S.flags[2]) continue;  // aborting: no more waits
+          if (!mbar_wait_bounded(smem_addr(&S.mbar[b]), par, kWaitLimitNs)) {
+            atomicOr(a.err, kErrWaitTimeout);
+            S.flags[2] = 1u;
+            continue;
+          }
+          if (!full) {
+            uint32_t key[kPPT];
+            int dz[kPPT];
+            tile_keys<kRot>(gc, P, S.tiles + (size_t)b * kTile + tid, lg, (uint32_t)pass, key, dz);
+  #pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+              if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
+                atomicOr(a.err, kErrDzBound);
+              uint4 fin;
+              const bool has = advance_run<kVar>(gc, run, key[j], dz[j], fin);
+              queue_push<kVar>(S, ring, wq, lane, has, fin, T);
+            }
+          }
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(smem_addr(&S.mbar[kStages + b]));
+            const uint32_t c = atomicAdd(&S.issue_cnt[b], 1u);
+            if (c == (uint32_t)kWarps - 1u) {  // the last warp done with this buffer refills it
+              S.issue_cnt[b] = 0u;
+              if (mbar_wait_bounded(smem_addr(&S.mbar[kStages + b]), par, kWaitLimitNs)) {
+                issue_tile(S, a, q + kStages);
+              } else {
+                atomicOr(a.err, kErrWaitTimeout);
+                S.flags[2] = 1u;
+              }
+            }
           }
         }
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(smem_addr(&S.mbar[kStages + b]));
-          const uint32_t c = atomicAdd(&S.issue_cnt[b], 1u);
-          if (c == (uint32_t)kWarps - 1u) {  // the last warp done with this buffer refills it
-            S.issue_cnt[b] = 0u;
-            if (mbar_wait_bounded(smem_addr(&S.mbar[kStages + b]), par, kWaitLimitNs)) {
-              issue_tile(S, a, q + kStages);
-            } else {
-              atomicOr(a.err, kErrWaitTimeout);
-              S.flags[2] = 1u;
+      } else {
+        // every thread streams its own points straight from L2, three tiles ahead
+        const float4* src = a.src + (size_t)pose_source(a, p) * a.src_stride + tid;
+        float4 b0[kPPT], b1[kPPT], b2[kPPT];
+#pragma unroll
+        for (int j = 0; j < kPPT; ++j) {
+          b0[j] = __ldg(src + j * kThreads);
+          b1[j] = __ldg(src + kTile + j * kThreads);
+          b2[j] = __ldg(src + 2 * kTile + j * kThreads);
+        }
+        for (int t = 0; t < a.n_tiles; ++t) {
+          float4 cur[kPPT];
+#pragma unroll
+          for (int j = 0; j < kPPT; ++j) {
+            cur[j] = b0[j];
+            b0[j] = b1[j];
+            b1[j] = b2[j];
+          }
+          if (t + 3 < a.n_tiles) {
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) b2[j] = __ldg(src + (size_t)(t + 3) * kTile + j * kThreads);
+          }
+          if (!full) {
+            uint32_t key[kPPT];
+            int dz[kPPT];
+            regs_keys<kRot>(gc, P, cur, lg, (uint32_t)pass, key, dz);
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+              if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
+                atomicOr(a.err, kErrDzBound);
+              uint4 fin;
+              const bool has = advance_run<kVar>(gc, run, key[j], dz[j], fin);
+              queue_push<kVar>(S, ring, wq, lane, has, fin, T);
             }
           }
         }
@@ -541,7 +593,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
   __syncthreads();
   if (tid == 0) {
     if (!aborted) atomicMax(a.max_passes, (uint32_t)passes);
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; kTmaTiles && i < kStages; ++i) {
       const uint32_t qq = q + (uint32_t)i;
       if (!mbar_wait_bounded(smem_addr(&S.mbar[qq % kStages]), (qq / kStages) & 1u, kWaitLimitNs))
         atomicOr(a.err, kErrWaitTimeout);
