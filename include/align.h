@@ -124,7 +124,9 @@ align_status align_round_poses(const float origin[3], const double* eta6, int64_
    ALIGN_POSES_DEVICE) or eta6 (P x 6 FP64, host); exactly one non-NULL.
    mi_out: P floats.  argmax_out: one int64 (may be NULL).  hist_out (may be NULL):
    P x K x K uint32 joint histograms, row = A symbol, column = B symbol.
-   P may be 0 (nothing is written; *argmax_out = -1). */
+   P may be 0 (nothing is written; *argmax_out = -1).  Host poses must be finite
+   (ALIGN_E_INVALID otherwise); points may hold NaN or infinities, which fall outside
+   the grid under every pose. */
 align_status align_eval_mi(align_grid* grid, const float* xyzB, int64_t nB, int flags,
                            const float* poses12, const double* eta6, int64_t P,
                            float* mi_out, int64_t* argmax_out, uint32_t* hist_out);

@@ -294,19 +294,28 @@ __device__ __forceinline__ void regs_keys(const GridConst& gc, const PoseRegs& P
   for (int j = 0; j < kPPT; ++j) {
     const float4 p = pts[j];
     float gx, gy, gz;
+    dz[j] = 0;
     if (kRot) {
       float ux, uy, uz;
       rotate_point(P.r, p.x, p.y, p.z, ux, uy, uz);
       gx = __fadd_rn(ux, P.t[0]);
       gy = __fadd_rn(uy, P.t[1]);
       gz = __fadd_rn(uz, P.t[2]);
+      key[j] = voxel_key_g(gx, gy, gz, gc.inv_res, gc.X, gc.Y, gc.Z, gc.res_mm, &dz[j]);
     } else {
+      // Pre-rotated copies hold finite values or +inf (pack_points_kernel), and host poses
+      // are finite, so g is never NaN: a saturating floor and unsigned compares decide
+      // "inside" exactly as the float compares would.
       gx = __fadd_rn(p.x, P.t[0]);
       gy = __fadd_rn(p.y, P.t[1]);
       gz = __fadd_rn(p.z, P.t[2]);
+      const int kx = __float2int_rd(__fmul_rn(gx, gc.inv_res));
+      const int ky = __float2int_rd(__fmul_rn(gy, gc.inv_res));
+      const int kz = __float2int_rd(__fmul_rn(gz, gc.inv_res));
+      const bool in = ((uint32_t)kx < (uint32_t)gc.X) & ((uint32_t)ky < (uint32_t)gc.Y) & ((uint32_t)kz < (uint32_t)gc.Z);
+      dz[j] = __float2int_rn(__fmul_rn(gz, 1000.0f)) - kz * gc.res_mm;
+      key[j] = in ? (uint32_t)((kz * gc.Y + ky) * gc.X + kx) : kEmptyKey;
     }
-    dz[j] = 0;
-    key[j] = voxel_key_g(gx, gy, gz, gc.inv_res, gc.X, gc.Y, gc.Z, gc.res_mm, &dz[j]);
     if (lg > 0 && key[j] != kEmptyKey && ((key[j] * 0x85EBCA77u) >> (32 - lg)) != part) key[j] = kEmptyKey;
   }
 }
@@ -423,6 +432,29 @@ __device__ __forceinline__ void reset_pose(const EvalSmem& S, int KK) {
   if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
 }
 
+__device__ __forceinline__ void load_tile(const float4* src, int t, float4* v) {
+#pragma unroll
+  for (int j = 0; j < kPPT; ++j) v[j] = __ldg(src + (size_t)t * kTile + j * kThreads);
+}
+
+// One tile of this thread's stream: keys, run stepping, queueing of finished runs.  A dz
+// outside its proven bound is remembered in `bad` (reported once per sweep).
+template <bool kVar, bool kRot>
+__device__ __forceinline__ void sweep_tile(const EvalSmem& S, const GridConst& gc, const PoseRegs& P,
+                                           const float4* pts, int lg, int pass, Run& run, WarpQueue& wq, uint4* ring,
+                                           int lane, int T, uint32_t& bad) {
+  uint32_t key[kPPT];
+  int dz[kPPT];
+  regs_keys<kRot>(gc, P, pts, lg, (uint32_t)pass, key, dz);
+#pragma unroll
+  for (int j = 0; j < kPPT; ++j) {
+    bad |= (uint32_t)(key[j] != kEmptyKey) & (uint32_t)((uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound));
+    uint4 fin;
+    const bool has = advance_run<kVar>(gc, run, key[j], dz[j], fin);
+    queue_push<kVar>(S, ring, wq, lane, has, fin, T);
+  }
+}
+
 template <bool kVar, bool kRot>
 __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, const EvalArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -520,38 +552,24 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
         // every thread streams its own points straight from L2, three tiles ahead
         const float4* src = a.src + (size_t)pose_source(a, p) * a.src_stride + tid;
         float4 b0[kPPT], b1[kPPT], b2[kPPT];
-#pragma unroll
-        for (int j = 0; j < kPPT; ++j) {
-          b0[j] = __ldg(src + j * kThreads);
-          b1[j] = __ldg(src + kTile + j * kThreads);
-          b2[j] = __ldg(src + 2 * kTile + j * kThreads);
-        }
-        for (int t = 0; t < a.n_tiles; ++t) {
-          float4 cur[kPPT];
-#pragma unroll
-          for (int j = 0; j < kPPT; ++j) {
-            cur[j] = b0[j];
-            b0[j] = b1[j];
-            b1[j] = b2[j];
+        load_tile(src, 0, b0);
+        load_tile(src, 1, b1);
+        load_tile(src, 2, b2);
+        uint32_t bad = 0u;
+        const int nt = a.n_tiles;
+        for (int t = 0; t < nt && !full; t += 3) {
+          sweep_tile<kVar, kRot>(S, gc, P, b0, lg, pass, run, wq, ring, lane, T, bad);
+          if (t + 3 < nt) load_tile(src, t + 3, b0);
+          if (t + 1 < nt) {
+            sweep_tile<kVar, kRot>(S, gc, P, b1, lg, pass, run, wq, ring, lane, T, bad);
+            if (t + 4 < nt) load_tile(src, t + 4, b1);
           }
-          if (t + 3 < a.n_tiles) {
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) b2[j] = __ldg(src + (size_t)(t + 3) * kTile + j * kThreads);
-          }
-          if (!full) {
-            uint32_t key[kPPT];
-            int dz[kPPT];
-            regs_keys<kRot>(gc, P, cur, lg, (uint32_t)pass, key, dz);
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) {
-              if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
-                atomicOr(a.err, kErrDzBound);
-              uint4 fin;
-              const bool has = advance_run<kVar>(gc, run, key[j], dz[j], fin);
-              queue_push<kVar>(S, ring, wq, lane, has, fin, T);
-            }
+          if (t + 2 < nt) {
+            sweep_tile<kVar, kRot>(S, gc, P, b2, lg, pass, run, wq, ring, lane, T, bad);
+            if (t + 5 < nt) load_tile(src, t + 5, b2);
           }
         }
+        if (bad) atomicOr(a.err, kErrDzBound);
       }
       if (!full) {
         queue_push<kVar>(S, ring, wq, lane, run.n != 0u, make_uint4(run.key, run.n, (uint32_t)run.s1, run.s2), T);
@@ -684,11 +702,18 @@ __global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int
     const int j = pos / kThreads;
     const int sidx = pos - j * kThreads;
     const int64_t src = (int64_t)sidx * L + (int64_t)kPPT * t + j;
-    float4 v = make_float4(nan, nan, nan, 0.0f);
+    // padding: NaN for raw tiles (the in-kernel rotation keeps NaN), +inf for rotated copies
+    const float pad = rots != nullptr ? __int_as_float(0x7f800000) : nan;
+    float4 v = make_float4(pad, pad, pad, 0.0f);
     if (src < n) {
       const float x = xyz[3 * src], y = xyz[3 * src + 1], z = xyz[3 * src + 2];
       if (rots != nullptr) {
         rotate_point(R, x, y, z, v.x, v.y, v.z);
+        // a non-finite coordinate can only come from a non-finite point (or an overflow),
+        // which the voxel map drops under every pose; +inf keeps it dropped
+        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) v = make_float4(__int_as_float(0x7f800000),
+                                                                               __int_as_float(0x7f800000),
+                                                                               __int_as_float(0x7f800000), 0.0f);
       } else {
         v.x = x;
         v.y = y;

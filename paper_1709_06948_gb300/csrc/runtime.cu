@@ -616,6 +616,8 @@ static align_status eval_common(align_grid* g, const float* xyzB, int64_t nB, in
       for (int64_t p = 0; p < P; ++p) pose_to_fp32(g->origin, eta6 + 6 * p, &tmp[(size_t)p * 12]);
       h_poses = tmp.data();
     }
+    for (int64_t i = 0; i < P * 12; ++i)
+      if (!std::isfinite(h_poses[i])) return fail(ALIGN_E_INVALID, "pose %lld is not finite", (long long)(i / 12));
     // a pageable source is staged before the call returns
     CU(cudaMemcpyAsync(g->poses.p, h_poses, (size_t)P * 48, cudaMemcpyHostToDevice, g->stream), "copy poses");
     d_poses = g->poses.as<float>();

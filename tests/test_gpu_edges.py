@@ -150,3 +150,39 @@ def test_large_angles(tiny):
     rng = np.random.default_rng(43)
     etas = np.concatenate([rng.uniform(-3, 3, (64, 3)), rng.uniform(-math.pi, math.pi, (64, 3))], 1)
     _compare(tiny.grid, tiny.xyzA, tiny.xyzB, etas)
+
+
+def test_non_finite_points_are_dropped(tiny):
+    """NaN / inf coordinates fall outside the grid under every pose (both load paths)."""
+    xyz = tiny.xyzB.copy()
+    xyz[::7, 0] = np.nan
+    xyz[1::11, 1] = np.inf
+    xyz[2::13, 2] = -np.inf
+    etas = scangen.tiny_poses()[::5]
+    _compare(tiny.grid, tiny.xyzA, xyz, etas)            # host poses: pre-rotated copies
+    import torch
+    from paper_1709_06948_gb300 import align
+    G = oracle_grid(tiny.grid)
+    L = lib_grid(tiny.grid)
+    symA, boxA = G.reference(tiny.xyzA)
+    align.align_set_reference(L, tiny.xyzA)
+    poses = G.round_pose(etas)
+    P = len(etas)
+    mi = torch.empty(P, device="cuda")
+    am = torch.empty(1, dtype=torch.int64, device="cuda")
+    hist = torch.empty((P, L.K, L.K), dtype=torch.int32, device="cuda")
+    align.align_eval_mi(L, torch.from_numpy(xyz).cuda(), poses12=torch.from_numpy(poses).cuda(), out=(mi, am, hist))
+    torch.cuda.synchronize()
+    _, ho, _ = G.eval_mi(symA, boxA, xyz, poses, with_hist=True)
+    assert np.array_equal(hist.cpu().numpy().view(np.uint32), ho)  # device poses: in-kernel rotation
+
+
+def test_non_finite_pose_rejected(tiny):
+    from paper_1709_06948_gb300 import align
+    L = lib_grid(tiny.grid)
+    align.align_set_reference(L, tiny.xyzA)
+    etas = np.zeros((3, 6))
+    etas[1, 0] = np.inf
+    with pytest.raises(align.AlignError) as e:
+        align.align_eval_mi(L, tiny.xyzB, eta6=etas)
+    assert e.value.status == align.ALIGN_E_INVALID
