@@ -28,62 +28,73 @@ struct GridConst {
   int32_t feature;        // 0 count, 1 z-variance, 2 joint
   int32_t Lc, Lv;         // occupied levels
   int32_t dz_bound;       // |dz| <= dz_bound for every in-grid point
-  uint32_t nlim;          // largest n whose S1, S2 fit the 32-bit table sums
+  int32_t dz_shift;       // smallest m with 2^m > 2 * dz_bound (the sweep checks dz + dz_bound < 2^m)
+  uint32_t nlim;          // largest n whose S1, S2 fit the 32-bit table sums for |dz| < 2^m - dz_bound
   int32_t boxA[6];        // A's occupied bbox (xmin > xmax when empty)
   uint32_t count_thresh[kMaxLevels];
   int64_t var_thresh[kMaxLevels];
 };
 
-// Pose-batched evaluation: per pose, per-voxel sums in a shared-memory hash table,
-// then the partial joint histogram c[a][b>=1] of the occupied B voxels inside boxA and
-// B's occupied bbox.
-struct EvalArgs {
-  const float4* src;        // point tiles: source arrays of n_tiles * tile float4 each
-                            // (raw xyz, or xyz pre-rotated by one rotation); padding is NaN
-  size_t src_stride;        // float4 entries per source array
-  const int32_t* pose_src;  // P: source array of each pose (nullptr: all use array 0)
-  int32_t n_tiles;          // tiles per source array (>= the pipeline depth)
-  const float* poses;       // P x 12
-  int32_t P;
-  const uint8_t* symA;      // V
-  uint32_t* out_c;          // P x K x K (B-occupied voxels inside boxA)
-  int32_t* out_box;         // P x 6
-  uint32_t* err;            // error bits
-  uint32_t* max_passes;     // running max of key-partition passes (seed for the next launch)
-  uint32_t* wide_count;     // voxels that overflowed into the 64-bit side sums
-  unsigned long long* wide; // per CTA: table_slots x 2 (S1 as two's complement, S2)
-  uint32_t* redo_list;      // P: poses whose table filled up, finished by the redo kernel
-  uint32_t* redo_count;     // entries in redo_list (zeroed before every launch)
-  int32_t table_slots;
-  int32_t passes0;          // initial key-partition passes (power of two)
-  int64_t* dump;            // optional: V x 3 (n, S1, S2) for pose 0 (parity checks; S1, S2
-                            // are accumulated whenever dump is set, whatever the feature)
+// Pose-batched evaluation over one or more scan pairs ("items").  Per pose: per-voxel sums
+// in a shared-memory hash table, then the partial joint histogram c[a][b>=1] of the
+// occupied B voxels inside boxA and B's occupied bbox; then the overlap, MI and argmax.
+struct EvalItem {
+  GridConst gc;               // the pair's grid, feature and A bbox
+  const uint8_t* symA;        // V
+  const int32_t* sat;         // (K-1) x (Z+1) x (Y+1) x (X+1)
+  const float4* src;          // point tiles: copies of n_tiles * tile float4 each (raw xyz, or
+                              // pre-rotated by one rotation); see pack_points_kernel
+  uint64_t src_stride;        // float4 entries per copy
+  const int32_t* pose_src;    // P: copy of each pose (nullptr: copy 0)
+  const float* poses;         // P x 12
+  int32_t n_tiles;            // tiles per copy (>= 3)
+  int32_t P;                  // poses of this item
+  int32_t pose_base;          // global index of the item's pose 0
+  int32_t pad0;
+  uint32_t* out_c;            // P x K x K
+  int32_t* out_box;           // P x 6
+  float* mi;                  // P
+  uint32_t* hist;             // optional P x K x K full joint histograms
+  unsigned long long* best;   // packed (MI, ~index) running maximum (zeroed before the launch)
+  int64_t* argmax;            // one
+  int64_t* dump;              // optional: V x 3 (n, S1, S2) of pose 0 (parity checks; S1, S2
+                              // are accumulated whenever dump is set, whatever the feature)
 };
 
-struct ComposeArgs {
-  const uint32_t* c;       // P x K x K
-  const int32_t* boxB;     // P x 6
-  const int32_t* sat;      // (K-1) x (Z+1) x (Y+1) x (X+1)
-  int32_t P;
-  float* mi;               // P
-  uint32_t* hist;          // optional P x K x K full joint histogram
-  unsigned long long* best;// packed (MI, ~index) running max
+struct EvalArgs {
+  EvalItem one;               // a copy of items[0] when n_items == 1 (read from the parameter bank)
+  const EvalItem* items;
+  const int32_t* pose_item;   // P: item of each global pose (nullptr: one item)
+  int32_t n_items;
+  int32_t P;                  // poses over all items
+  int32_t K;                  // largest symbol count over the items
+  int32_t table_slots;
+  int32_t passes0;            // initial key-partition passes (power of two)
+  int32_t n_buckets;          // table_slots / 4
+  uint32_t* err;              // error bits
+  uint32_t* max_passes;       // running max of key-partition passes (seed for the next launch)
+  uint32_t* wide_count;       // voxels that needed the 64-bit side sums
+  unsigned long long* wide;   // per CTA: table_slots x 2 (S1 as two's complement, S2)
+  uint32_t* redo_list;        // P: poses whose table overflowed, finished by the redo kernel
+  uint32_t* redo_count;       // entries in redo_list (zeroed before every launch)
 };
 
 // Launch helpers (defined in eval.cu / reference.cu).
 int eval_tile_points();
 int eval_min_tiles();
+int eval_threads();
 size_t eval_smem_bytes(int K, int table_slots);
 int eval_table_slots_for(int K, size_t smem_budget);
-// rotate: tiles hold raw xyz (the kernel applies each pose's rotation); otherwise each
-// pose's source array already holds R p for that pose's rotation.
-cudaError_t launch_eval(const GridConst& gc, const EvalArgs& a, int n_ctas, bool rotate, cudaStream_t s);
+// var: accumulate z sums; rotate: tiles hold raw xyz (the kernel applies each pose's
+// rotation) instead of pre-rotated copies.  Launches the eval and redo kernels.
+cudaError_t launch_eval(const EvalArgs& a, int n_ctas, bool var, bool rotate, cudaStream_t s);
+// Overlap box, phi column, MI and the running argmax of every pose; then each item's argmax.
+cudaError_t launch_compose(const EvalArgs& a, cudaStream_t s);
+cudaError_t launch_argmax_finalize(const EvalItem* items, int n_items, cudaStream_t s);
 // xyz (n x 3 fp32) -> n_out float4 with NaN padding; with rots (n_rot x 9), one
 // pre-rotated copy u = R p per rotation (same FMA order as the voxel map).
 cudaError_t launch_pack_points(const float* xyz, int64_t n, int64_t n_out, const float* rots, int n_rot,
                                float4* out, cudaStream_t s);
-cudaError_t launch_compose(const GridConst& gc, const ComposeArgs& a, cudaStream_t s);
-cudaError_t launch_argmax_finalize(const unsigned long long* best, int64_t* out, cudaStream_t s);
 
 cudaError_t launch_ref_accumulate(const GridConst& gc, const float* xyz, int64_t n, const float* pose12,
                                   uint32_t* cnt, unsigned long long* s1, unsigned long long* s2,

@@ -1,27 +1,27 @@
 // eval.cu — the pose-batched MI hot path (arXiv 1709.06948, Algorithm 1 loop body for
-// a whole batch of candidate poses; Sec. III-A features; Eqs. 1-5).
+// whole batches of candidate poses of one or more scan pairs; Sec. III-A features; Eqs. 1-5).
 //
-// pack_points_kernel: scan B as float4 tiles (NaN padding), either raw xyz or one
-// pre-rotated copy u = R p per distinct rotation of the batch (a search lattice has 32
-// rotations for 4,096 poses, so the 9-FMA rotation leaves the per-pose loop).  The tiles
-// are laid out as kThreads streams: thread s of a CTA reads, tile after tile, the points
-// s*L, s*L+1, ... of B's given order (L = kPPT * tiles), so each thread walks a stretch
-// of consecutive scan points.
+// pack_points_kernel: scan B as float4 tiles, either raw xyz (NaN padding) or one
+// pre-rotated copy u = R p per distinct rotation of the batch (+inf padding; a search
+// lattice has 32 rotations for 4,096 poses, so the 9-FMA rotation leaves the per-pose
+// loop).  The tiles are laid out as kThreads streams: thread s of a CTA reads, tile after
+// tile, the points s*L, s*L+1, ... of B's given order (L = kPPT * tiles), so each thread
+// walks a stretch of consecutive scan points.
 //
-// eval_kernel: persistent, one CTA per SM, one pose at a time per CTA.  The tiles of the
-// pose's source array arrive by 1-D bulk (TMA) copies on a cyclic mbarrier ring whose
-// schedule already knows the CTA's next pose, so the copies never stall at pose
-// boundaries.  Per point and pose: voxel key and dz (device_common.cuh).  Each thread
-// keeps the run of equal keys it is walking in registers (n, S1, S2); when the key
-// changes, the finished run is added into a shared-memory open-addressing hash table
-// with 32-bit shared atomics.  After the sweep one pass over the table gives the feature
-// symbols, B's occupied bbox and the partial joint histogram c[a][b >= 1] of the occupied
-// voxels inside A's bbox.
-//  - A pose with more occupied voxels than fit the table is handed to redo_kernel (which
-//    splits the keys into 2, 4, ... hash partitions, one sweep each); a crowded table
-//    makes the CTA sweep its following poses in twice as many partitions.
-//  - A voxel with more points than the 32-bit sums allow diverts its later runs to 64-bit
-//    side sums in global memory (per CTA, indexed by table slot).
+// eval_kernel: persistent, one CTA per SM, one pose at a time per CTA; the poses of all
+// items are one list, and each pose brings its item's grid constants.  Every thread
+// streams its own points straight from L2, three tiles ahead, computes the voxel key and
+// dz (device_common.cuh) and keeps the run of equal keys it is walking in registers
+// (n, S1, S2).  Finished runs go to a per-warp ring in shared memory; 32 at a time the
+// whole warp adds them into a shared-memory open-addressing hash table (buckets of 4
+// keys, 32-bit shared atomics).  After the sweep one pass over the table gives the
+// feature symbols, B's occupied bbox and the partial joint histogram c[a][b >= 1] of the
+// occupied voxels inside A's bbox.
+//  - A pose with more occupied voxels than fit the table, or with a voxel so full that
+//    its 32-bit sums may have wrapped, is finished by redo_kernel: plain sweeps with the
+//    keys split into 2, 4, ... hash partitions, each run added at once, and 64-bit side
+//    sums in global memory for voxels beyond the 32-bit bound.  A crowded table makes the
+//    CTA sweep its following poses in twice as many partitions.
 //
 // compose_kernel: per pose, the overlap box (Algorithm 1), A's symbol counts over it from
 // per-symbol prefix sums, the phi column h[a][0], then Eqs. 2-5 in FP32 with a fixed
@@ -37,35 +37,83 @@ namespace {
 
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
-constexpr int kPPT = 1;                       // points per thread per tile
-constexpr int kTile = kThreads * kPPT;        // points per tile
-constexpr uint32_t kTileBytes = kTile * 16u;  // float4 per point
-constexpr int kStages = 3;
-// Tile delivery: true = bulk (TMA) copies into a shared-memory ring; false = every thread
-// loads its own stream's points from L2 into registers, three tiles ahead.
-constexpr bool kTmaTiles = false;
-constexpr uint32_t kQueue = 64;               // finished runs buffered per warp
+constexpr int kPPT = 1;                 // points per thread per tile
+constexpr int kTile = kThreads * kPPT;  // points per tile
+constexpr int kMinTiles = 3;            // prefetch depth
+constexpr uint32_t kQueue = 64;         // finished runs buffered per warp (32 drained at a time)
+constexpr int kProbeBuckets = 64;       // probe budget per key (buckets of 4 slots)
 constexpr int kMaxPasses = 1 << 16;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr int kGcWords = (int)(sizeof(GridConst) / 4);
 
 __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
 
+// ---------------------------------------------------------------------------------
+// Shared memory by 32-bit shared-window address (explicit ld/st/red/atom.shared).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void red_add(uint32_t a, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_add(uint32_t a, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ uint32_t atom_cas(uint32_t a, uint32_t cmp, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "r"(a), "r"(cmp), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_min_s32(uint32_t a, int v) {
+  asm volatile("red.shared.min.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_max_s32(uint32_t a, int v) {
+  asm volatile("red.shared.max.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lane_mask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Layout: per-warp rings | flags (16 B) | table keys (T x 4 B) | table values (T x 12 B:
+// n, S1, S2) | histogram | grid constants | bbox | current item.  The flags sit just below
+// the keys so that the hot loop reaches them at a fixed offset from the key base.
 struct EvalSmem {
-  float4* tiles;
-  uint4* queue;         // per warp: a ring of kQueue finished runs (key, n, S1, S2)
+  uint4* queue;       // per warp: kQueue finished runs (key, n, S1, S2)
+  uint32_t* flags;    // occupied count, table full, (unused), sums need the exact path
   uint32_t* tkey;
-  uint32_t* tcnt;
-  int32_t* ts1;
-  uint32_t* ts2;
+  uint32_t* tval;     // 3 words per slot
   uint32_t* hist;
-  uint32_t* ct;
-  int64_t* vt;
-  uint64_t* mbar;       // [0, kStages): full, [kStages, 2 kStages): empty
-  uint32_t* issue_cnt;  // kStages
-  uint32_t* sched;      // q_start, n_consume, src_cur, src_next
-  int32_t* box;         // 6
-  uint32_t* flags;      // occupied count, table full, abort, sums need the exact path
+  GridConst* gc;      // the current item's grid constants
+  int32_t* box;       // 6
+  int32_t* item;      // the item whose constants are loaded
+  // shared-window addresses
+  uint32_t a_queue, a_key, a_vals, a_hist, a_box;
 };
+constexpr uint32_t kFlagOccupied = 16u;  // byte offsets of the flags below a_key
+constexpr uint32_t kFlagFull = 12u;
+constexpr uint32_t kFlagWide = 4u;
 
 __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, uint8_t* base) {
   size_t off = 0;
@@ -75,81 +123,68 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, ui
     off += bytes;
     return o;
   };
-  size_t o_tiles = take(kTmaTiles ? (size_t)kStages * kTileBytes : 16, 128);
   size_t o_queue = take((size_t)kWarps * kQueue * 16, 16);
+  size_t o_flags = take(16, 16);
   size_t o_key = take((size_t)T * 4, 16);
-  size_t o_cnt = take((size_t)T * 4, 16);
-  size_t o_s1 = take((size_t)T * 4, 16);
-  size_t o_s2 = take((size_t)T * 4, 16);
+  size_t o_vals = take((size_t)T * 12, 16);
   size_t o_hist = take((size_t)round4(K * K) * 4, 16);
-  size_t o_ct = take(kMaxLevels * 4 + 4, 16);
-  size_t o_vt = take(kMaxLevels * 8 + 8, 16);
-  size_t o_mbar = take(2 * kStages * 8, 8);
-  size_t o_issue = take(kStages * 4, 4);
-  size_t o_sched = take(4 * 4, 4);
+  size_t o_gc = take(sizeof(GridConst), 16);
   size_t o_box = take(6 * 4, 4);
-  size_t o_flags = take(4 * 4, 4);
+  size_t o_item = take(4, 4);
   if (s) {
-    s->tiles = (float4*)(base + o_tiles);
     s->queue = (uint4*)(base + o_queue);
-    s->tkey = (uint32_t*)(base + o_key);
-    s->tcnt = (uint32_t*)(base + o_cnt);
-    s->ts1 = (int32_t*)(base + o_s1);
-    s->ts2 = (uint32_t*)(base + o_s2);
-    s->hist = (uint32_t*)(base + o_hist);
-    s->ct = (uint32_t*)(base + o_ct);
-    s->vt = (int64_t*)(base + o_vt);
-    s->mbar = (uint64_t*)(base + o_mbar);
-    s->issue_cnt = (uint32_t*)(base + o_issue);
-    s->sched = (uint32_t*)(base + o_sched);
-    s->box = (int32_t*)(base + o_box);
     s->flags = (uint32_t*)(base + o_flags);
+    s->tkey = (uint32_t*)(base + o_key);
+    s->tval = (uint32_t*)(base + o_vals);
+    s->hist = (uint32_t*)(base + o_hist);
+    s->gc = (GridConst*)(base + o_gc);
+    s->box = (int32_t*)(base + o_box);
+    s->item = (int32_t*)(base + o_item);
+#ifdef __CUDA_ARCH__
+    const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(base);
+    s->a_queue = a0 + (uint32_t)o_queue;
+    s->a_key = a0 + (uint32_t)o_key;
+    s->a_vals = a0 + (uint32_t)o_vals;
+    s->a_hist = a0 + (uint32_t)o_hist;
+    s->a_box = a0 + (uint32_t)o_box;
+#endif
   }
   return off;
 }
 
-__device__ __forceinline__ uint32_t pose_source(const EvalArgs& a, int p) {
-  return a.pose_src ? (uint32_t)a.pose_src[p] : 0u;
-}
+// Per-pose constants of the voxel map, kept in registers.
+struct VoxelConst {
+  float inv_res;
+  int X, Y, Z, res_mm, dz_bound;
+  uint32_t nlim;
+};
 
-// Issue the bulk copy for consumption index q: within the current pose's sweeps it is a
-// tile of the current source array, past them a tile of the next pose's array.
-__device__ __forceinline__ void issue_tile(const EvalSmem& S, const EvalArgs& a, uint32_t q) {
-  const uint32_t b = q % kStages;
-  const uint32_t rel = q - S.sched[0];
-  uint32_t src, tile;
-  if (rel < S.sched[1]) {
-    src = S.sched[2];
-    tile = rel % (uint32_t)a.n_tiles;
-  } else {
-    src = S.sched[3];
-    tile = (rel - S.sched[1]) % (uint32_t)a.n_tiles;
-  }
-  const uint32_t full = smem_addr(&S.mbar[b]);
-  mbar_arrive_expect_tx(full, kTileBytes);
-  bulk_copy_g2s(smem_addr(S.tiles + (size_t)b * kTile), a.src + (size_t)src * a.src_stride + (size_t)tile * kTile,
-                kTileBytes, full);
+__device__ __forceinline__ VoxelConst voxel_const(const GridConst& g) {
+  return VoxelConst{g.inv_res, g.X, g.Y, g.Z, g.res_mm, g.dz_bound, g.nlim};
 }
 
 // Find or insert `key` in the open-addressing table: buckets of 4 key slots read with one
 // 16-byte load, probed linearly; slots of a bucket fill in order, so a bucket with a free
-// slot ends the search.  Returns -1 when the probe budget is spent (table full).
-__device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T) {
-  const uint32_t nb = (uint32_t)T >> 2;
+// slot ends the search.  Returns -1 when kProbeBuckets buckets were searched in vain (the
+// pose then counts as overflowing the table).
+__device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, uint32_t nb) {
   uint32_t b = __umulhi(key * 0x9E3779B1u, nb);
-  for (uint32_t i = 0; i < nb + 4; ++i) {
-    uint4 k4;
-    asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(k4.x), "=r"(k4.y), "=r"(k4.z), "=r"(k4.w)
-                 : "r"(smem_addr(S.tkey + 4 * b)));
+#pragma unroll 1
+  for (int i = 0; i < kProbeBuckets; ++i) {
+    const uint4 k4 = lds128(S.a_key + 16u * b);
     if (k4.x == key) return (int)(4 * b);
     if (k4.y == key) return (int)(4 * b + 1);
     if (k4.z == key) return (int)(4 * b + 2);
     if (k4.w == key) return (int)(4 * b + 3);
-    const int e = (k4.x == kEmptyKey) ? 0 : (k4.y == kEmptyKey) ? 1 : (k4.z == kEmptyKey) ? 2 : (k4.w == kEmptyKey) ? 3 : -1;
+    const int e = (k4.x == kEmptyKey)   ? 0
+                  : (k4.y == kEmptyKey) ? 1
+                  : (k4.z == kEmptyKey) ? 2
+                  : (k4.w == kEmptyKey) ? 3
+                                        : -1;
     if (e >= 0) {
-      const uint32_t old = atomicCAS(&S.tkey[4 * b + e], kEmptyKey, key);
-      if (old == kEmptyKey || old == key) return (int)(4 * b + e);
+      const uint32_t s = 4 * b + (uint32_t)e;
+      const uint32_t old = atom_cas(S.a_key + 4u * s, kEmptyKey, key);
+      if (old == kEmptyKey || old == key) return (int)s;
       continue;  // another lane took that slot: read the bucket again
     }
     b = (b + 1 == nb) ? 0u : b + 1;
@@ -157,127 +192,90 @@ __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, int T
   return -1;
 }
 
-// Add one finished run (n points of one voxel, sums s1, s2) to the table.
+// Add one finished run (key, n, S1, S2) to the table (fire-and-forget shared reductions).
+// A voxel whose count ends above nlim may have wrapped its 32-bit sums; the table scan
+// sends such a pose to the exact path.
 template <bool kVar>
-__device__ __forceinline__ void add_run(const EvalSmem& S, const GridConst& gc, unsigned long long* wide, uint32_t key,
-                                        uint32_t n, int s1, uint32_t s2, int T) {
-  if (*(volatile uint32_t*)&S.flags[1]) return;  // table already full: the pose is redone
-  const int slot = table_slot(S, key, T);
+__device__ __forceinline__ void table_add(const EvalSmem& S, const uint4& e, uint32_t nb) {
+  if (lds32(S.a_key - kFlagFull)) return;  // table already full: the pose is redone
+  const int slot = table_slot(S, e.x, nb);
   if (slot < 0) {
-    S.flags[1] = 1u;
+    sts32(S.a_key - kFlagFull, 1u);
     return;
   }
+  const uint32_t v = S.a_vals + 12u * (uint32_t)slot;
+  red_add(v, e.y);
   if (kVar) {
-    const uint32_t old = atomicAdd(&S.tcnt[slot], n);
-    if (old + n <= gc.nlim) {
-      atomicAdd(&S.ts1[slot], s1);
-      atomicAdd(&S.ts2[slot], s2);
+    red_add(v + 4u, e.z);
+    red_add(v + 8u, e.w);
+  }
+}
+
+// Exact path (redo_kernel): add one run, with 64-bit side sums for voxels beyond nlim.
+template <bool kVar>
+__device__ __forceinline__ void add_run(const EvalSmem& S, const VoxelConst& vc, unsigned long long* wide, uint32_t key,
+                                        uint32_t n, int s1, uint32_t s2, uint32_t nb) {
+  if (lds32(S.a_key - kFlagFull)) return;  // table already full: the pose restarts
+  const int slot = table_slot(S, key, nb);
+  if (slot < 0) {
+    sts32(S.a_key - kFlagFull, 1u);
+    return;
+  }
+  const uint32_t v = S.a_vals + 12u * (uint32_t)slot;
+  if (kVar) {
+    const uint32_t old = atom_add(v, n);
+    if (old + n <= vc.nlim) {
+      red_add(v + 4u, (uint32_t)s1);
+      red_add(v + 8u, s2);
     } else {
       atomicAdd(&wide[2 * slot], (unsigned long long)(long long)s1);
       atomicAdd(&wide[2 * slot + 1], (unsigned long long)s2);
-      S.flags[3] = 1u;
     }
   } else {
-    atomicAdd(&S.tcnt[slot], n);
+    red_add(v, n);
   }
 }
 
-// Fast path: add a finished run with fire-and-forget 32-bit shared atomics.  A voxel whose
-// count ends above nlim may have wrapped its sums; the table scan sends such a pose to the
-// exact path (redo_kernel).
-template <bool kVar>
-__device__ __forceinline__ void fast_add(const EvalSmem& S, const uint4& e, int T) {
-  if (*(volatile uint32_t*)&S.flags[1]) return;
-  const int slot = table_slot(S, e.x, T);
-  if (slot < 0) {
-    S.flags[1] = 1u;
-    return;
-  }
-  atomicAdd(&S.tcnt[slot], e.y);
-  if (kVar) {
-    atomicAdd(&S.ts1[slot], (int)e.z);
-    atomicAdd(&S.ts2[slot], e.w);
-  }
-}
-
-// Per-warp ring of finished runs: lanes append what they finished at this step; once 32
-// are waiting, the whole warp adds 32 of them to the table at once.
-struct WarpQueue {
-  uint32_t head;
-  uint32_t fill;
-};
-
-template <bool kVar>
-__device__ __forceinline__ void queue_drain(const EvalSmem& S, uint4* ring, WarpQueue& wq, int lane, int T,
-                                            uint32_t count) {
-  __syncwarp();
-  if ((uint32_t)lane < count) fast_add<kVar>(S, ring[(wq.head + (uint32_t)lane) & (kQueue - 1)], T);
-  __syncwarp();
-  wq.head = (wq.head + count) & (kQueue - 1);
-  wq.fill -= count;
-}
-
-template <bool kVar>
-__device__ __forceinline__ void queue_push(const EvalSmem& S, uint4* ring, WarpQueue& wq, int lane, bool has,
-                                           const uint4& e, int T) {
-  const uint32_t m = __ballot_sync(kFull, has);
-  if (m == 0u) return;
-  if (has) ring[(wq.head + wq.fill + (uint32_t)__popc(m & ((1u << lane) - 1u))) & (kQueue - 1)] = e;
-  wq.fill += (uint32_t)__popc(m);
-  if (wq.fill >= 32u) queue_drain<kVar>(S, ring, wq, lane, T, 32u);
-}
-
-// The run of equal keys a thread is walking.  Keys outside the current partition (and
-// points outside the grid) are skipped without ending the run.
+// The run of equal keys a thread is walking.  Points outside the grid (or outside the
+// current key partition) carry kEmptyKey and form runs of their own, which are dropped.
 struct Run {
   uint32_t key;
   uint32_t n;
-  int s1;
+  uint32_t s1;  // two's complement
   uint32_t s2;
 };
 
-// Advance a run by one point; returns true (and the finished run in `fin`) when the key
-// changes.  A run stays below nlim points so that its 32-bit sums cannot overflow.
+// Per-warp ring of finished runs in shared memory: lanes append what they finished at
+// this step (compacted by a ballot); once 32 are waiting the whole warp adds entries
+// 0..31 to the table and moves the rest down, so the ring never wraps.
 template <bool kVar>
-__device__ __forceinline__ bool advance_run(const GridConst& gc, Run& r, uint32_t key, int dz, uint4& fin) {
-  if (key == kEmptyKey) return false;
-  if (key == r.key && (!kVar || r.n < gc.nlim)) {
-    r.n += 1u;
-    if (kVar) {
-      r.s1 += dz;
-      r.s2 += (uint32_t)(dz * dz);
-    }
-    return false;
+__device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count,
+                                           uint32_t nb) {
+  const int lane = (int)(threadIdx.x & 31u);
+  __syncwarp();
+  if ((uint32_t)lane < count) {
+    const uint4 e = lds128(ring + 16u * (uint32_t)lane);
+    if (e.x != kEmptyKey) table_add<kVar>(S, e, nb);
   }
-  const bool done = r.n != 0u;
-  fin = make_uint4(r.key, r.n, (uint32_t)r.s1, r.s2);
-  r.key = key;
-  r.n = 1u;
-  r.s1 = dz;
-  r.s2 = (uint32_t)(dz * dz);
-  return done;
+  // move the entries beyond `count` down, one word at a time (lane l reads entry l + count
+  // and writes entry l, which only it has read)
+  if ((uint32_t)lane + count < fill) {
+    const uint32_t dst = ring + 16u * (uint32_t)lane, src = dst + 16u * count;
+#pragma unroll
+    for (uint32_t w = 0; w < 16u; w += 4u) sts32(dst + w, lds32(src + w));
+  }
+  __syncwarp();
+  fill -= count;
 }
 
-// Exact path (redo_kernel): the run goes straight to the table, with 64-bit side sums
-// for voxels beyond nlim points.
+// Append the finished runs of the lanes with `done` set, then drain if 32 are waiting.
 template <bool kVar>
-__device__ __forceinline__ void step_run(const EvalSmem& S, const GridConst& gc, unsigned long long* wide, Run& r,
-                                         uint32_t key, int dz, int T) {
-  if (key == kEmptyKey) return;
-  // a run stays below nlim points so that its 32-bit sums cannot overflow
-  if (key == r.key && (!kVar || r.n < gc.nlim)) {
-    r.n += 1u;
-    if (kVar) {
-      r.s1 += dz;
-      r.s2 += (uint32_t)(dz * dz);
-    }
-    return;
-  }
-  if (r.n != 0u) add_run<kVar>(S, gc, wide, r.key, r.n, r.s1, r.s2, T);
-  r.key = key;
-  r.n = 1u;
-  r.s1 = dz;
-  r.s2 = (uint32_t)(dz * dz);
+__device__ __forceinline__ void ring_push(const EvalSmem& S, uint32_t ring, uint32_t lane_lt, bool done,
+                                          const Run& r, uint32_t& fill, uint32_t nb) {
+  const uint32_t m = __ballot_sync(kFull, done);
+  if (done) sts128(ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), make_uint4(r.key, r.n, r.s1, r.s2));
+  fill += (uint32_t)__popc(m);
+  if (fill >= 32u) ring_drain<kVar>(S, ring, fill, 32u, nb);
 }
 
 struct PoseRegs {
@@ -285,151 +283,38 @@ struct PoseRegs {
   float t[3];
 };
 
-// Keys of this thread's kPPT points (in registers) under the pose (key partition `part`
-// of 2^lg).
+// Key and dz of one point under the pose; key = kEmptyKey (and dz = 0) outside the grid.
 template <bool kRot>
-__device__ __forceinline__ void regs_keys(const GridConst& gc, const PoseRegs& P, const float4* pts, int lg,
-                                          uint32_t part, uint32_t* key, int* dz) {
+__device__ __forceinline__ void point_key(const VoxelConst& vc, const PoseRegs& P, const float4& p, uint32_t& key,
+                                          int& dz) {
+  if (kRot) {
+    float ux, uy, uz;
+    rotate_point(P.r, p.x, p.y, p.z, ux, uy, uz);
+    dz = 0;
+    key = voxel_key_g(__fadd_rn(ux, P.t[0]), __fadd_rn(uy, P.t[1]), __fadd_rn(uz, P.t[2]), vc.inv_res, vc.X, vc.Y,
+                      vc.Z, vc.res_mm, &dz);
+  } else {
+    // Pre-rotated copies hold finite values or +inf (pack_points_kernel), and host poses
+    // are finite, so g is never NaN: a saturating floor and unsigned compares decide
+    // "inside" exactly as the float compares would.
+    const float gx = __fadd_rn(p.x, P.t[0]);
+    const float gy = __fadd_rn(p.y, P.t[1]);
+    const float gz = __fadd_rn(p.z, P.t[2]);
+    const uint32_t kx = (uint32_t)__float2int_rd(__fmul_rn(gx, vc.inv_res));
+    const uint32_t ky = (uint32_t)__float2int_rd(__fmul_rn(gy, vc.inv_res));
+    const uint32_t kz = (uint32_t)__float2int_rd(__fmul_rn(gz, vc.inv_res));
+    const bool in = (kx < (uint32_t)vc.X) & (ky < (uint32_t)vc.Y) & (kz < (uint32_t)vc.Z);
+    const uint32_t zq = (uint32_t)__float2int_rn(__fmul_rn(gz, 1000.0f));
+    dz = in ? (int)(zq - kz * (uint32_t)vc.res_mm) : 0;
+    key = in ? (kz * (uint32_t)vc.Y + ky) * (uint32_t)vc.X + kx : kEmptyKey;
+  }
+}
+
+__device__ __forceinline__ void load_pose(const float* poses, PoseRegs& P) {
 #pragma unroll
-  for (int j = 0; j < kPPT; ++j) {
-    const float4 p = pts[j];
-    float gx, gy, gz;
-    dz[j] = 0;
-    if (kRot) {
-      float ux, uy, uz;
-      rotate_point(P.r, p.x, p.y, p.z, ux, uy, uz);
-      gx = __fadd_rn(ux, P.t[0]);
-      gy = __fadd_rn(uy, P.t[1]);
-      gz = __fadd_rn(uz, P.t[2]);
-      key[j] = voxel_key_g(gx, gy, gz, gc.inv_res, gc.X, gc.Y, gc.Z, gc.res_mm, &dz[j]);
-    } else {
-      // Pre-rotated copies hold finite values or +inf (pack_points_kernel), and host poses
-      // are finite, so g is never NaN: a saturating floor and unsigned compares decide
-      // "inside" exactly as the float compares would.
-      gx = __fadd_rn(p.x, P.t[0]);
-      gy = __fadd_rn(p.y, P.t[1]);
-      gz = __fadd_rn(p.z, P.t[2]);
-      const int kx = __float2int_rd(__fmul_rn(gx, gc.inv_res));
-      const int ky = __float2int_rd(__fmul_rn(gy, gc.inv_res));
-      const int kz = __float2int_rd(__fmul_rn(gz, gc.inv_res));
-      const bool in = ((uint32_t)kx < (uint32_t)gc.X) & ((uint32_t)ky < (uint32_t)gc.Y) & ((uint32_t)kz < (uint32_t)gc.Z);
-      dz[j] = __float2int_rn(__fmul_rn(gz, 1000.0f)) - kz * gc.res_mm;
-      key[j] = in ? (uint32_t)((kz * gc.Y + ky) * gc.X + kx) : kEmptyKey;
-    }
-    if (lg > 0 && key[j] != kEmptyKey && ((key[j] * 0x85EBCA77u) >> (32 - lg)) != part) key[j] = kEmptyKey;
-  }
-}
-
-// The same for this thread's points of one tile (`pts`: the tile plus the thread index;
-// the thread's points are kThreads apart).
-template <bool kRot>
-__device__ __forceinline__ void tile_keys(const GridConst& gc, const PoseRegs& P, const float4* pts, int lg,
-                                          uint32_t part, uint32_t* key, int* dz) {
-  float4 v[kPPT];
+  for (int i = 0; i < 9; ++i) P.r[i] = __ldg(poses + i);
 #pragma unroll
-  for (int j = 0; j < kPPT; ++j) v[j] = pts[j * kThreads];
-  regs_keys<kRot>(gc, P, v, lg, part, key, dz);
-}
-
-__device__ __forceinline__ void load_pose(const EvalArgs& a, int p, PoseRegs& P) {
-#pragma unroll
-  for (int i = 0; i < 9; ++i) P.r[i] = __ldg(a.poses + 12 * (size_t)p + i);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) P.t[i] = __ldg(a.poses + 12 * (size_t)p + 9 + i);
-}
-
-// Read (and clear) the table after a sweep: symbols, bbox and histogram unless `discard`.
-// The CTA-wide occupied count is added to S.flags[0].
-template <bool kVar, bool kExact>
-__device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& gc, const EvalArgs& a,
-                                           unsigned long long* wide, int T, int K, int p, bool discard) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX, mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
-  uint32_t occupied = 0;
-  for (int s = tid; s < T; s += kThreads) {
-    const uint32_t k = S.tkey[s];
-    if (k == kEmptyKey) continue;
-    ++occupied;
-    const uint64_t n = S.tcnt[s];
-    int64_t s1 = S.ts1[s];
-    uint64_t s2 = S.ts2[s];
-    if (!kExact && kVar && n > gc.nlim) S.flags[3] = 1u;  // sums may have wrapped: exact path
-    if (kExact && kVar && n > gc.nlim) {
-      s1 += (int64_t)wide[2 * s];
-      s2 += wide[2 * s + 1];
-      wide[2 * s] = 0ull;
-      wide[2 * s + 1] = 0ull;
-      if (!discard) atomicAdd(a.wide_count, 1u);
-    }
-    S.tkey[s] = kEmptyKey;
-    S.tcnt[s] = 0u;
-    S.ts1[s] = 0;
-    S.ts2[s] = 0u;
-    if (discard) continue;
-    const int kx = (int)(k % (uint32_t)gc.X);
-    const uint32_t r = k / (uint32_t)gc.X;
-    const int ky = (int)(r % (uint32_t)gc.Y);
-    const int kz = (int)(r / (uint32_t)gc.Y);
-    mn0 = min(mn0, kx); mn1 = min(mn1, ky); mn2 = min(mn2, kz);
-    mx0 = max(mx0, kx); mx1 = max(mx1, ky); mx2 = max(mx2, kz);
-    const int sB = feature_symbol(gc.feature, gc.Lc, gc.Lv, S.ct, S.vt, n, s1, s2);
-    if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
-        kz <= gc.boxA[5])
-      atomicAdd(&S.hist[(int)__ldg(a.symA + k) * K + sB], 1u);
-    if (a.dump != nullptr && p == 0) {
-      a.dump[3 * (size_t)k] = (int64_t)n;
-      a.dump[3 * (size_t)k + 1] = s1;
-      a.dump[3 * (size_t)k + 2] = (int64_t)s2;
-    }
-  }
-  occupied = __reduce_add_sync(kFull, occupied);
-  if (lane == 0 && occupied) atomicAdd(&S.flags[0], occupied);
-  mn0 = __reduce_min_sync(kFull, mn0); mn1 = __reduce_min_sync(kFull, mn1);
-  mn2 = __reduce_min_sync(kFull, mn2); mx0 = __reduce_max_sync(kFull, mx0);
-  mx1 = __reduce_max_sync(kFull, mx1); mx2 = __reduce_max_sync(kFull, mx2);
-  if (lane == 0 && !discard && mn0 != INT_MAX) {
-    atomicMin(&S.box[0], mn0); atomicMin(&S.box[1], mn1); atomicMin(&S.box[2], mn2);
-    atomicMax(&S.box[3], mx0); atomicMax(&S.box[4], mx1); atomicMax(&S.box[5], mx2);
-  }
-}
-
-__device__ __forceinline__ void init_smem(const EvalSmem& S, const GridConst& gc, int T, int KK) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < T; i += kThreads) {
-    S.tkey[i] = kEmptyKey;
-    S.tcnt[i] = 0u;
-    S.ts1[i] = 0;
-    S.ts2[i] = 0u;
-  }
-  for (int i = tid; i < KK; i += kThreads) S.hist[i] = 0u;
-  if (tid < kMaxLevels) {
-    S.ct[tid] = gc.count_thresh[tid];
-    S.vt[tid] = gc.var_thresh[tid];
-  }
-  if (tid == 0) {
-    S.box[0] = S.box[1] = S.box[2] = INT_MAX;
-    S.box[3] = S.box[4] = S.box[5] = INT_MIN;
-    S.flags[0] = S.flags[1] = S.flags[2] = S.flags[3] = 0u;
-  }
-}
-
-// Store the pose's partial histogram and bbox, then reset them for the next pose.
-__device__ __forceinline__ void emit_pose(const EvalSmem& S, const EvalArgs& a, int KK, int p) {
-  const int tid = threadIdx.x;
-  uint32_t* oc = a.out_c + (size_t)p * KK;
-  for (int i = tid; i < KK; i += kThreads) {
-    oc[i] = S.hist[i];
-    S.hist[i] = 0u;
-  }
-  if (tid < 6) a.out_box[6 * (size_t)p + tid] = S.box[tid];
-  __syncthreads();
-  if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
-}
-
-__device__ __forceinline__ void reset_pose(const EvalSmem& S, int KK) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < KK; i += kThreads) S.hist[i] = 0u;
-  if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
+  for (int i = 0; i < 3; ++i) P.t[i] = __ldg(poses + 9 + i);
 }
 
 __device__ __forceinline__ void load_tile(const float4* src, int t, float4* v) {
@@ -437,151 +322,237 @@ __device__ __forceinline__ void load_tile(const float4* src, int t, float4* v) {
   for (int j = 0; j < kPPT; ++j) v[j] = __ldg(src + (size_t)t * kTile + j * kThreads);
 }
 
-// One tile of this thread's stream: keys, run stepping, queueing of finished runs.  A dz
-// outside its proven bound is remembered in `bad` (reported once per sweep).
-template <bool kVar, bool kRot>
-__device__ __forceinline__ void sweep_tile(const EvalSmem& S, const GridConst& gc, const PoseRegs& P,
-                                           const float4* pts, int lg, int pass, Run& run, WarpQueue& wq, uint4* ring,
-                                           int lane, int T, uint32_t& bad) {
-  uint32_t key[kPPT];
-  int dz[kPPT];
-  regs_keys<kRot>(gc, P, pts, lg, (uint32_t)pass, key, dz);
-#pragma unroll
-  for (int j = 0; j < kPPT; ++j) {
-    bad |= (uint32_t)(key[j] != kEmptyKey) & (uint32_t)((uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound));
-    uint4 fin;
-    const bool has = advance_run<kVar>(gc, run, key[j], dz[j], fin);
-    queue_push<kVar>(S, ring, wq, lane, has, fin, T);
+// Make `it` the current item: its grid constants into shared memory.  Called by all
+// threads at a pose boundary.
+__device__ __forceinline__ void select_item(const EvalSmem& S, const EvalArgs& a, int it) {
+  if (*(volatile int32_t*)S.item == it) return;
+  __syncthreads();
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&a.items[it].gc);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(S.gc);
+  for (int i = threadIdx.x; i < kGcWords; i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
+  if (threadIdx.x == 0) *S.item = it;
+  __syncthreads();
+}
+
+// Read (and clear) the table after a sweep: symbols, bbox and histogram unless `discard`.
+// The CTA-wide occupied count is added to S.flags[0].
+template <bool kVar, bool kExact>
+__device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& gc, const EvalItem& I,
+                                           unsigned long long* wide, uint32_t* wide_count, int T, int lp,
+                                           bool discard) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int K = gc.K;
+  int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX, mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
+  uint32_t occupied = 0;
+  for (int s = tid; s < T; s += kThreads) {
+    const uint32_t k = lds32(S.a_key + 4u * (uint32_t)s);
+    if (k == kEmptyKey) continue;
+    ++occupied;
+    const uint32_t v = S.a_vals + 12u * (uint32_t)s;
+    const uint64_t n = lds32(v);
+    int64_t s1 = (int32_t)lds32(v + 4u);
+    uint64_t s2 = lds32(v + 8u);
+    if (!kExact && kVar && n > gc.nlim) sts32(S.a_key - kFlagWide, 1u);  // sums may have wrapped: exact path
+    if (kExact && kVar && n > gc.nlim) {
+      s1 += (int64_t)wide[2 * s];
+      s2 += wide[2 * s + 1];
+      wide[2 * s] = 0ull;
+      wide[2 * s + 1] = 0ull;
+      if (!discard) atomicAdd(wide_count, 1u);
+    }
+    sts32(S.a_key + 4u * (uint32_t)s, kEmptyKey);
+    sts32(v, 0u);
+    sts32(v + 4u, 0u);
+    sts32(v + 8u, 0u);
+    if (discard) continue;
+    const int kx = (int)(k % (uint32_t)gc.X);
+    const uint32_t r = k / (uint32_t)gc.X;
+    const int ky = (int)(r % (uint32_t)gc.Y);
+    const int kz = (int)(r / (uint32_t)gc.Y);
+    mn0 = min(mn0, kx); mn1 = min(mn1, ky); mn2 = min(mn2, kz);
+    mx0 = max(mx0, kx); mx1 = max(mx1, ky); mx2 = max(mx2, kz);
+    const int sB = feature_symbol(gc.feature, gc.Lc, gc.Lv, gc.count_thresh, gc.var_thresh, n, s1, s2);
+    if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
+        kz <= gc.boxA[5])
+      red_add(S.a_hist + 4u * (uint32_t)((int)__ldg(I.symA + k) * K + sB), 1u);
+    if (I.dump != nullptr && lp == 0) {
+      I.dump[3 * (size_t)k] = (int64_t)n;
+      I.dump[3 * (size_t)k + 1] = s1;
+      I.dump[3 * (size_t)k + 2] = (int64_t)s2;
+    }
+  }
+  occupied = __reduce_add_sync(kFull, occupied);
+  if (lane == 0 && occupied) red_add(S.a_key - kFlagOccupied, occupied);
+  mn0 = __reduce_min_sync(kFull, mn0); mn1 = __reduce_min_sync(kFull, mn1);
+  mn2 = __reduce_min_sync(kFull, mn2); mx0 = __reduce_max_sync(kFull, mx0);
+  mx1 = __reduce_max_sync(kFull, mx1); mx2 = __reduce_max_sync(kFull, mx2);
+  if (lane == 0 && !discard && mn0 != INT_MAX) {
+    red_min_s32(S.a_box, mn0); red_min_s32(S.a_box + 4, mn1); red_min_s32(S.a_box + 8, mn2);
+    red_max_s32(S.a_box + 12, mx0); red_max_s32(S.a_box + 16, mx1); red_max_s32(S.a_box + 20, mx2);
   }
 }
 
-template <bool kVar, bool kRot>
-__global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, const EvalArgs a) {
+__device__ __forceinline__ void init_smem(const EvalSmem& S, int T, int KK) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < T; i += kThreads) {
+    S.tkey[i] = kEmptyKey;
+    S.tval[3 * i] = 0u;
+    S.tval[3 * i + 1] = 0u;
+    S.tval[3 * i + 2] = 0u;
+  }
+  for (int i = tid; i < KK; i += kThreads) S.hist[i] = 0u;
+  if (tid == 0) {
+    S.box[0] = S.box[1] = S.box[2] = INT_MAX;
+    S.box[3] = S.box[4] = S.box[5] = INT_MIN;
+    S.flags[0] = S.flags[1] = S.flags[2] = S.flags[3] = 0u;
+    *S.item = -1;
+  }
+}
+
+// Store the pose's partial histogram and bbox, then reset them for the next pose.
+__device__ __forceinline__ void emit_pose(const EvalSmem& S, const EvalItem& I, int lp) {
+  const int tid = threadIdx.x;
+  const int KK = S.gc->K * S.gc->K;
+  uint32_t* oc = I.out_c + (size_t)lp * KK;
+  for (int i = tid; i < KK; i += kThreads) {
+    oc[i] = S.hist[i];
+    S.hist[i] = 0u;
+  }
+  if (tid < 6) I.out_box[6 * (size_t)lp + tid] = S.box[tid];
+  __syncthreads();
+  if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
+  __syncthreads();
+}
+
+__device__ __forceinline__ void reset_pose(const EvalSmem& S) {
+  const int tid = threadIdx.x;
+  const int KK = S.gc->K * S.gc->K;
+  for (int i = tid; i < KK; i += kThreads) S.hist[i] = 0u;
+  if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
+}
+
+__device__ __forceinline__ int item_of(const EvalArgs& a, int gp) { return a.pose_item ? __ldg(a.pose_item + gp) : 0; }
+
+// The item of a pose.  With a single item its fields (and the voxel map constants of the
+// sweep) are read straight from the kernel parameters, which costs no registers.
+template <bool kOne>
+__device__ __forceinline__ const EvalItem& item_at(const EvalArgs& a, int it) {
+  if constexpr (kOne) {
+    return a.one;
+  } else {
+    return a.items[it];
+  }
+}
+
+__device__ __forceinline__ const float4* pose_tiles(const EvalItem& I, int lp) {
+  const int src = I.pose_src ? __ldg(I.pose_src + lp) : 0;
+  return I.src + (size_t)src * I.src_stride;
+}
+
+// One tile of this thread's stream: key, run step, ring append of the finished run.
+// `bad` collects dz + dz_bound of every in-grid point (checked against 2^dz_shift).
+template <bool kVar, bool kRot, bool kPart>
+__device__ __forceinline__ void sweep_tile(const EvalSmem& S, const VoxelConst& vc, const PoseRegs& P,
+                                           const float4* pts, int lg, uint32_t part, Run& run, uint32_t ring,
+                                           uint32_t lane_lt, uint32_t& fill, uint32_t nb, uint32_t& bad) {
+#pragma unroll
+  for (int j = 0; j < kPPT; ++j) {
+    uint32_t key;
+    int dz;
+    point_key<kRot>(vc, P, pts[j], key, dz);
+    if (kPart && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != part) key = kEmptyKey;
+    bad |= (uint32_t)(dz + vc.dz_bound);
+    const bool done = key != run.key;
+    ring_push<kVar>(S, ring, lane_lt, done, run, fill, nb);
+    run.n = (done ? 0u : run.n) + 1u;
+    if (kVar) {
+      run.s1 = (done ? 0u : run.s1) + (uint32_t)dz;
+      run.s2 = (done ? 0u : run.s2) + (uint32_t)(dz * dz);
+    }
+    run.key = key;
+  }
+}
+
+// One pass over all tiles of the pose: every thread streams its own points straight from
+// L2, three tiles ahead.  A run is cut every `cut` tiles so that its 32-bit sums stay
+// below nlim points.  Returns the bad-dz flag.
+template <bool kVar, bool kRot, bool kPart>
+__device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const VoxelConst& vc, const PoseRegs& P,
+                                               const float4* src, int nt, int lg, uint32_t part, uint32_t ring,
+                                               uint32_t lane_lt, uint32_t nb, int cut) {
+  Run run{kEmptyKey, 0u, 0u, 0u};
+  uint32_t fill = 0u, bad = 0u;
+  float4 b0[kPPT], b1[kPPT], b2[kPPT];
+  load_tile(src, 0, b0);
+  load_tile(src, 1, b1);
+  load_tile(src, 2, b2);
+  int next_cut = cut;
+  for (int t = 0; t < nt; t += 3) {
+    if (t >= next_cut) {  // uniform; only when a stream is longer than nlim points
+      ring_push<kVar>(S, ring, lane_lt, true, run, fill, nb);
+      run = Run{kEmptyKey, 0u, 0u, 0u};
+      next_cut += cut;
+    }
+    sweep_tile<kVar, kRot, kPart>(S, vc, P, b0, lg, part, run, ring, lane_lt, fill, nb, bad);
+    if (t + 3 < nt) load_tile(src, t + 3, b0);
+    if (t + 1 < nt) {
+      sweep_tile<kVar, kRot, kPart>(S, vc, P, b1, lg, part, run, ring, lane_lt, fill, nb, bad);
+      if (t + 4 < nt) load_tile(src, t + 4, b1);
+    }
+    if (t + 2 < nt) {
+      sweep_tile<kVar, kRot, kPart>(S, vc, P, b2, lg, part, run, ring, lane_lt, fill, nb, bad);
+      if (t + 5 < nt) load_tile(src, t + 5, b2);
+    }
+  }
+  ring_push<kVar>(S, ring, lane_lt, true, run, fill, nb);
+  while (fill > 0u) ring_drain<kVar>(S, ring, fill, min(fill, 32u), nb);
+  return bad;
+}
+
+template <bool kVar, bool kRot, bool kOne>
+__global__ void __launch_bounds__(kThreads, 1) eval_kernel(const __grid_constant__ EvalArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
   const int T = a.table_slots;
-  const int K = gc.K, KK = K * K;
-  eval_smem_layout(K, T, &S, smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31;
+  eval_smem_layout(a.K, T, &S, smem_raw);
+  const int tid = threadIdx.x;
   const uint32_t cap = (uint32_t)T - (uint32_t)T / 10u;  // above 90% full the table counts as crowded
-  uint4* ring = S.queue + (size_t)(tid >> 5) * kQueue;
+  const uint32_t ring = S.a_queue + (uint32_t)(tid >> 5) * kQueue * 16u;
+  const uint32_t lane_lt = lane_mask_lt();
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
-  const int G = gridDim.x;
 
-  init_smem(S, gc, T, KK);
-  int passes = a.passes0;
-  if (kTmaTiles && tid == 0) {
-    for (int b = 0; b < kStages; ++b) {
-      mbar_init(smem_addr(&S.mbar[b]), 1u);
-      mbar_init(smem_addr(&S.mbar[kStages + b]), (uint32_t)kWarps);
-      S.issue_cnt[b] = 0u;
-    }
-    const int p0 = blockIdx.x;
-    S.sched[0] = 0u;
-    S.sched[1] = (uint32_t)passes * (uint32_t)a.n_tiles;
-    S.sched[2] = pose_source(a, p0);
-    S.sched[3] = pose_source(a, p0 + G < a.P ? p0 + G : p0);
-    fence_mbar_init();
-  }
+  init_smem(S, T, a.K * a.K);
   __syncthreads();
-  if (kTmaTiles && tid == 0)
-    for (int b = 0; b < kStages; ++b) issue_tile(S, a, (uint32_t)b);
+  int passes = a.passes0;
 
-  uint32_t q = 0;  // consumption counter, identical in every warp
-  bool aborted = false;
-
-  for (int p = blockIdx.x; p < a.P && !aborted; p += G) {
-    if (kTmaTiles && p != (int)blockIdx.x) {
-      if (tid == 0) {  // the pose's sweeps start at q; every warp is past the previous pose
-        S.sched[0] = q;
-        S.sched[1] = (uint32_t)passes * (uint32_t)a.n_tiles;
-        S.sched[2] = pose_source(a, p);
-        S.sched[3] = pose_source(a, p + G < a.P ? p + G : p);
-      }
-      __syncthreads();
-    }
+  for (int gp = blockIdx.x; gp < a.P; gp += gridDim.x) {
+    const int it = kOne ? 0 : item_of(a, gp);
+    select_item(S, a, it);
+    const EvalItem& I = item_at<kOne>(a, it);
+    const int lp = gp - I.pose_base;
+    const VoxelConst vc = voxel_const(kOne ? a.one.gc : *S.gc);
+    const int dz_shift = kOne ? a.one.gc.dz_shift : S.gc->dz_shift;
+    const int nt = I.n_tiles;
+    const int cut = max(3, (int)min(vc.nlim / (uint32_t)kPPT, (uint32_t)INT_MAX) / 3 * 3);
     PoseRegs P;
-    load_pose(a, p, P);
+    load_pose(I.poses + 12 * (size_t)lp, P);
+    const float4* src = pose_tiles(I, lp) + tid;
     const int pose_passes = passes;
     const int lg = __ffs(pose_passes) - 1;
     uint32_t max_occupied = 0;
     bool full = false;
     for (int pass = 0; pass < pose_passes; ++pass) {
-      Run run{kEmptyKey, 0u, 0, 0u};
-      WarpQueue wq{0u, 0u};
-      // ---- sweep all tiles of the pose's source array ----
-      if constexpr (kTmaTiles) {
-        for (int t = 0; t < a.n_tiles; ++t, ++q) {
-          const uint32_t b = q % kStages;
-          const uint32_t par = (q / kStages) & 1u;
-          if (*(volatile uint32_t*)&S.flags[2]) continue;  // aborting: no more waits
-          if (!mbar_wait_bounded(smem_addr(&S.mbar[b]), par, kWaitLimitNs)) {
-            atomicOr(a.err, kErrWaitTimeout);
-            S.flags[2] = 1u;
-            continue;
-          }
-          if (!full) {
-            uint32_t key[kPPT];
-            int dz[kPPT];
-            tile_keys<kRot>(gc, P, S.tiles + (size_t)b * kTile + tid, lg, (uint32_t)pass, key, dz);
-  #pragma unroll
-            for (int j = 0; j < kPPT; ++j) {
-              if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
-                atomicOr(a.err, kErrDzBound);
-              uint4 fin;
-              const bool has = advance_run<kVar>(gc, run, key[j], dz[j], fin);
-              queue_push<kVar>(S, ring, wq, lane, has, fin, T);
-            }
-          }
-          __syncwarp();
-          if (lane == 0) {
-            mbar_arrive(smem_addr(&S.mbar[kStages + b]));
-            const uint32_t c = atomicAdd(&S.issue_cnt[b], 1u);
-            if (c == (uint32_t)kWarps - 1u) {  // the last warp done with this buffer refills it
-              S.issue_cnt[b] = 0u;
-              if (mbar_wait_bounded(smem_addr(&S.mbar[kStages + b]), par, kWaitLimitNs)) {
-                issue_tile(S, a, q + kStages);
-              } else {
-                atomicOr(a.err, kErrWaitTimeout);
-                S.flags[2] = 1u;
-              }
-            }
-          }
-        }
-      } else {
-        // every thread streams its own points straight from L2, three tiles ahead
-        const float4* src = a.src + (size_t)pose_source(a, p) * a.src_stride + tid;
-        float4 b0[kPPT], b1[kPPT], b2[kPPT];
-        load_tile(src, 0, b0);
-        load_tile(src, 1, b1);
-        load_tile(src, 2, b2);
-        uint32_t bad = 0u;
-        const int nt = a.n_tiles;
-        for (int t = 0; t < nt && !full; t += 3) {
-          sweep_tile<kVar, kRot>(S, gc, P, b0, lg, pass, run, wq, ring, lane, T, bad);
-          if (t + 3 < nt) load_tile(src, t + 3, b0);
-          if (t + 1 < nt) {
-            sweep_tile<kVar, kRot>(S, gc, P, b1, lg, pass, run, wq, ring, lane, T, bad);
-            if (t + 4 < nt) load_tile(src, t + 4, b1);
-          }
-          if (t + 2 < nt) {
-            sweep_tile<kVar, kRot>(S, gc, P, b2, lg, pass, run, wq, ring, lane, T, bad);
-            if (t + 5 < nt) load_tile(src, t + 5, b2);
-          }
-        }
-        if (bad) atomicOr(a.err, kErrDzBound);
-      }
       if (!full) {
-        queue_push<kVar>(S, ring, wq, lane, run.n != 0u, make_uint4(run.key, run.n, (uint32_t)run.s1, run.s2), T);
-        while (wq.fill > 0u) queue_drain<kVar>(S, ring, wq, lane, T, min(wq.fill, 32u));
+        const uint32_t bad =
+            lg == 0 ? sweep_pose<kVar, kRot, false>(S, vc, P, src, nt, 0, 0u, ring, lane_lt, (uint32_t)a.n_buckets, cut)
+                    : sweep_pose<kVar, kRot, true>(S, vc, P, src, nt, lg, (uint32_t)pass, ring, lane_lt,
+                                                   (uint32_t)a.n_buckets, cut);
+        if (bad >> dz_shift) atomicOr(a.err, kErrDzBound);
       }
       __syncthreads();
-      if (S.flags[2]) {
-        aborted = true;
-        break;
-      }
       full = full || S.flags[1] != 0u;
-      scan_table<kVar, false>(S, gc, a, wide, T, K, p, full);
+      scan_table<kVar, false>(S, kOne ? a.one.gc : *S.gc, I, wide, a.wide_count, T, lp, full);
       __syncthreads();
       max_occupied = max(max_occupied, S.flags[0]);
       full = full || S.flags[3] != 0u;
@@ -591,80 +562,86 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const GridConst gc, c
         S.flags[3] = 0u;
       }
     }
-    if (aborted) break;
     if (full) {
-      // the remaining sweeps of this pose were consumed without work; finish it later
-      reset_pose(S, KK);
+      // finished later by the exact path
+      reset_pose(S);
       if (tid == 0) {
         S.flags[1] = 0u;
-        a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)p;
+        a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)gp;
       }
       if (passes < kMaxPasses) passes *= 2;
       __syncthreads();
       continue;
     }
-    emit_pose(S, a, KK, p);
+    emit_pose(S, I, lp);
     if (max_occupied > cap && passes < kMaxPasses) passes *= 2;  // crowded: more partitions next
   }
-
-  // Drain the prefetched tiles still in flight before the CTA's shared memory is released.
-  __syncthreads();
-  if (tid == 0) {
-    if (!aborted) atomicMax(a.max_passes, (uint32_t)passes);
-    for (int i = 0; kTmaTiles && i < kStages; ++i) {
-      const uint32_t qq = q + (uint32_t)i;
-      if (!mbar_wait_bounded(smem_addr(&S.mbar[qq % kStages]), (qq / kStages) & 1u, kWaitLimitNs))
-        atomicOr(a.err, kErrWaitTimeout);
-    }
-  }
+  if (tid == 0) atomicMax(a.max_passes, (uint32_t)passes);
 }
 
-// Poses whose table filled up in eval_kernel: plain loads (no prefetch ring), and on a full
-// table the pose simply restarts with twice the key partitions.
+// Poses that eval_kernel could not finish: plain sweeps; each run goes straight into the
+// table with 64-bit side sums for voxels beyond the 32-bit bound; a full table restarts
+// the pose with twice the key partitions.
 template <bool kVar, bool kRot>
-__global__ void __launch_bounds__(kThreads, 1) redo_kernel(const GridConst gc, const EvalArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) redo_kernel(const __grid_constant__ EvalArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
   const int T = a.table_slots;
-  const int K = gc.K, KK = K * K;
-  eval_smem_layout(K, T, &S, smem_raw);
+  eval_smem_layout(a.K, T, &S, smem_raw);
   const int tid = threadIdx.x;
+  const uint32_t nb = (uint32_t)T >> 2;
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
   const uint32_t n_redo = *(volatile const uint32_t*)a.redo_count;
   if (blockIdx.x >= n_redo) return;
-  init_smem(S, gc, T, KK);
+  init_smem(S, T, a.K * a.K);
   __syncthreads();
   int passes = 2 * (int)*(volatile const uint32_t*)a.max_passes;
   if (passes < 2) passes = 2;
   if (passes > kMaxPasses) passes = kMaxPasses;
   for (uint32_t i = blockIdx.x; i < n_redo; i += gridDim.x) {
-    const int p = (int)a.redo_list[i];
+    const int gp = (int)a.redo_list[i];
+    const int it = item_of(a, gp);
+    select_item(S, a, it);
+    const EvalItem& I = a.items[it];
+    const int lp = gp - I.pose_base;
+    const VoxelConst vc = voxel_const(*S.gc);
     PoseRegs P;
-    load_pose(a, p, P);
-    const float4* src = a.src + (size_t)pose_source(a, p) * a.src_stride;
+    load_pose(I.poses + 12 * (size_t)lp, P);
+    const float4* src = pose_tiles(I, lp) + tid;
     int pass = 0;
     while (pass < passes) {
       const int lg = __ffs(passes) - 1;
-      Run run{kEmptyKey, 0u, 0, 0u};
-      for (int t = 0; t < a.n_tiles; ++t) {
-        uint32_t key[kPPT];
-        int dz[kPPT];
-        tile_keys<kRot>(gc, P, src + (size_t)t * kTile + tid, lg, (uint32_t)pass, key, dz);
+      Run run{kEmptyKey, 0u, 0u, 0u};
+      uint32_t bad = 0u;
+      for (int t = 0; t < I.n_tiles; ++t) {
+        float4 v[kPPT];
+        load_tile(src, t, v);
 #pragma unroll
         for (int j = 0; j < kPPT; ++j) {
-          if (key[j] != kEmptyKey && (uint32_t)(dz[j] + gc.dz_bound) > (uint32_t)(2 * gc.dz_bound))
-            atomicOr(a.err, kErrDzBound);
-          step_run<kVar>(S, gc, wide, run, key[j], dz[j], T);
+          uint32_t key;
+          int dz;
+          point_key<kRot>(vc, P, v[j], key, dz);
+          if (key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != (uint32_t)pass) key = kEmptyKey;
+          bad |= (uint32_t)((uint32_t)(dz + vc.dz_bound) > (uint32_t)(2 * vc.dz_bound));
+          if (key != run.key || (kVar && run.n >= vc.nlim)) {
+            if (run.key != kEmptyKey && run.n != 0u)
+              add_run<kVar>(S, vc, wide, run.key, run.n, (int)run.s1, run.s2, nb);
+            run = Run{key, 0u, 0u, 0u};
+          }
+          run.n += 1u;
+          run.s1 += (uint32_t)dz;
+          run.s2 += (uint32_t)(dz * dz);
         }
       }
-      if (run.n != 0u) add_run<kVar>(S, gc, wide, run.key, run.n, run.s1, run.s2, T);
+      if (bad) atomicOr(a.err, kErrDzBound);
+      if (run.key != kEmptyKey && run.n != 0u) add_run<kVar>(S, vc, wide, run.key, run.n, (int)run.s1, run.s2, nb);
       __syncthreads();
       const bool full = S.flags[1] != 0u;
-      scan_table<kVar, true>(S, gc, a, wide, T, K, p, full);
+      scan_table<kVar, true>(S, *S.gc, I, wide, a.wide_count, T, lp, full);
       __syncthreads();
       if (tid == 0) S.flags[0] = 0u;
       if (full) {
-        reset_pose(S, KK);
+        reset_pose(S);
         if (tid == 0) S.flags[1] = 0u;
         if (passes >= kMaxPasses) {
           if (tid == 0) atomicOr(a.err, kErrPassLimit);
@@ -678,19 +655,19 @@ __global__ void __launch_bounds__(kThreads, 1) redo_kernel(const GridConst gc, c
       ++pass;
       __syncthreads();
     }
-    emit_pose(S, a, KK, p);
-    __syncthreads();
+    emit_pose(S, I, lp);
   }
   if (tid == 0) atomicMax(a.max_passes, (uint32_t)passes);
 }
 
-// xyz -> float4 tiles (NaN padding), optionally one rotated copy per rotation.  Tile t,
-// position j*kThreads + s holds point s*L + kPPT*t + j of B (L = kPPT * tiles): stream s
-// visits consecutive points of B, kPPT per tile.
+// xyz -> float4 tiles, optionally one rotated copy per rotation.  Tile t, position
+// j*kThreads + s holds point s*L + kPPT*t + j of B (L = kPPT * tiles): stream s visits
+// consecutive points of B, kPPT per tile.
 __global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int64_t n_out,
                                    const float* __restrict__ rots, float4* out) {
   const int r = blockIdx.y;
   const float nan = __int_as_float(0x7fc00000);
+  const float inf = __int_as_float(0x7f800000);
   float R[9];
   if (rots != nullptr)
     for (int i = 0; i < 9; ++i) R[i] = rots[9 * r + i];
@@ -703,7 +680,7 @@ __global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int
     const int sidx = pos - j * kThreads;
     const int64_t src = (int64_t)sidx * L + (int64_t)kPPT * t + j;
     // padding: NaN for raw tiles (the in-kernel rotation keeps NaN), +inf for rotated copies
-    const float pad = rots != nullptr ? __int_as_float(0x7f800000) : nan;
+    const float pad = rots != nullptr ? inf : nan;
     float4 v = make_float4(pad, pad, pad, 0.0f);
     if (src < n) {
       const float x = xyz[3 * src], y = xyz[3 * src + 1], z = xyz[3 * src + 2];
@@ -711,9 +688,7 @@ __global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int
         rotate_point(R, x, y, z, v.x, v.y, v.z);
         // a non-finite coordinate can only come from a non-finite point (or an overflow),
         // which the voxel map drops under every pose; +inf keeps it dropped
-        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) v = make_float4(__int_as_float(0x7f800000),
-                                                                               __int_as_float(0x7f800000),
-                                                                               __int_as_float(0x7f800000), 0.0f);
+        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) v = make_float4(inf, inf, inf, 0.0f);
       } else {
         v.x = x;
         v.y = y;
@@ -751,14 +726,17 @@ __device__ __forceinline__ float neg_plogp(uint64_t c, float N) {
   return -q * logf(q);
 }
 
-__global__ void __launch_bounds__(kComposeThreads) compose_kernel(const GridConst gc, const ComposeArgs a) {
+__global__ void __launch_bounds__(kComposeThreads) compose_kernel(const __grid_constant__ EvalArgs a) {
   __shared__ uint32_t h[kMaxSymbols * kMaxSymbols];
   __shared__ long long cntA[kMaxSymbols];
   __shared__ float red[kComposeThreads / 32];
-  const int p = blockIdx.x;
+  const int gp = blockIdx.x;
   const int tid = threadIdx.x;
+  const EvalItem& I = a.items[item_of(a, gp)];
+  const GridConst& gc = I.gc;
+  const int lp = gp - I.pose_base;
   const int K = gc.K, KK = K * K;
-  const int32_t* bb = a.boxB + 6 * (size_t)p;
+  const int32_t* bb = I.out_box + 6 * (size_t)lp;
   int lo[3], hi[3];
   bool empty = false;
 #pragma unroll
@@ -768,11 +746,11 @@ __global__ void __launch_bounds__(kComposeThreads) compose_kernel(const GridCons
     empty |= lo[i] > hi[i];
   }
   const long long N = empty ? 0 : (long long)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
-  for (int i = tid; i < KK; i += kComposeThreads) h[i] = empty ? 0u : a.c[(size_t)p * KK + i];
+  for (int i = tid; i < KK; i += kComposeThreads) h[i] = empty ? 0u : I.out_c[(size_t)lp * KK + i];
   if (!empty && tid >= 1 && tid < K) {
     // count of A symbol `tid` over the box from its 3-D prefix sums (8 corners)
     const int X1 = gc.X + 1, Y1 = gc.Y + 1;
-    const int32_t* S = a.sat + (size_t)(tid - 1) * (size_t)(gc.Z + 1) * Y1 * X1;
+    const int32_t* S = I.sat + (size_t)(tid - 1) * (size_t)(gc.Z + 1) * Y1 * X1;
     const int x0 = lo[0], y0 = lo[1], z0 = lo[2], x1 = hi[0] + 1, y1 = hi[1] + 1, z1 = hi[2] + 1;
     cntA[tid] = sat_at(S, X1, Y1, x1, y1, z1) - sat_at(S, X1, Y1, x0, y1, z1) - sat_at(S, X1, Y1, x1, y0, z1) -
                 sat_at(S, X1, Y1, x1, y1, z0) + sat_at(S, X1, Y1, x0, y0, z1) + sat_at(S, X1, Y1, x0, y1, z0) +
@@ -807,38 +785,41 @@ __global__ void __launch_bounds__(kComposeThreads) compose_kernel(const GridCons
   hy = block_sum_fixed(hy, red);
   const float mi = empty ? 0.0f : (hx + hy) - hxy;
   if (tid == 0) {
-    a.mi[p] = mi;
+    I.mi[lp] = mi;
     const uint32_t u = __float_as_uint(mi);
     const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    atomicMax(a.best, ((unsigned long long)ord << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)p));
+    atomicMax(I.best, ((unsigned long long)ord << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)lp));
   }
-  if (a.hist != nullptr)
-    for (int i = tid; i < KK; i += kComposeThreads) a.hist[(size_t)p * KK + i] = h[i];
+  if (I.hist != nullptr)
+    for (int i = tid; i < KK; i += kComposeThreads) I.hist[(size_t)lp * KK + i] = h[i];
 }
 
-__global__ void argmax_finalize_kernel(const unsigned long long* best, int64_t* out) {
-  const unsigned long long b = *best;
-  *out = (b == 0ull) ? -1 : (int64_t)(0xFFFFFFFFu - (uint32_t)(b & 0xFFFFFFFFull));
+__global__ void argmax_finalize_kernel(const EvalItem* items, int n_items) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_items) return;
+  const unsigned long long b = *items[i].best;
+  *items[i].argmax = (b == 0ull) ? -1 : (int64_t)(0xFFFFFFFFu - (uint32_t)(b & 0xFFFFFFFFull));
 }
 
 template <bool kVar, bool kRot>
-cudaError_t launch_eval_t(const GridConst& gc, const EvalArgs& a, int n_ctas, size_t smem, cudaStream_t s) {
-  cudaError_t e =
-      cudaFuncSetAttribute(eval_kernel<kVar, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_eval_t(const EvalArgs& a, int n_ctas, size_t smem, cudaStream_t s) {
+  auto* k = a.n_items == 1 ? eval_kernel<kVar, kRot, true> : eval_kernel<kVar, kRot, false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(redo_kernel<kVar, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  eval_kernel<kVar, kRot><<<n_ctas, kThreads, smem, s>>>(gc, a);
+  k<<<n_ctas, kThreads, smem, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  redo_kernel<kVar, kRot><<<n_ctas, kThreads, smem, s>>>(gc, a);
+  redo_kernel<kVar, kRot><<<n_ctas, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 int eval_tile_points() { return kTile; }
-int eval_min_tiles() { return kStages; }
+int eval_min_tiles() { return kMinTiles; }
+int eval_threads() { return kThreads; }
 
 size_t eval_smem_bytes(int K, int table_slots) { return eval_smem_layout(K, table_slots, nullptr, nullptr); }
 
@@ -848,14 +829,11 @@ int eval_table_slots_for(int K, size_t smem_budget) {
   return lo;
 }
 
-cudaError_t launch_eval(const GridConst& gc, const EvalArgs& a, int n_ctas, bool rotate, cudaStream_t s) {
-  const size_t smem = eval_smem_bytes(gc.K, a.table_slots);
-  const bool var = !(gc.feature == 0 && a.dump == nullptr);  // the count feature needs no z sums
+cudaError_t launch_eval(const EvalArgs& a, int n_ctas, bool var, bool rotate, cudaStream_t s) {
+  const size_t smem = eval_smem_bytes(a.K, a.table_slots);
   if (var)
-    return rotate ? launch_eval_t<true, true>(gc, a, n_ctas, smem, s)
-                  : launch_eval_t<true, false>(gc, a, n_ctas, smem, s);
-  return rotate ? launch_eval_t<false, true>(gc, a, n_ctas, smem, s)
-                : launch_eval_t<false, false>(gc, a, n_ctas, smem, s);
+    return rotate ? launch_eval_t<true, true>(a, n_ctas, smem, s) : launch_eval_t<true, false>(a, n_ctas, smem, s);
+  return rotate ? launch_eval_t<false, true>(a, n_ctas, smem, s) : launch_eval_t<false, false>(a, n_ctas, smem, s);
 }
 
 cudaError_t launch_pack_points(const float* xyz, int64_t n, int64_t n_out, const float* rots, int n_rot, float4* out,
@@ -869,14 +847,15 @@ cudaError_t launch_pack_points(const float* xyz, int64_t n, int64_t n_out, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_compose(const GridConst& gc, const ComposeArgs& a, cudaStream_t s) {
+cudaError_t launch_compose(const EvalArgs& a, cudaStream_t s) {
   if (a.P <= 0) return cudaSuccess;
-  compose_kernel<<<a.P, kComposeThreads, 0, s>>>(gc, a);
+  compose_kernel<<<a.P, kComposeThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_argmax_finalize(const unsigned long long* best, int64_t* out, cudaStream_t s) {
-  argmax_finalize_kernel<<<1, 1, 0, s>>>(best, out);
+cudaError_t launch_argmax_finalize(const EvalItem* items, int n_items, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  argmax_finalize_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(items, n_items);
   return cudaGetLastError();
 }
 

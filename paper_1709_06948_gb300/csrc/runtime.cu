@@ -86,7 +86,7 @@ struct align_grid {
   DevBuf symA, sat;
   // evaluation workspace
   DevBuf xyz, poses, out_c, out_box, mi, hist, best, argmax, err, max_passes, wide_count, wide, dump;
-  DevBuf pts4, pose_src, rots, redo_list, redo_count;
+  DevBuf pts4, pose_src, rots, redo_list, redo_count, items;
   int64_t n_points = 0;  // points staged in `xyz`
   int32_t passes_seed = 1;
   int64_t stats[5] = {0, 0, 0, 0, 0};
@@ -219,7 +219,11 @@ align_status validate_desc(const align_grid_desc* d, GridConst* gc) {
   // 1000 * k_z * res when res is not exactly a whole number of mm in binary.
   const double drift = std::fabs(mm - (double)res_mm) * (double)gc->Z;
   gc->dz_bound = (int32_t)(res_mm + 4 + (int64_t)std::ceil(drift));
-  const uint64_t D = (uint64_t)gc->dz_bound;
+  int m = 0;
+  while ((1 << m) <= 2 * gc->dz_bound) ++m;
+  gc->dz_shift = m;
+  // the sweep's check accepts dz in [-dz_bound, 2^m - 1 - dz_bound]
+  const uint64_t D = (uint64_t)((1 << m) - 1 - gc->dz_bound);
   gc->nlim = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull / (D * D), 0x7FFFFFFFull / D);
   for (int i = 0; i < 3; ++i) gc->boxA[i] = INT_MAX, gc->boxA[3 + i] = INT_MIN;
   return ALIGN_OK;
@@ -349,25 +353,43 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
                         g->pts4.as<float4>(), g->stream),
      "launch pack");
 
+  EvalItem item{};
+  item.gc = g->gc;
+  item.symA = g->symA.as<uint8_t>();
+  item.sat = g->sat.as<int32_t>();
+  item.src = g->pts4.as<float4>();
+  item.src_stride = (uint64_t)n_pad;
+  item.pose_src = rotate ? nullptr : g->pose_src.as<int32_t>();
+  item.poses = d_poses;
+  item.n_tiles = n_tiles;
+  item.P = (int32_t)P;
+  item.pose_base = 0;
+  item.out_c = g->out_c.as<uint32_t>();
+  item.out_box = g->out_box.as<int32_t>();
+  item.mi = out.mi;
+  item.hist = out.hist;
+  item.best = g->best.as<unsigned long long>();
+  item.argmax = out.argmax;
+  item.dump = out.dump;
+  CU(g->items.ensure(sizeof(EvalItem)), "allocate item table");
+  CU(cudaMemcpyAsync(g->items.p, &item, sizeof(EvalItem), cudaMemcpyHostToDevice, g->stream), "copy item table");
+
   EvalArgs a{};
-  a.src = g->pts4.as<float4>();
-  a.src_stride = (size_t)n_pad;
-  a.pose_src = rotate ? nullptr : g->pose_src.as<int32_t>();
-  a.n_tiles = n_tiles;
-  a.poses = d_poses;
+  a.one = item;
+  a.items = g->items.as<EvalItem>();
+  a.pose_item = nullptr;
+  a.n_items = 1;
   a.P = (int32_t)P;
-  a.symA = g->symA.as<uint8_t>();
-  a.out_c = g->out_c.as<uint32_t>();
-  a.out_box = g->out_box.as<int32_t>();
+  a.K = K;
+  a.table_slots = g->table_slots;
+  a.n_buckets = g->table_slots / 4;
+  a.passes0 = g->passes_seed;
   a.err = g->err.as<uint32_t>();
   a.max_passes = g->max_passes.as<uint32_t>();
   a.wide_count = g->wide_count.as<uint32_t>();
   a.wide = g->wide.as<unsigned long long>();
   a.redo_list = g->redo_list.as<uint32_t>();
   a.redo_count = g->redo_count.as<uint32_t>();
-  a.table_slots = g->table_slots;
-  a.passes0 = g->passes_seed;
-  a.dump = out.dump;
   std::array<cudaEvent_t, 3> evs{};
   if (g->profiling) {
     if (g->ev_pool.empty()) {
@@ -378,19 +400,11 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
     }
     CU(cudaEventRecord(evs[0], g->stream), "record event");
   }
-  CU(launch_eval(g->gc, a, n_ctas, rotate, g->stream), "launch eval kernel");
+  const bool var = g->gc.feature != ALIGN_FEAT_COUNT || out.dump != nullptr;
+  CU(launch_eval(a, n_ctas, var, rotate, g->stream), "launch eval kernel");
   if (g->profiling) CU(cudaEventRecord(evs[1], g->stream), "record event");
-
-  ComposeArgs c{};
-  c.c = g->out_c.as<uint32_t>();
-  c.boxB = g->out_box.as<int32_t>();
-  c.sat = g->sat.as<int32_t>();
-  c.P = (int32_t)P;
-  c.mi = out.mi;
-  c.hist = out.hist;
-  c.best = g->best.as<unsigned long long>();
-  CU(launch_compose(g->gc, c, g->stream), "launch compose kernel");
-  CU(launch_argmax_finalize(g->best.as<unsigned long long>(), out.argmax, g->stream), "launch argmax");
+  CU(launch_compose(a, g->stream), "launch compose kernel");
+  CU(launch_argmax_finalize(a.items, 1, g->stream), "launch argmax");
   if (g->profiling) {
     CU(cudaEventRecord(evs[2], g->stream), "record event");
     g->ev_pending.push_back(evs);
@@ -487,7 +501,7 @@ align_status align_destroy_grid(align_grid* g) {
   cudaStreamSynchronize(g->stream);
   for (DevBuf* b : {&g->symA, &g->sat, &g->xyz, &g->poses, &g->out_c, &g->out_box, &g->mi, &g->hist, &g->best,
                     &g->argmax, &g->err, &g->max_passes, &g->wide_count, &g->wide, &g->dump, &g->pts4,
-                    &g->pose_src, &g->rots, &g->redo_list, &g->redo_count})
+                    &g->pose_src, &g->rots, &g->redo_list, &g->redo_count, &g->items})
     b->release();
   for (auto* v : {&g->ev_pending, &g->ev_pool})
     for (auto& evs : *v)
