@@ -187,6 +187,55 @@ align_status align_profile(align_grid* grid, int32_t mode, double out[3]);
 align_status align_reference_noalloc(const align_grid_desc* desc, const float* xyzA, int64_t nA,
                                      uint8_t* symA, int32_t* boxA, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------
+   Batching: many scan pairs, each with its own grid (reference scan A resident) and its
+   own pose batch, evaluated in one persistent launch (Algorithm 1's MI evaluation for
+   every pair and pose; Eqs. 1-5).  Results are identical to align_eval_mi on each pair.
+   --------------------------------------------------------------------------------- */
+typedef struct align_pair {
+  align_grid* grid;        /* reference set; every grid of a batch on the batch's device */
+  const float* xyzB;       /* nB x 3 fp32 (device with ALIGN_XYZ_DEVICE) */
+  int64_t nB;
+  const float* poses12;    /* P x 12 fp32 (device with ALIGN_POSES_DEVICE), or NULL */
+  const double* eta6;      /* P x 6 FP64 host, or NULL; exactly one of the two when P > 0 */
+  int64_t P;
+  float* mi_out;           /* P (device with ALIGN_OUT_DEVICE) */
+  int64_t* argmax_out;     /* 1 or NULL: index of the largest MI, lowest on ties, -1 if P == 0 */
+} align_pair;
+
+typedef struct align_batch align_batch;
+
+/* Extra flags of align_eval_batch. */
+enum {
+  ALIGN_BATCH_GRAPH = 8,   /* capture the launch sequence as a CUDA graph; replay it while
+                              the batch keeps its shape (pairs, sizes, grids) */
+  ALIGN_BATCH_TUNE = 16    /* pick the kernel shape by timing the candidates on this batch;
+                              the choice is cached per batch class (and in the file named by
+                              the environment variable ALIGN_TUNE_CACHE, if set) */
+};
+
+/* A batch owns its device workspace, a CUDA stream of its own (graphs cannot be captured
+   on the legacy default stream) and its graph.  Work queued on cuda_stream before a call
+   (e.g. the producer of device inputs) is ordered before the batch's work. */
+align_status align_batch_create(void* cuda_stream, align_batch** out);
+align_status align_batch_destroy(align_batch* b);
+
+/* Evaluate every pair's poses in one persistent launch (plus packing, composition and
+   argmax launches).  Inputs are copied into the batch's workspace first, so the caller's
+   buffers may be reused when the call returns; the call waits for the results.  Pairs
+   with P == 0 get argmax -1.  ALIGN_E_INVALID for bad arguments, ALIGN_E_NOREF if a grid
+   has no reference, ALIGN_E_OOM / ALIGN_E_CUDA as usual. */
+align_status align_eval_batch(align_batch* b, const align_pair* pairs, int32_t n_pairs, int flags);
+
+/* Fix the kernel shape (0..2, see align_batch_stats) or return to the default (-1). */
+align_status align_batch_set_shape(align_batch* b, int32_t shape);
+
+/* Counters: [0] batch launches, [1] graph captures, [2] graph replays, [3] kernel shape of
+   the last launch (0: 1024 threads x 1 point per tile, 1: 1024 x 2, 2: 512 x 1 with two
+   CTAs per SM), [4] table slots per CTA, [5] kernels launched by the library, [6] device
+   time of the last launch in microseconds (pack to argmax), [7] tuner trials run. */
+align_status align_batch_stats(const align_batch* b, int64_t out[8]);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* align_last_error(void);
 

@@ -20,6 +20,7 @@ ALIGN_E_INVALID, ALIGN_E_OOM, ALIGN_E_CUDA, ALIGN_E_BUSY, ALIGN_E_TIMEOUT, ALIGN
     -1, -2, -3, -4, -5, -6, -7)
 ALIGN_FEAT_COUNT, ALIGN_FEAT_ZVAR, ALIGN_FEAT_COUNT_ZVAR = 0, 1, 2
 ALIGN_XYZ_DEVICE, ALIGN_POSES_DEVICE, ALIGN_OUT_DEVICE = 1, 2, 4
+ALIGN_BATCH_GRAPH, ALIGN_BATCH_TUNE = 8, 16
 
 _STATUS_NAMES = {0: "ALIGN_OK", 1: "ALIGN_NOT_READY", -1: "ALIGN_E_INVALID", -2: "ALIGN_E_OOM", -3: "ALIGN_E_CUDA",
                  -4: "ALIGN_E_BUSY", -5: "ALIGN_E_TIMEOUT", -6: "ALIGN_E_NOREF", -7: "ALIGN_E_INTERNAL"}
@@ -27,7 +28,8 @@ _STATUS_NAMES = {0: "ALIGN_OK", 1: "ALIGN_NOT_READY", -1: "ALIGN_E_INVALID", -2:
 # Every entry point include/align.h declares (checked by the tests against the .so).
 EXPORTS = ["align_create_grid", "align_destroy_grid", "align_grid_info", "align_set_reference",
            "align_get_reference", "align_round_poses", "align_eval_mi", "align_accumulate", "align_search",
-           "align_search_ex", "align_eval_stats", "align_profile", "align_reference_noalloc", "align_last_error"]
+           "align_search_ex", "align_eval_stats", "align_profile", "align_reference_noalloc", "align_batch_create",
+           "align_batch_destroy", "align_eval_batch", "align_batch_set_shape", "align_batch_stats", "align_last_error"]
 
 
 class AlignError(RuntimeError):
@@ -40,6 +42,11 @@ class GridDesc(C.Structure):
     _fields_ = [("origin", C.c_float * 3), ("res_m", C.c_float), ("dims", C.c_int32 * 3), ("feature", C.c_int32),
                 ("count_levels", C.c_int32), ("var_levels", C.c_int32), ("count_thresh", C.c_void_p),
                 ("var_thresh", C.c_void_p)]
+
+
+class AlignPair(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("xyzB", C.c_void_p), ("nB", C.c_int64), ("poses12", C.c_void_p),
+                ("eta6", C.c_void_p), ("P", C.c_int64), ("mi_out", C.c_void_p), ("argmax_out", C.c_void_p)]
 
 
 _lib = None
@@ -75,6 +82,11 @@ def load(build_if_missing: bool = True):
         "align_eval_stats": [P, P],
         "align_profile": [P, i32, P],
         "align_reference_noalloc": [P, P, i64, P, P, P],
+        "align_batch_create": [P, P],
+        "align_batch_destroy": [P],
+        "align_eval_batch": [P, P, i32, C.c_int],
+        "align_batch_set_shape": [P, i32],
+        "align_batch_stats": [P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -334,3 +346,131 @@ def align_reference_noalloc(desc_kw: dict, xyzA, symA_out, boxA_out, stream=None
     _check(lib.align_reference_noalloc(C.byref(d), C.c_void_p(xyzA.data_ptr()), int(xyzA.shape[0]),
                                        C.c_void_p(symA_out.data_ptr()), C.c_void_p(boxA_out.data_ptr()),
                                        C.c_void_p(raw)))
+
+
+# ---------------------------------------------------------------------------------------
+# batching: many scan pairs in one persistent launch
+# ---------------------------------------------------------------------------------------
+def _stream_raw(stream):
+    stream_obj = stream
+    if stream is None:
+        try:
+            import torch
+            stream_obj = torch.cuda.current_stream() if torch.cuda.is_available() else None
+        except Exception:
+            stream_obj = None
+    raw = 0
+    if stream_obj is not None:
+        raw = stream_obj if isinstance(stream_obj, int) else int(stream_obj.cuda_stream)
+    return raw, stream_obj
+
+
+class Batch:
+    """Owns an align_batch* (device workspace, captured graph)."""
+
+    def __init__(self, handle, stream_obj):
+        self._h = handle
+        self._stream_obj = stream_obj
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().align_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def align_batch_create(stream=None) -> Batch:
+    raw, obj = _stream_raw(stream)
+    h = C.c_void_p()
+    _check(load().align_batch_create(C.c_void_p(raw), C.byref(h)))
+    return Batch(h, obj)
+
+
+def align_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def align_eval_batch(batch: Batch, pairs, graph=False, tune=False, out=None):
+    """Evaluate many pairs in one launch.  `pairs`: sequence of (grid, xyzB, eta6) or
+    (grid, xyzB, None, poses12).  Host inputs -> list of (mi np.float32[P], argmax int).
+    With CUDA tensors for the points (all pairs), the poses (all pairs) or `out` (a list of
+    (mi, argmax) CUDA tensors), those buffers are device memory."""
+    lib = load()
+    n = len(pairs)
+    arr = (AlignPair * max(n, 1))()
+    keep = []
+    flags = (ALIGN_BATCH_GRAPH if graph else 0) | (ALIGN_BATCH_TUNE if tune else 0)
+    results = []
+    dev_pts = n > 0 and all(_is_torch_cuda(p[1]) for p in pairs)
+    dev_poses = n > 0 and all(len(p) > 3 and p[3] is not None and _is_torch_cuda(p[3]) for p in pairs)
+    if dev_pts:
+        flags |= ALIGN_XYZ_DEVICE
+    if dev_poses:
+        flags |= ALIGN_POSES_DEVICE
+    if out is not None:
+        flags |= ALIGN_OUT_DEVICE
+    for i, p in enumerate(pairs):
+        grid, xyz = p[0], p[1]
+        eta6 = p[2] if len(p) > 2 else None
+        poses12 = p[3] if len(p) > 3 else None
+        pptr, nB, fl, kp = _points_arg(xyz)
+        if bool(fl & ALIGN_XYZ_DEVICE) != dev_pts:
+            raise ValueError("points must be all host arrays or all CUDA tensors")
+        keep.append(kp)
+        arr[i].grid = grid.handle
+        arr[i].xyzB = pptr
+        arr[i].nB = nB
+        if (eta6 is None) == (poses12 is None):
+            raise ValueError("give exactly one of eta6 and poses12 per pair")
+        if eta6 is not None:
+            if dev_poses:
+                raise ValueError("eta6 is host memory; give poses12 tensors for every pair")
+            eh = _host(eta6, np.float64, (6,))
+            keep.append(eh)
+            arr[i].eta6 = eh.ctypes.data
+            arr[i].P = int(eh.shape[0])
+        elif dev_poses:
+            arr[i].poses12 = poses12.data_ptr()
+            arr[i].P = int(poses12.numel() // 12)
+        else:
+            ph = _host(poses12, np.float32, (12,))
+            keep.append(ph)
+            arr[i].poses12 = ph.ctypes.data
+            arr[i].P = int(ph.shape[0])
+        if out is not None:
+            mi_t, am_t = out[i]
+            arr[i].mi_out = mi_t.data_ptr()
+            arr[i].argmax_out = None if am_t is None else am_t.data_ptr()
+            results.append((mi_t, am_t))
+        else:
+            mi = np.empty(int(arr[i].P), dtype=np.float32)
+            am = np.full(1, -1, dtype=np.int64)
+            arr[i].mi_out = mi.ctypes.data
+            arr[i].argmax_out = am.ctypes.data
+            results.append((mi, am))
+    _check(lib.align_eval_batch(batch.handle, arr, n, flags))
+    del keep
+    if out is not None:
+        return results
+    return [(mi, int(am[0])) for mi, am in results]
+
+
+def align_batch_set_shape(batch: Batch, shape: int):
+    _check(load().align_batch_set_shape(batch.handle, int(shape)))
+
+
+def align_batch_stats(batch: Batch):
+    out = np.zeros(8, dtype=np.int64)
+    _check(load().align_batch_stats(batch.handle, out.ctypes.data_as(C.c_void_p)))
+    keys = ["launches", "graph_captures", "graph_replays", "shape", "table_slots", "kernel_launches",
+            "last_us", "tuner_trials"]
+    return {k: int(v) for k, v in zip(keys, out)}

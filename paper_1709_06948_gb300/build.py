@@ -32,8 +32,30 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+# eval.cu is compiled once per kernel shape (threads per CTA, points per thread per tile,
+# resident CTAs per SM); see EvalKernels in csrc/align_internal.h.
+EVAL_SHAPES = [("1024x1", 1024, 1, 1), ("1024x2", 1024, 2, 1), ("512x1", 512, 1, 2)]
+
+
+def _units():
+    """(source, object name, extra flags) for every translation unit."""
+    units = []
+    for f in sorted(os.listdir(CSRC)):
+        if not f.endswith(".cu"):
+            continue
+        src = os.path.join(CSRC, f)
+        if f == "eval.cu":
+            for name, threads, ppt, ctas in EVAL_SHAPES:
+                units.append((src, f"eval_{name}.o", [f"-DMI_EVAL_THREADS={threads}", f"-DMI_EVAL_PPT={ppt}",
+                                                      f"-DMI_EVAL_CTAS_PER_SM={ctas}",
+                                                      f"-DMI_EVAL_SHAPE_FN=eval_shape_{name}"]))
+        else:
+            units.append((src, f + ".o", []))
+    return units
+
+
 def _sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return sorted({u[0] for u in _units()})
 
 
 def _deps():
@@ -48,9 +70,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     exe = nvcc()
     objs = []
 
-    def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-        cmd = [exe, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+    def compile_one(unit):
+        src, obj_name, defs = unit
+        obj = os.path.join(OUT_DIR, obj_name)
+        cmd = [exe, *NVCC_FLAGS, *defs, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -59,7 +82,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(compile_one, _sources()))
+        objs = list(ex.map(compile_one, _units()))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [exe, "-shared", *ARCH, "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -64,7 +64,7 @@ struct EvalItem {
 struct EvalArgs {
   EvalItem one;               // a copy of items[0] when n_items == 1 (read from the parameter bank)
   const EvalItem* items;
-  const int32_t* pose_item;   // P: item of each global pose (nullptr: one item)
+  const int32_t* item_start;  // n_items + 1 ascending global pose offsets (nullptr: one item)
   int32_t n_items;
   int32_t P;                  // poses over all items
   int32_t K;                  // largest symbol count over the items
@@ -79,22 +79,50 @@ struct EvalArgs {
   uint32_t* redo_count;       // entries in redo_list (zeroed before every launch)
 };
 
-// Launch helpers (defined in eval.cu / reference.cu).
-int eval_tile_points();
-int eval_min_tiles();
-int eval_threads();
-size_t eval_smem_bytes(int K, int table_slots);
-int eval_table_slots_for(int K, size_t smem_budget);
-// var: accumulate z sums; rotate: tiles hold raw xyz (the kernel applies each pose's
-// rotation) instead of pre-rotated copies.  Launches the eval and redo kernels.
-cudaError_t launch_eval(const EvalArgs& a, int n_ctas, bool var, bool rotate, cudaStream_t s);
-// Overlap box, phi column, MI and the running argmax of every pose; then each item's argmax.
-cudaError_t launch_compose(const EvalArgs& a, cudaStream_t s);
-cudaError_t launch_argmax_finalize(const EvalItem* items, int n_items, cudaStream_t s);
-// xyz (n x 3 fp32) -> n_out float4 with NaN padding; with rots (n_rot x 9), one
-// pre-rotated copy u = R p per rotation (same FMA order as the voxel map).
-cudaError_t launch_pack_points(const float* xyz, int64_t n, int64_t n_out, const float* rots, int n_rot,
-                               float4* out, cudaStream_t s);
+// One point-tile PackCopy of a batch: scan xyz (n points) -> out (n_out float4), raw
+// (rotate == 0) or pre-rotated by R.
+struct PackCopy {
+  const float* xyz;
+  int64_t n;
+  int64_t n_out;
+  float4* out;
+  float R[9];
+  int32_t rotate;
+  int32_t pad0;
+};
+
+// One compiled shape of the eval path.  eval.cu is compiled once per shape (threads per
+// CTA, points per thread per tile, resident CTAs per SM); the tile layout of the packed
+// points belongs to the shape, so a launch packs and evaluates with the same one.
+struct EvalKernels {
+  const char* name;
+  int threads;      // threads per CTA: one stream of scan points each
+  int ppt;          // points per thread per tile
+  int ctas_per_sm;  // resident CTAs per SM, each evaluating one pose at a time with its own table
+  int (*tile_points)();
+  int (*min_tiles)();
+  size_t (*smem_bytes)(int K, int table_slots);
+  int (*table_slots_for)(int K, size_t smem_budget);
+  // Raise the kernels' dynamic shared-memory limit on the current device (once per device,
+  // before any launch or stream capture).
+  cudaError_t (*setup)();
+  // var: accumulate z sums; rotate: tiles hold raw xyz (the kernel applies each pose's
+  // rotation) instead of pre-rotated copies.  Launches the eval and redo kernels.  A launch
+  // with item_start == nullptr is a single-item launch (its item is read from `one`).
+  cudaError_t (*launch_eval)(const EvalArgs& a, int n_ctas, bool var, bool rotate, cudaStream_t s);
+  // xyz (n x 3 fp32) -> n_out float4 with NaN padding; with rots (n_rot x 9), one
+  // pre-rotated copy u = R p per rotation (same FMA order as the voxel map).
+  cudaError_t (*launch_pack_points)(const float* xyz, int64_t n, int64_t n_out, const float* rots, int n_rot,
+                                    float4* out, cudaStream_t s);
+  cudaError_t (*launch_pack_batch)(const PackCopy* copies, int n_copies, int64_t max_out, cudaStream_t s);
+  // Overlap box, phi column, MI and the running argmax of every pose.
+  cudaError_t (*launch_compose)(const EvalArgs& a, cudaStream_t s);
+  // Each item's argmax from its packed running maximum.
+  cudaError_t (*launch_argmax_finalize)(const EvalItem* items, int n_items, cudaStream_t s);
+};
+constexpr int kEvalShapes = 3;
+// 0: 1024 threads x 1 point, one CTA per SM; 1: 1024 x 2; 2: 512 x 1, two CTAs per SM.
+const EvalKernels& eval_shape(int i);
 
 cudaError_t launch_ref_accumulate(const GridConst& gc, const float* xyz, int64_t n, const float* pose12,
                                   uint32_t* cnt, unsigned long long* s1, unsigned long long* s2,

@@ -1,0 +1,597 @@
+// batch.cu — many scan pairs in one persistent launch (align_eval_batch).
+//
+// Every pair keeps its own grid (resident reference state of scan A) and pose batch; the
+// launch evaluates all pairs' poses as one list, each pose carrying its pair's grid
+// constants (EvalItem).  The launch sequence (clear, pack, eval + redo, compose, argmax)
+// can be captured as a CUDA graph and replayed while the batch keeps its shape; inputs are
+// copied into the batch's own buffers before each launch, so the graph's pointers stay
+// valid.  The kernel shape is fixed, the default, or picked by timing the candidates on the
+// batch itself (tuner below).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "align.h"
+#include "align_internal.h"
+#include "runtime_internal.h"
+
+using namespace mialign;
+
+namespace {
+
+#define BCU(call, what)                                                    \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) return report_cuda_error(e_, (what));           \
+  } while (0)
+
+constexpr size_t kPrerotBudget = (size_t)8 << 30;  // bytes of pre-rotated tiles per batch
+
+// Per-pair plan of one batch launch.
+struct PairPlan {
+  align_grid* g = nullptr;
+  int64_t nB = 0, P = 0;
+  int32_t n_tiles = 0;
+  int64_t n_pad = 0;
+  int n_copies = 1;          // tile copies: rotations (pre-rotated) or 1 (raw)
+  bool prerot = false;
+  std::vector<float> hposes;  // host fp32 poses (when given on the host)
+  std::vector<int32_t> idx;   // pose -> rotation copy
+  std::vector<float> rots;    // distinct rotations
+  int64_t xyz_off = 0;        // floats
+  int64_t pose_off = 0;       // poses (global pose index of pose 0)
+  int64_t pts_off = 0;        // float4
+  int64_t outc_off = 0;       // uint32
+};
+
+// Workspace sizes of one launch; a change of any of them re-allocates and drops the graph.
+struct Sizes {
+  size_t xyz = 0, poses = 0, pts = 0, pose_src = 0, copies = 0, items = 0, starts = 0, outc = 0, box = 0,
+         best = 0, mi = 0, argmax = 0, redo = 0, wide = 0;
+};
+
+std::string env_cache_path() {
+  const char* p = std::getenv("ALIGN_TUNE_CACHE");
+  return p ? std::string(p) : std::string();
+}
+
+// Tuner cache: batch class -> shape.  Shared by all batches of the process.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const std::string path = env_cache_path();
+  if (path.empty()) return;
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return;
+  char key[512];
+  int shape = 0;
+  while (std::fscanf(f, "%511s %d", key, &shape) == 2)
+    if (shape >= 0 && shape < kEvalShapes) g_tune[key] = shape;
+  std::fclose(f);
+}
+
+void tune_store_locked(const std::string& key, int shape) {
+  g_tune[key] = shape;
+  const std::string path = env_cache_path();
+  if (path.empty()) return;
+  FILE* f = std::fopen(path.c_str(), "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d\n", key.c_str(), shape);
+  std::fclose(f);
+}
+
+// floor(log2(v)) for v >= 1 (0 otherwise): the size classes of the tuner's cache key.
+int bucket_log2(int64_t v) {
+  int b = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++b;
+  }
+  return b;
+}
+
+}  // namespace
+
+struct align_batch {
+  cudaStream_t user_stream = nullptr;  // the caller's stream (ordering of device inputs)
+  cudaStream_t stream = nullptr;       // the batch's own stream (capturable; the legacy
+                                       // default stream cannot be captured)
+  cudaEvent_t ev_in = nullptr;
+  int device = 0;
+  int n_sm = 0;
+  size_t smem_optin = 0;
+  std::string device_name;
+  int shape_fixed = -1;
+  int32_t passes_seed = 1;
+  DevBuf xyz, poses, pts, pose_src, copies, items, starts, outc, box, best, mi, argmax, redo_list, redo_count, wide,
+      status;
+  Sizes cap;
+  // graph of the last launch sequence
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t> sig;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+void drop_graph(align_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->sig.clear();
+}
+
+// Grow a buffer; any growth invalidates the captured graph.
+align_status grow(align_batch* b, DevBuf& buf, size_t& cap, size_t bytes, const char* what, bool zero = false) {
+  if (bytes <= cap && buf.p) return ALIGN_OK;
+  drop_graph(b);
+  const size_t want = std::max<size_t>(bytes, 256);
+  BCU(buf.ensure(want), what);
+  cap = want;
+  if (zero) BCU(cudaMemsetAsync(buf.p, 0, want, b->stream), what);
+  return ALIGN_OK;
+}
+
+struct Launch {
+  const EvalKernels* ek = nullptr;
+  int shape = 0;
+  EvalArgs a{};
+  int n_ctas = 0;
+  bool var = false, rotate = false;
+  int n_items = 0;
+  int n_copies = 0;
+  int64_t max_out = 0;
+};
+
+// The launch sequence that a graph captures: clear, pack, eval + redo, compose, argmax.
+align_status enqueue_launch(align_batch* b, const Launch& L) {
+  cudaStream_t s = b->stream;
+  BCU(cudaMemsetAsync(b->best.p, 0, (size_t)L.n_items * 8, s), "clear argmax keys");
+  BCU(cudaMemsetAsync(b->redo_count.p, 0, 4, s), "clear redo count");
+  BCU(L.ek->launch_pack_batch(b->copies.as<PackCopy>(), L.n_copies, L.max_out, s), "launch pack");
+  BCU(L.ek->launch_eval(L.a, L.n_ctas, L.var, L.rotate, s), "launch eval kernel");
+  BCU(L.ek->launch_compose(L.a, s), "launch compose kernel");
+  BCU(L.ek->launch_argmax_finalize(L.a.items, L.n_items, s), "launch argmax");
+  return ALIGN_OK;
+}
+
+align_status run_launch(align_batch* b, const Launch& L, bool use_graph, const std::vector<int64_t>& sig) {
+  BCU(cudaEventRecord(b->ev0, b->stream), "record event");
+  if (use_graph) {
+    if (!b->exec || b->sig != sig) {
+      drop_graph(b);
+      cudaGraph_t graph = nullptr;
+      BCU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      align_status st = enqueue_launch(b, L);
+      cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+      if (st != ALIGN_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      BCU(e, "end capture");
+      e = cudaGraphInstantiate(&b->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      BCU(e, "instantiate graph");
+      b->sig = sig;
+      b->stats[1] += 1;
+    } else {
+      b->stats[2] += 1;
+    }
+    BCU(cudaGraphLaunch(b->exec, b->stream), "launch graph");
+  } else {
+    align_status st = enqueue_launch(b, L);
+    if (st != ALIGN_OK) return st;
+  }
+  BCU(cudaEventRecord(b->ev1, b->stream), "record event");
+  b->stats[0] += 1;
+  b->stats[5] += 5;  // pack, eval, redo, compose, argmax
+  return ALIGN_OK;
+}
+
+// Read the kernels' status words (synchronises the stream).
+align_status collect(align_batch* b) {
+  uint32_t v[3] = {0, 0, 0};
+  BCU(cudaMemcpyAsync(v, b->status.p, 12, cudaMemcpyDeviceToHost, b->stream), "read status");
+  BCU(cudaStreamSynchronize(b->stream), "synchronize");
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->stats[6] = (int64_t)std::llround(ms * 1000.0);
+  // reset the error word and the wide-voxel count; the partition count stays a running max
+  BCU(cudaMemsetAsync(b->status.p, 0, 4, b->stream), "reset status");
+  BCU(cudaMemsetAsync(b->status.as<uint32_t>() + 2, 0, 4, b->stream), "reset status");
+  if (v[1] > (uint32_t)b->passes_seed && v[1] <= (1u << 16) && (v[1] & (v[1] - 1)) == 0)
+    b->passes_seed = (int32_t)v[1];
+  if (v[0] & kErrWaitTimeout) return report_error(ALIGN_E_TIMEOUT, "a bounded device wait gave up");
+  if (v[0] & kErrDzBound) return report_error(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");
+  if (v[0] & kErrPassLimit) return report_error(ALIGN_E_INTERNAL, "key partitioning limit reached");
+  return ALIGN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+align_status align_batch_create(void* cuda_stream, align_batch** out) {
+  if (!out) return report_error(ALIGN_E_INVALID, "out is NULL");
+  *out = nullptr;
+  int n_dev = 0;
+  cudaError_t e = cudaGetDeviceCount(&n_dev);
+  if (e != cudaSuccess || n_dev < 1) {
+    (void)cudaGetLastError();
+    return report_error(ALIGN_E_CUDA, "no usable CUDA device");
+  }
+  int dev = 0;
+  BCU(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaDeviceProp prop;
+  BCU(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+  if (prop.major < 10) return report_errorf(ALIGN_E_CUDA, "this library is built for sm_103a (found sm_%d%d)",
+                                            prop.major, prop.minor);
+  for (int i = 0; i < kEvalShapes; ++i) BCU(eval_shape(i).setup(), "set up eval kernels");
+  align_batch* b = new (std::nothrow) align_batch();
+  if (!b) return report_error(ALIGN_E_OOM, "host allocation failed");
+  b->user_stream = (cudaStream_t)cuda_stream;
+  b->device = dev;
+  b->n_sm = prop.multiProcessorCount;
+  b->smem_optin = prop.sharedMemPerBlockOptin;
+  b->device_name = prop.name;
+  for (char& c : b->device_name)
+    if (c == ' ') c = '_';
+  if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    delete b;
+    return report_error(ALIGN_E_CUDA, "creating the batch's events and stream failed");
+  }
+  *out = b;
+  return ALIGN_OK;
+}
+
+align_status align_batch_destroy(align_batch* b) {
+  if (!b) return ALIGN_OK;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  for (DevBuf* d : {&b->xyz, &b->poses, &b->pts, &b->pose_src, &b->copies, &b->items, &b->starts, &b->outc, &b->box,
+                    &b->best, &b->mi, &b->argmax, &b->redo_list, &b->redo_count, &b->wide, &b->status})
+    d->release();
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return ALIGN_OK;
+}
+
+align_status align_batch_set_shape(align_batch* b, int32_t shape) {
+  if (!b) return report_error(ALIGN_E_INVALID, "batch is NULL");
+  if (shape < -1 || shape >= kEvalShapes) return report_error(ALIGN_E_INVALID, "shape out of range");
+  b->shape_fixed = shape;
+  return ALIGN_OK;
+}
+
+align_status align_batch_stats(const align_batch* b, int64_t out[8]) {
+  if (!b || !out) return report_error(ALIGN_E_INVALID, "NULL argument");
+  for (int i = 0; i < 8; ++i) out[i] = b->stats[i];
+  return ALIGN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Plan, stage and launch one batch with kernel shape `shape`; outputs stay in the batch's
+// buffers (copied out by the caller).
+align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, const align_pair* pairs,
+                              const std::vector<int32_t>& which, int flags, int shape) {
+  const EvalKernels& ek = eval_shape(shape);
+  const int n = (int)plans.size();
+  const bool xyz_dev = (flags & ALIGN_XYZ_DEVICE) != 0;
+  bool rotate = false, var = false;
+  int maxK = 2;
+  for (const PairPlan& pp : plans) {
+    if (pp.hposes.empty()) rotate = true;  // device poses: every pair rotates in the kernel
+    if (pp.g->gc.feature != ALIGN_FEAT_COUNT) var = true;
+    maxK = std::max(maxK, (int)pp.g->gc.K);
+  }
+  // ---- layout ----
+  const int tile = ek.tile_points();
+  int64_t xyz_f = 0, poses_n = 0, pts_n = 0, outc_n = 0, max_out = 0;
+  int n_copies = 0;
+  // One pre-rotated copy per distinct rotation when every pair's rotations repeat (lattices)
+  // and the copies fit the budget; otherwise every pair's tiles are raw and the kernel
+  // rotates (one launch has one tile kind).
+  size_t prerot_bytes = 0;
+  for (PairPlan& pp : plans) {
+    pp.n_tiles = (int32_t)std::max<int64_t>(ek.min_tiles(), (pp.nB + tile - 1) / tile);
+    pp.n_pad = (int64_t)pp.n_tiles * tile;
+    if (rotate) continue;
+    const int max_groups = (int)std::max<int64_t>(1, pp.P / 4);
+    const int groups = group_pose_rotations(pp.hposes.data(), pp.P, pp.rots, pp.idx, max_groups);
+    prerot_bytes += (size_t)std::max(groups, 1) * (size_t)pp.n_pad * 16;
+    if (groups <= 0 || prerot_bytes > kPrerotBudget) rotate = true;
+  }
+  for (PairPlan& pp : plans) {
+    pp.prerot = !rotate;
+    pp.n_copies = rotate ? 1 : (int)(pp.rots.size() / 9);
+    pp.xyz_off = xyz_f;
+    pp.pose_off = poses_n;
+    pp.pts_off = pts_n;
+    pp.outc_off = outc_n;
+    xyz_f += pp.nB * 3;
+    poses_n += pp.P;
+    pts_n += (int64_t)pp.n_copies * pp.n_pad;
+    outc_n += pp.P * (int64_t)pp.g->gc.K * pp.g->gc.K;
+    n_copies += pp.n_copies;
+    max_out = std::max(max_out, pp.n_pad);
+  }
+  if (poses_n >= INT32_MAX) return report_error(ALIGN_E_INVALID, "too many poses in one batch");
+  if (n_copies > 65535) return report_error(ALIGN_E_INVALID, "too many tile copies in one batch");
+  const int T = ek.table_slots_for(maxK, b->smem_optin);
+  const int n_ctas = b->n_sm * ek.ctas_per_sm;
+  // ---- workspace ----
+  align_status st;
+#define GROW(buf, field, bytes, what, zero) \
+  if ((st = grow(b, b->buf, b->cap.field, (bytes), (what), (zero))) != ALIGN_OK) return st;
+  GROW(xyz, xyz, (size_t)xyz_f * 4, "allocate points", false);
+  GROW(poses, poses, (size_t)poses_n * 48, "allocate poses", false);
+  GROW(pts, pts, (size_t)pts_n * 16, "allocate tiles", false);
+  GROW(pose_src, pose_src, (size_t)poses_n * 4, "allocate pose sources", false);
+  GROW(copies, copies, (size_t)n_copies * sizeof(PackCopy), "allocate copy table", false);
+  GROW(items, items, (size_t)n * sizeof(EvalItem), "allocate item table", false);
+  GROW(starts, starts, (size_t)(n + 1) * 4, "allocate item starts", false);
+  GROW(outc, outc, (size_t)outc_n * 4, "allocate histograms", false);
+  GROW(box, box, (size_t)poses_n * 24, "allocate boxes", false);
+  GROW(best, best, (size_t)n * 8, "allocate argmax keys", false);
+  GROW(mi, mi, (size_t)poses_n * 4, "allocate MI", false);
+  GROW(argmax, argmax, (size_t)n * 8, "allocate argmax", false);
+  GROW(redo_list, redo, (size_t)poses_n * 4, "allocate redo list", false);
+  GROW(wide, wide, (size_t)n_ctas * 2 * T * 8, "allocate wide sums", true);
+#undef GROW
+  if (!b->status.p || !b->redo_count.p) {
+    drop_graph(b);
+    BCU(b->status.ensure(16), "allocate status words");
+    BCU(b->redo_count.ensure(16), "allocate redo count");
+    BCU(cudaMemsetAsync(b->status.p, 0, 16, b->stream), "clear status words");
+  }
+  // ---- stage inputs and tables (outside any graph) ----
+  cudaStream_t s = b->stream;
+  std::vector<float> hp;
+  std::vector<int32_t> hsrc((size_t)poses_n, 0);
+  std::vector<PackCopy> hcopies;
+  std::vector<EvalItem> hitems((size_t)n);
+  std::vector<int32_t> hstarts((size_t)n + 1);
+  hcopies.reserve((size_t)n_copies);
+  if (!rotate) hp.resize((size_t)poses_n * 12);
+  for (int i = 0; i < n; ++i) {
+    PairPlan& pp = plans[(size_t)i];
+    const align_pair& q = pairs[which[(size_t)i]];
+    align_grid* g = pp.g;
+    if (pp.nB > 0)
+      BCU(cudaMemcpyAsync(b->xyz.as<float>() + pp.xyz_off, q.xyzB, (size_t)pp.nB * 12,
+                          xyz_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+          "copy points");
+    if (!pp.hposes.empty() && !rotate) {
+      std::memcpy(&hp[(size_t)pp.pose_off * 12], pp.hposes.data(), (size_t)pp.P * 48);
+    } else if (!pp.hposes.empty()) {
+      BCU(cudaMemcpyAsync(b->poses.as<float>() + pp.pose_off * 12, pp.hposes.data(), (size_t)pp.P * 48,
+                          cudaMemcpyHostToDevice, s),
+          "copy poses");
+    } else {
+      BCU(cudaMemcpyAsync(b->poses.as<float>() + pp.pose_off * 12, q.poses12, (size_t)pp.P * 48,
+                          cudaMemcpyDeviceToDevice, s),
+          "copy poses");
+    }
+    if (pp.prerot)
+      for (int64_t p = 0; p < pp.P; ++p) hsrc[(size_t)(pp.pose_off + p)] = pp.idx[(size_t)p];
+    for (int c = 0; c < pp.n_copies; ++c) {
+      PackCopy pc{};
+      pc.xyz = b->xyz.as<float>() + pp.xyz_off;
+      pc.n = pp.nB;
+      pc.n_out = pp.n_pad;
+      pc.out = b->pts.as<float4>() + pp.pts_off + (int64_t)c * pp.n_pad;
+      pc.rotate = pp.prerot ? 1 : 0;
+      for (int k = 0; k < 9; ++k) pc.R[k] = pp.prerot ? pp.rots[(size_t)c * 9 + k] : 0.0f;
+      hcopies.push_back(pc);
+    }
+    EvalItem& it = hitems[(size_t)i];
+    it.gc = g->gc;
+    it.symA = g->symA.as<uint8_t>();
+    it.sat = g->sat.as<int32_t>();
+    it.src = b->pts.as<float4>() + pp.pts_off;
+    it.src_stride = (uint64_t)pp.n_pad;
+    it.pose_src = pp.prerot ? b->pose_src.as<int32_t>() + pp.pose_off : nullptr;
+    it.poses = b->poses.as<float>() + pp.pose_off * 12;
+    it.n_tiles = pp.n_tiles;
+    it.P = (int32_t)pp.P;
+    it.pose_base = (int32_t)pp.pose_off;
+    it.out_c = b->outc.as<uint32_t>() + pp.outc_off;
+    it.out_box = b->box.as<int32_t>() + pp.pose_off * 6;
+    it.mi = b->mi.as<float>() + pp.pose_off;
+    it.hist = nullptr;
+    it.best = b->best.as<unsigned long long>() + i;
+    it.argmax = b->argmax.as<int64_t>() + i;
+    it.dump = nullptr;
+    hstarts[(size_t)i] = (int32_t)pp.pose_off;
+  }
+  hstarts[(size_t)n] = (int32_t)poses_n;
+  if (!rotate && poses_n > 0)
+    BCU(cudaMemcpyAsync(b->poses.p, hp.data(), (size_t)poses_n * 48, cudaMemcpyHostToDevice, s), "copy poses");
+  if (poses_n > 0)
+    BCU(cudaMemcpyAsync(b->pose_src.p, hsrc.data(), (size_t)poses_n * 4, cudaMemcpyHostToDevice, s),
+        "copy pose sources");
+  BCU(cudaMemcpyAsync(b->copies.p, hcopies.data(), hcopies.size() * sizeof(PackCopy), cudaMemcpyHostToDevice, s),
+      "copy copy table");
+  BCU(cudaMemcpyAsync(b->items.p, hitems.data(), hitems.size() * sizeof(EvalItem), cudaMemcpyHostToDevice, s),
+      "copy item table");
+  BCU(cudaMemcpyAsync(b->starts.p, hstarts.data(), hstarts.size() * 4, cudaMemcpyHostToDevice, s),
+      "copy item starts");
+  // ---- launch ----
+  Launch L;
+  L.ek = &ek;
+  L.shape = shape;
+  L.n_ctas = n_ctas;
+  L.var = var;
+  L.rotate = rotate;
+  L.n_items = n;
+  L.n_copies = n_copies;
+  L.max_out = max_out;
+  EvalArgs& a = L.a;
+  a.items = b->items.as<EvalItem>();
+  a.item_start = b->starts.as<int32_t>();
+  a.n_items = n;
+  a.P = (int32_t)poses_n;
+  a.K = maxK;
+  a.table_slots = T;
+  a.n_buckets = T / 4;
+  a.passes0 = b->passes_seed;
+  uint32_t* status = b->status.as<uint32_t>();
+  a.err = status;
+  a.max_passes = status + 1;
+  a.wide_count = status + 2;
+  a.wide = b->wide.as<unsigned long long>();
+  a.redo_list = b->redo_list.as<uint32_t>();
+  a.redo_count = b->redo_count.as<uint32_t>();
+  const std::vector<int64_t> sig = {shape,   n,       rotate,     var,      a.passes0, T, n_ctas,
+                                    poses_n, n_copies, max_out,   maxK,     (int64_t)(uintptr_t)b->pts.p,
+                                    (int64_t)(uintptr_t)b->items.p};
+  st = run_launch(b, L, (flags & ALIGN_BATCH_GRAPH) != 0, sig);
+  if (st != ALIGN_OK) return st;
+  b->stats[3] = shape;
+  b->stats[4] = T;
+  return ALIGN_OK;
+}
+
+}  // namespace
+
+extern "C" align_status align_eval_batch(align_batch* b, const align_pair* pairs, int32_t n_pairs, int flags) {
+  if (!b) return report_error(ALIGN_E_INVALID, "batch is NULL");
+  if (n_pairs < 0 || (n_pairs > 0 && !pairs)) return report_error(ALIGN_E_INVALID, "bad pair array");
+  BCU(cudaSetDevice(b->device), "cudaSetDevice");
+  // work already queued on the caller's stream (device inputs) comes first
+  BCU(cudaEventRecord(b->ev_in, b->user_stream), "record event");
+  BCU(cudaStreamWaitEvent(b->stream, b->ev_in, 0), "wait event");
+  const bool poses_dev = (flags & ALIGN_POSES_DEVICE) != 0;
+  const bool out_dev = (flags & ALIGN_OUT_DEVICE) != 0;
+  std::vector<PairPlan> plans;
+  std::vector<int32_t> which;  // plan -> pair index
+  for (int32_t i = 0; i < n_pairs; ++i) {
+    const align_pair& q = pairs[i];
+    if (!q.grid) return report_errorf(ALIGN_E_INVALID, "pair %d: grid is NULL", i);
+    if (q.grid->device != b->device) return report_errorf(ALIGN_E_INVALID, "pair %d: grid on another device", i);
+    if (!q.grid->has_ref) return report_errorf(ALIGN_E_NOREF, "pair %d: no reference scan set", i);
+    if (q.nB < 0 || q.nB >= INT32_MAX) return report_errorf(ALIGN_E_INVALID, "pair %d: nB out of range", i);
+    if (q.nB > 0 && !q.xyzB) return report_errorf(ALIGN_E_INVALID, "pair %d: xyzB is NULL", i);
+    if (q.P < 0 || q.P >= INT32_MAX) return report_errorf(ALIGN_E_INVALID, "pair %d: P out of range", i);
+    if (q.P > 0 && ((q.poses12 == nullptr) == (q.eta6 == nullptr)))
+      return report_errorf(ALIGN_E_INVALID, "pair %d: give exactly one of poses12 and eta6", i);
+    if (q.P > 0 && q.eta6 && poses_dev) return report_errorf(ALIGN_E_INVALID, "pair %d: eta6 must be host memory", i);
+    if (q.P > 0 && !q.mi_out) return report_errorf(ALIGN_E_INVALID, "pair %d: mi_out is NULL", i);
+    if (q.P == 0) continue;
+    PairPlan pp;
+    pp.g = q.grid;
+    pp.nB = q.nB;
+    pp.P = q.P;
+    if (q.eta6) {
+      pp.hposes.resize((size_t)q.P * 12);
+      for (int64_t p = 0; p < q.P; ++p) round_pose_host(q.grid->origin, q.eta6 + 6 * p, &pp.hposes[(size_t)p * 12]);
+    } else if (!poses_dev) {
+      pp.hposes.assign(q.poses12, q.poses12 + (size_t)q.P * 12);
+    }
+    for (float v : pp.hposes)
+      if (!std::isfinite(v)) return report_errorf(ALIGN_E_INVALID, "pair %d: a pose is not finite", i);
+    plans.push_back(std::move(pp));
+    which.push_back(i);
+  }
+  // pairs without poses: argmax -1
+  for (int32_t i = 0; i < n_pairs; ++i) {
+    if (pairs[i].P != 0 || !pairs[i].argmax_out) continue;
+    const int64_t none = -1;
+    if (out_dev)
+      BCU(cudaMemcpyAsync(pairs[i].argmax_out, &none, 8, cudaMemcpyHostToDevice, b->stream), "write argmax");
+    else
+      *pairs[i].argmax_out = -1;
+  }
+  if (plans.empty()) {
+    BCU(cudaStreamSynchronize(b->stream), "synchronize");
+    return ALIGN_OK;
+  }
+  // kernel shape: fixed, tuned (cached per batch class) or the default
+  int shape = b->shape_fixed >= 0 ? b->shape_fixed : 0;
+  if (b->shape_fixed < 0 && (flags & ALIGN_BATCH_TUNE)) {
+    int64_t pts_tot = 0, poses_tot = 0;
+    int maxK = 0;
+    bool dev_poses = false;
+    for (const PairPlan& pp : plans) {
+      pts_tot += pp.nB;
+      poses_tot += pp.P;
+      maxK = std::max(maxK, (int)pp.g->gc.K);
+      dev_poses = dev_poses || pp.hposes.empty();
+    }
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s/pairs%d/pts%d/poses%d/K%d/devposes%d", b->device_name.c_str(),
+                  bucket_log2((int64_t)plans.size()), bucket_log2(pts_tot / (int64_t)plans.size() + 1),
+                  bucket_log2(poses_tot + 1), maxK, dev_poses ? 1 : 0);
+    const std::string key = buf;
+    bool known = false;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      tune_load_locked();
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        shape = it->second;
+        known = true;
+      }
+    }
+    if (!known) {
+      // time every shape on this batch: one warm-up run, then the sum of two timed runs
+      double best_ms = 0.0;
+      int best = 0;
+      for (int c = 0; c < kEvalShapes; ++c) {
+        double total = 0.0;
+        for (int rep = 0; rep < 3; ++rep) {
+          align_status st = eval_batch_shape(b, plans, pairs, which, flags & ~ALIGN_BATCH_GRAPH, c);
+          if (st != ALIGN_OK) return st;
+          st = collect(b);
+          if (st != ALIGN_OK) return st;
+          if (rep > 0) total += (double)b->stats[6] / 1000.0;
+        }
+        b->stats[7] += 1;
+        if (c == 0 || total < best_ms) {
+          best_ms = total;
+          best = c;
+        }
+      }
+      shape = best;
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      tune_store_locked(key, shape);
+    }
+  }
+  align_status st = eval_batch_shape(b, plans, pairs, which, flags, shape);
+  if (st != ALIGN_OK) return st;
+  // outputs
+  const cudaMemcpyKind kind = out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (size_t k = 0; k < plans.size(); ++k) {
+    const align_pair& q = pairs[which[k]];
+    BCU(cudaMemcpyAsync(q.mi_out, b->mi.as<float>() + plans[k].pose_off, (size_t)plans[k].P * 4, kind, b->stream),
+        "read MI");
+    if (q.argmax_out)
+      BCU(cudaMemcpyAsync(q.argmax_out, b->argmax.as<int64_t>() + k, 8, kind, b->stream), "read argmax");
+  }
+  return collect(b);
+}

@@ -26,18 +26,37 @@
 // compose_kernel: per pose, the overlap box (Algorithm 1), A's symbol counts over it from
 // per-symbol prefix sums, the phi column h[a][0], then Eqs. 2-5 in FP32 with a fixed
 // reduction order, and the packed (MI, index) maximum for Eq. 1.
+#include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "align_internal.h"
 #include "device_common.cuh"
+
+// The shape this translation unit is compiled for (see EvalKernels).
+#ifndef MI_EVAL_THREADS
+#define MI_EVAL_THREADS 1024
+#endif
+#ifndef MI_EVAL_PPT
+#define MI_EVAL_PPT 1
+#endif
+#ifndef MI_EVAL_CTAS_PER_SM
+#define MI_EVAL_CTAS_PER_SM 1
+#endif
+#ifndef MI_EVAL_SHAPE_FN
+#define MI_EVAL_SHAPE_FN eval_shape_1024x1
+#endif
+#define MI_STR2(x) #x
+#define MI_STR(x) MI_STR2(x)
 
 namespace mialign {
 
 namespace {
 
-constexpr int kThreads = 1024;
+constexpr int kThreads = MI_EVAL_THREADS;
+constexpr int kCtasPerSm = MI_EVAL_CTAS_PER_SM;
 constexpr int kWarps = kThreads / 32;
-constexpr int kPPT = 1;                 // points per thread per tile
+constexpr int kPPT = MI_EVAL_PPT;       // points per thread per tile
 constexpr int kTile = kThreads * kPPT;  // points per tile
 constexpr int kMinTiles = 3;            // prefetch depth
 constexpr uint32_t kQueue = 64;         // finished runs buffered per warp (32 drained at a time)
@@ -432,7 +451,17 @@ __device__ __forceinline__ void reset_pose(const EvalSmem& S) {
   if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
 }
 
-__device__ __forceinline__ int item_of(const EvalArgs& a, int gp) { return a.pose_item ? __ldg(a.pose_item + gp) : 0; }
+// Item of global pose gp: the last item whose start is <= gp (binary search).
+__device__ __forceinline__ int item_of(const EvalArgs& a, int gp) {
+  if (a.item_start == nullptr) return 0;
+  int lo = 0, hi = a.n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(a.item_start + mid) <= gp) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 // The item of a pose.  With a single item its fields (and the voxel map constants of the
 // sweep) are read straight from the kernel parameters, which costs no registers.
@@ -511,7 +540,7 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const VoxelCon
 }
 
 template <bool kVar, bool kRot, bool kOne>
-__global__ void __launch_bounds__(kThreads, 1) eval_kernel(const __grid_constant__ EvalArgs a) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid_constant__ EvalArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
   const int T = a.table_slots;
@@ -583,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(const __grid_constant
 // table with 64-bit side sums for voxels beyond the 32-bit bound; a full table restarts
 // the pose with twice the key partitions.
 template <bool kVar, bool kRot>
-__global__ void __launch_bounds__(kThreads, 1) redo_kernel(const __grid_constant__ EvalArgs a) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid_constant__ EvalArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
   const int T = a.table_slots;
@@ -699,6 +728,38 @@ __global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int
   }
 }
 
+// The same packing for every tile copy of a batch (one copy per blockIdx.y).
+__global__ void pack_batch_kernel(const PackCopy* __restrict__ copies) {
+  const PackCopy& c = copies[blockIdx.y];
+  const float nan = __int_as_float(0x7fc00000);
+  const float inf = __int_as_float(0x7f800000);
+  const bool rot = c.rotate != 0;
+  float R[9];
+  for (int i = 0; i < 9; ++i) R[i] = c.R[i];
+  const int64_t L = c.n_out / kThreads;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n_out; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = i / kTile;
+    const int pos = (int)(i - t * kTile);
+    const int j = pos / kThreads;
+    const int sidx = pos - j * kThreads;
+    const int64_t src = (int64_t)sidx * L + (int64_t)kPPT * t + j;
+    const float pad = rot ? inf : nan;
+    float4 v = make_float4(pad, pad, pad, 0.0f);
+    if (src < c.n) {
+      const float x = c.xyz[3 * src], y = c.xyz[3 * src + 1], z = c.xyz[3 * src + 2];
+      if (rot) {
+        rotate_point(R, x, y, z, v.x, v.y, v.z);
+        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) v = make_float4(inf, inf, inf, 0.0f);
+      } else {
+        v.x = x;
+        v.y = y;
+        v.z = z;
+      }
+    }
+    c.out[i] = v;
+  }
+}
+
 // -----------------------------------------------------------------------------------
 // Compose: overlap box, A's counts over it, phi column, Eqs. 2-5, Eq. 1 key.
 // -----------------------------------------------------------------------------------
@@ -802,28 +863,38 @@ __global__ void argmax_finalize_kernel(const EvalItem* items, int n_items) {
 }
 
 template <bool kVar, bool kRot>
+cudaError_t setup_t(int smem) {
+  cudaError_t e = cudaFuncSetAttribute(eval_kernel<kVar, kRot, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(eval_kernel<kVar, kRot, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(redo_kernel<kVar, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+template <bool kVar, bool kRot>
 cudaError_t launch_eval_t(const EvalArgs& a, int n_ctas, size_t smem, cudaStream_t s) {
-  auto* k = a.n_items == 1 ? eval_kernel<kVar, kRot, true> : eval_kernel<kVar, kRot, false>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(redo_kernel<kVar, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  auto* k = a.item_start == nullptr ? eval_kernel<kVar, kRot, true> : eval_kernel<kVar, kRot, false>;
   k<<<n_ctas, kThreads, smem, s>>>(a);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   redo_kernel<kVar, kRot><<<n_ctas, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-}  // namespace
-
 int eval_tile_points() { return kTile; }
 int eval_min_tiles() { return kMinTiles; }
-int eval_threads() { return kThreads; }
 
 size_t eval_smem_bytes(int K, int table_slots) { return eval_smem_layout(K, table_slots, nullptr, nullptr); }
 
 int eval_table_slots_for(int K, size_t smem_budget) {
+  if (kCtasPerSm > 1) {  // share the SM's shared memory between its resident CTAs
+    int dev = 0, per_sm = 0, reserved = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess)
+      smem_budget = std::min(smem_budget, (size_t)(per_sm / kCtasPerSm - reserved));
+  }
   int lo = 32;
   while (eval_smem_bytes(K, lo + 32) <= smem_budget && lo < (1 << 16)) lo += 32;
   return lo;
@@ -834,6 +905,36 @@ cudaError_t launch_eval(const EvalArgs& a, int n_ctas, bool var, bool rotate, cu
   if (var)
     return rotate ? launch_eval_t<true, true>(a, n_ctas, smem, s) : launch_eval_t<true, false>(a, n_ctas, smem, s);
   return rotate ? launch_eval_t<false, true>(a, n_ctas, smem, s) : launch_eval_t<false, false>(a, n_ctas, smem, s);
+}
+
+cudaError_t eval_setup() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return cudaSuccess;
+  int smem = 0;
+  e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if ((e = setup_t<true, true>(smem)) != cudaSuccess) return e;
+  if ((e = setup_t<true, false>(smem)) != cudaSuccess) return e;
+  if ((e = setup_t<false, true>(smem)) != cudaSuccess) return e;
+  if ((e = setup_t<false, false>(smem)) != cudaSuccess) return e;
+  done[dev] = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_pack_batch(const PackCopy* copies, int n_copies, int64_t max_out, cudaStream_t s) {
+  if (n_copies <= 0) return cudaSuccess;
+  const int threads = 256;
+  int64_t bx = (max_out + threads - 1) / threads;
+  if (bx > 1024) bx = 1024;
+  if (bx < 1) bx = 1;
+  pack_batch_kernel<<<dim3((unsigned)bx, (unsigned)n_copies), threads, 0, s>>>(copies);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack_points(const float* xyz, int64_t n, int64_t n_out, const float* rots, int n_rot, float4* out,
@@ -857,6 +958,15 @@ cudaError_t launch_argmax_finalize(const EvalItem* items, int n_items, cudaStrea
   if (n_items <= 0) return cudaSuccess;
   argmax_finalize_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(items, n_items);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+const EvalKernels& MI_EVAL_SHAPE_FN() {
+  static const EvalKernels k{MI_STR(MI_EVAL_SHAPE_FN), kThreads, kPPT, kCtasPerSm, eval_tile_points, eval_min_tiles,
+                             eval_smem_bytes, eval_table_slots_for, eval_setup, launch_eval, launch_pack_points,
+                             launch_pack_batch, launch_compose, launch_argmax_finalize};
+  return k;
 }
 
 }  // namespace mialign

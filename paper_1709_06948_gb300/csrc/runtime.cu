@@ -17,6 +17,7 @@
 
 #include "align.h"
 #include "align_internal.h"
+#include "runtime_internal.h"
 
 using namespace mialign;
 
@@ -46,56 +47,9 @@ align_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, (what));  \
   } while (0)
 
-struct DevBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= cap && p != nullptr) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    size_t want = std::max<size_t>(bytes, 256);
-    cudaError_t e = cudaMalloc(&p, want);
-    if (e == cudaSuccess) cap = want;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-  template <class T>
-  T* as() const {
-    return static_cast<T*>(p);
-  }
-};
 
 }  // namespace
 
-struct align_grid {
-  GridConst gc{};
-  float origin[3];
-  float res_m;
-  int64_t V = 0;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  int n_sm = 0;
-  int table_slots = 0;
-  bool has_ref = false;
-  int32_t boxA[6];
-  DevBuf symA, sat;
-  // evaluation workspace
-  DevBuf xyz, poses, out_c, out_box, mi, hist, best, argmax, err, max_passes, wide_count, wide, dump;
-  DevBuf pts4, pose_src, rots, redo_list, redo_count, items;
-  int64_t n_points = 0;  // points staged in `xyz`
-  int32_t passes_seed = 1;
-  int64_t stats[5] = {0, 0, 0, 0, 0};
-  // event timing (align_profile): one (before eval, after eval, after argmax) triple per
-  // launch, drained into the totals at the next synchronising call or profile read
-  bool profiling = false;
-  std::vector<std::array<cudaEvent_t, 3>> ev_pending, ev_pool;
-  double prof[3] = {0.0, 0.0, 0.0};
-};
 
 namespace {
 
@@ -240,8 +194,9 @@ align_status check_grid(align_grid* g) {
 align_status upload_points(align_grid* g, const float* xyz, int64_t n, int flags, int32_t* n_tiles_out) {
   if (n < 0 || n >= INT32_MAX) return fail(ALIGN_E_INVALID, "point count out of range");
   if (n > 0 && !xyz) return fail(ALIGN_E_INVALID, "xyz is NULL");
-  const int tile = eval_tile_points();
-  const int64_t n_tiles = std::max<int64_t>(eval_min_tiles(), (n + tile - 1) / tile);
+  const EvalKernels& ek = eval_shape(0);
+  const int tile = ek.tile_points();
+  const int64_t n_tiles = std::max<int64_t>(ek.min_tiles(), (n + tile - 1) / tile);
   CU(g->xyz.ensure(std::max<size_t>(1, (size_t)n) * 3 * sizeof(float)), "allocate point buffer");
   if (n > 0) {
     const cudaMemcpyKind kind = (flags & ALIGN_XYZ_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -327,7 +282,8 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
 
   // Pack B into float4 tiles; when many poses share a rotation, one pre-rotated copy per
   // distinct rotation (the kernel then only translates).
-  const int64_t n_pad = (int64_t)n_tiles * eval_tile_points();
+  const EvalKernels& ek = eval_shape(0);
+  const int64_t n_pad = (int64_t)n_tiles * ek.tile_points();
   bool rotate = true;
   int n_rot = 0;
   if (h_poses != nullptr) {
@@ -349,7 +305,7 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
     }
   }
   CU(g->pts4.ensure((size_t)std::max(n_rot, 1) * (size_t)n_pad * 16), "allocate tiles");
-  CU(launch_pack_points(g->xyz.as<float>(), g->n_points, n_pad, rotate ? nullptr : g->rots.as<float>(), n_rot,
+  CU(ek.launch_pack_points(g->xyz.as<float>(), g->n_points, n_pad, rotate ? nullptr : g->rots.as<float>(), n_rot,
                         g->pts4.as<float4>(), g->stream),
      "launch pack");
 
@@ -377,7 +333,7 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
   EvalArgs a{};
   a.one = item;
   a.items = g->items.as<EvalItem>();
-  a.pose_item = nullptr;
+  a.item_start = nullptr;
   a.n_items = 1;
   a.P = (int32_t)P;
   a.K = K;
@@ -401,10 +357,10 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
     CU(cudaEventRecord(evs[0], g->stream), "record event");
   }
   const bool var = g->gc.feature != ALIGN_FEAT_COUNT || out.dump != nullptr;
-  CU(launch_eval(a, n_ctas, var, rotate, g->stream), "launch eval kernel");
+  CU(ek.launch_eval(a, n_ctas, var, rotate, g->stream), "launch eval kernel");
   if (g->profiling) CU(cudaEventRecord(evs[1], g->stream), "record event");
-  CU(launch_compose(a, g->stream), "launch compose kernel");
-  CU(launch_argmax_finalize(a.items, 1, g->stream), "launch argmax");
+  CU(ek.launch_compose(a, g->stream), "launch compose kernel");
+  CU(ek.launch_argmax_finalize(a.items, 1, g->stream), "launch argmax");
   if (g->profiling) {
     CU(cudaEventRecord(evs[2], g->stream), "record event");
     g->ev_pending.push_back(evs);
@@ -480,6 +436,7 @@ align_status align_create_grid(const align_grid_desc* desc, void* cuda_stream, a
   cudaDeviceProp prop;
   CU(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
   if (prop.major < 10) return fail(ALIGN_E_CUDA, "this library is built for sm_103a (found sm_%d%d)", prop.major, prop.minor);
+  for (int i = 0; i < kEvalShapes; ++i) CU(eval_shape(i).setup(), "set up eval kernels");
   align_grid* g = new (std::nothrow) align_grid();
   if (!g) return fail(ALIGN_E_OOM, "host allocation failed");
   g->gc = gc;
@@ -489,7 +446,7 @@ align_status align_create_grid(const align_grid_desc* desc, void* cuda_stream, a
   g->stream = (cudaStream_t)cuda_stream;
   g->device = dev;
   g->n_sm = prop.multiProcessorCount;
-  g->table_slots = eval_table_slots_for(gc.K, prop.sharedMemPerBlockOptin);
+  g->table_slots = eval_shape(0).table_slots_for(gc.K, prop.sharedMemPerBlockOptin);
   for (int i = 0; i < 6; ++i) g->boxA[i] = i < 3 ? INT_MAX : INT_MIN;
   *out = g;
   return ALIGN_OK;
@@ -797,6 +754,32 @@ align_status align_profile(align_grid* g, int32_t mode, double out[3]) {
 
 // Helpers for other translation units of the library (validation, messages, pose rounding).
 namespace mialign {
+const EvalKernels& eval_shape_1024x1();
+const EvalKernels& eval_shape_1024x2();
+const EvalKernels& eval_shape_512x1();
+const EvalKernels& eval_shape(int i) {
+  switch (i) {
+    case 1:
+      return eval_shape_1024x2();
+    case 2:
+      return eval_shape_512x1();
+    default:
+      return eval_shape_1024x1();
+  }
+}
+align_status report_errorf(align_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  return fail(st, "%s", buf);
+}
+int group_pose_rotations(const float* poses12, int64_t P, std::vector<float>& rots, std::vector<int32_t>& idx,
+                         int max_groups) {
+  return group_rotations(poses12, P, rots, idx, max_groups);
+}
+align_status check_grid_device(align_grid* g) { return check_grid(g); }
 align_status check_grid_desc(const align_grid_desc* desc, GridConst* gc) { return validate_desc(desc, gc); }
 align_status report_error(align_status st, const char* msg) { return fail(st, "%s", msg); }
 align_status report_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }

@@ -1,0 +1,76 @@
+// runtime_internal.h — host-side state shared by the library's C-ABI translation units
+// (grids, device buffers, error reporting).  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstdint>
+#include <vector>
+
+#include "align.h"
+#include "align_internal.h"
+
+namespace mialign {
+
+// A growable device allocation (cudaMalloc; contents undefined after growth).
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p != nullptr) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) cap = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+// Error reporting into the thread-local message of align_last_error.
+align_status report_errorf(align_status st, const char* fmt, ...);
+// Distinct rotations (bitwise-equal 3x3 blocks) of a host pose batch and each pose's
+// group; -1 when there are more than max_groups.
+int group_pose_rotations(const float* poses12, int64_t P, std::vector<float>& rots, std::vector<int32_t>& idx,
+                         int max_groups);
+align_status check_grid_device(align_grid* g);
+
+}  // namespace mialign
+
+// A grid: its voxel map, the resident reference state of scan A, and the workspace of its
+// own evaluations.
+struct align_grid {
+  mialign::GridConst gc{};
+  float origin[3];
+  float res_m;
+  int64_t V = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n_sm = 0;
+  int table_slots = 0;
+  bool has_ref = false;
+  int32_t boxA[6];
+  mialign::DevBuf symA, sat;
+  // evaluation workspace
+  mialign::DevBuf xyz, poses, out_c, out_box, mi, hist, best, argmax, err, max_passes, wide_count, wide, dump;
+  mialign::DevBuf pts4, pose_src, rots, redo_list, redo_count, items;
+  int64_t n_points = 0;  // points staged in `xyz`
+  int32_t passes_seed = 1;
+  int64_t stats[5] = {0, 0, 0, 0, 0};
+  // event timing (align_profile): one (before eval, after eval, after argmax) triple per
+  // launch, drained into the totals at the next synchronising call or profile read
+  bool profiling = false;
+  std::vector<std::array<cudaEvent_t, 3>> ev_pending, ev_pool;
+  double prof[3] = {0.0, 0.0, 0.0};
+};

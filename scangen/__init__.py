@@ -348,3 +348,33 @@ def lidar_poses(center=(0, 0, 0, 0, 0, 0), half_width=(2.0, 2.0, 0.25, math.radi
                 counts=(8, 8, 2, 2, 2, 8)) -> np.ndarray:
     """4,096 poses: 8 tx x 8 ty x 2 tz x 2 roll x 2 pitch x 8 yaw around center."""
     return pose_grid(center, half_width, counts)
+
+
+# ----------------------------------------------------------------------------------
+# Batched and served workloads: many pairs of uneven sizes and grid resolutions
+# ----------------------------------------------------------------------------------
+BATCH_RESOLUTIONS = (0.25, 0.5, 1.0)
+
+
+def batched_pairs(n_pairs: int = 64, seed: int = SEED_BASE + 3, n_scenes: int = 4, n_min: int = 20000,
+                  n_max: int = 130000, n_beams: int = 64, az_step_deg: float = 0.15) -> list:
+    """n_pairs independent pairs: point counts log-uniform in [n_min, n_max] (subsampled,
+    scan order kept, from n_scenes ray-cast pairs), grid resolution cycling over 0.25 /
+    0.5 / 1 m with dims covering 80 x 80 x 8 m.  Both scans of a pair get the same count."""
+    rng = np.random.default_rng(seed)
+    bases = [lidar_pair(seed=seed + 100 + k, n_beams=n_beams, az_step_deg=az_step_deg) for k in range(n_scenes)]
+    out = []
+    for i in range(n_pairs):
+        base = bases[i % n_scenes]
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        A = subsample(base.xyzA, n, rng)
+        B = subsample(base.xyzB, n, rng)
+        res = BATCH_RESOLUTIONS[i % len(BATCH_RESOLUTIONS)]
+        out.append(Pair(A, B, base.T.copy(), lidar_grid(res)))
+    return out
+
+
+def poisson_arrivals(rate_hz: float, n: int, seed: int = SEED_BASE + 4) -> np.ndarray:
+    """Arrival times (s) of n requests of a Poisson process with the given mean rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_hz, n))

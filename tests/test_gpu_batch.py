@@ -1,0 +1,161 @@
+"""Many pairs in one persistent launch (align_eval_batch) against the oracle and against
+align_eval_mi on each pair alone: grids of different resolutions, features and symbol
+counts in one launch; empty inputs; graph capture and replay; every kernel shape; the
+tuner; device-resident inputs and outputs.
+
+Bar: each pair's MI within 1e-5 nats of the oracle's FP64 MI and its argmax equal (or
+within the FP32 band); bit-identical MI and argmax to the same pair evaluated alone."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scangen
+from tests.helpers import check_argmax, lib_grid, mi_tolerance, oracle_grid
+
+pytestmark = pytest.mark.gpu
+NT = oracle.host_cores()
+
+
+class Case:
+    def __init__(self, xyzA, xyzB, spec, etas):
+        from paper_1709_06948_gb300 import align
+        self.spec, self.xyzA, self.xyzB, self.etas = spec, xyzA, xyzB, etas
+        self.L = lib_grid(spec)
+        align.align_set_reference(self.L, xyzA)
+        self._oracle = None
+
+    def oracle_mi(self):
+        if self._oracle is None:
+            G = oracle_grid(self.spec)
+            symA, boxA = G.reference(self.xyzA)
+            mo, _, _ = G.eval_mi(symA, boxA, self.xyzB, G.round_pose(self.etas), nthreads=NT)
+            self._oracle = mo
+        return self._oracle
+
+
+@pytest.fixture(scope="module")
+def cases():
+    rng = np.random.default_rng(51)
+    out = []
+    t = scangen.tiny_pair()
+    out.append(Case(t.xyzA, t.xyzB, t.grid, scangen.tiny_poses()[::3]))
+    t2 = scangen.tiny_pair(seed=scangen.SEED_BASE + 52, n=3000)
+    out.append(Case(t2.xyzA, t2.xyzB, t2.grid, scangen.tiny_poses()[::7]))
+    lp = scangen.lidar_pair(seed=scangen.SEED_BASE + 53, n_beams=32)
+    for res in (1.0, 0.5):
+        spec = scangen.lidar_grid(res)
+        B = scangen.subsample(lp.xyzB, 30000 if res == 1.0 else 45000, rng)
+        etas = scangen.lidar_poses(center=lp.T, half_width=(1.0, 1.0, 0.1, 0.01, 0.01, 0.05))[::29]
+        out.append(Case(lp.xyzA, B, spec, etas))
+    joint = scangen.GridSpec(origin=(-40.0, -40.0, -1.0), res_m=0.5, dims=(160, 160, 16), feature=2,
+                             count_levels=7, var_levels=8)
+    out.append(Case(lp.xyzA, lp.xyzB[:20000], joint, scangen.lidar_poses(center=lp.T)[::97]))
+    return out
+
+
+def _pairs(cases):
+    return [(c.L, c.xyzB, c.etas) for c in cases]
+
+
+def test_batch_matches_oracle_and_single(cases):
+    from paper_1709_06948_gb300 import align
+    b = align.align_batch_create()
+    res = align.align_eval_batch(b, _pairs(cases))
+    for c, (mi, am) in zip(cases, res):
+        mo = c.oracle_mi()
+        assert mi.shape == (len(c.etas),)
+        assert np.max(np.abs(mi.astype(np.float64) - mo)) <= mi_tolerance()
+        check_argmax(am, mo)
+        mi1, am1, _ = align.align_eval_mi(c.L, c.xyzB, eta6=c.etas)
+        assert np.array_equal(mi, mi1) and am == am1
+    st = align.align_batch_stats(b)
+    assert st["launches"] == 1 and st["kernel_launches"] == 5
+
+
+def test_every_shape_same_result(cases):
+    from paper_1709_06948_gb300 import align
+    b = align.align_batch_create()
+    ref = align.align_eval_batch(b, _pairs(cases))
+    for shape in range(3):
+        align.align_batch_set_shape(b, shape)
+        res = align.align_eval_batch(b, _pairs(cases))
+        assert align.align_batch_stats(b)["shape"] == shape
+        for (mi0, am0), (mi, am) in zip(ref, res):
+            assert np.array_equal(mi0, mi) and am0 == am
+
+
+def test_graph_replay(cases):
+    """Same shape, new poses: the graph is captured once and replayed; results equal the
+    non-graph launch."""
+    from paper_1709_06948_gb300 import align
+    b = align.align_batch_create()
+    g = align.align_batch_create()
+    shifted = []
+    for k in range(3):
+        pairs = [(c.L, c.xyzB, c.etas + np.array([0.05 * k, -0.03 * k, 0, 0, 0, 0.002 * k])) for c in cases]
+        r_graph = align.align_eval_batch(g, pairs, graph=True)
+        r_plain = align.align_eval_batch(b, pairs)
+        for (mi0, am0), (mi, am) in zip(r_plain, r_graph):
+            assert np.array_equal(mi0, mi) and am0 == am
+        shifted.append(r_graph)
+    st = align.align_batch_stats(g)
+    assert st["graph_captures"] == 1 and st["graph_replays"] == 2
+
+
+def test_tuner_picks_a_shape_and_caches(cases, tmp_path, monkeypatch):
+    from paper_1709_06948_gb300 import align
+    b = align.align_batch_create()
+    ref = align.align_eval_batch(b, _pairs(cases))
+    res = align.align_eval_batch(b, _pairs(cases), tune=True)
+    st = align.align_batch_stats(b)
+    assert st["tuner_trials"] == 3 and 0 <= st["shape"] < 3
+    res2 = align.align_eval_batch(b, _pairs(cases), tune=True)
+    assert align.align_batch_stats(b)["tuner_trials"] == 3  # cached
+    for (mi0, am0), (mi1, am1), (mi2, am2) in zip(ref, res, res2):
+        assert np.array_equal(mi0, mi1) and np.array_equal(mi0, mi2) and am0 == am1 == am2
+
+
+def test_device_inputs_outputs(cases):
+    import torch
+    from paper_1709_06948_gb300 import align
+    b = align.align_batch_create()
+    ref = align.align_eval_batch(b, _pairs(cases))
+    pairs, outs = [], []
+    for c in cases:
+        poses = torch.from_numpy(align.align_round_poses(c.spec.origin, c.etas)).cuda()
+        pairs.append((c.L, torch.from_numpy(c.xyzB).cuda(), None, poses))
+        outs.append((torch.empty(len(c.etas), device="cuda"), torch.empty(1, dtype=torch.int64, device="cuda")))
+    align.align_eval_batch(b, pairs, out=outs)
+    torch.cuda.synchronize()
+    for (mi0, am0), (mi_t, am_t) in zip(ref, outs):
+        assert np.array_equal(mi0, mi_t.cpu().numpy()) and am0 == int(am_t.item())
+
+
+def test_empty_pairs_in_a_batch(cases):
+    from paper_1709_06948_gb300 import align
+    b = align.align_batch_create()
+    c = cases[0]
+    pairs = [(c.L, c.xyzB, np.zeros((0, 6))), (c.L, np.zeros((0, 3), np.float32), c.etas), (c.L, c.xyzB, c.etas)]
+    res = align.align_eval_batch(b, pairs)
+    assert res[0][0].shape == (0,) and res[0][1] == -1
+    assert np.all(res[1][0] == 0.0) and res[1][1] == 0
+    mi1, am1, _ = align.align_eval_mi(c.L, c.xyzB, eta6=c.etas)
+    assert np.array_equal(res[2][0], mi1) and res[2][1] == am1
+    assert align.align_eval_batch(b, []) == []
+
+
+def test_batch_errors(cases):
+    from paper_1709_06948_gb300 import align
+    b = align.align_batch_create()
+    c = cases[0]
+    L = lib_grid(c.spec)  # no reference
+    with pytest.raises(align.AlignError) as e:
+        align.align_eval_batch(b, [(L, c.xyzB, c.etas)])
+    assert e.value.status == align.ALIGN_E_NOREF
+    bad = c.etas.copy()
+    bad[0, 0] = math.nan
+    with pytest.raises(align.AlignError) as e:
+        align.align_eval_batch(b, [(c.L, c.xyzB, bad)])
+    assert e.value.status == align.ALIGN_E_INVALID
