@@ -236,6 +236,56 @@ align_status align_batch_set_shape(align_batch* b, int32_t shape);
    time of the last launch in microseconds (pack to argmax), [7] tuner trials run. */
 align_status align_batch_stats(const align_batch* b, int64_t out[8]);
 
+/* ---------------------------------------------------------------------------------
+   Serving: alignment requests (a lattice search of scan B against a resident reference
+   scan A, as align_search_ex) submitted at any time.  A worker thread runs continuous
+   batching: at every step it admits queued requests while request slots and the device
+   memory budget allow, evaluates the current lattice level of every active request in
+   one batched launch (align_eval_batch), moves each request to its next level, and
+   retires finished ones, freeing their slot and memory.  A request's result is the same
+   as align_search_ex on its grid alone.
+   --------------------------------------------------------------------------------- */
+typedef struct align_server align_server;
+
+typedef struct align_request {
+  int32_t ref_id;          /* from align_server_add_reference */
+  const float* xyzB;       /* nB x 3 fp32, host memory, copied by align_submit */
+  int64_t nB;
+  double init[6];          /* lattice centre of level 0 (eta) */
+  double range[6];         /* half-widths of level 0 (they halve every level) */
+  int32_t counts[6];       /* samples per axis (tx, ty, tz, rx, ry, rz); {0} = {8,8,2,2,2,8} */
+  int32_t levels;
+} align_request;
+
+typedef struct align_result {
+  double T[6];             /* final centre (eta) */
+  float mi;                /* its MI */
+  int32_t status;          /* ALIGN_OK or the failure of the step that ran the request */
+  double t_submit, t_start, t_done;  /* seconds on the server's monotonic clock */
+} align_result;
+
+/* hbm_budget_bytes: device memory the server may hold for references and active requests
+   (estimated per request from its sizes); max_slots: most requests active at once. */
+align_status align_server_create(size_t hbm_budget_bytes, int32_t max_slots, align_server** out);
+/* Keep scan A (host, nA x 3 fp32) resident as a reference under `desc`; *ref_id names it. */
+align_status align_server_add_reference(align_server* s, const align_grid_desc* desc, const float* xyzA,
+                                        int64_t nA, int32_t* ref_id);
+/* Queue a request; *ticket identifies it.  ALIGN_E_OOM if it could never fit the budget. */
+align_status align_submit(align_server* s, const align_request* req, uint64_t* ticket);
+/* ALIGN_NOT_READY while the request runs; ALIGN_OK with *out filled (once) when done. */
+align_status align_poll(align_server* s, uint64_t ticket, align_result* out);
+/* Block until done or timeout_ms elapses (ALIGN_E_TIMEOUT); timeout_ms < 0 waits forever. */
+align_status align_wait(align_server* s, uint64_t ticket, int64_t timeout_ms, align_result* out);
+/* Seconds on the server's monotonic clock (the clock of align_result's times). */
+double align_server_now(const align_server* s);
+/* [0] batched steps, [1] requests admitted, [2] requests done, [3] most requests active
+   at once, [4] pose evaluations, [5] device bytes held now (estimate), [6] peak of [5],
+   [7] requests waiting in the queue. */
+align_status align_server_stats(align_server* s, int64_t out[8]);
+/* Stops the worker after its current step; queued and active requests are dropped.  No
+   call on the server (align_wait included) may be in progress or follow. */
+align_status align_server_destroy(align_server* s);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* align_last_error(void);
 

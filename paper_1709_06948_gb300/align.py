@@ -29,7 +29,9 @@ _STATUS_NAMES = {0: "ALIGN_OK", 1: "ALIGN_NOT_READY", -1: "ALIGN_E_INVALID", -2:
 EXPORTS = ["align_create_grid", "align_destroy_grid", "align_grid_info", "align_set_reference",
            "align_get_reference", "align_round_poses", "align_eval_mi", "align_accumulate", "align_search",
            "align_search_ex", "align_eval_stats", "align_profile", "align_reference_noalloc", "align_batch_create",
-           "align_batch_destroy", "align_eval_batch", "align_batch_set_shape", "align_batch_stats", "align_last_error"]
+           "align_batch_destroy", "align_eval_batch", "align_batch_set_shape", "align_batch_stats",
+           "align_server_create", "align_server_add_reference", "align_submit", "align_poll", "align_wait",
+           "align_server_now", "align_server_stats", "align_server_destroy", "align_last_error"]
 
 
 class AlignError(RuntimeError):
@@ -47,6 +49,16 @@ class GridDesc(C.Structure):
 class AlignPair(C.Structure):
     _fields_ = [("grid", C.c_void_p), ("xyzB", C.c_void_p), ("nB", C.c_int64), ("poses12", C.c_void_p),
                 ("eta6", C.c_void_p), ("P", C.c_int64), ("mi_out", C.c_void_p), ("argmax_out", C.c_void_p)]
+
+
+class AlignRequest(C.Structure):
+    _fields_ = [("ref_id", C.c_int32), ("xyzB", C.c_void_p), ("nB", C.c_int64), ("init", C.c_double * 6),
+                ("range", C.c_double * 6), ("counts", C.c_int32 * 6), ("levels", C.c_int32)]
+
+
+class AlignResult(C.Structure):
+    _fields_ = [("T", C.c_double * 6), ("mi", C.c_float), ("status", C.c_int32), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double)]
 
 
 _lib = None
@@ -87,11 +99,20 @@ def load(build_if_missing: bool = True):
         "align_eval_batch": [P, P, i32, C.c_int],
         "align_batch_set_shape": [P, i32],
         "align_batch_stats": [P, P],
+        "align_server_create": [C.c_size_t, i32, P],
+        "align_server_add_reference": [P, P, P, i64, P],
+        "align_submit": [P, P, P],
+        "align_poll": [P, C.c_uint64, P],
+        "align_wait": [P, C.c_uint64, i64, P],
+        "align_server_stats": [P, P],
+        "align_server_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = C.c_int
+    lib.align_server_now.argtypes = [P]
+    lib.align_server_now.restype = C.c_double
     lib.align_last_error.argtypes = []
     lib.align_last_error.restype = C.c_char_p
     _lib = lib
@@ -473,4 +494,102 @@ def align_batch_stats(batch: Batch):
     _check(load().align_batch_stats(batch.handle, out.ctypes.data_as(C.c_void_p)))
     keys = ["launches", "graph_captures", "graph_replays", "shape", "table_slots", "kernel_launches",
             "last_us", "tuner_trials"]
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+# ---------------------------------------------------------------------------------------
+# serving: continuous batching of alignment requests
+# ---------------------------------------------------------------------------------------
+class Server:
+    """Owns an align_server* (worker thread, resident references, batch workspace)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().align_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def align_server_create(hbm_budget_bytes: int, max_slots: int) -> Server:
+    h = C.c_void_p()
+    _check(load().align_server_create(int(hbm_budget_bytes), int(max_slots), C.byref(h)))
+    return Server(h)
+
+
+def align_server_destroy(server: Server):
+    server.close()
+
+
+def align_server_add_reference(server: Server, xyzA, origin, res_m, dims, feature=ALIGN_FEAT_ZVAR, count_levels=7,
+                               var_levels=15) -> int:
+    d = GridDesc()
+    d.origin = (C.c_float * 3)(*[float(v) for v in origin])
+    d.res_m = float(res_m)
+    d.dims = (C.c_int32 * 3)(*[int(v) for v in dims])
+    d.feature = int(feature)
+    d.count_levels = int(count_levels)
+    d.var_levels = int(var_levels)
+    a = _host(xyzA, np.float32, (3,))
+    rid = C.c_int32(-1)
+    _check(load().align_server_add_reference(server.handle, C.byref(d), a.ctypes.data_as(C.c_void_p),
+                                             int(a.shape[0]), C.byref(rid)))
+    return int(rid.value)
+
+
+def align_submit(server: Server, ref_id: int, xyzB, init, rng, levels=6, counts=None) -> int:
+    a = _host(xyzB, np.float32, (3,))
+    r = AlignRequest()
+    r.ref_id = int(ref_id)
+    r.xyzB = a.ctypes.data
+    r.nB = int(a.shape[0])
+    r.init = (C.c_double * 6)(*[float(v) for v in init])
+    r.range = (C.c_double * 6)(*[float(v) for v in rng])
+    r.counts = (C.c_int32 * 6)(*([0] * 6 if counts is None else [int(v) for v in counts]))
+    r.levels = int(levels)
+    t = C.c_uint64(0)
+    _check(load().align_submit(server.handle, C.byref(r), C.byref(t)))
+    return int(t.value)
+
+
+def _result_dict(res: AlignResult):
+    return {"T": np.array(res.T[:], dtype=np.float64), "mi": float(res.mi), "status": int(res.status),
+            "t_submit": float(res.t_submit), "t_start": float(res.t_start), "t_done": float(res.t_done)}
+
+
+def align_poll(server: Server, ticket: int):
+    """The result dict when done, else None."""
+    res = AlignResult()
+    st = load().align_poll(server.handle, C.c_uint64(ticket), C.byref(res))
+    if st == ALIGN_NOT_READY:
+        return None
+    _check(st)
+    return _result_dict(res)
+
+
+def align_wait(server: Server, ticket: int, timeout_ms: int = -1):
+    res = AlignResult()
+    _check(load().align_wait(server.handle, C.c_uint64(ticket), int(timeout_ms), C.byref(res)))
+    return _result_dict(res)
+
+
+def align_server_now(server: Server) -> float:
+    return float(load().align_server_now(server.handle))
+
+
+def align_server_stats(server: Server):
+    out = np.zeros(8, dtype=np.int64)
+    _check(load().align_server_stats(server.handle, out.ctypes.data_as(C.c_void_p)))
+    keys = ["steps", "admitted", "done", "max_active", "pose_evals", "bytes_held", "bytes_peak", "queued"]
     return {k: int(v) for k, v in zip(keys, out)}

@@ -780,6 +780,11 @@ int group_pose_rotations(const float* poses12, int64_t P, std::vector<float>& ro
   return group_rotations(poses12, P, rots, idx, max_groups);
 }
 align_status check_grid_device(align_grid* g) { return check_grid(g); }
+void lattice_poses(const float origin[3], const double c[6], const double r[6], const int32_t m[6],
+                   std::vector<double>& eta, std::vector<float>& poses) {
+  build_lattice(c, r, m, eta);
+  round_lattice(origin, eta, m, poses);
+}
 align_status check_grid_desc(const align_grid_desc* desc, GridConst* gc) { return validate_desc(desc, gc); }
 align_status report_error(align_status st, const char* msg) { return fail(st, "%s", msg); }
 align_status report_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }

@@ -45,6 +45,10 @@ align_status report_errorf(align_status st, const char* fmt, ...);
 int group_pose_rotations(const float* poses12, int64_t P, std::vector<float>& rots, std::vector<int32_t>& idx,
                          int max_groups);
 align_status check_grid_device(align_grid* g);
+// One level of the coarse-to-fine lattice: FP64 poses around centre c (ranges r, m samples
+// per axis; order rx, ry, rz, tx, ty, tz with tz fastest) and their rounded FP32 form.
+void lattice_poses(const float origin[3], const double c[6], const double r[6], const int32_t m[6],
+                   std::vector<double>& eta, std::vector<float>& poses);
 
 }  // namespace mialign
 
