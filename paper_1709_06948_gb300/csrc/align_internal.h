@@ -50,7 +50,7 @@ struct EvalItem {
   int32_t n_tiles;            // tiles per copy (>= 3)
   int32_t P;                  // poses of this item
   int32_t pose_base;          // global index of the item's pose 0
-  int32_t pad0;
+  int32_t passes0;            // initial key partitions of this item's poses (power of two; 0: the launch's)
   uint32_t* out_c;            // P x K x K
   int32_t* out_box;           // P x 6
   float* mi;                  // P
@@ -59,6 +59,7 @@ struct EvalItem {
   int64_t* argmax;            // one
   int64_t* dump;              // optional: V x 3 (n, S1, S2) of pose 0 (parity checks; S1, S2
                               // are accumulated whenever dump is set, whatever the feature)
+  uint32_t* item_passes;      // optional: running max of the partitions this item's poses used
 };
 
 struct EvalArgs {

@@ -56,7 +56,7 @@ struct PairPlan {
 // Workspace sizes of one launch; a change of any of them re-allocates and drops the graph.
 struct Sizes {
   size_t xyz = 0, poses = 0, pts = 0, pose_src = 0, copies = 0, items = 0, starts = 0, outc = 0, box = 0,
-         best = 0, mi = 0, argmax = 0, redo = 0, wide = 0;
+         best = 0, mi = 0, argmax = 0, redo = 0, wide = 0, ipasses = 0;
 };
 
 std::string env_cache_path() {
@@ -115,9 +115,10 @@ struct align_batch {
   size_t smem_optin = 0;
   std::string device_name;
   int shape_fixed = -1;
-  int32_t passes_seed = 1;
   DevBuf xyz, poses, pts, pose_src, copies, items, starts, outc, box, best, mi, argmax, redo_list, redo_count, wide,
-      status;
+      status, ipasses;
+  std::vector<align_grid*> last_grids;  // grids of the last launch (per-item partition feedback)
+  int last_shape = 0;
   Sizes cap;
   // graph of the last launch sequence
   cudaGraphExec_t exec = nullptr;
@@ -160,6 +161,7 @@ struct Launch {
 align_status enqueue_launch(align_batch* b, const Launch& L) {
   cudaStream_t s = b->stream;
   BCU(cudaMemsetAsync(b->best.p, 0, (size_t)L.n_items * 8, s), "clear argmax keys");
+  BCU(cudaMemsetAsync(b->ipasses.p, 0, (size_t)L.n_items * 4, s), "clear partition counts");
   BCU(cudaMemsetAsync(b->redo_count.p, 0, 4, s), "clear redo count");
   BCU(L.ek->launch_pack_batch(b->copies.as<PackCopy>(), L.n_copies, L.max_out, s), "launch pack");
   BCU(L.ek->launch_eval(L.a, L.n_ctas, L.var, L.rotate, s), "launch eval kernel");
@@ -204,15 +206,23 @@ align_status run_launch(align_batch* b, const Launch& L, bool use_graph, const s
 // Read the kernels' status words (synchronises the stream).
 align_status collect(align_batch* b) {
   uint32_t v[3] = {0, 0, 0};
+  std::vector<uint32_t> ip(b->last_grids.size(), 0);
   BCU(cudaMemcpyAsync(v, b->status.p, 12, cudaMemcpyDeviceToHost, b->stream), "read status");
+  if (!ip.empty())
+    BCU(cudaMemcpyAsync(ip.data(), b->ipasses.p, ip.size() * 4, cudaMemcpyDeviceToHost, b->stream),
+        "read partition counts");
   BCU(cudaStreamSynchronize(b->stream), "synchronize");
+  // seed each grid's next launches with the partitions its poses needed (a power of two)
+  for (size_t i = 0; i < ip.size(); ++i) {
+    align_grid* g = b->last_grids[i];
+    int32_t& seed = g->passes_seed[b->last_shape];
+    if (ip[i] > (uint32_t)seed && ip[i] <= (1u << 16) && (ip[i] & (ip[i] - 1)) == 0) seed = (int32_t)ip[i];
+  }
   float ms = 0.0f;
   if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->stats[6] = (int64_t)std::llround(ms * 1000.0);
   // reset the error word and the wide-voxel count; the partition count stays a running max
   BCU(cudaMemsetAsync(b->status.p, 0, 4, b->stream), "reset status");
   BCU(cudaMemsetAsync(b->status.as<uint32_t>() + 2, 0, 4, b->stream), "reset status");
-  if (v[1] > (uint32_t)b->passes_seed && v[1] <= (1u << 16) && (v[1] & (v[1] - 1)) == 0)
-    b->passes_seed = (int32_t)v[1];
   if (v[0] & kErrWaitTimeout) return report_error(ALIGN_E_TIMEOUT, "a bounded device wait gave up");
   if (v[0] & kErrDzBound) return report_error(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");
   if (v[0] & kErrPassLimit) return report_error(ALIGN_E_INTERNAL, "key partitioning limit reached");
@@ -268,7 +278,7 @@ align_status align_batch_destroy(align_batch* b) {
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
   for (DevBuf* d : {&b->xyz, &b->poses, &b->pts, &b->pose_src, &b->copies, &b->items, &b->starts, &b->outc, &b->box,
-                    &b->best, &b->mi, &b->argmax, &b->redo_list, &b->redo_count, &b->wide, &b->status})
+                    &b->best, &b->mi, &b->argmax, &b->redo_list, &b->redo_count, &b->wide, &b->status, &b->ipasses})
     d->release();
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
@@ -361,6 +371,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   GROW(mi, mi, (size_t)poses_n * 4, "allocate MI", false);
   GROW(argmax, argmax, (size_t)n * 8, "allocate argmax", false);
   GROW(redo_list, redo, (size_t)poses_n * 4, "allocate redo list", false);
+  GROW(ipasses, ipasses, (size_t)n * 4, "allocate partition counts", false);
   GROW(wide, wide, (size_t)n_ctas * 2 * T * 8, "allocate wide sums", true);
 #undef GROW
   if (!b->status.p || !b->redo_count.p) {
@@ -427,6 +438,8 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     it.best = b->best.as<unsigned long long>() + i;
     it.argmax = b->argmax.as<int64_t>() + i;
     it.dump = nullptr;
+    it.passes0 = g->passes_seed[shape];
+    it.item_passes = b->ipasses.as<uint32_t>() + i;
     hstarts[(size_t)i] = (int32_t)pp.pose_off;
   }
   hstarts[(size_t)n] = (int32_t)poses_n;
@@ -459,7 +472,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   a.K = maxK;
   a.table_slots = T;
   a.n_buckets = T / 4;
-  a.passes0 = b->passes_seed;
+  a.passes0 = 1;  // every item brings its grid's own partition count
   uint32_t* status = b->status.as<uint32_t>();
   a.err = status;
   a.max_passes = status + 1;
@@ -467,6 +480,9 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   a.wide = b->wide.as<unsigned long long>();
   a.redo_list = b->redo_list.as<uint32_t>();
   a.redo_count = b->redo_count.as<uint32_t>();
+  b->last_grids.clear();
+  for (const PairPlan& pp : plans) b->last_grids.push_back(pp.g);
+  b->last_shape = shape;
   const std::vector<int64_t> sig = {shape,   n,       rotate,     var,      a.passes0, T, n_ctas,
                                     poses_n, n_copies, max_out,   maxK,     (int64_t)(uintptr_t)b->pts.p,
                                     (int64_t)(uintptr_t)b->items.p};

@@ -554,11 +554,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
   init_smem(S, T, a.K * a.K);
   __syncthreads();
   int passes = a.passes0;
+  int cur = -1;  // item of the previous pose: key partitions are learned per item
 
   for (int gp = blockIdx.x; gp < a.P; gp += gridDim.x) {
     const int it = kOne ? 0 : item_of(a, gp);
     select_item(S, a, it);
     const EvalItem& I = item_at<kOne>(a, it);
+    if (it != cur) {
+      if (cur >= 0 && tid == 0 && item_at<kOne>(a, cur).item_passes)
+        atomicMax(item_at<kOne>(a, cur).item_passes, (uint32_t)passes);
+      cur = it;
+      if (I.passes0 > 0) passes = I.passes0;
+    }
     const int lp = gp - I.pose_base;
     const VoxelConst vc = voxel_const(kOne ? a.one.gc : *S.gc);
     const int dz_shift = kOne ? a.one.gc.dz_shift : S.gc->dz_shift;
@@ -605,7 +612,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
     emit_pose(S, I, lp);
     if (max_occupied > cap && passes < kMaxPasses) passes *= 2;  // crowded: more partitions next
   }
-  if (tid == 0) atomicMax(a.max_passes, (uint32_t)passes);
+  if (tid == 0) {
+    atomicMax(a.max_passes, (uint32_t)passes);
+    if (cur >= 0 && item_at<kOne>(a, cur).item_passes) atomicMax(item_at<kOne>(a, cur).item_passes, (uint32_t)passes);
+  }
 }
 
 // Poses that eval_kernel could not finish: plain sweeps; each run goes straight into the

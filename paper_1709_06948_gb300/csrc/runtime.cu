@@ -320,6 +320,8 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
   item.n_tiles = n_tiles;
   item.P = (int32_t)P;
   item.pose_base = 0;
+  item.passes0 = g->passes_seed[0];
+  item.item_passes = nullptr;
   item.out_c = g->out_c.as<uint32_t>();
   item.out_box = g->out_box.as<int32_t>();
   item.mi = out.mi;
@@ -339,7 +341,7 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
   a.K = K;
   a.table_slots = g->table_slots;
   a.n_buckets = g->table_slots / 4;
-  a.passes0 = g->passes_seed;
+  a.passes0 = g->passes_seed[0];
   a.err = g->err.as<uint32_t>();
   a.max_passes = g->max_passes.as<uint32_t>();
   a.wide_count = g->wide_count.as<uint32_t>();
@@ -401,8 +403,8 @@ align_status collect_status(align_grid* g) {
   CU(cudaMemsetAsync(g->err.p, 0, 4, g->stream), "reset error word");
   CU(cudaMemsetAsync(g->wide_count.p, 0, 4, g->stream), "reset counters");
   // seed the next launch with the largest partition count a pose needed (a power of two)
-  if (vals[1] > (uint32_t)g->passes_seed && vals[1] <= (1u << 16) && (vals[1] & (vals[1] - 1)) == 0)
-    g->passes_seed = (int32_t)vals[1];
+  if (vals[1] > (uint32_t)g->passes_seed[0] && vals[1] <= (1u << 16) && (vals[1] & (vals[1] - 1)) == 0)
+    g->passes_seed[0] = (int32_t)vals[1];
   g->stats[0] = vals[1];
   g->stats[1] = vals[2];
   if (vals[0] & kErrWaitTimeout) return fail(ALIGN_E_TIMEOUT, "a bounded device wait gave up");
@@ -730,6 +732,7 @@ align_status align_search(align_grid* g, const float* xyzB, int64_t nB, int flag
 align_status align_eval_stats(align_grid* g, int64_t out[5]) {
   if (!g || !out) return fail(ALIGN_E_INVALID, "NULL argument");
   for (int i = 0; i < 5; ++i) out[i] = g->stats[i];
+  out[0] = std::max<int64_t>(out[0], g->passes_seed[0]);  // batched launches feed back through the seed
   return ALIGN_OK;
 }
 

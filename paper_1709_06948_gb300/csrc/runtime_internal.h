@@ -70,7 +70,8 @@ struct align_grid {
   mialign::DevBuf xyz, poses, out_c, out_box, mi, hist, best, argmax, err, max_passes, wide_count, wide, dump;
   mialign::DevBuf pts4, pose_src, rots, redo_list, redo_count, items;
   int64_t n_points = 0;  // points staged in `xyz`
-  int32_t passes_seed = 1;
+  // key partitions the next launch starts with, per kernel shape (its table size)
+  int32_t passes_seed[mialign::kEvalShapes] = {1, 1, 1};
   int64_t stats[5] = {0, 0, 0, 0, 0};
   // event timing (align_profile): one (before eval, after eval, after argmax) triple per
   // launch, drained into the totals at the next synchronising call or profile read
