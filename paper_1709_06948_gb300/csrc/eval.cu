@@ -90,6 +90,14 @@ __device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
 }
+// st.shared.v4 under a predicate (no branch around the store).
+__device__ __forceinline__ void sts128_if(bool p, uint32_t a, uint4 v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.shared.v4.u32 [%1], {%2, %3, %4, %5};\n\t}" ::"r"(
+          (uint32_t)p),
+      "r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+      : "memory");
+}
 __device__ __forceinline__ void red_add(uint32_t a, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
@@ -185,12 +193,31 @@ __device__ __forceinline__ VoxelConst voxel_const(const GridConst& g) {
 // Find or insert `key` in the open-addressing table: buckets of 4 key slots read with one
 // 16-byte load, probed linearly; slots of a bucket fill in order, so a bucket with a free
 // slot ends the search.  Returns -1 when kProbeBuckets buckets were searched in vain (the
-// pose then counts as overflowing the table).
+// pose then counts as overflowing the table).  The home bucket is tried in straight-line
+// code; the loop over further buckets is a separate (rarely called) function.
+__device__ __noinline__ int table_slot_slow(uint32_t a_key, uint32_t key, uint32_t nb, uint32_t b);
 __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, uint32_t nb) {
-  uint32_t b = __umulhi(key * 0x9E3779B1u, nb);
+  const uint32_t b = __umulhi(key * 0x9E3779B1u, nb);
+  const uint4 k4 = lds128(S.a_key + 16u * b);
+  const uint32_t hit = (uint32_t)(k4.x == key) | ((uint32_t)(k4.y == key) << 1) | ((uint32_t)(k4.z == key) << 2) |
+                       ((uint32_t)(k4.w == key) << 3);
+  const uint32_t emp = (uint32_t)(k4.x == kEmptyKey) | ((uint32_t)(k4.y == kEmptyKey) << 1) |
+                       ((uint32_t)(k4.z == kEmptyKey) << 2) | ((uint32_t)(k4.w == kEmptyKey) << 3);
+  int slot = -1;
+  if (hit) {
+    slot = (int)(4 * b) + __ffs(hit) - 1;
+  } else if (emp) {
+    const uint32_t s = 4 * b + (uint32_t)(__ffs(emp) - 1);
+    const uint32_t old = atom_cas(S.a_key + 4u * s, kEmptyKey, key);
+    if (old == kEmptyKey || old == key) slot = (int)s;
+  }
+  if (slot < 0) slot = table_slot_slow(S.a_key, key, nb, b);
+  return slot;
+}
+__device__ __noinline__ int table_slot_slow(uint32_t a_key, uint32_t key, uint32_t nb, uint32_t b) {
 #pragma unroll 1
   for (int i = 0; i < kProbeBuckets; ++i) {
-    const uint4 k4 = lds128(S.a_key + 16u * b);
+    const uint4 k4 = lds128(a_key + 16u * b);
     if (k4.x == key) return (int)(4 * b);
     if (k4.y == key) return (int)(4 * b + 1);
     if (k4.z == key) return (int)(4 * b + 2);
@@ -202,7 +229,7 @@ __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, uint3
                                         : -1;
     if (e >= 0) {
       const uint32_t s = 4 * b + (uint32_t)e;
-      const uint32_t old = atom_cas(S.a_key + 4u * s, kEmptyKey, key);
+      const uint32_t old = atom_cas(a_key + 4u * s, kEmptyKey, key);
       if (old == kEmptyKey || old == key) return (int)s;
       continue;  // another lane took that slot: read the bucket again
     }
@@ -292,9 +319,10 @@ template <bool kVar>
 __device__ __forceinline__ void ring_push(const EvalSmem& S, uint32_t ring, uint32_t lane_lt, bool done,
                                           const Run& r, uint32_t& fill, uint32_t nb) {
   const uint32_t m = __ballot_sync(kFull, done);
-  if (done) sts128(ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), make_uint4(r.key, r.n, r.s1, r.s2));
+  sts128_if(done, ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), make_uint4(r.key, r.n, r.s1, r.s2));
   fill += (uint32_t)__popc(m);
-  if (fill >= 32u) ring_drain<kVar>(S, ring, fill, 32u, nb);
+  // fill is the same in every lane; the vote lets the compiler know the branch is uniform
+  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVar>(S, ring, fill, 32u, nb);
 }
 
 struct PoseRegs {
@@ -517,7 +545,21 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const VoxelCon
   load_tile(src, 1, b1);
   load_tile(src, 2, b2);
   int next_cut = cut;
-  for (int t = 0; t < nt; t += 3) {
+  int t = 0;
+  for (; t + 6 <= nt; t += 3) {  // all three prefetches in range: no guards
+    if (t >= next_cut) {
+      ring_push<kVar>(S, ring, lane_lt, true, run, fill, nb);
+      run = Run{kEmptyKey, 0u, 0u, 0u};
+      next_cut += cut;
+    }
+    sweep_tile<kVar, kRot, kPart>(S, vc, P, b0, lg, part, run, ring, lane_lt, fill, nb, bad);
+    load_tile(src, t + 3, b0);
+    sweep_tile<kVar, kRot, kPart>(S, vc, P, b1, lg, part, run, ring, lane_lt, fill, nb, bad);
+    load_tile(src, t + 4, b1);
+    sweep_tile<kVar, kRot, kPart>(S, vc, P, b2, lg, part, run, ring, lane_lt, fill, nb, bad);
+    load_tile(src, t + 5, b2);
+  }
+  for (; t < nt; t += 3) {
     if (t >= next_cut) {  // uniform; only when a stream is longer than nlim points
       ring_push<kVar>(S, ring, lane_lt, true, run, fill, nb);
       run = Run{kEmptyKey, 0u, 0u, 0u};
