@@ -31,6 +31,7 @@ struct GridConst {
   int32_t dz_shift;       // smallest m with 2^m > 2 * dz_bound (the sweep checks dz + dz_bound < 2^m)
   uint32_t nlim;          // largest n whose S1, S2 fit the 32-bit table sums for |dz| < 2^m - dz_bound
   int32_t boxA[6];        // A's occupied bbox (xmin > xmax when empty)
+  uint64_t div_x, div_y;  // floor((2^64 - 1) / X) + 1 (0 when X == 1): k / X = umulhi64(div_x, k) for k < 2^32
   uint32_t count_thresh[kMaxLevels];
   int64_t var_thresh[kMaxLevels];
 };

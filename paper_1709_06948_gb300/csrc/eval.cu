@@ -382,6 +382,39 @@ __device__ __forceinline__ void select_item(const EvalSmem& S, const EvalArgs& a
   __syncthreads();
 }
 
+// Feature symbol of a voxel whose sums fit the 32-bit table (n <= nlim, so n*S2 < 2^64 and
+// S1^2 < 2^62): the same integer tests as feature_symbol, in 64-bit arithmetic.  The variance
+// test n*S2 - S1^2 >= t*n^2 compares the 128-bit product t*n^2 by its high and low words.
+__device__ __forceinline__ int feature_symbol_small(const GridConst& gc, uint32_t n, int32_t s1, uint32_t s2) {
+  if (n == 0u) return 0;
+  int lc = 0, lv = 0;
+  if (gc.feature != 1) {  // count level: #{j : n >= ct[j]}, a prefix of the ascending thresholds
+    int lo = 0, hi = gc.Lc - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (n >= gc.count_thresh[mid]) lo = mid + 1;
+      else hi = mid;
+    }
+    lc = lo;
+  }
+  if (gc.feature != 0) {  // variance level: #{j : n*S2 - S1^2 >= vt[j] * n^2}
+    const uint64_t spread = (uint64_t)n * s2 - (uint64_t)((int64_t)s1 * s1);  // >= 0 (Cauchy-Schwarz)
+    const uint64_t n2 = (uint64_t)n * n;
+    int lo = 0, hi = gc.Lv - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      const uint64_t t = (uint64_t)gc.var_thresh[mid];  // thresholds are >= 0
+      const bool reached = __umul64hi(t, n2) == 0ull && t * n2 <= spread;
+      if (reached) lo = mid + 1;
+      else hi = mid;
+    }
+    lv = lo;
+  }
+  if (gc.feature == 0) return 1 + lc;
+  if (gc.feature == 1) return 1 + lv;
+  return 1 + lc * gc.Lv + lv;
+}
+
 // Read (and clear) the table after a sweep: symbols, bbox and histogram unless `discard`.
 // The CTA-wide occupied count is added to S.flags[0].
 template <bool kVar, bool kExact>
@@ -413,13 +446,16 @@ __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& g
     sts32(v + 4u, 0u);
     sts32(v + 8u, 0u);
     if (discard) continue;
-    const int kx = (int)(k % (uint32_t)gc.X);
-    const uint32_t r = k / (uint32_t)gc.X;
-    const int ky = (int)(r % (uint32_t)gc.Y);
-    const int kz = (int)(r / (uint32_t)gc.Y);
+    const uint32_t r = gc.div_x ? (uint32_t)__umul64hi(gc.div_x, k) : k;  // k / X
+    const uint32_t q = gc.div_y ? (uint32_t)__umul64hi(gc.div_y, r) : r;  // r / Y
+    const int kx = (int)(k - r * (uint32_t)gc.X);
+    const int ky = (int)(r - q * (uint32_t)gc.Y);
+    const int kz = (int)q;
     mn0 = min(mn0, kx); mn1 = min(mn1, ky); mn2 = min(mn2, kz);
     mx0 = max(mx0, kx); mx1 = max(mx1, ky); mx2 = max(mx2, kz);
-    const int sB = feature_symbol(gc.feature, gc.Lc, gc.Lv, gc.count_thresh, gc.var_thresh, n, s1, s2);
+    const int sB = (kExact || n > gc.nlim)
+                       ? feature_symbol(gc.feature, gc.Lc, gc.Lv, gc.count_thresh, gc.var_thresh, n, s1, s2)
+                       : feature_symbol_small(gc, (uint32_t)n, (int32_t)s1, (uint32_t)s2);
     if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
         kz <= gc.boxA[5])
       red_add(S.a_hist + 4u * (uint32_t)((int)__ldg(I.symA + k) * K + sB), 1u);

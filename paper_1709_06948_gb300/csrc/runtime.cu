@@ -180,6 +180,10 @@ align_status validate_desc(const align_grid_desc* d, GridConst* gc) {
   const uint64_t D = (uint64_t)((1 << m) - 1 - gc->dz_bound);
   gc->nlim = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull / (D * D), 0x7FFFFFFFull / D);
   for (int i = 0; i < 3; ++i) gc->boxA[i] = INT_MAX, gc->boxA[3 + i] = INT_MIN;
+  // division of 32-bit keys by X and Y as a 64-bit multiply-high (Lemire, Kaser and Kurz,
+  // "Faster remainder by direct computation", 2019: exact for every 32-bit dividend)
+  gc->div_x = gc->X > 1 ? UINT64_MAX / (uint64_t)gc->X + 1 : 0;
+  gc->div_y = gc->Y > 1 ? UINT64_MAX / (uint64_t)gc->Y + 1 : 0;
   return ALIGN_OK;
 }
 
