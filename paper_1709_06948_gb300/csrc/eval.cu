@@ -417,59 +417,93 @@ __device__ __forceinline__ int feature_symbol_small(const GridConst& gc, uint32_
 
 // Read (and clear) the table after a sweep: symbols, bbox and histogram unless `discard`.
 // The CTA-wide occupied count is added to S.flags[0].
+// Bbox accumulators of a warp's share of the table scan.
+struct ScanBox {
+  int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX, mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
+};
+
+// One occupied slot: read and clear it, then (unless `discard`) its voxel's coordinates,
+// feature symbol and joint-histogram entry.
+template <bool kVar, bool kExact>
+__device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& gc, const EvalItem& I,
+                                           unsigned long long* wide, uint32_t* wide_count, uint32_t s, int lp,
+                                           bool discard, ScanBox& bx) {
+  const uint32_t k = lds32(S.a_key + 4u * s);
+  const uint32_t v = S.a_vals + 12u * s;
+  const uint64_t n = lds32(v);
+  int64_t s1 = (int32_t)lds32(v + 4u);
+  uint64_t s2 = lds32(v + 8u);
+  if (!kExact && kVar && n > gc.nlim) sts32(S.a_key - kFlagWide, 1u);  // sums may have wrapped: exact path
+  if (kExact && kVar && n > gc.nlim) {
+    s1 += (int64_t)wide[2 * s];
+    s2 += wide[2 * s + 1];
+    wide[2 * s] = 0ull;
+    wide[2 * s + 1] = 0ull;
+    if (!discard) atomicAdd(wide_count, 1u);
+  }
+  sts32(S.a_key + 4u * s, kEmptyKey);
+  sts32(v, 0u);
+  sts32(v + 4u, 0u);
+  sts32(v + 8u, 0u);
+  if (discard) return;
+  const uint32_t r = gc.div_x ? (uint32_t)__umul64hi(gc.div_x, k) : k;  // k / X
+  const uint32_t q = gc.div_y ? (uint32_t)__umul64hi(gc.div_y, r) : r;  // r / Y
+  const int kx = (int)(k - r * (uint32_t)gc.X);
+  const int ky = (int)(r - q * (uint32_t)gc.Y);
+  const int kz = (int)q;
+  bx.mn0 = min(bx.mn0, kx); bx.mn1 = min(bx.mn1, ky); bx.mn2 = min(bx.mn2, kz);
+  bx.mx0 = max(bx.mx0, kx); bx.mx1 = max(bx.mx1, ky); bx.mx2 = max(bx.mx2, kz);
+  const int sB = (kExact || n > gc.nlim)
+                     ? feature_symbol(gc.feature, gc.Lc, gc.Lv, gc.count_thresh, gc.var_thresh, n, s1, s2)
+                     : feature_symbol_small(gc, (uint32_t)n, (int32_t)s1, (uint32_t)s2);
+  if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
+      kz <= gc.boxA[5])
+    red_add(S.a_hist + 4u * (uint32_t)((int)__ldg(I.symA + k) * gc.K + sB), 1u);
+  if (I.dump != nullptr && lp == 0) {
+    I.dump[3 * (size_t)k] = (int64_t)n;
+    I.dump[3 * (size_t)k + 1] = s1;
+    I.dump[3 * (size_t)k + 2] = (int64_t)s2;
+  }
+}
+
+// Read (and clear) the table after a sweep: symbols, bbox and histogram unless `discard`.
+// Every warp scans a contiguous share of the slots and compacts the occupied ones into a
+// list (in its run ring, empty after the sweep), so that the per-voxel work runs with all
+// 32 lanes busy.  The CTA-wide occupied count is added to the occupied flag word.
 template <bool kVar, bool kExact>
 __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& gc, const EvalItem& I,
                                            unsigned long long* wide, uint32_t* wide_count, int T, int lp,
                                            bool discard) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int K = gc.K;
-  int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX, mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
-  uint32_t occupied = 0;
-  for (int s = tid; s < T; s += kThreads) {
-    const uint32_t k = lds32(S.a_key + 4u * (uint32_t)s);
-    if (k == kEmptyKey) continue;
-    ++occupied;
-    const uint32_t v = S.a_vals + 12u * (uint32_t)s;
-    const uint64_t n = lds32(v);
-    int64_t s1 = (int32_t)lds32(v + 4u);
-    uint64_t s2 = lds32(v + 8u);
-    if (!kExact && kVar && n > gc.nlim) sts32(S.a_key - kFlagWide, 1u);  // sums may have wrapped: exact path
-    if (kExact && kVar && n > gc.nlim) {
-      s1 += (int64_t)wide[2 * s];
-      s2 += wide[2 * s + 1];
-      wide[2 * s] = 0ull;
-      wide[2 * s + 1] = 0ull;
-      if (!discard) atomicAdd(wide_count, 1u);
-    }
-    sts32(S.a_key + 4u * (uint32_t)s, kEmptyKey);
-    sts32(v, 0u);
-    sts32(v + 4u, 0u);
-    sts32(v + 8u, 0u);
-    if (discard) continue;
-    const uint32_t r = gc.div_x ? (uint32_t)__umul64hi(gc.div_x, k) : k;  // k / X
-    const uint32_t q = gc.div_y ? (uint32_t)__umul64hi(gc.div_y, r) : r;  // r / Y
-    const int kx = (int)(k - r * (uint32_t)gc.X);
-    const int ky = (int)(r - q * (uint32_t)gc.Y);
-    const int kz = (int)q;
-    mn0 = min(mn0, kx); mn1 = min(mn1, ky); mn2 = min(mn2, kz);
-    mx0 = max(mx0, kx); mx1 = max(mx1, ky); mx2 = max(mx2, kz);
-    const int sB = (kExact || n > gc.nlim)
-                       ? feature_symbol(gc.feature, gc.Lc, gc.Lv, gc.count_thresh, gc.var_thresh, n, s1, s2)
-                       : feature_symbol_small(gc, (uint32_t)n, (int32_t)s1, (uint32_t)s2);
-    if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
-        kz <= gc.boxA[5])
-      red_add(S.a_hist + 4u * (uint32_t)((int)__ldg(I.symA + k) * K + sB), 1u);
-    if (I.dump != nullptr && lp == 0) {
-      I.dump[3 * (size_t)k] = (int64_t)n;
-      I.dump[3 * (size_t)k + 1] = s1;
-      I.dump[3 * (size_t)k + 2] = (int64_t)s2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lane_lt = lane_mask_lt();
+  const uint32_t list = S.a_queue + (uint32_t)warp * kQueue * 16u;
+  const int per = (T + kWarps * 32 - 1) / (kWarps * 32) * 32;
+  const int beg = warp * per, end = min(T, beg + per);
+  ScanBox bx;
+  uint32_t cnt = 0, occupied = 0;
+  for (int base = beg; base < end; base += 32) {
+    const int s = base + lane;
+    const bool occ = s < end && lds32(S.a_key + 4u * (uint32_t)s) != kEmptyKey;
+    const uint32_t m = __ballot_sync(kFull, occ);
+    if (occ) sts32(list + 4u * (cnt + (uint32_t)__popc(m & lane_lt)), (uint32_t)s);
+    cnt += (uint32_t)__popc(m);
+    occupied += (uint32_t)__popc(m);
+    if (cnt >= 32u) {
+      __syncwarp();
+      scan_entry<kVar, kExact>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
+      // move the rest down (lane l reads entry l + 32 and writes entry l, which only it read)
+      if ((uint32_t)lane + 32u < cnt) sts32(list + 4u * (uint32_t)lane, lds32(list + 4u * ((uint32_t)lane + 32u)));
+      __syncwarp();
+      cnt -= 32u;
     }
   }
-  occupied = __reduce_add_sync(kFull, occupied);
+  __syncwarp();
+  if ((uint32_t)lane < cnt)
+    scan_entry<kVar, kExact>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
   if (lane == 0 && occupied) red_add(S.a_key - kFlagOccupied, occupied);
-  mn0 = __reduce_min_sync(kFull, mn0); mn1 = __reduce_min_sync(kFull, mn1);
-  mn2 = __reduce_min_sync(kFull, mn2); mx0 = __reduce_max_sync(kFull, mx0);
-  mx1 = __reduce_max_sync(kFull, mx1); mx2 = __reduce_max_sync(kFull, mx2);
+  const int mn0 = __reduce_min_sync(kFull, bx.mn0), mn1 = __reduce_min_sync(kFull, bx.mn1);
+  const int mn2 = __reduce_min_sync(kFull, bx.mn2), mx0 = __reduce_max_sync(kFull, bx.mx0);
+  const int mx1 = __reduce_max_sync(kFull, bx.mx1), mx2 = __reduce_max_sync(kFull, bx.mx2);
   if (lane == 0 && !discard && mn0 != INT_MAX) {
     red_min_s32(S.a_box, mn0); red_min_s32(S.a_box + 4, mn1); red_min_s32(S.a_box + 8, mn2);
     red_max_s32(S.a_box + 12, mx0); red_max_s32(S.a_box + 16, mx1); red_max_s32(S.a_box + 20, mx2);
