@@ -79,6 +79,9 @@ struct EvalArgs {
   unsigned long long* wide;   // per CTA: table_slots x 2 (S1 as two's complement, S2)
   uint32_t* redo_list;        // P: poses whose table overflowed, finished by the redo kernel
   uint32_t* redo_count;       // entries in redo_list (zeroed before every launch)
+  uint4* ovf;                 // per CTA: ovf_cap runs (key, n, S1, S2) whose home bucket was full
+  int32_t ovf_cap;
+  int32_t pad1;
 };
 
 // One point-tile PackCopy of a batch: scan xyz (n points) -> out (n_out float4), raw
@@ -102,6 +105,7 @@ struct EvalKernels {
   int ppt;          // points per thread per tile
   int ctas_per_sm;  // resident CTAs per SM, each evaluating one pose at a time with its own table
   int (*tile_points)();
+  int (*ovf_cap)();  // overflow-list entries per CTA (EvalArgs::ovf holds CTAs x this many)
   int (*min_tiles)();
   size_t (*smem_bytes)(int K, int table_slots);
   int (*table_slots_for)(int K, size_t smem_budget);

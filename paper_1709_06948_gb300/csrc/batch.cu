@@ -56,7 +56,7 @@ struct PairPlan {
 // Workspace sizes of one launch; a change of any of them re-allocates and drops the graph.
 struct Sizes {
   size_t xyz = 0, poses = 0, pts = 0, pose_src = 0, copies = 0, items = 0, starts = 0, outc = 0, box = 0,
-         best = 0, mi = 0, argmax = 0, redo = 0, wide = 0, ipasses = 0;
+         best = 0, mi = 0, argmax = 0, redo = 0, wide = 0, ipasses = 0, ovf = 0;
 };
 
 std::string env_cache_path() {
@@ -116,7 +116,7 @@ struct align_batch {
   std::string device_name;
   int shape_fixed = -1;
   DevBuf xyz, poses, pts, pose_src, copies, items, starts, outc, box, best, mi, argmax, redo_list, redo_count, wide,
-      status, ipasses;
+      status, ipasses, ovf;
   std::vector<align_grid*> last_grids;  // grids of the last launch (per-item partition feedback)
   int last_shape = 0;
   Sizes cap;
@@ -278,7 +278,7 @@ align_status align_batch_destroy(align_batch* b) {
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
   for (DevBuf* d : {&b->xyz, &b->poses, &b->pts, &b->pose_src, &b->copies, &b->items, &b->starts, &b->outc, &b->box,
-                    &b->best, &b->mi, &b->argmax, &b->redo_list, &b->redo_count, &b->wide, &b->status, &b->ipasses})
+                    &b->best, &b->mi, &b->argmax, &b->redo_list, &b->redo_count, &b->wide, &b->status, &b->ipasses, &b->ovf})
     d->release();
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
@@ -373,6 +373,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   GROW(redo_list, redo, (size_t)poses_n * 4, "allocate redo list", false);
   GROW(ipasses, ipasses, (size_t)n * 4, "allocate partition counts", false);
   GROW(wide, wide, (size_t)n_ctas * 2 * T * 8, "allocate wide sums", true);
+  GROW(ovf, ovf, (size_t)n_ctas * ek.ovf_cap() * 16, "allocate overflow lists", false);
 #undef GROW
   if (!b->status.p || !b->redo_count.p) {
     drop_graph(b);
@@ -480,6 +481,8 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   a.wide = b->wide.as<unsigned long long>();
   a.redo_list = b->redo_list.as<uint32_t>();
   a.redo_count = b->redo_count.as<uint32_t>();
+  a.ovf = b->ovf.as<uint4>();
+  a.ovf_cap = ek.ovf_cap();
   b->last_grids.clear();
   for (const PairPlan& pp : plans) b->last_grids.push_back(pp.g);
   b->last_shape = shape;

@@ -61,6 +61,7 @@ constexpr int kTile = kThreads * kPPT;  // points per tile
 constexpr int kMinTiles = 3;            // prefetch depth
 constexpr uint32_t kQueue = 64;         // finished runs buffered per warp (32 drained at a time)
 constexpr int kProbeBuckets = 64;       // probe budget per key (buckets of 4 slots)
+constexpr int kOvfCap = 4096;           // overflow list entries per CTA
 constexpr int kMaxPasses = 1 << 16;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr int kGcWords = (int)(sizeof(GridConst) / 4);
@@ -128,7 +129,7 @@ __device__ __forceinline__ uint32_t lane_mask_lt() {
 // the keys so that the hot loop reaches them at a fixed offset from the key base.
 struct EvalSmem {
   uint4* queue;       // per warp: kQueue finished runs (key, n, S1, S2)
-  uint32_t* flags;    // occupied count, table full, (unused), sums need the exact path
+  uint32_t* flags;    // occupied count, table full, overflow entries, sums need the exact path
   uint32_t* tkey;
   uint32_t* tval;     // 3 words per slot
   uint32_t* hist;
@@ -140,6 +141,7 @@ struct EvalSmem {
 };
 constexpr uint32_t kFlagOccupied = 16u;  // byte offsets of the flags below a_key
 constexpr uint32_t kFlagFull = 12u;
+constexpr uint32_t kFlagOvf = 8u;        // entries in the CTA's overflow list
 constexpr uint32_t kFlagWide = 4u;
 
 __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, uint8_t* base) {
@@ -242,18 +244,55 @@ __device__ __noinline__ int table_slot_slow(uint32_t a_key, uint32_t key, uint32
 // A voxel whose count ends above nlim may have wrapped its 32-bit sums; the table scan
 // sends such a pose to the exact path.
 template <bool kVar>
-__device__ __forceinline__ void table_add(const EvalSmem& S, const uint4& e, uint32_t nb) {
-  if (lds32(S.a_key - kFlagFull)) return;  // table already full: the pose is redone
-  const int slot = table_slot(S, e.x, nb);
-  if (slot < 0) {
-    sts32(S.a_key - kFlagFull, 1u);
-    return;
-  }
+__device__ __forceinline__ void table_add_slot(const EvalSmem& S, const uint4& e, int slot) {
   const uint32_t v = S.a_vals + 12u * (uint32_t)slot;
   red_add(v, e.y);
   if (kVar) {
     red_add(v + 4u, e.z);
     red_add(v + 8u, e.w);
+  }
+}
+
+// Fast path of the sweep: the key's home bucket only, in straight-line code.  A run whose
+// home bucket holds neither its key nor a free slot (or whose insert lost a race) goes to
+// the CTA's overflow list in global memory, which the whole CTA inserts after the sweep
+// (insert_overflow).  A full overflow list marks the pose for the exact path.
+template <bool kVar>
+__device__ __forceinline__ void table_add(const EvalSmem& S, const uint4& e, const EvalArgs& a) {
+  const uint32_t b = __umulhi(e.x * 0x9E3779B1u, (uint32_t)a.n_buckets);
+  const uint4 k4 = lds128(S.a_key + 16u * b);
+  int slot = -1;
+  if (k4.x == e.x) slot = (int)(4 * b);
+  else if (k4.y == e.x) slot = (int)(4 * b + 1);
+  else if (k4.z == e.x) slot = (int)(4 * b + 2);
+  else if (k4.w == e.x) slot = (int)(4 * b + 3);
+  else {
+    const int f = (k4.x == kEmptyKey) ? 0 : (k4.y == kEmptyKey) ? 1 : (k4.z == kEmptyKey) ? 2 : (k4.w == kEmptyKey) ? 3 : -1;
+    if (f >= 0) {
+      const uint32_t s = 4 * b + (uint32_t)f;
+      const uint32_t old = atom_cas(S.a_key + 4u * s, kEmptyKey, e.x);
+      if (old == kEmptyKey || old == e.x) slot = (int)s;
+    }
+  }
+  if (slot >= 0) {
+    table_add_slot<kVar>(S, e, slot);
+  } else {
+    const uint32_t i = atom_add(S.a_key - kFlagOvf, 1u);
+    if (i < (uint32_t)a.ovf_cap) a.ovf[(size_t)blockIdx.x * (uint32_t)a.ovf_cap + i] = e;
+    else sts32(S.a_key - kFlagFull, 1u);
+  }
+}
+
+// After a sweep: insert the overflow list with the full probe (all threads of the CTA).
+template <bool kVar>
+__device__ __forceinline__ void insert_overflow(const EvalSmem& S, const EvalArgs& a) {
+  const uint32_t n = min(*(volatile uint32_t*)&S.flags[2], (uint32_t)a.ovf_cap);
+  const uint4* ovf = a.ovf + (size_t)blockIdx.x * (uint32_t)a.ovf_cap;
+  for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
+    const uint4 e = ovf[i];
+    const int slot = table_slot(S, e.x, (uint32_t)a.n_buckets);
+    if (slot < 0) sts32(S.a_key - kFlagFull, 1u);
+    else table_add_slot<kVar>(S, e, slot);
   }
 }
 
@@ -296,12 +335,12 @@ struct Run {
 // 0..31 to the table and moves the rest down, so the ring never wraps.
 template <bool kVar>
 __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count,
-                                           uint32_t nb) {
+                                           const EvalArgs& a) {
   const int lane = (int)(threadIdx.x & 31u);
   __syncwarp();
   if ((uint32_t)lane < count) {
     const uint4 e = lds128(ring + 16u * (uint32_t)lane);
-    if (e.x != kEmptyKey) table_add<kVar>(S, e, nb);
+    if (e.x != kEmptyKey) table_add<kVar>(S, e, a);
   }
   // move the entries beyond `count` down, one word at a time (lane l reads entry l + count
   // and writes entry l, which only it has read)
@@ -317,12 +356,12 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
 // Append the finished runs of the lanes with `done` set, then drain if 32 are waiting.
 template <bool kVar>
 __device__ __forceinline__ void ring_push(const EvalSmem& S, uint32_t ring, uint32_t lane_lt, bool done,
-                                          const Run& r, uint32_t& fill, uint32_t nb) {
+                                          const Run& r, uint32_t& fill, const EvalArgs& a) {
   const uint32_t m = __ballot_sync(kFull, done);
   sts128_if(done, ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), make_uint4(r.key, r.n, r.s1, r.s2));
   fill += (uint32_t)__popc(m);
   // fill is the same in every lane; the vote lets the compiler know the branch is uniform
-  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVar>(S, ring, fill, 32u, nb);
+  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVar>(S, ring, fill, 32u, a);
 }
 
 struct PoseRegs {
@@ -580,9 +619,9 @@ __device__ __forceinline__ const float4* pose_tiles(const EvalItem& I, int lp) {
 // One tile of this thread's stream: key, run step, ring append of the finished run.
 // `bad` collects dz + dz_bound of every in-grid point (checked against 2^dz_shift).
 template <bool kVar, bool kRot, bool kPart>
-__device__ __forceinline__ void sweep_tile(const EvalSmem& S, const VoxelConst& vc, const PoseRegs& P,
-                                           const float4* pts, int lg, uint32_t part, Run& run, uint32_t ring,
-                                           uint32_t lane_lt, uint32_t& fill, uint32_t nb, uint32_t& bad) {
+__device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
+                                           const PoseRegs& P, const float4* pts, int lg, uint32_t part, Run& run,
+                                           uint32_t ring, uint32_t lane_lt, uint32_t& fill, uint32_t& bad) {
 #pragma unroll
   for (int j = 0; j < kPPT; ++j) {
     uint32_t key;
@@ -591,7 +630,7 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const VoxelConst& 
     if (kPart && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != part) key = kEmptyKey;
     bad |= (uint32_t)(dz + vc.dz_bound);
     const bool done = key != run.key;
-    ring_push<kVar>(S, ring, lane_lt, done, run, fill, nb);
+    ring_push<kVar>(S, ring, lane_lt, done, run, fill, a);
     run.n = (done ? 0u : run.n) + 1u;
     if (kVar) {
       run.s1 = (done ? 0u : run.s1) + (uint32_t)dz;
@@ -605,9 +644,9 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const VoxelConst& 
 // L2, three tiles ahead.  A run is cut every `cut` tiles so that its 32-bit sums stay
 // below nlim points.  Returns the bad-dz flag.
 template <bool kVar, bool kRot, bool kPart>
-__device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const VoxelConst& vc, const PoseRegs& P,
-                                               const float4* src, int nt, int lg, uint32_t part, uint32_t ring,
-                                               uint32_t lane_lt, uint32_t nb, int cut) {
+__device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
+                                               const PoseRegs& P, const float4* src, int nt, int lg, uint32_t part,
+                                               uint32_t ring, uint32_t lane_lt, int cut) {
   Run run{kEmptyKey, 0u, 0u, 0u};
   uint32_t fill = 0u, bad = 0u;
   float4 b0[kPPT], b1[kPPT], b2[kPPT];
@@ -618,36 +657,36 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const VoxelCon
   int t = 0;
   for (; t + 6 <= nt; t += 3) {  // all three prefetches in range: no guards
     if (t >= next_cut) {
-      ring_push<kVar>(S, ring, lane_lt, true, run, fill, nb);
+      ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
-    sweep_tile<kVar, kRot, kPart>(S, vc, P, b0, lg, part, run, ring, lane_lt, fill, nb, bad);
+    sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b0, lg, part, run, ring, lane_lt, fill, bad);
     load_tile(src, t + 3, b0);
-    sweep_tile<kVar, kRot, kPart>(S, vc, P, b1, lg, part, run, ring, lane_lt, fill, nb, bad);
+    sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b1, lg, part, run, ring, lane_lt, fill, bad);
     load_tile(src, t + 4, b1);
-    sweep_tile<kVar, kRot, kPart>(S, vc, P, b2, lg, part, run, ring, lane_lt, fill, nb, bad);
+    sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b2, lg, part, run, ring, lane_lt, fill, bad);
     load_tile(src, t + 5, b2);
   }
   for (; t < nt; t += 3) {
     if (t >= next_cut) {  // uniform; only when a stream is longer than nlim points
-      ring_push<kVar>(S, ring, lane_lt, true, run, fill, nb);
+      ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
-    sweep_tile<kVar, kRot, kPart>(S, vc, P, b0, lg, part, run, ring, lane_lt, fill, nb, bad);
+    sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b0, lg, part, run, ring, lane_lt, fill, bad);
     if (t + 3 < nt) load_tile(src, t + 3, b0);
     if (t + 1 < nt) {
-      sweep_tile<kVar, kRot, kPart>(S, vc, P, b1, lg, part, run, ring, lane_lt, fill, nb, bad);
+      sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b1, lg, part, run, ring, lane_lt, fill, bad);
       if (t + 4 < nt) load_tile(src, t + 4, b1);
     }
     if (t + 2 < nt) {
-      sweep_tile<kVar, kRot, kPart>(S, vc, P, b2, lg, part, run, ring, lane_lt, fill, nb, bad);
+      sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b2, lg, part, run, ring, lane_lt, fill, bad);
       if (t + 5 < nt) load_tile(src, t + 5, b2);
     }
   }
-  ring_push<kVar>(S, ring, lane_lt, true, run, fill, nb);
-  while (fill > 0u) ring_drain<kVar>(S, ring, fill, min(fill, 32u), nb);
+  ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
+  while (fill > 0u) ring_drain<kVar>(S, ring, fill, min(fill, 32u), a);
   return bad;
 }
 
@@ -693,12 +732,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
     for (int pass = 0; pass < pose_passes; ++pass) {
       if (!full) {
         const uint32_t bad =
-            lg == 0 ? sweep_pose<kVar, kRot, false>(S, vc, P, src, nt, 0, 0u, ring, lane_lt, (uint32_t)a.n_buckets, cut)
-                    : sweep_pose<kVar, kRot, true>(S, vc, P, src, nt, lg, (uint32_t)pass, ring, lane_lt,
-                                                   (uint32_t)a.n_buckets, cut);
+            lg == 0 ? sweep_pose<kVar, kRot, false>(S, a, vc, P, src, nt, 0, 0u, ring, lane_lt, cut)
+                    : sweep_pose<kVar, kRot, true>(S, a, vc, P, src, nt, lg, (uint32_t)pass, ring, lane_lt, cut);
         if (bad >> dz_shift) atomicOr(a.err, kErrDzBound);
       }
       __syncthreads();
+      if (!full && *(volatile uint32_t*)&S.flags[2] != 0u) {  // runs whose home bucket was full
+        insert_overflow<kVar>(S, a);
+        __syncthreads();
+      }
       full = full || S.flags[1] != 0u;
       scan_table<kVar, false>(S, kOne ? a.one.gc : *S.gc, I, wide, a.wide_count, T, lp, full);
       __syncthreads();
@@ -707,6 +749,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
       __syncthreads();
       if (tid == 0) {
         S.flags[0] = 0u;
+        S.flags[2] = 0u;
         S.flags[3] = 0u;
       }
     }
@@ -1005,6 +1048,7 @@ cudaError_t launch_eval_t(const EvalArgs& a, int n_ctas, size_t smem, cudaStream
 }
 
 int eval_tile_points() { return kTile; }
+int eval_ovf_cap() { return kOvfCap; }
 int eval_min_tiles() { return kMinTiles; }
 
 size_t eval_smem_bytes(int K, int table_slots) { return eval_smem_layout(K, table_slots, nullptr, nullptr); }
@@ -1085,7 +1129,7 @@ cudaError_t launch_argmax_finalize(const EvalItem* items, int n_items, cudaStrea
 }  // namespace
 
 const EvalKernels& MI_EVAL_SHAPE_FN() {
-  static const EvalKernels k{MI_STR(MI_EVAL_SHAPE_FN), kThreads, kPPT, kCtasPerSm, eval_tile_points, eval_min_tiles,
+  static const EvalKernels k{MI_STR(MI_EVAL_SHAPE_FN), kThreads, kPPT, kCtasPerSm, eval_tile_points, eval_ovf_cap, eval_min_tiles,
                              eval_smem_bytes, eval_table_slots_for, eval_setup, launch_eval, launch_pack_points,
                              launch_pack_batch, launch_compose, launch_argmax_finalize};
   return k;

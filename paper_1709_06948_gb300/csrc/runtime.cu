@@ -352,6 +352,9 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
   a.wide = g->wide.as<unsigned long long>();
   a.redo_list = g->redo_list.as<uint32_t>();
   a.redo_count = g->redo_count.as<uint32_t>();
+  CU(g->ovf.ensure((size_t)n_ctas * ek.ovf_cap() * 16), "allocate overflow lists");
+  a.ovf = g->ovf.as<uint4>();
+  a.ovf_cap = ek.ovf_cap();
   std::array<cudaEvent_t, 3> evs{};
   if (g->profiling) {
     if (g->ev_pool.empty()) {
@@ -464,7 +467,7 @@ align_status align_destroy_grid(align_grid* g) {
   cudaStreamSynchronize(g->stream);
   for (DevBuf* b : {&g->symA, &g->sat, &g->xyz, &g->poses, &g->out_c, &g->out_box, &g->mi, &g->hist, &g->best,
                     &g->argmax, &g->err, &g->max_passes, &g->wide_count, &g->wide, &g->dump, &g->pts4,
-                    &g->pose_src, &g->rots, &g->redo_list, &g->redo_count, &g->items})
+                    &g->pose_src, &g->rots, &g->redo_list, &g->redo_count, &g->items, &g->ovf})
     b->release();
   for (auto* v : {&g->ev_pending, &g->ev_pool})
     for (auto& evs : *v)

@@ -68,7 +68,7 @@ struct align_grid {
   mialign::DevBuf symA, sat;
   // evaluation workspace
   mialign::DevBuf xyz, poses, out_c, out_box, mi, hist, best, argmax, err, max_passes, wide_count, wide, dump;
-  mialign::DevBuf pts4, pose_src, rots, redo_list, redo_count, items;
+  mialign::DevBuf pts4, pose_src, rots, redo_list, redo_count, items, ovf;
   int64_t n_points = 0;  // points staged in `xyz`
   // key partitions the next launch starts with, per kernel shape (its table size)
   int32_t passes_seed[mialign::kEvalShapes] = {1, 1, 1};
