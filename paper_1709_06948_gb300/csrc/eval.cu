@@ -99,6 +99,27 @@ __device__ __forceinline__ void sts128_if(bool p, uint32_t a, uint4 v) {
       "r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
       : "memory");
 }
+__device__ __forceinline__ void sts32_if(bool p, uint32_t a, uint32_t v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.shared.u32 [%1], %2;\n\t}" ::"r"((uint32_t)p),
+               "r"(a), "r"(v)
+               : "memory");
+}
+__device__ __forceinline__ void red_add_if(bool p, uint32_t a, uint32_t v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q red.shared.add.u32 [%1], %2;\n\t}" ::"r"(
+                   (uint32_t)p),
+               "r"(a), "r"(v)
+               : "memory");
+}
+// CAS under a predicate; returns `cmp` when not executed.
+__device__ __forceinline__ uint32_t atom_cas_if(bool p, uint32_t a, uint32_t cmp, uint32_t v) {
+  uint32_t old;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\tmov.u32 %0, %3;\n\t@q atom.shared.cas.b32 %0, [%2], %3, %4;\n\t}"
+      : "=r"(old)
+      : "r"((uint32_t)p), "r"(a), "r"(cmp), "r"(v)
+      : "memory");
+  return old;
+}
 __device__ __forceinline__ void red_add(uint32_t a, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
@@ -253,36 +274,6 @@ __device__ __forceinline__ void table_add_slot(const EvalSmem& S, const uint4& e
   }
 }
 
-// Fast path of the sweep: the key's home bucket only, in straight-line code.  A run whose
-// home bucket holds neither its key nor a free slot (or whose insert lost a race) goes to
-// the CTA's overflow list in global memory, which the whole CTA inserts after the sweep
-// (insert_overflow).  A full overflow list marks the pose for the exact path.
-template <bool kVar>
-__device__ __forceinline__ void table_add(const EvalSmem& S, const uint4& e, const EvalArgs& a) {
-  const uint32_t b = __umulhi(e.x * 0x9E3779B1u, (uint32_t)a.n_buckets);
-  const uint4 k4 = lds128(S.a_key + 16u * b);
-  int slot = -1;
-  if (k4.x == e.x) slot = (int)(4 * b);
-  else if (k4.y == e.x) slot = (int)(4 * b + 1);
-  else if (k4.z == e.x) slot = (int)(4 * b + 2);
-  else if (k4.w == e.x) slot = (int)(4 * b + 3);
-  else {
-    const int f = (k4.x == kEmptyKey) ? 0 : (k4.y == kEmptyKey) ? 1 : (k4.z == kEmptyKey) ? 2 : (k4.w == kEmptyKey) ? 3 : -1;
-    if (f >= 0) {
-      const uint32_t s = 4 * b + (uint32_t)f;
-      const uint32_t old = atom_cas(S.a_key + 4u * s, kEmptyKey, e.x);
-      if (old == kEmptyKey || old == e.x) slot = (int)s;
-    }
-  }
-  if (slot >= 0) {
-    table_add_slot<kVar>(S, e, slot);
-  } else {
-    const uint32_t i = atom_add(S.a_key - kFlagOvf, 1u);
-    if (i < (uint32_t)a.ovf_cap) a.ovf[(size_t)blockIdx.x * (uint32_t)a.ovf_cap + i] = e;
-    else sts32(S.a_key - kFlagFull, 1u);
-  }
-}
-
 // After a sweep: insert the overflow list with the full probe (all threads of the CTA).
 template <bool kVar>
 __device__ __forceinline__ void insert_overflow(const EvalSmem& S, const EvalArgs& a) {
@@ -332,23 +323,43 @@ struct Run {
 
 // Per-warp ring of finished runs in shared memory: lanes append what they finished at
 // this step (compacted by a ballot); once 32 are waiting the whole warp adds entries
-// 0..31 to the table and moves the rest down, so the ring never wraps.
+// 0..31 to the table and moves the rest down, so the ring never wraps.  The insert is
+// written with predicated shared-memory operations so that the drain is one straight
+// sequence; only a run whose home bucket is full branches off to the overflow list.
 template <bool kVar>
 __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count,
                                            const EvalArgs& a) {
-  const int lane = (int)(threadIdx.x & 31u);
+  const uint32_t lane = threadIdx.x & 31u;
   __syncwarp();
-  if ((uint32_t)lane < count) {
-    const uint4 e = lds128(ring + 16u * (uint32_t)lane);
-    if (e.x != kEmptyKey) table_add<kVar>(S, e, a);
+  uint4 e = lds128(ring + 16u * lane);  // the ring holds 64 entries: always in bounds
+  if (lane >= count) e.x = kEmptyKey;
+  const bool valid = e.x != kEmptyKey;
+  const uint32_t b = __umulhi(e.x * 0x9E3779B1u, (uint32_t)a.n_buckets);
+  const uint32_t kb = S.a_key + 16u * b;
+  const uint4 k4 = lds128(kb);
+  int slot = (k4.x == e.x) ? 0 : (k4.y == e.x) ? 1 : (k4.z == e.x) ? 2 : (k4.w == e.x) ? 3 : -1;
+  const int f = (k4.x == kEmptyKey) ? 0 : (k4.y == kEmptyKey) ? 1 : (k4.z == kEmptyKey) ? 2 : (k4.w == kEmptyKey) ? 3 : -1;
+  const bool ins = valid && slot < 0 && f >= 0;
+  const uint32_t old = atom_cas_if(ins, kb + 4u * (uint32_t)f, kEmptyKey, e.x);
+  if (ins && (old == kEmptyKey || old == e.x)) slot = f;
+  const bool ok = valid && slot >= 0;
+  const uint32_t v = S.a_vals + 12u * (4u * b + (uint32_t)slot);
+  red_add_if(ok, v, e.y);
+  if (kVar) {
+    red_add_if(ok, v + 4u, e.z);
+    red_add_if(ok, v + 8u, e.w);
+  }
+  if (valid && slot < 0) {  // home bucket full (or insert race lost): overflow list
+    const uint32_t i = atom_add(S.a_key - kFlagOvf, 1u);
+    if (i < (uint32_t)a.ovf_cap) a.ovf[(size_t)blockIdx.x * (uint32_t)a.ovf_cap + i] = e;
+    else sts32(S.a_key - kFlagFull, 1u);
   }
   // move the entries beyond `count` down, one word at a time (lane l reads entry l + count
-  // and writes entry l, which only it has read)
-  if ((uint32_t)lane + count < fill) {
-    const uint32_t dst = ring + 16u * (uint32_t)lane, src = dst + 16u * count;
+  // and writes entry l, which only it has read; entry l + count < 64 for count <= 32)
+  const bool mv = lane + count < fill;
+  const uint32_t dst = ring + 16u * lane, src = dst + 16u * count;
 #pragma unroll
-    for (uint32_t w = 0; w < 16u; w += 4u) sts32(dst + w, lds32(src + w));
-  }
+  for (uint32_t w = 0; w < 16u; w += 4u) sts32_if(mv, dst + w, lds32(src + w));
   __syncwarp();
   fill -= count;
 }
