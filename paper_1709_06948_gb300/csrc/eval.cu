@@ -58,7 +58,11 @@ constexpr int kCtasPerSm = MI_EVAL_CTAS_PER_SM;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPPT = MI_EVAL_PPT;       // points per thread per tile
 constexpr int kTile = kThreads * kPPT;  // points per tile
-constexpr int kMinTiles = 3;            // prefetch depth
+#ifndef MI_EVAL_DEPTH
+#define MI_EVAL_DEPTH 3
+#endif
+constexpr int kDepth = MI_EVAL_DEPTH;   // tiles loaded ahead into registers
+constexpr int kMinTiles = 3;
 constexpr uint32_t kQueue = 64;         // finished runs buffered per warp (32 drained at a time)
 constexpr int kProbeBuckets = 64;       // probe budget per key (buckets of 4 slots)
 constexpr int kOvfCap = 4096;           // overflow list entries per CTA
@@ -414,9 +418,29 @@ __device__ __forceinline__ void load_pose(const float* poses, PoseRegs& P) {
   for (int i = 0; i < 3; ++i) P.t[i] = __ldg(poses + 9 + i);
 }
 
+// Tile layout (kTile float4 slots of storage per tile): x,y of the tile's points as float2
+// in the first half, z as float in the next quarter (12 bytes read per point).  `src` is
+// the copy's base plus this thread's index.
 __device__ __forceinline__ void load_tile(const float4* src, int t, float4* v) {
+  const float4* tile = src - threadIdx.x + (size_t)t * kTile;
+  const float2* xy = reinterpret_cast<const float2*>(tile);
+  const float* z = reinterpret_cast<const float*>(tile) + 2 * kTile;
 #pragma unroll
-  for (int j = 0; j < kPPT; ++j) v[j] = __ldg(src + (size_t)t * kTile + j * kThreads);
+  for (int j = 0; j < kPPT; ++j) {
+    const float2 p = __ldg(xy + threadIdx.x + j * kThreads);
+    v[j].x = p.x;
+    v[j].y = p.y;
+    v[j].z = __ldg(z + threadIdx.x + j * kThreads);
+  }
+}
+
+// Store point `i` (position within its tile copy) in the tile layout above.
+__device__ __forceinline__ void store_point(float4* out, int64_t i, float x, float y, float z) {
+  const int64_t t = i / kTile;
+  const int pos = (int)(i - t * kTile);
+  float4* tile = out + t * kTile;
+  reinterpret_cast<float2*>(tile)[pos] = make_float2(x, y);
+  (reinterpret_cast<float*>(tile) + 2 * kTile)[pos] = z;
 }
 
 // Make `it` the current item: its grid constants into shared memory.  Called by all
@@ -652,7 +676,7 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
 }
 
 // One pass over all tiles of the pose: every thread streams its own points straight from
-// L2, three tiles ahead.  A run is cut every `cut` tiles so that its 32-bit sums stay
+// L2, kDepth tiles ahead.  A run is cut every `cut` tiles so that its 32-bit sums stay
 // below nlim points.  Returns the bad-dz flag.
 template <bool kVar, bool kRot, bool kPart>
 __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
@@ -660,40 +684,36 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs
                                                uint32_t ring, uint32_t lane_lt, int cut) {
   Run run{kEmptyKey, 0u, 0u, 0u};
   uint32_t fill = 0u, bad = 0u;
-  float4 b0[kPPT], b1[kPPT], b2[kPPT];
-  load_tile(src, 0, b0);
-  load_tile(src, 1, b1);
-  load_tile(src, 2, b2);
+  float4 buf[kDepth][kPPT];  // register ring of the next kDepth tiles
+#pragma unroll
+  for (int d = 0; d < kDepth; ++d)
+    if (d < nt) load_tile(src, d, buf[d]);
   int next_cut = cut;
   int t = 0;
-  for (; t + 6 <= nt; t += 3) {  // all three prefetches in range: no guards
-    if (t >= next_cut) {
-      ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
-      run = Run{kEmptyKey, 0u, 0u, 0u};
-      next_cut += cut;
-    }
-    sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b0, lg, part, run, ring, lane_lt, fill, bad);
-    load_tile(src, t + 3, b0);
-    sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b1, lg, part, run, ring, lane_lt, fill, bad);
-    load_tile(src, t + 4, b1);
-    sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b2, lg, part, run, ring, lane_lt, fill, bad);
-    load_tile(src, t + 5, b2);
-  }
-  for (; t < nt; t += 3) {
+  for (; t + 2 * kDepth <= nt; t += kDepth) {  // every prefetch in range: no guards
     if (t >= next_cut) {  // uniform; only when a stream is longer than nlim points
       ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
-    sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b0, lg, part, run, ring, lane_lt, fill, bad);
-    if (t + 3 < nt) load_tile(src, t + 3, b0);
-    if (t + 1 < nt) {
-      sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b1, lg, part, run, ring, lane_lt, fill, bad);
-      if (t + 4 < nt) load_tile(src, t + 4, b1);
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d) {
+      sweep_tile<kVar, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad);
+      load_tile(src, t + kDepth + d, buf[d]);
     }
-    if (t + 2 < nt) {
-      sweep_tile<kVar, kRot, kPart>(S, a, vc, P, b2, lg, part, run, ring, lane_lt, fill, bad);
-      if (t + 5 < nt) load_tile(src, t + 5, b2);
+  }
+  for (; t < nt; t += kDepth) {
+    if (t >= next_cut) {
+      ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
+      run = Run{kEmptyKey, 0u, 0u, 0u};
+      next_cut += cut;
+    }
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d) {
+      if (t + d < nt) {
+        sweep_tile<kVar, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad);
+        if (t + kDepth + d < nt) load_tile(src, t + kDepth + d, buf[d]);
+      }
     }
   }
   ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
@@ -900,7 +920,7 @@ __global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int
         v.z = z;
       }
     }
-    o[i] = v;
+    store_point(o, i, v.x, v.y, v.z);
   }
 }
 
@@ -932,7 +952,7 @@ __global__ void pack_batch_kernel(const PackCopy* __restrict__ copies) {
         v.z = z;
       }
     }
-    c.out[i] = v;
+    store_point(c.out, i, v.x, v.y, v.z);
   }
 }
 
