@@ -6,7 +6,7 @@
 // lattice has 32 rotations for 4,096 poses, so the 9-FMA rotation leaves the per-pose
 // loop).  The tiles are laid out as kThreads streams: thread s of a CTA reads, tile after
 // tile, the points s*L, s*L+1, ... of B's given order (L = kPPT * tiles), so each thread
-// walks a stretch of consecutive scan points.
+// walks a stretch of consecutive scan points (stream_of: which stream a thread walks).
 //
 // eval_kernel: persistent, one CTA per SM, one pose at a time per CTA; the poses of all
 // items are one list, and each pose brings its item's grid constants.  Every thread
@@ -885,6 +885,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
   if (tid == 0) atomicMax(a.max_passes, (uint32_t)passes);
 }
 
+// Stream (stretch of consecutive scan points) walked by thread `tid`: lane l of warp w takes
+// stream l * kWarps + w, so every warp samples the whole scan and the warps of a CTA finish
+// their sweeps (and drains) at about the same time.
+__device__ __forceinline__ int stream_of(int tid) { return (tid & 31) * kWarps + (tid >> 5); }
+
 // xyz -> float4 tiles, optionally one rotated copy per rotation.  Tile t, position
 // j*kThreads + s holds point s*L + kPPT*t + j of B (L = kPPT * tiles): stream s visits
 // consecutive points of B, kPPT per tile.
@@ -902,8 +907,7 @@ __global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int
     const int64_t t = i / kTile;
     const int pos = (int)(i - t * kTile);
     const int j = pos / kThreads;
-    const int sidx = pos - j * kThreads;
-    const int64_t src = (int64_t)sidx * L + (int64_t)kPPT * t + j;
+    const int64_t src = (int64_t)stream_of(pos - j * kThreads) * L + (int64_t)kPPT * t + j;
     // padding: NaN for raw tiles (the in-kernel rotation keeps NaN), +inf for rotated copies
     const float pad = rots != nullptr ? inf : nan;
     float4 v = make_float4(pad, pad, pad, 0.0f);
@@ -937,8 +941,7 @@ __global__ void pack_batch_kernel(const PackCopy* __restrict__ copies) {
     const int64_t t = i / kTile;
     const int pos = (int)(i - t * kTile);
     const int j = pos / kThreads;
-    const int sidx = pos - j * kThreads;
-    const int64_t src = (int64_t)sidx * L + (int64_t)kPPT * t + j;
+    const int64_t src = (int64_t)stream_of(pos - j * kThreads) * L + (int64_t)kPPT * t + j;
     const float pad = rot ? inf : nan;
     float4 v = make_float4(pad, pad, pad, 0.0f);
     if (src < c.n) {
