@@ -503,6 +503,8 @@ __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& g
                                            unsigned long long* wide, uint32_t* wide_count, uint32_t s, int lp,
                                            bool discard, ScanBox& bx) {
   const uint32_t k = lds32(S.a_key + 4u * s);
+  // A's symbol of the voxel, requested first: its L2 latency overlaps the work below
+  const int sA = discard ? 0 : (int)__ldg(I.symA + k);
   const uint32_t v = S.a_vals + 12u * s;
   const uint64_t n = lds32(v);
   int64_t s1 = (int32_t)lds32(v + 4u);
@@ -532,7 +534,7 @@ __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& g
                      : feature_symbol_small(gc, (uint32_t)n, (int32_t)s1, (uint32_t)s2);
   if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
       kz <= gc.boxA[5])
-    red_add(S.a_hist + 4u * (uint32_t)((int)__ldg(I.symA + k) * gc.K + sB), 1u);
+    red_add(S.a_hist + 4u * (uint32_t)(sA * gc.K + sB), 1u);
   if (I.dump != nullptr && lp == 0) {
     I.dump[3 * (size_t)k] = (int64_t)n;
     I.dump[3 * (size_t)k + 1] = s1;
