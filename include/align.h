@@ -152,6 +152,20 @@ align_status align_search_ex(align_grid* grid, const float* xyzB, int64_t nB, in
                              const double init[6], const double range[6], const int32_t counts[6],
                              int32_t levels, double T_out[6], float* mi_out, int64_t* level_best);
 
+/* Nelder-Mead refinement, the optimiser of Algorithm 1 ("Update T_c using Nelder-Mead
+   optimization"; Nelder and Mead 1965, cited in Sec. III-C), maximising MI over eta.
+   S simplices run in lockstep, each from its start (starts: S x 6 FP64, host): initial
+   vertices x0 and x0 + step[i] e_i (Sec. IV uses step = {8, 8, 1, 0.1, 0.1, 0.8});
+   coefficients reflection 1, expansion 2, contraction 1/2, shrink 1/2; vertices ordered by
+   -MI with equal values keeping their order.  Every phase of an iteration evaluates the
+   points of all simplices that need one in one batched evaluation (align_eval_mi's path).
+   A simplex stops after max_iter iterations, or earlier when ftol > 0 and all its vertices'
+   MI lie within ftol of its best.  T_out: S x 6 best vertices; mi_out (may be NULL): their
+   MI; iters_out (may be NULL): iterations run.  xyzB as for align_eval_mi. */
+align_status align_refine_nm(align_grid* grid, const float* xyzB, int64_t nB, int flags, const double* starts,
+                             int32_t S, const double step[6], int32_t max_iter, double ftol, double* T_out,
+                             float* mi_out, int32_t* iters_out);
+
 /* Counters of the last synchronising evaluation on this grid (host ints):
    [0] key-partition passes of the hardest pose so far, [1] voxels that needed the
    wide (64-bit) side sums, [2] hash-table slots per CTA, [3] CTAs of the last eval

@@ -64,6 +64,8 @@ def _load():
             "orc_argmax": (i64, [P, i64]),
             "orc_search": (None, [P, P, P, P, i64, P, P, P, i32, i32, P, P, P]),
             "orc_lattice": (None, [P, P, P, P]),
+            "orc_nm_mi": (i32, [P, P, P, P, i64, P, P, i32, f64, P, P]),
+            "orc_nm_quadratic": (i32, [P, P, P, P, i32, f64, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -221,6 +223,25 @@ class Grid:
                        _ptr(_f64(init)), _ptr(_f64(rng)), _ptr(cnt), int(levels), int(nthreads), _ptr(T),
                        C.byref(mi), _ptr(lb))
         return T, float(mi.value), lb
+
+    def nm(self, symA, boxA, xyzB, x0, step, max_iter, ftol=0.0):
+        """Nelder-Mead on -MI (Algorithm 1's optimiser), FP64 MI of every vertex."""
+        xyzB = _f32(xyzB).reshape(-1, 3)
+        T = np.zeros(6, dtype=np.float64)
+        mi = C.c_double(0.0)
+        it = _load().orc_nm_mi(self.ref, _ptr(np.ascontiguousarray(symA, dtype=np.uint8)),
+                               _ptr(np.ascontiguousarray(boxA, dtype=np.int32)), _ptr(xyzB), xyzB.shape[0],
+                               _ptr(_f64(x0)), _ptr(_f64(step)), int(max_iter), float(ftol), _ptr(T), C.byref(mi))
+        return T, float(mi.value), int(it)
+
+
+def nm_quadratic(w, c, x0, step, max_iter, ftol=0.0):
+    """Nelder-Mead (the oracle's implementation) on sum_i w_i (x_i - c_i)^2."""
+    x = np.zeros(6, dtype=np.float64)
+    f = C.c_double(0.0)
+    it = _load().orc_nm_quadratic(_ptr(_f64(w)), _ptr(_f64(c)), _ptr(_f64(x0)), _ptr(_f64(step)), int(max_iter),
+                                  float(ftol), _ptr(x), C.byref(f))
+    return x, float(f.value), int(it)
 
 
 def mi_from_hist(h, N=None) -> float:

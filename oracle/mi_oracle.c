@@ -385,3 +385,147 @@ void orc_search(const orc_grid* g, const uint8_t* symA, const int32_t boxA[6],
   free(poses);
   free(mi);
 }
+
+
+/* ------------------------------------------------------------------------------------
+   Nelder-Mead (Nelder and Mead 1965), six parameters, standard coefficients.
+   ------------------------------------------------------------------------------------ */
+#define NM_N 6
+
+/* Reorder vertices by f, stable (insertion sort keeps equal values in their order). */
+static void nm_sort(double sim[NM_N + 1][NM_N], double fsim[NM_N + 1]) {
+  for (int i = 1; i <= NM_N; ++i) {
+    double fx = fsim[i];
+    double x[NM_N];
+    memcpy(x, sim[i], sizeof(x));
+    int j = i - 1;
+    while (j >= 0 && fsim[j] > fx) {
+      fsim[j + 1] = fsim[j];
+      memcpy(sim[j + 1], sim[j], sizeof(x));
+      --j;
+    }
+    fsim[j + 1] = fx;
+    memcpy(sim[j + 1], x, sizeof(x));
+  }
+}
+
+int32_t orc_nm(orc_objective f, void* ctx, const double x0[6], const double step[6], int32_t max_iter,
+               double ftol, double x_out[6], double* f_out) {
+  const double rho = 1.0, chi = 2.0, psi = 0.5, sigma = 0.5;
+  double sim[NM_N + 1][NM_N], fsim[NM_N + 1];
+  for (int i = 0; i <= NM_N; ++i) {
+    memcpy(sim[i], x0, sizeof(sim[i]));
+    if (i > 0) sim[i][i - 1] = x0[i - 1] + step[i - 1];
+    fsim[i] = f(sim[i], ctx);
+  }
+  nm_sort(sim, fsim);
+  int32_t it = 0;
+  while (it < max_iter) {
+    if (ftol > 0.0) {
+      double spread = 0.0;
+      for (int i = 1; i <= NM_N; ++i) {
+        const double d = fabs(fsim[i] - fsim[0]);
+        if (d > spread) spread = d;
+      }
+      if (spread <= ftol) break;
+    }
+    double xbar[NM_N];
+    for (int j = 0; j < NM_N; ++j) {
+      double acc = 0.0;
+      for (int i = 0; i < NM_N; ++i) acc += sim[i][j];  /* all vertices but the worst */
+      xbar[j] = acc / (double)NM_N;
+    }
+    double xr[NM_N], xe[NM_N], xc[NM_N];
+    for (int j = 0; j < NM_N; ++j) xr[j] = (1.0 + rho) * xbar[j] - rho * sim[NM_N][j];
+    const double fr = f(xr, ctx);
+    int shrink = 0;
+    if (fr < fsim[0]) {
+      for (int j = 0; j < NM_N; ++j) xe[j] = (1.0 + rho * chi) * xbar[j] - rho * chi * sim[NM_N][j];
+      const double fe = f(xe, ctx);
+      if (fe < fr) {
+        memcpy(sim[NM_N], xe, sizeof(xe));
+        fsim[NM_N] = fe;
+      } else {
+        memcpy(sim[NM_N], xr, sizeof(xr));
+        fsim[NM_N] = fr;
+      }
+    } else if (fr < fsim[NM_N - 1]) {
+      memcpy(sim[NM_N], xr, sizeof(xr));
+      fsim[NM_N] = fr;
+    } else if (fr < fsim[NM_N]) {  /* outside contraction */
+      for (int j = 0; j < NM_N; ++j) xc[j] = (1.0 + psi * rho) * xbar[j] - psi * rho * sim[NM_N][j];
+      const double fc = f(xc, ctx);
+      if (fc <= fr) {
+        memcpy(sim[NM_N], xc, sizeof(xc));
+        fsim[NM_N] = fc;
+      } else {
+        shrink = 1;
+      }
+    } else {  /* inside contraction */
+      for (int j = 0; j < NM_N; ++j) xc[j] = (1.0 - psi) * xbar[j] + psi * sim[NM_N][j];
+      const double fc = f(xc, ctx);
+      if (fc < fsim[NM_N]) {
+        memcpy(sim[NM_N], xc, sizeof(xc));
+        fsim[NM_N] = fc;
+      } else {
+        shrink = 1;
+      }
+    }
+    if (shrink) {
+      for (int i = 1; i <= NM_N; ++i) {
+        for (int j = 0; j < NM_N; ++j) sim[i][j] = sim[0][j] + sigma * (sim[i][j] - sim[0][j]);
+        fsim[i] = f(sim[i], ctx);
+      }
+    }
+    nm_sort(sim, fsim);
+    ++it;
+  }
+  memcpy(x_out, sim[0], sizeof(sim[0]));
+  if (f_out) *f_out = fsim[0];
+  return it;
+}
+
+typedef struct {
+  const orc_grid* g;
+  const uint8_t* symA;
+  const int32_t* boxA;
+  const float* xyzB;
+  int64_t nB;
+} nm_mi_ctx;
+
+static double nm_neg_mi(const double x[6], void* vctx) {
+  const nm_mi_ctx* c = (const nm_mi_ctx*)vctx;
+  float pose[12];
+  double mi = 0.0;
+  orc_round_pose(c->g, x, pose);
+  orc_eval_mi(c->g, c->symA, c->boxA, c->xyzB, c->nB, pose, 0, 1, &mi, NULL, NULL);
+  return -mi;
+}
+
+int32_t orc_nm_mi(const orc_grid* g, const uint8_t* symA, const int32_t boxA[6], const float* xyzB,
+                  int64_t nB, const double x0[6], const double step[6], int32_t max_iter, double ftol,
+                  double T_out[6], double* mi_out) {
+  nm_mi_ctx ctx = {g, symA, boxA, xyzB, nB};
+  double f = 0.0;
+  const int32_t it = orc_nm(nm_neg_mi, &ctx, x0, step, max_iter, ftol, T_out, &f);
+  if (mi_out) *mi_out = -f;
+  return it;
+}
+
+typedef struct {
+  const double* w;
+  const double* c;
+} nm_quad_ctx;
+
+static double nm_quad(const double x[6], void* vctx) {
+  const nm_quad_ctx* q = (const nm_quad_ctx*)vctx;
+  double s = 0.0;
+  for (int i = 0; i < 6; ++i) s += q->w[i] * (x[i] - q->c[i]) * (x[i] - q->c[i]);
+  return s;
+}
+
+int32_t orc_nm_quadratic(const double w[6], const double c[6], const double x0[6], const double step[6],
+                         int32_t max_iter, double ftol, double x_out[6], double* f_out) {
+  nm_quad_ctx q = {w, c};
+  return orc_nm(nm_quad, &q, x0, step, max_iter, ftol, x_out, f_out);
+}

@@ -108,6 +108,27 @@ void orc_search(const orc_grid* g, const uint8_t* symA, const int32_t boxA[6],
 /* The lattice of one search level: P = prod(counts) poses (eta, FP64), rotation axes outer. */
 void orc_lattice(const double center[6], const double range[6], const int32_t counts[6], double* eta_out);
 
+/* Nelder-Mead minimisation over R^6 (the optimiser of Algorithm 1, "Update T_c using
+   Nelder-Mead optimization"; Nelder and Mead 1965, cited in Sec. III-C).  Initial simplex:
+   x0 and x0 + step[i] e_i (Sec. IV gives the step sizes).  Coefficients: reflection 1,
+   expansion 2, contraction 1/2, shrink 1/2.  Each iteration orders the vertices by f
+   (equal values keep their previous order), reflects the worst through the centroid of the
+   others, and expands, contracts or shrinks.  Stops after max_iter iterations, or earlier
+   when ftol > 0 and every vertex is within ftol of the best.  Returns the iterations run;
+   x_out / f_out: the best vertex.  f(x, ctx) is the objective. */
+typedef double (*orc_objective)(const double x[6], void* ctx);
+int32_t orc_nm(orc_objective f, void* ctx, const double x0[6], const double step[6], int32_t max_iter,
+               double ftol, double x_out[6], double* f_out);
+
+/* Nelder-Mead on f(eta) = -MI(round(eta)) with the FP64 MI of orc_eval_mi. */
+int32_t orc_nm_mi(const orc_grid* g, const uint8_t* symA, const int32_t boxA[6], const float* xyzB,
+                  int64_t nB, const double x0[6], const double step[6], int32_t max_iter, double ftol,
+                  double T_out[6], double* mi_out);
+
+/* Nelder-Mead on the quadratic f(x) = sum_i w_i (x_i - c_i)^2 (test objective). */
+int32_t orc_nm_quadratic(const double w[6], const double c[6], const double x0[6], const double step[6],
+                         int32_t max_iter, double ftol, double x_out[6], double* f_out);
+
 #ifdef __cplusplus
 }
 #endif

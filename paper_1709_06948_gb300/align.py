@@ -31,7 +31,7 @@ EXPORTS = ["align_create_grid", "align_destroy_grid", "align_grid_info", "align_
            "align_search_ex", "align_eval_stats", "align_profile", "align_reference_noalloc", "align_batch_create",
            "align_batch_destroy", "align_eval_batch", "align_batch_set_shape", "align_batch_stats",
            "align_server_create", "align_server_add_reference", "align_submit", "align_poll", "align_wait",
-           "align_server_now", "align_server_stats", "align_server_destroy", "align_last_error"]
+           "align_server_now", "align_server_stats", "align_server_destroy", "align_refine_nm", "align_last_error"]
 
 
 class AlignError(RuntimeError):
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
         "align_wait": [P, C.c_uint64, i64, P],
         "align_server_stats": [P, P],
         "align_server_destroy": [P],
+        "align_refine_nm": [P, P, i64, C.c_int, P, i32, P, i32, C.c_double, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -322,6 +323,23 @@ def align_search(grid: Grid, xyzB, init, rng, levels=6, counts=None):
                                T.ctypes.data_as(C.c_void_p), C.byref(mi), lb.ctypes.data_as(C.c_void_p)))
     del keep
     return T, float(mi.value), lb[:levels]
+
+
+def align_refine_nm(grid: Grid, xyzB, starts, step=(8.0, 8.0, 1.0, 0.1, 0.1, 0.8), max_iter=100, ftol=0.0):
+    """Nelder-Mead from every start (S x 6); returns (T [S, 6], MI [S], iterations [S])."""
+    pptr, n, flags, keep = _points_arg(xyzB)
+    st = _host(starts, np.float64, (6,))
+    S = int(st.shape[0])
+    stp = _host(step, np.float64).reshape(6)
+    T = np.zeros((S, 6), dtype=np.float64)
+    mi = np.zeros(S, dtype=np.float32)
+    it = np.zeros(S, dtype=np.int32)
+    _check(load().align_refine_nm(grid.handle, pptr, n, flags, st.ctypes.data_as(C.c_void_p), S,
+                                  stp.ctypes.data_as(C.c_void_p), int(max_iter), float(ftol),
+                                  T.ctypes.data_as(C.c_void_p), mi.ctypes.data_as(C.c_void_p),
+                                  it.ctypes.data_as(C.c_void_p)))
+    del keep
+    return T, mi, it
 
 
 def align_eval_stats(grid: Grid):

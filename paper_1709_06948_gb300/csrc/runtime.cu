@@ -730,6 +730,191 @@ align_status align_search_ex(align_grid* g, const float* xyzB, int64_t nB, int f
   return ALIGN_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Nelder-Mead refinement (Algorithm 1's optimiser), S simplices in lockstep: every phase of
+// an iteration (reflections; expansions or contractions; shrinks) evaluates the points of
+// all simplices that need one in a single batched evaluation.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+struct NmSimplex {
+  double x[7][6];
+  double f[7];   // -MI
+  int32_t it = 0;
+  bool done = false;
+  double xbar[6], xr[6], x2[6];
+  double fr = 0.0;
+  int stage = 0;  // 0 accept reflection, 1 expansion, 2 outside contraction, 3 inside contraction
+  bool shrink = false;
+};
+
+// Order the vertices by f; equal values keep their order.
+void nm_sort(NmSimplex& s) {
+  for (int i = 1; i < 7; ++i) {
+    double xi[6];
+    std::memcpy(xi, s.x[i], sizeof(xi));
+    const double fi = s.f[i];
+    int j = i - 1;
+    while (j >= 0 && s.f[j] > fi) {
+      s.f[j + 1] = s.f[j];
+      std::memcpy(s.x[j + 1], s.x[j], sizeof(xi));
+      --j;
+    }
+    s.f[j + 1] = fi;
+    std::memcpy(s.x[j + 1], xi, sizeof(xi));
+  }
+}
+
+// -MI of a list of points (FP64 eta) through one batched evaluation.
+align_status nm_eval(align_grid* g, int32_t n_tiles, const std::vector<const double*>& pts, std::vector<double>& f) {
+  const int64_t P = (int64_t)pts.size();
+  f.assign((size_t)P, 0.0);
+  if (P == 0) return ALIGN_OK;
+  std::vector<float> poses((size_t)P * 12), mi((size_t)P);
+  for (int64_t p = 0; p < P; ++p) pose_to_fp32(g->origin, pts[(size_t)p], &poses[(size_t)p * 12]);
+  int64_t am = 0;
+  align_status st = eval_common(g, nullptr, g->n_points, 0, poses.data(), nullptr, P, mi.data(), &am, nullptr,
+                                nullptr, true, n_tiles);
+  if (st != ALIGN_OK) return st;
+  for (int64_t p = 0; p < P; ++p) f[(size_t)p] = -(double)mi[(size_t)p];
+  return ALIGN_OK;
+}
+
+}  // namespace
+
+align_status align_refine_nm(align_grid* g, const float* xyzB, int64_t nB, int flags, const double* starts,
+                             int32_t S, const double step[6], int32_t max_iter, double ftol, double* T_out,
+                             float* mi_out, int32_t* iters_out) {
+  align_status st = check_grid(g);
+  if (st != ALIGN_OK) return st;
+  if (!g->has_ref) return fail(ALIGN_E_NOREF, "no reference scan set");
+  if (S < 0 || (S > 0 && (!starts || !T_out))) return fail(ALIGN_E_INVALID, "bad simplex arrays");
+  if (!step || max_iter < 0) return fail(ALIGN_E_INVALID, "bad step or max_iter");
+  for (int32_t i = 0; i < S * 6; ++i)
+    if (!std::isfinite(starts[i])) return fail(ALIGN_E_INVALID, "start %d is not finite", i / 6);
+  for (int a = 0; a < 6; ++a)
+    if (!std::isfinite(step[a])) return fail(ALIGN_E_INVALID, "step not finite");
+  if (S == 0) return ALIGN_OK;
+  st = ensure_status_words(g);
+  if (st != ALIGN_OK) return st;
+  int32_t n_tiles = 0;
+  st = upload_points(g, xyzB, nB, flags, &n_tiles);
+  if (st != ALIGN_OK) return st;
+  const double rho = 1.0, chi = 2.0, psi = 0.5, sigma = 0.5;
+  std::vector<NmSimplex> sx((size_t)S);
+  std::vector<const double*> pts;
+  std::vector<double> f;
+  // initial simplices: x0 and x0 + step[i] e_i
+  for (int32_t k = 0; k < S; ++k)
+    for (int i = 0; i < 7; ++i) {
+      std::memcpy(sx[(size_t)k].x[i], starts + 6 * k, 6 * sizeof(double));
+      if (i > 0) sx[(size_t)k].x[i][i - 1] = starts[6 * k + i - 1] + step[i - 1];
+      pts.push_back(sx[(size_t)k].x[i]);
+    }
+  st = nm_eval(g, n_tiles, pts, f);
+  if (st != ALIGN_OK) return st;
+  for (int32_t k = 0; k < S; ++k) {
+    for (int i = 0; i < 7; ++i) sx[(size_t)k].f[i] = f[(size_t)(7 * k + i)];
+    nm_sort(sx[(size_t)k]);
+    sx[(size_t)k].done = max_iter == 0;
+  }
+  for (;;) {
+    // convergence test, centroid and reflection of every active simplex
+    pts.clear();
+    std::vector<NmSimplex*> act;
+    for (NmSimplex& s : sx) {
+      if (s.done) continue;
+      if (ftol > 0.0) {
+        double spread = 0.0;
+        for (int i = 1; i < 7; ++i) spread = std::max(spread, std::fabs(s.f[i] - s.f[0]));
+        if (spread <= ftol) {
+          s.done = true;
+          continue;
+        }
+      }
+      for (int j = 0; j < 6; ++j) {
+        double acc = 0.0;
+        for (int i = 0; i < 6; ++i) acc += s.x[i][j];
+        s.xbar[j] = acc / 6.0;
+        s.xr[j] = (1.0 + rho) * s.xbar[j] - rho * s.x[6][j];
+      }
+      act.push_back(&s);
+      pts.push_back(s.xr);
+    }
+    if (act.empty()) break;
+    st = nm_eval(g, n_tiles, pts, f);
+    if (st != ALIGN_OK) return st;
+    // second point: expansion or contraction
+    pts.clear();
+    std::vector<NmSimplex*> second;
+    for (size_t q = 0; q < act.size(); ++q) {
+      NmSimplex& s = *act[q];
+      s.fr = f[q];
+      s.shrink = false;
+      if (s.fr < s.f[0]) {
+        s.stage = 1;
+        for (int j = 0; j < 6; ++j) s.x2[j] = (1.0 + rho * chi) * s.xbar[j] - rho * chi * s.x[6][j];
+      } else if (s.fr < s.f[5]) {
+        s.stage = 0;
+      } else if (s.fr < s.f[6]) {
+        s.stage = 2;
+        for (int j = 0; j < 6; ++j) s.x2[j] = (1.0 + psi * rho) * s.xbar[j] - psi * rho * s.x[6][j];
+      } else {
+        s.stage = 3;
+        for (int j = 0; j < 6; ++j) s.x2[j] = (1.0 - psi) * s.xbar[j] + psi * s.x[6][j];
+      }
+      if (s.stage != 0) {
+        second.push_back(&s);
+        pts.push_back(s.x2);
+      } else {
+        std::memcpy(s.x[6], s.xr, sizeof(s.xr));
+        s.f[6] = s.fr;
+      }
+    }
+    st = nm_eval(g, n_tiles, pts, f);
+    if (st != ALIGN_OK) return st;
+    pts.clear();
+    std::vector<NmSimplex*> shrinking;
+    for (size_t q = 0; q < second.size(); ++q) {
+      NmSimplex& s = *second[q];
+      const double f2 = f[q];
+      if (s.stage == 1) {
+        if (f2 < s.fr) {
+          std::memcpy(s.x[6], s.x2, sizeof(s.x2));
+          s.f[6] = f2;
+        } else {
+          std::memcpy(s.x[6], s.xr, sizeof(s.xr));
+          s.f[6] = s.fr;
+        }
+      } else if ((s.stage == 2 && f2 <= s.fr) || (s.stage == 3 && f2 < s.f[6])) {
+        std::memcpy(s.x[6], s.x2, sizeof(s.x2));
+        s.f[6] = f2;
+      } else {
+        s.shrink = true;
+        for (int i = 1; i < 7; ++i) {
+          for (int j = 0; j < 6; ++j) s.x[i][j] = s.x[0][j] + sigma * (s.x[i][j] - s.x[0][j]);
+          pts.push_back(s.x[i]);
+        }
+        shrinking.push_back(&s);
+      }
+    }
+    st = nm_eval(g, n_tiles, pts, f);
+    if (st != ALIGN_OK) return st;
+    for (size_t q = 0; q < shrinking.size(); ++q)
+      for (int i = 1; i < 7; ++i) shrinking[q]->f[i] = f[q * 6 + (size_t)(i - 1)];
+    for (NmSimplex* s : act) {
+      nm_sort(*s);
+      if (++s->it >= max_iter) s->done = true;
+    }
+  }
+  for (int32_t k = 0; k < S; ++k) {
+    std::memcpy(T_out + 6 * k, sx[(size_t)k].x[0], 6 * sizeof(double));
+    if (mi_out) mi_out[k] = (float)(-sx[(size_t)k].f[0]);
+    if (iters_out) iters_out[k] = sx[(size_t)k].it;
+  }
+  return ALIGN_OK;
+}
+
 align_status align_search(align_grid* g, const float* xyzB, int64_t nB, int flags, const double init[6],
                           const double range[6], int32_t levels, double T_out[6], float* mi_out) {
   const int32_t counts[6] = {8, 8, 2, 2, 2, 8};

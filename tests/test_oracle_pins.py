@@ -359,3 +359,38 @@ def test_search_recovers_tiny_within_final_step():
     assert np.all(np.abs(Tout[:2] - T[:2]) <= 0.3)
     assert abs(Tout[5] - T[5]) <= 2 * final_step[5] + math.radians(1.0)
     assert mi > 0
+
+
+def _quad(w, c, v):
+    s = 0.0  # same operation order as the oracle's test objective
+    for i in range(6):
+        s += float(w[i]) * (float(v[i]) - float(c[i])) * (float(v[i]) - float(c[i]))
+    return s
+
+
+def test_nelder_mead_matches_scipy_on_quadratics():
+    """The oracle's Nelder-Mead (Algorithm 1's optimiser) equals SciPy's implementation of
+    the same method (standard coefficients, given initial simplex) step for step on
+    quadratic objectives without ties (SciPy's maxiter counts the initial simplex)."""
+    optimize = pytest.importorskip("scipy.optimize")
+    step = np.array([8, 8, 1, 0.1, 0.1, 0.8])
+    for seed in range(4):
+        rng = np.random.default_rng(seed)
+        w = rng.uniform(0.3, 3, 6)
+        c = rng.uniform(-1, 1, 6) * np.array([2, 2, 0.3, 0.05, 0.05, 0.3])
+        x0 = rng.uniform(-1, 1, 6) * np.array([3, 3, 0.3, 0.05, 0.05, 0.2])
+        sim = np.array([x0] + [x0 + np.eye(6)[i] * step[i] for i in range(6)])
+        for it in (1, 7, 25, 60):
+            x, f, n = oracle.nm_quadratic(w, c, x0, step, it)
+            r = optimize.minimize(lambda v: _quad(w, c, v), x0, method="Nelder-Mead",
+                                  options=dict(initial_simplex=sim, maxiter=it + 1, xatol=0, fatol=0,
+                                               maxfev=100000))
+            assert n == it
+            assert np.array_equal(x, r.x) and f == r.fun
+
+
+def test_nelder_mead_converges_and_stops_on_ftol():
+    w = np.ones(6)
+    c = np.array([0.5, -0.25, 0.1, 0.02, -0.01, 0.2])
+    x, f, n = oracle.nm_quadratic(w, c, np.zeros(6), np.array([1, 1, 1, 0.1, 0.1, 0.1]), 2000, ftol=1e-14)
+    assert n < 2000 and f < 1e-10 and np.max(np.abs(x - c)) < 1e-4
