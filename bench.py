@@ -264,6 +264,60 @@ def run_batched(align, steps):
     return out
 
 
+def run_refine(align, pair, L, T_search):
+    """Nelder-Mead refinement (Algorithm 1's optimiser) of the search result: 64 simplices
+    from starts scattered around it, 40 iterations each, batched evaluations."""
+    rng = np.random.default_rng(scangen.SEED_BASE + 6)
+    S, iters = 64, 40
+    starts = T_search[None, :] + rng.normal(0, 1, (S, 6)) * np.array([0.3, 0.3, 0.05, 0.004, 0.004, 0.01])
+    step = np.array([0.3, 0.3, 0.1, 0.005, 0.005, 0.02])
+    align.align_refine_nm(L, pair.xyzB, starts[:4], step=step, max_iter=2)  # warm-up
+    t0 = time.perf_counter()
+    T, mi, it = align.align_refine_nm(L, pair.xyzB, starts, step=step, max_iter=iters)
+    dt = time.perf_counter() - t0
+    k = int(np.argmax(mi))
+    return {"workload": f"{S} simplices x {iters} iterations on the 120k-point pair, started around the "
+                        "lattice-search result (step 0.3 m / 0.1 m / 0.005 rad / 0.02 rad)",
+            "ms": dt * 1e3, "best_mi": float(mi[k]),
+            "best_T": [float(x) for x in T[k]],
+            "xy_error_m": float(np.hypot(T[k][0] - pair.T[0], T[k][1] - pair.T[1])),
+            "note": "each iteration evaluates the reflections, then expansions/contractions, then shrinks of "
+                    "all simplices in one batched evaluation each"}
+
+
+def run_large(align, steps):
+    """128-beam pair (~260k points), 400x400x40 grid at 0.2 m (6.4M voxels), joint count x
+    z-variance feature (57 symbols), one 32,768-pose lattice per launch."""
+    import torch
+    pair = scangen.large_pair()
+    spec = pair.grid
+    L = align.align_create_grid(spec.origin, spec.res_m, spec.dims, spec.feature, spec.count_levels,
+                                spec.var_levels)
+    align.align_set_reference(L, pair.xyzA)
+    etas = scangen.large_poses()
+    P = len(etas)
+    B = torch.from_numpy(pair.xyzB).cuda()
+    align.align_eval_mi(L, B, eta6=etas)  # warm-up (learns the key partitions)
+    torch.cuda.synchronize()
+    align.align_profile(L, 1)
+    wall = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        mi, am, _ = align.align_eval_mi(L, B, eta6=etas)
+        wall.append(time.perf_counter() - t0)
+    ev_ms, comp_ms, n = align.align_profile(L, 2)
+    align.align_profile(L, 0)
+    st = align.align_eval_stats(L)
+    out = {"workload": f"large: {pair.xyzB.shape[0]}-point 128-beam pair, grid 400x400x40 @ 0.2 m (6.4M voxels), "
+                       f"joint count x z-variance 57 symbols, {P} lattice poses per launch (+-10 m, +-30 deg yaw)",
+           "pose_evals_per_s_wall": P / statistics.median(wall),
+           "ms_per_launch_wall": statistics.median(wall) * 1e3,
+           "eval_kernel_ms": ev_ms / max(n, 1), "key_partitions": st["passes"],
+           "argmax_eta": [float(x) for x in etas[am]], "T_true": [float(x) for x in pair.T], "mi_max": float(mi[am])}
+    L.close()
+    return out
+
+
 def run_serving(align):
     """Poisson arrivals (200 req/s) of alignment requests against 16 resident references;
     continuous batching server vs the plain loop (one request at a time, one launch per
@@ -494,12 +548,16 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{n_sample} of the 4,096 level-0 lattice poses on the same pair, "
                                           f"{dt:.1f} s wall on {cores} threads (MI evaluations only)"}
+    if rank == 0 and ws == 1 and args.mode == "search" and not args.no_refine:
+        line["refine"] = run_refine(align, pair, L, np.array(T, dtype=np.float64))
     L.close()
     if rank == 0 and ws == 1 and args.mode == "search":
         if not args.no_batched:
             line["batched"] = run_batched(align, max(3, min(args.steps, 10)))
         if not args.no_serving:
             line["serving"] = run_serving(align)
+        if not args.no_large:
+            line["large"] = run_large(align, 2)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -520,6 +578,8 @@ def main():
     ap.add_argument("--poses", type=int, default=4096)
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-pair batched leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-requests leg")
+    ap.add_argument("--no-refine", action="store_true", help="skip the Nelder-Mead refinement leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the large-grid leg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -230,6 +230,11 @@ int group_rotations(const float* poses12, int64_t P, std::vector<float>& rots, s
   rots.clear();
   idx.resize((size_t)P);
   for (int64_t p = 0; p < P; ++p) {
+    // lattices list poses rotation-major: most poses share the previous pose's rotation
+    if (p > 0 && std::memcmp(poses12 + 12 * p, poses12 + 12 * (p - 1), 9 * sizeof(float)) == 0) {
+      idx[(size_t)p] = idx[(size_t)(p - 1)];
+      continue;
+    }
     RotKey k;
     std::memcpy(k.w, poses12 + 12 * p, sizeof(k.w));
     auto it = seen.find(k);

@@ -378,3 +378,37 @@ def poisson_arrivals(rate_hz: float, n: int, seed: int = SEED_BASE + 4) -> np.nd
     """Arrival times (s) of n requests of a Poisson process with the given mean rate."""
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate_hz, n))
+
+
+# ----------------------------------------------------------------------------------
+# Large workload: 128-beam scanner, 0.2 m grid, joint count x z-variance feature
+# ----------------------------------------------------------------------------------
+def large_grid() -> GridSpec:
+    """400 x 400 x 40 voxels at 0.2 m (6.4M voxels); joint count (7 levels) x z-variance
+    (8 levels) feature: 1 + 7 * 8 = 57 symbols."""
+    return GridSpec(origin=(-40.0, -40.0, -1.0), res_m=0.2, dims=(400, 400, 40), feature=2, count_levels=7,
+                    var_levels=8)
+
+
+def large_pair(seed: int = SEED_BASE + 5, T=None) -> Pair:
+    """128 beams over -25 .. +15 deg, 0.15 deg azimuth (2,400 steps), hits <= 120 m, range
+    noise N(0, 0.02 m); B from a pose offset up to 10 m / 30 deg yaw."""
+    rng = np.random.default_rng(seed)
+    scene = urban_scene(rng)
+    if T is None:
+        r = 10.0 * math.sqrt(rng.uniform())
+        a = rng.uniform(-math.pi, math.pi)
+        T = np.array([r * math.cos(a), r * math.sin(a), rng.uniform(-0.1, 0.1), math.radians(rng.uniform(-1, 1)),
+                      math.radians(rng.uniform(-1, 1)), math.radians(rng.uniform(-30, 30))])
+    T = np.asarray(T, dtype=np.float64)
+    kw = dict(n_beams=128, elev_deg=(-25.0, 15.0), az_step_deg=0.15, max_range=120.0, rng=rng)
+    A = raycast(scene, np.zeros(6), **kw)
+    B = raycast(scene, T, **kw)
+    return Pair(A.astype(np.float32), B.astype(np.float32), T, large_grid())
+
+
+def large_poses(center=(0, 0, 0, 0, 0, 0)) -> np.ndarray:
+    """32,768 poses: 16 tx x 16 ty x 2 tz x 2 roll x 2 pitch x 16 yaw over +-10 m, +-0.25 m,
+    +-1 deg, +-30 deg around center."""
+    return pose_grid(center, (10.0, 10.0, 0.25, math.radians(1.0), math.radians(1.0), math.radians(30.0)),
+                     (16, 16, 2, 2, 2, 16))
