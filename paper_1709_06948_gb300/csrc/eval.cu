@@ -114,6 +114,23 @@ __device__ __forceinline__ void red_add_if(bool p, uint32_t a, uint32_t v) {
                "r"(a), "r"(v)
                : "memory");
 }
+// Shared atomic add under a predicate; returns 0 when not executed.
+__device__ __forceinline__ uint32_t atom_add_if(bool p, uint32_t a, uint32_t v) {
+  uint32_t old;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\tmov.u32 %0, 0;\n\t@q atom.shared.add.u32 %0, [%2], %3;\n\t}"
+      : "=r"(old)
+      : "r"((uint32_t)p), "r"(a), "r"(v)
+      : "memory");
+  return old;
+}
+// 16-byte global store under a predicate.
+__device__ __forceinline__ void stg128_if(bool p, uint4* g, uint4 v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.global.v4.u32 [%1], {%2, %3, %4, %5};\n\t}" ::"r"(
+                   (uint32_t)p),
+               "l"(g), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
 // CAS under a predicate; returns `cmp` when not executed.
 __device__ __forceinline__ uint32_t atom_cas_if(bool p, uint32_t a, uint32_t cmp, uint32_t v) {
   uint32_t old;
@@ -353,11 +370,12 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
     red_add_if(ok, v + 4u, e.z);
     red_add_if(ok, v + 8u, e.w);
   }
-  if (valid && slot < 0) {  // home bucket full (or insert race lost): overflow list
-    const uint32_t i = atom_add(S.a_key - kFlagOvf, 1u);
-    if (i < (uint32_t)a.ovf_cap) a.ovf[(size_t)blockIdx.x * (uint32_t)a.ovf_cap + i] = e;
-    else sts32(S.a_key - kFlagFull, 1u);
-  }
+  // home bucket full (or insert race lost): the run goes to the overflow list
+  const bool ov = valid && slot < 0;
+  const uint32_t i = atom_add_if(ov, S.a_key - kFlagOvf, 1u);
+  const bool ov_ok = ov && i < (uint32_t)a.ovf_cap;
+  stg128_if(ov_ok, a.ovf + ((size_t)blockIdx.x * (uint32_t)a.ovf_cap + (ov_ok ? i : 0u)), e);
+  sts32_if(ov && !ov_ok, S.a_key - kFlagFull, 1u);
   // move the entries beyond `count` down, one word at a time (lane l reads entry l + count
   // and writes entry l, which only it has read; entry l + count < 64 for count <= 32)
   const bool mv = lane + count < fill;
@@ -529,7 +547,9 @@ __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& g
   const int kz = (int)q;
   bx.mn0 = min(bx.mn0, kx); bx.mn1 = min(bx.mn1, ky); bx.mn2 = min(bx.mn2, kz);
   bx.mx0 = max(bx.mx0, kx); bx.mx1 = max(bx.mx1, ky); bx.mx2 = max(bx.mx2, kz);
-  const int sB = (kExact || n > gc.nlim)
+  // The fast path redoes any pose with a voxel above nlim (flag above), so its symbols only
+  // need the 64-bit test; the exact path takes the 128-bit one where needed.
+  const int sB = (kExact && n > gc.nlim)
                      ? feature_symbol(gc.feature, gc.Lc, gc.Lv, gc.count_thresh, gc.var_thresh, n, s1, s2)
                      : feature_symbol_small(gc, (uint32_t)n, (int32_t)s1, (uint32_t)s2);
   if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
