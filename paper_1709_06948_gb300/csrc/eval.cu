@@ -10,7 +10,7 @@
 //
 // eval_kernel: persistent, one CTA per SM, one pose at a time per CTA; the poses of all
 // items are one list, and each pose brings its item's grid constants.  Every thread
-// streams its own points straight from L2, three tiles ahead, computes the voxel key and
+// streams its own points straight from L2, four tiles ahead, computes the voxel key and
 // dz (device_common.cuh) and keeps the run of equal keys it is walking in registers
 // (n, S1, S2).  Finished runs go to a per-warp ring in shared memory; 32 at a time the
 // whole warp adds them into a shared-memory open-addressing hash table (buckets of 4
@@ -59,7 +59,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kPPT = MI_EVAL_PPT;       // points per thread per tile
 constexpr int kTile = kThreads * kPPT;  // points per tile
 #ifndef MI_EVAL_DEPTH
-#define MI_EVAL_DEPTH 3
+#define MI_EVAL_DEPTH 4
 #endif
 constexpr int kDepth = MI_EVAL_DEPTH;   // tiles loaded ahead into registers
 constexpr int kMinTiles = 3;
