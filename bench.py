@@ -565,6 +565,113 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------------------------------
+# synthetic stand-ins for the paper's accuracy experiments (Figs. 4-5) and cost surfaces
+# (Fig. 6); not part of the default run
+# --------------------------------------------------------------------------------------
+ACC_T_ERRORS = (1.0, 3.0, 5.0, 7.0, 9.0)
+ACC_YAW_ERRORS = (2.0, 5.0, 10.0, 15.0, 20.0)
+PAPER_SIMPLEX = np.array([8.0, 8.0, 1.0, 0.1, 0.1, 0.8])  # Sec. IV
+
+
+def _rot_err(a, b):
+    """Angle (rad) of R(a)^T R(b)."""
+    Ra, Rb = scangen.rot_zyx(a), scangen.rot_zyx(b)
+    c = (np.trace(Ra.T @ Rb) - 1.0) / 2.0
+    return float(np.arccos(np.clip(c, -1.0, 1.0)))
+
+
+def run_accuracy(args):
+    """Final alignment error against the initial error, for the count (MI-N) and z-variance
+    (MI-VARZ) features at 1 m voxels: Nelder-Mead from the identity with the paper's simplex
+    (Algorithm 1), and lattice search + Nelder-Mead.  Pairs: 64-beam ray-cast scans with the
+    true offset of the given size in a random direction."""
+    from paper_1709_06948_gb300 import align
+    import torch
+    torch.cuda.set_device(0)
+    n_pairs = args.pairs
+    feats = {"MI-N": dict(feature=0, count_levels=7, var_levels=1), "MI-VARZ": dict(feature=1, count_levels=1,
+                                                                                      var_levels=15)}
+    rng = np.random.default_rng(scangen.SEED_BASE + 7)
+    results = {}
+    for kind, errors in (("translation_m", ACC_T_ERRORS), ("yaw_deg", ACC_YAW_ERRORS)):
+        for e in errors:
+            for k in range(n_pairs):
+                a = rng.uniform(-math.pi, math.pi)
+                if kind == "translation_m":
+                    T = np.array([e * math.cos(a), e * math.sin(a), rng.uniform(-0.1, 0.1), 0.0, 0.0,
+                                  math.radians(rng.uniform(-3, 3))])
+                else:
+                    r = rng.uniform(0, 2)
+                    T = np.array([r * math.cos(a), r * math.sin(a), 0.0, 0.0, 0.0,
+                                  math.radians(e) * (1 if rng.uniform() < 0.5 else -1)])
+                pair = scangen.lidar_pair(seed=scangen.SEED_BASE + 1000 + 37 * k + int(10 * e), T=T)
+                for fname, fk in feats.items():
+                    spec = scangen.lidar_grid(1.0)
+                    L = align.align_create_grid(spec.origin, spec.res_m, spec.dims, fk["feature"], fk["count_levels"],
+                                                fk["var_levels"])
+                    align.align_set_reference(L, pair.xyzA)
+                    Tn, _, _ = align.align_refine_nm(L, pair.xyzB, np.zeros((1, 6)), step=PAPER_SIMPLEX, max_iter=150)
+                    rngs = np.array([10.0, 10.0, 0.5, math.radians(2.0), math.radians(2.0), math.radians(25.0)])
+                    Ts, _, _ = align.align_search(L, pair.xyzB, np.zeros(6), rngs, levels=5,
+                                                  counts=(12, 12, 2, 2, 2, 12))
+                    Tl, _, _ = align.align_refine_nm(L, pair.xyzB, Ts[None, :],
+                                                     step=np.array([0.5, 0.5, 0.2, 0.01, 0.01, 0.03]), max_iter=60)
+                    for meth, Tf in (("nm_paper_simplex", Tn[0]), ("lattice_then_nm", Tl[0])):
+                        key = f"{fname}/{meth}/{kind}={e:g}"
+                        r = results.setdefault(key, {"t_err": [], "r_err": []})
+                        r["t_err"].append(float(np.linalg.norm(Tf[:3] - T[:3])))
+                        r["r_err"].append(_rot_err(Tf, T))
+                    L.close()
+    summary = {k: {"mean_translation_error_m": float(np.mean(v["t_err"])),
+                   "mean_rotation_error_rad": float(np.mean(v["r_err"])),
+                   "success_rate_t_lt_0.5m": float(np.mean(np.array(v["t_err"]) < 0.5)), "pairs": len(v["t_err"])}
+               for k, v in results.items()}
+    print(json.dumps({"mode": "accuracy", "data": "synthetic (64-beam ray-cast pairs; the paper's Ford/KITTI data "
+                                                  "are not available)", "grid": "80x80x8 @ 1 m",
+                      "results": summary}))
+    return 0
+
+
+def run_surface(args):
+    """MI over (t_x, t_y) on a 0.25 m grid within +-8 m of the truth, and over heading within
+    +-30 deg at 0.5 deg, other parameters at the truth: the peak's offset from the truth and
+    the number of strict local maxima (8-neighbourhood) of the 2-D surface."""
+    from paper_1709_06948_gb300 import align
+    import torch
+    torch.cuda.set_device(0)
+    pair = scangen.lidar_pair()
+    out = {}
+    for fname, feat in (("MI-N", (0, 7, 1)), ("MI-VARZ", (1, 1, 15))):
+        spec = scangen.lidar_grid(1.0)
+        L = align.align_create_grid(spec.origin, spec.res_m, spec.dims, *feat)
+        align.align_set_reference(L, pair.xyzA)
+        g = np.arange(-8.0, 8.0001, 0.25)
+        etas = np.repeat(pair.T[None, :], len(g) * len(g), 0)
+        etas[:, 0] = pair.T[0] + np.repeat(g, len(g))
+        etas[:, 1] = pair.T[1] + np.tile(g, len(g))
+        mi, am, _ = align.align_eval_mi(L, pair.xyzB, eta6=etas)
+        S = mi.reshape(len(g), len(g))
+        inner = S[1:-1, 1:-1]
+        nb = np.stack([S[1 + dy:S.shape[0] - 1 + dy, 1 + dx:S.shape[1] - 1 + dx]
+                       for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dy, dx) != (0, 0)])
+        n_max = int(np.sum(np.all(inner > nb, axis=0)))
+        h = np.arange(-30.0, 30.0001, 0.5)
+        eh = np.repeat(pair.T[None, :], len(h), 0)
+        eh[:, 5] = pair.T[5] + np.radians(h)
+        mh, amh, _ = align.align_eval_mi(L, pair.xyzB, eta6=eh)
+        out[fname] = {"xy_peak_offset_m": [float(etas[am][0] - pair.T[0]), float(etas[am][1] - pair.T[1])],
+                      "xy_strict_local_maxima": n_max, "xy_grid": f"{len(g)}x{len(g)} at 0.25 m",
+                      "heading_peak_offset_deg": float(h[amh]),
+                      "heading_strict_local_maxima": int(np.sum((mh[1:-1] > mh[:-2]) & (mh[1:-1] > mh[2:])))}
+        if args.surface_out:
+            np.save(f"{args.surface_out}_{fname}_xy.npy", S)
+            np.save(f"{args.surface_out}_{fname}_heading.npy", mh)
+        L.close()
+    print(json.dumps({"mode": "surface", "data": "synthetic 64-beam pair, grid 80x80x8 @ 1 m", "results": out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -572,9 +679,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="search", choices=["search", "eval"],
+    ap.add_argument("--mode", default="search", choices=["search", "eval", "accuracy", "surface"],
                     help="search: reference build + 6-level search per step (default); "
-                         "eval: reference build + one align_eval_mi of --poses poses per step")
+                         "eval: reference build + one align_eval_mi of --poses poses per step; "
+                         "accuracy: final error vs initial error (synthetic Figs. 4-5); "
+                         "surface: MI cost surfaces around the truth (synthetic Fig. 6)")
+    ap.add_argument("--pairs", type=int, default=4, help="accuracy mode: pairs per initial error")
+    ap.add_argument("--surface-out", default=None, help="surface mode: prefix of .npy files for the surfaces")
     ap.add_argument("--poses", type=int, default=4096)
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-pair batched leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-requests leg")
@@ -585,6 +696,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "accuracy":
+        return run_accuracy(args)
+    if args.mode == "surface":
+        return run_surface(args)
     return run_ours(args)
 
 

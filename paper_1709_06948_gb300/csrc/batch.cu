@@ -220,9 +220,8 @@ align_status collect(align_batch* b) {
   }
   float ms = 0.0f;
   if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->stats[6] = (int64_t)std::llround(ms * 1000.0);
-  // reset the error word and the wide-voxel count; the partition count stays a running max
-  BCU(cudaMemsetAsync(b->status.p, 0, 4, b->stream), "reset status");
-  BCU(cudaMemsetAsync(b->status.as<uint32_t>() + 2, 0, 4, b->stream), "reset status");
+  // reset the error word, the partition maximum and the wide-voxel count (per launch)
+  BCU(cudaMemsetAsync(b->status.p, 0, 12, b->stream), "reset status");
   if (v[0] & kErrWaitTimeout) return report_error(ALIGN_E_TIMEOUT, "a bounded device wait gave up");
   if (v[0] & kErrDzBound) return report_error(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");
   if (v[0] & kErrPassLimit) return report_error(ALIGN_E_INTERNAL, "key partitioning limit reached");

@@ -781,7 +781,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
     const int pose_passes = passes;
     const int lg = __ffs(pose_passes) - 1;
     uint32_t max_occupied = 0;
-    bool full = false;
+    bool full = false;        // pose handed to the exact path
+    bool overflowed = false;  // ... because its keys did not fit: more partitions help
     for (int pass = 0; pass < pose_passes; ++pass) {
       if (!full) {
         const uint32_t bad =
@@ -794,11 +795,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
         insert_overflow<kVar>(S, a);
         __syncthreads();
       }
-      full = full || S.flags[1] != 0u;
+      overflowed = overflowed || S.flags[1] != 0u;
+      full = full || overflowed;
       scan_table<kVar, false>(S, kOne ? a.one.gc : *S.gc, I, wide, a.wide_count, T, lp, full);
       __syncthreads();
       max_occupied = max(max_occupied, S.flags[0]);
-      full = full || S.flags[3] != 0u;
+      full = full || S.flags[3] != 0u;  // a voxel beyond the 32-bit sums: wide sums, not partitions
       __syncthreads();
       if (tid == 0) {
         S.flags[0] = 0u;
@@ -813,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
         S.flags[1] = 0u;
         a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)gp;
       }
-      if (passes < kMaxPasses) passes *= 2;
+      if (overflowed && passes < kMaxPasses) passes *= 2;
       __syncthreads();
       continue;
     }
@@ -842,9 +844,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
   if (blockIdx.x >= n_redo) return;
   init_smem(S, T, a.K * a.K);
   __syncthreads();
-  int passes = 2 * (int)*(volatile const uint32_t*)a.max_passes;
-  if (passes < 2) passes = 2;
-  if (passes > kMaxPasses) passes = kMaxPasses;
+  int passes_used = 1;
   for (uint32_t i = blockIdx.x; i < n_redo; i += gridDim.x) {
     const int gp = (int)a.redo_list[i];
     const int it = item_of(a, gp);
@@ -855,6 +855,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
     PoseRegs P;
     load_pose(I.poses + 12 * (size_t)lp, P);
     const float4* src = pose_tiles(I, lp) + tid;
+    // Start from the item's partition count: a pose redone for its wide sums needs no more,
+    // one redone for a full table doubles below until its partitions fit.
+    int passes = max(1, min(I.passes0 > 0 ? I.passes0 : a.passes0, kMaxPasses));
     int pass = 0;
     while (pass < passes) {
       const int lg = __ffs(passes) - 1;
@@ -868,7 +871,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
           uint32_t key;
           int dz;
           point_key<kRot>(vc, P, v[j], key, dz);
-          if (key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != (uint32_t)pass) key = kEmptyKey;
+          if (lg > 0 && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != (uint32_t)pass) key = kEmptyKey;
           bad |= (uint32_t)((uint32_t)(dz + vc.dz_bound) > (uint32_t)(2 * vc.dz_bound));
           if (key != run.key || (kVar && run.n >= vc.nlim)) {
             if (run.key != kEmptyKey && run.n != 0u)
@@ -902,9 +905,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
       ++pass;
       __syncthreads();
     }
+    passes_used = max(passes_used, passes);
     emit_pose(S, I, lp);
   }
-  if (tid == 0) atomicMax(a.max_passes, (uint32_t)passes);
+  if (tid == 0) atomicMax(a.max_passes, (uint32_t)passes_used);
 }
 
 // Stream (stretch of consecutive scan points) walked by thread `tid`: lane l of warp w takes

@@ -414,6 +414,7 @@ align_status collect_status(align_grid* g) {
   }
   CU(cudaMemsetAsync(g->err.p, 0, 4, g->stream), "reset error word");
   CU(cudaMemsetAsync(g->wide_count.p, 0, 4, g->stream), "reset counters");
+  CU(cudaMemsetAsync(g->max_passes.p, 0, 4, g->stream), "reset counters");  // a per-launch maximum
   // seed the next launch with the largest partition count a pose needed (a power of two)
   if (vals[1] > (uint32_t)g->passes_seed[0] && vals[1] <= (1u << 16) && (vals[1] & (vals[1] - 1)) == 0)
     g->passes_seed[0] = (int32_t)vals[1];

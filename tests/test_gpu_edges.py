@@ -186,3 +186,22 @@ def test_non_finite_pose_rejected(tiny):
     with pytest.raises(align.AlignError) as e:
         align.align_eval_mi(L, tiny.xyzB, eta6=etas)
     assert e.value.status == align.ALIGN_E_INVALID
+
+
+def test_exact_path_does_not_escalate_partitions():
+    """Poses finished on the exact path (wide sums) many times over: the partition count the
+    next launches start with must stay where the data put it (no growth per launch)."""
+    from paper_1709_06948_gb300 import align
+    rng = np.random.default_rng(38)
+    spec = scangen.lidar_grid(0.5)
+    dense = np.stack([rng.uniform(1.01, 1.49, 25000), rng.uniform(2.01, 2.49, 25000), rng.uniform(0.01, 0.49, 25000)], 1)
+    xyz = dense.astype(np.float32)
+    L = lib_grid(spec)
+    align.align_set_reference(L, xyz)
+    etas = np.zeros((3, 6))
+    first, _, _ = align.align_eval_mi(L, xyz, eta6=etas)
+    for _ in range(20):
+        mi, _, _ = align.align_eval_mi(L, xyz, eta6=etas)
+        assert np.array_equal(mi, first)
+    st = align.align_eval_stats(L)
+    assert st["wide_voxels"] >= 1 and st["passes"] <= 2
