@@ -17,6 +17,7 @@ enum : uint32_t {
   kErrDzBound = 1u,       // |dz| above the bound the 32-bit sums were sized for
   kErrWaitTimeout = 2u,   // a bounded mbarrier wait gave up
   kErrPassLimit = 4u,     // key partitioning could not make the table fit
+  kErrLattice = 8u,       // a device-built lattice level found its previous argmax out of range
 };
 
 // Grid constants passed by value to every kernel (Sec. III-A grid + feature definition).
@@ -129,6 +130,28 @@ struct EvalKernels {
 constexpr int kEvalShapes = 3;
 // 0: 1024 threads x 1 point, one CTA per SM; 1: 1024 x 2; 2: 512 x 1, two CTAs per SM.
 const EvalKernels& eval_shape(int i);
+
+// One level of a lattice search built on the device (lattice.cu).  Centre: c_prev, moved
+// to the previous level's argmax sample when am_prev is set (else c_prev itself).  Pose p:
+// rotation cand[opt][p / n_trans] (opt = the previous argmax's rotation sample, 0 without
+// one), translation t' = fp32(centre_t + offset_t - origin_t) in FP64.
+struct LatticeLevel {
+  double r[6];              // this level's ranges
+  double r_prev[6];         // the previous level's ranges
+  int32_t m[6];             // samples per pose component (tx, ty, tz, rx, ry, rz; the same every level)
+  float origin[3];
+  int32_t n_rot;            // rotation samples m[3] * m[4] * m[5]
+  int32_t P;                // poses per level
+  const double* c_prev;     // 6: the previous level's centre (or the initial centre)
+  const int64_t* am_prev;   // the previous level's argmax (nullptr at level 0)
+  const float* cand;        // rotations: (options) x n_rot x 9
+  double* c_out;            // 6: this level's centre
+  float* poses;             // P x 12
+  int32_t* pose_src;        // P: rotation sample of each pose (its pre-rotated copy)
+  float* rots;              // n_rot x 9
+  uint32_t* err;            // error bits
+};
+cudaError_t launch_lattice_level(const LatticeLevel& L, cudaStream_t s);
 
 cudaError_t launch_ref_accumulate(const GridConst& gc, const float* xyz, int64_t n, const float* pose12,
                                   uint32_t* cnt, unsigned long long* s1, unsigned long long* s2,

@@ -267,10 +267,48 @@ struct EvalOut {
   int64_t* dump;      // device or null
 };
 
+// Whether a batch of P poses with n_rot distinct rotations gets one pre-rotated tile copy
+// per rotation (else one raw copy, rotated per pose by the kernel).
+int max_rotation_copies(int64_t P, int32_t n_tiles) {
+  const EvalKernels& ek = eval_shape(0);
+  const int64_t n_pad = (int64_t)n_tiles * ek.tile_points();
+  const int max_groups = (int)std::max<int64_t>(1, P / 4);
+  const size_t budget = (size_t)512 << 20;
+  const int cap_mem = (int)std::max<int64_t>(0, (int64_t)(budget / ((size_t)n_pad * 16)));
+  return std::min(max_groups, cap_mem);
+}
+
+align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_poses, int64_t P, bool rotate,
+                               int n_rot, const EvalOut& out);
+
 // Enqueue pack + eval + redo + compose + argmax for poses already on the device.
 // h_poses (may be NULL): the same poses on the host, used to find shared rotations.
 align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, const float* h_poses, int64_t P,
                           const EvalOut& out) {
+  bool rotate = true;
+  int n_rot = 0;
+  if (h_poses != nullptr) {
+    std::vector<float> rots;
+    std::vector<int32_t> idx;
+    const int groups = group_rotations(h_poses, P, rots, idx, max_rotation_copies(P, n_tiles));
+    if (groups > 0) {
+      CU(g->rots.ensure(rots.size() * 4), "allocate rotations");
+      CU(cudaMemcpyAsync(g->rots.p, rots.data(), rots.size() * 4, cudaMemcpyHostToDevice, g->stream),
+         "copy rotations");
+      CU(g->pose_src.ensure((size_t)P * 4), "allocate pose sources");
+      CU(cudaMemcpyAsync(g->pose_src.p, idx.data(), (size_t)P * 4, cudaMemcpyHostToDevice, g->stream),
+         "copy pose sources");
+      rotate = false;
+      n_rot = groups;
+    }
+  }
+  return enqueue_eval_core(g, n_tiles, d_poses, P, rotate, n_rot, out);
+}
+
+// The launches of one evaluation.  Unless `rotate`, g->rots holds n_rot rotations and
+// g->pose_src each pose's rotation (on the device, in stream order).
+align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_poses, int64_t P, bool rotate,
+                               int n_rot, const EvalOut& out) {
   const int K = g->gc.K;
   const size_t KK = (size_t)K * K;
   CU(g->out_c.ensure((size_t)P * KK * sizeof(uint32_t)), "allocate histograms");
@@ -293,26 +331,6 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
   // distinct rotation (the kernel then only translates).
   const EvalKernels& ek = eval_shape(0);
   const int64_t n_pad = (int64_t)n_tiles * ek.tile_points();
-  bool rotate = true;
-  int n_rot = 0;
-  if (h_poses != nullptr) {
-    const int max_groups = (int)std::max<int64_t>(1, P / 4);
-    const size_t budget = (size_t)512 << 20;
-    const int cap_mem = (int)std::max<int64_t>(0, (int64_t)(budget / ((size_t)n_pad * 16)));
-    std::vector<float> rots;
-    std::vector<int32_t> idx;
-    const int groups = group_rotations(h_poses, P, rots, idx, std::min(max_groups, cap_mem));
-    if (groups > 0) {
-      CU(g->rots.ensure(rots.size() * 4), "allocate rotations");
-      CU(cudaMemcpyAsync(g->rots.p, rots.data(), rots.size() * 4, cudaMemcpyHostToDevice, g->stream),
-         "copy rotations");
-      CU(g->pose_src.ensure((size_t)P * 4), "allocate pose sources");
-      CU(cudaMemcpyAsync(g->pose_src.p, idx.data(), (size_t)P * 4, cudaMemcpyHostToDevice, g->stream),
-         "copy pose sources");
-      rotate = false;
-      n_rot = groups;
-    }
-  }
   CU(g->pts4.ensure((size_t)std::max(n_rot, 1) * (size_t)n_pad * 16), "allocate tiles");
   CU(ek.launch_pack_points(g->xyz.as<float>(), g->n_points, n_pad, rotate ? nullptr : g->rots.as<float>(), n_rot,
                         g->pts4.as<float4>(), g->stream),
@@ -423,6 +441,162 @@ align_status collect_status(align_grid* g) {
   if (vals[0] & kErrWaitTimeout) return fail(ALIGN_E_TIMEOUT, "a bounded device wait gave up");
   if (vals[0] & kErrDzBound) return fail(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");
   if (vals[0] & kErrPassLimit) return fail(ALIGN_E_INTERNAL, "key partitioning limit reached");
+  if (vals[0] & kErrLattice) return fail(ALIGN_E_INTERNAL, "a lattice level found its argmax out of range");
+  return ALIGN_OK;
+}
+
+// Largest rotation table (rotation samples squared) of a search whose levels are built on
+// the device; larger rotation lattices take the synchronous path.
+constexpr int64_t kMaxLatticeCand = 16384;
+
+// Centre of the next level: the sample `am` of the lattice around c with ranges r (the same
+// FP64 operations as build_lattice).
+void lattice_sample(const double c[6], const double r[6], const int32_t m[6], int64_t am, double out[6]) {
+  int64_t rem = am;
+  int32_t i[6];
+  i[2] = (int32_t)(rem % m[2]); rem /= m[2];
+  i[1] = (int32_t)(rem % m[1]); rem /= m[1];
+  i[0] = (int32_t)(rem % m[0]); rem /= m[0];
+  i[5] = (int32_t)(rem % m[5]); rem /= m[5];
+  i[4] = (int32_t)(rem % m[4]); rem /= m[4];
+  i[3] = (int32_t)rem;
+  for (int a = 0; a < 6; ++a) out[a] = c[a] + lattice_step(r[a], m[a], i[a]);
+}
+
+// Rotation sample jr of a lattice around rotation centre c (components 3..5), as angles.
+void rotation_sample(const double c[6], const double r[6], const int32_t m[6], int32_t jr, double eta[6]) {
+  const int32_t irz = jr % m[5], iry = (jr / m[5]) % m[4], irx = jr / (m[5] * m[4]);
+  eta[0] = eta[1] = eta[2] = 0.0;
+  eta[3] = c[3] + lattice_step(r[3], m[3], irx);
+  eta[4] = c[4] + lattice_step(r[4], m[4], iry);
+  eta[5] = c[5] + lattice_step(r[5], m[5], irz);
+}
+
+// Coarse-to-fine lattice search with every level built on the device from the previous
+// level's argmax (lattice.cu), so that the levels follow each other on the stream.  Only
+// the rotations need the host (FP64 cos/sin, as every other pose rounding): for level l it
+// prepares the rotation of every (rotation sample of level l-1, rotation sample of level l)
+// pair, which needs level l-1's centre, i.e. level l-2's argmax.  The host therefore waits
+// for level l-2 while level l-1 runs, and the device always has the next level queued.
+// Results are identical to the level-by-level search: the same poses, bit for bit.
+align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6], const double r0[6],
+                              const int32_t m[6], int64_t P, int32_t n_rot, int32_t levels, double T_out[6],
+                              float* mi_out, int64_t* level_best) {
+  const int64_t n_trans = P / n_rot;
+  const size_t slot = (size_t)n_rot * n_rot * 9;  // floats of one level's rotation table
+  struct Rec {
+    int64_t am;
+    unsigned long long best;
+    uint32_t max_passes;
+    uint32_t pad;
+  };
+  CU(g->lat_c.ensure((size_t)(levels + 1) * 6 * sizeof(double)), "allocate lattice centres");
+  CU(g->lat_cand.ensure(2 * slot * sizeof(float)), "allocate rotation tables");
+  CU(g->poses.ensure((size_t)P * 48), "allocate poses");
+  CU(g->rots.ensure((size_t)n_rot * 36), "allocate rotations");
+  CU(g->pose_src.ensure((size_t)P * 4), "allocate pose sources");
+  CU(g->mi.ensure((size_t)P * 4), "allocate MI");
+  CU(g->argmax.ensure(8), "allocate argmax");
+  CU(g->lat_cand_h.ensure(2 * slot * sizeof(float)), "allocate pinned rotation tables");
+  CU(g->lat_rec_h.ensure((size_t)levels * sizeof(Rec)), "allocate pinned read-back");
+  CU(g->lat_c_h.ensure(6 * sizeof(double)), "allocate pinned centre");
+  while ((int32_t)g->lat_ev.size() < levels) {
+    cudaEvent_t e;
+    CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
+    g->lat_ev.push_back(e);
+  }
+  // the previous search's copies out of the pinned buffers must be done before they change
+  CU(cudaStreamSynchronize(g->stream), "synchronize");
+  Rec* rec = g->lat_rec_h.as<Rec>();
+  std::vector<std::array<double, 6>> c((size_t)levels + 1), r((size_t)levels);
+  for (int a = 0; a < 6; ++a) c[0][a] = c0[a], r[0][a] = r0[a];
+  for (int32_t l = 1; l < levels; ++l)
+    for (int a = 0; a < 6; ++a) r[(size_t)l][a] = r[(size_t)l - 1][a] * 0.5;
+  std::memcpy(g->lat_c_h.p, c0, 6 * sizeof(double));
+  CU(cudaMemcpyAsync(g->lat_c.p, g->lat_c_h.p, 6 * sizeof(double), cudaMemcpyHostToDevice, g->stream),
+     "copy centre");
+  double* d_c = g->lat_c.as<double>();
+  uint32_t passes_used = 0;
+  for (int32_t l = 0; l < levels; ++l) {
+    if (l >= 2) {  // level l-1's centre, from level l-2's argmax
+      CU(cudaEventSynchronize(g->lat_ev[(size_t)l - 2]), "wait for a lattice level");
+      const Rec& q = rec[l - 2];
+      if (q.am < 0 || q.am >= P) return fail(ALIGN_E_INTERNAL, "argmax out of range");
+      lattice_sample(c[(size_t)l - 2].data(), r[(size_t)l - 2].data(), m, q.am, c[(size_t)l - 1].data());
+      passes_used = std::max(passes_used, q.max_passes);
+      if (q.max_passes > (uint32_t)g->passes_seed[0] && q.max_passes <= (1u << 16) &&
+          (q.max_passes & (q.max_passes - 1)) == 0)
+        g->passes_seed[0] = (int32_t)q.max_passes;
+    }
+    // rotation table of level l: options = rotation samples of level l-1 (one at level 0)
+    float* tab = g->lat_cand_h.as<float>() + (size_t)(l % 2) * slot;
+    const int32_t n_opt = l == 0 ? 1 : n_rot;
+    for (int32_t opt = 0; opt < n_opt; ++opt) {
+      double centre[6];
+      if (l == 0) {
+        std::memcpy(centre, c[0].data(), sizeof(centre));
+      } else {
+        rotation_sample(c[(size_t)l - 1].data(), r[(size_t)l - 1].data(), m, opt, centre);
+      }
+      for (int32_t jr = 0; jr < n_rot; ++jr) {
+        double eta[6];
+        float p12[12];
+        rotation_sample(centre, r[(size_t)l].data(), m, jr, eta);
+        pose_to_fp32(g->origin, eta, p12);
+        std::memcpy(tab + ((size_t)opt * n_rot + jr) * 9, p12, 9 * sizeof(float));
+      }
+    }
+    float* d_tab = g->lat_cand.as<float>() + (size_t)(l % 2) * slot;
+    CU(cudaMemcpyAsync(d_tab, tab, (size_t)n_opt * n_rot * 36, cudaMemcpyHostToDevice, g->stream),
+       "copy rotation table");
+    LatticeLevel L{};
+    for (int a = 0; a < 6; ++a) {
+      L.r[a] = r[(size_t)l][a];
+      L.r_prev[a] = l > 0 ? r[(size_t)l - 1][a] : 0.0;
+      L.m[a] = m[a];
+    }
+    for (int a = 0; a < 3; ++a) L.origin[a] = g->origin[a];
+    L.n_rot = n_rot;
+    L.P = (int32_t)P;
+    L.c_prev = d_c + 6 * (size_t)l;
+    L.am_prev = l > 0 ? g->argmax.as<int64_t>() : nullptr;
+    L.cand = d_tab;
+    L.c_out = d_c + 6 * ((size_t)l + 1);
+    L.poses = g->poses.as<float>();
+    L.pose_src = g->pose_src.as<int32_t>();
+    L.rots = g->rots.as<float>();
+    L.err = g->err.as<uint32_t>();
+    CU(launch_lattice_level(L, g->stream), "launch lattice level");
+    EvalOut o{};
+    o.mi = g->mi.as<float>();
+    o.argmax = g->argmax.as<int64_t>();
+    align_status st = enqueue_eval_core(g, n_tiles, g->poses.as<float>(), P, false, n_rot, o);
+    if (st != ALIGN_OK) return st;
+    CU(cudaMemcpyAsync(&rec[l].am, g->argmax.p, 8, cudaMemcpyDeviceToHost, g->stream), "read argmax");
+    CU(cudaMemcpyAsync(&rec[l].best, g->best.p, 8, cudaMemcpyDeviceToHost, g->stream), "read best");
+    CU(cudaMemcpyAsync(&rec[l].max_passes, g->max_passes.p, 4, cudaMemcpyDeviceToHost, g->stream),
+       "read counters");
+    CU(cudaMemsetAsync(g->max_passes.p, 0, 4, g->stream), "reset counters");
+    CU(cudaEventRecord(g->lat_ev[(size_t)l], g->stream), "record event");
+  }
+  align_status st = collect_status(g);  // synchronises the stream
+  if (st != ALIGN_OK) return st;
+  for (int32_t l = std::max(0, levels - 2); l < levels; ++l) {
+    if (rec[l].am < 0 || rec[l].am >= P) return fail(ALIGN_E_INTERNAL, "argmax out of range");
+    lattice_sample(c[(size_t)l].data(), r[(size_t)l].data(), m, rec[l].am, c[(size_t)l + 1].data());
+  }
+  for (int32_t l = 0; l < levels; ++l) {
+    passes_used = std::max(passes_used, rec[l].max_passes);
+    if (level_best) level_best[l] = rec[l].am;
+  }
+  g->stats[0] = passes_used;
+  std::memcpy(T_out, c[(size_t)levels].data(), 6 * sizeof(double));
+  if (mi_out) {  // the MI of the last level's argmax, from its packed running maximum
+    const uint32_t ord = (uint32_t)(rec[levels - 1].best >> 32);
+    const uint32_t u = (ord & 0x80000000u) ? (ord & 0x7FFFFFFFu) : ~ord;
+    std::memcpy(mi_out, &u, 4);
+  }
+  (void)n_trans;
   return ALIGN_OK;
 }
 
@@ -473,8 +647,11 @@ align_status align_destroy_grid(align_grid* g) {
   cudaStreamSynchronize(g->stream);
   for (DevBuf* b : {&g->symA, &g->sat, &g->xyz, &g->poses, &g->out_c, &g->out_box, &g->mi, &g->hist, &g->best,
                     &g->argmax, &g->err, &g->max_passes, &g->wide_count, &g->wide, &g->dump, &g->pts4,
-                    &g->pose_src, &g->rots, &g->redo_list, &g->redo_count, &g->items, &g->ovf})
+                    &g->pose_src, &g->rots, &g->redo_list, &g->redo_count, &g->items, &g->ovf, &g->lat_c,
+                    &g->lat_cand})
     b->release();
+  for (HostBuf* b : {&g->lat_cand_h, &g->lat_rec_h, &g->lat_c_h}) b->release();
+  for (cudaEvent_t e : g->lat_ev) cudaEventDestroy(e);
   for (auto* v : {&g->ev_pending, &g->ev_pool})
     for (auto& evs : *v)
       for (cudaEvent_t e : evs) cudaEventDestroy(e);
@@ -710,6 +887,9 @@ align_status align_search_ex(align_grid* g, const float* xyzB, int64_t nB, int f
   double c[6], r[6];
   std::memcpy(c, init, sizeof(c));
   std::memcpy(r, range, sizeof(r));
+  const int32_t n_rot = counts[3] * counts[4] * counts[5];
+  if (levels >= 1 && (int64_t)n_rot * n_rot <= kMaxLatticeCand && n_rot <= max_rotation_copies(P, n_tiles))
+    return search_pipelined(g, n_tiles, c, r, counts, P, n_rot, levels, T_out, mi_out, level_best);
   std::vector<double> eta;
   std::vector<float> poses;
   float best_mi = 0.0f;

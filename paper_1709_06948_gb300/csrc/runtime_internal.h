@@ -38,6 +38,31 @@ struct DevBuf {
   }
 };
 
+// A growable page-locked host allocation (asynchronous copies from and to it).
+struct HostBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p != nullptr) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMallocHost(&p, want);
+    if (e == cudaSuccess) cap = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
 // Error reporting into the thread-local message of align_last_error.
 align_status report_errorf(align_status st, const char* fmt, ...);
 // Distinct rotations (bitwise-equal 3x3 blocks) of a host pose batch and each pose's
@@ -69,6 +94,10 @@ struct align_grid {
   // evaluation workspace
   mialign::DevBuf xyz, poses, out_c, out_box, mi, hist, best, argmax, err, max_passes, wide_count, wide, dump;
   mialign::DevBuf pts4, pose_src, rots, redo_list, redo_count, items, ovf;
+  // device-built lattice levels (align_search_ex): centres, rotation tables, read-backs
+  mialign::DevBuf lat_c, lat_cand;
+  mialign::HostBuf lat_cand_h, lat_rec_h, lat_c_h;
+  std::vector<cudaEvent_t> lat_ev;
   int64_t n_points = 0;  // points staged in `xyz`
   // key partitions the next launch starts with, per kernel shape (its table size)
   int32_t passes_seed[mialign::kEvalShapes] = {1, 1, 1};

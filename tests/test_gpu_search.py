@@ -53,3 +53,18 @@ def test_search_default_counts_runs():
     align.align_set_reference(L, pair.xyzA)
     T, mi, _ = align.align_search(L, pair.xyzB, np.zeros(6), [1, 1, 0.5, 0.04, 0.04, 0.09], levels=2)
     assert np.all(np.isfinite(T)) and mi > 0
+
+
+@pytest.mark.parametrize("counts,levels", [((3, 3, 3, 3, 3, 3), 1), ((3, 3, 3, 3, 3, 3), 2),
+                                           ((2, 2, 2, 4, 4, 4), 5), ((2, 3, 1, 1, 5, 3), 3),
+                                           ((1, 1, 1, 12, 12, 1), 2)])
+def test_search_schedules_match_oracle(counts, levels):
+    """Levels built on the device (small rotation lattices) and level by level on the host
+    (a 144-rotation lattice) give the oracle's choices at every level."""
+    T_true = np.array([-0.4, 0.5, -0.1, math.radians(-1.0), math.radians(2.0), math.radians(-4.0)])
+    pair = scangen.tiny_pair(T=T_true)
+    rng = np.array([1.0, 1.0, 0.5, math.radians(2.5), math.radians(2.5), math.radians(5.0)])
+    T, mi, lb, To, mio, lbo = _both(pair, np.array([0.1, -0.1, 0.0, 0.0, 0.01, -0.02]), rng, counts, levels)
+    assert lb.tolist() == lbo.tolist()
+    assert T.tolist() == To.tolist()
+    assert abs(mi - mio) <= 1e-5
