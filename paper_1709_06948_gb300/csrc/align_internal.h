@@ -31,6 +31,10 @@ struct GridConst {
   int32_t dz_bound;       // |dz| <= dz_bound for every in-grid point
   int32_t dz_shift;       // smallest m with 2^m > 2 * dz_bound (the sweep checks dz + dz_bound < 2^m)
   uint32_t nlim;          // largest n whose S1, S2 fit the 32-bit table sums for |dz| < 2^m - dz_bound
+  uint32_t nlim_pack;     // largest n of the packed word n * 2^ns + sum(dz + dz_bound) (and of S2)
+  int32_t ns_shift;       // ns, the shift of n in the packed word
+  int32_t wide_shift;     // ns + b, b the largest with 2^(b+1) - 2 <= nlim_pack: two n fields
+                          // below 2^b sum to at most nlim_pack
   int32_t boxA[6];        // A's occupied bbox (xmin > xmax when empty)
   uint64_t div_x, div_y;  // floor((2^64 - 1) / X) + 1 (0 when X == 1): k / X = umulhi64(div_x, k) for k < 2^32
   uint32_t count_thresh[kMaxLevels];
@@ -108,15 +112,16 @@ struct EvalKernels {
   int (*tile_points)();
   int (*ovf_cap)();  // overflow-list entries per CTA (EvalArgs::ovf holds CTAs x this many)
   int (*min_tiles)();
-  size_t (*smem_bytes)(int K, int table_slots);
-  int (*table_slots_for)(int K, size_t smem_budget);
+  // vw: table value words per slot (eval_layout)
+  size_t (*smem_bytes)(int K, int table_slots, int vw);
+  int (*table_slots_for)(int K, int vw, size_t smem_budget);
   // Raise the kernels' dynamic shared-memory limit on the current device (once per device,
   // before any launch or stream capture).
   cudaError_t (*setup)();
-  // var: accumulate z sums; rotate: tiles hold raw xyz (the kernel applies each pose's
-  // rotation) instead of pre-rotated copies.  Launches the eval and redo kernels.  A launch
-  // with item_start == nullptr is a single-item launch (its item is read from `one`).
-  cudaError_t (*launch_eval)(const EvalArgs& a, int n_ctas, bool var, bool rotate, cudaStream_t s);
+  // vw: table layout (eval_layout); rotate: tiles hold raw xyz (the kernel applies each
+  // pose's rotation) instead of pre-rotated copies.  Launches the eval and redo kernels.  A
+  // launch with item_start == nullptr is a single-item launch (its item is read from `one`).
+  cudaError_t (*launch_eval)(const EvalArgs& a, int n_ctas, int vw, bool rotate, cudaStream_t s);
   // xyz (n x 3 fp32) -> n_out float4 with NaN padding; with rots (n_rot x 9), one
   // pre-rotated copy u = R p per rotation (same FMA order as the voxel map).
   cudaError_t (*launch_pack_points)(const float* xyz, int64_t n, int64_t n_out, const float* rots, int n_rot,
@@ -128,6 +133,14 @@ struct EvalKernels {
   cudaError_t (*launch_argmax_finalize)(const EvalItem* items, int n_items, cudaStream_t s);
 };
 constexpr int kEvalShapes = 3;
+// Table value words per slot for a launch over grids with constants gc: 1 without z sums
+// (count feature), 2 (n and the biased z sum packed in one word, then S2) when the packed
+// word holds at least kPackMinN points per voxel, else 3 (n, S1, S2).
+constexpr uint32_t kPackMinN = 2000;
+inline int eval_layout(const GridConst& gc, bool var) {
+  if (!var) return 1;
+  return gc.nlim_pack >= kPackMinN ? 2 : 3;
+}
 // 0: 1024 threads x 1 point, one CTA per SM; 1: 1024 x 2; 2: 512 x 1, two CTAs per SM.
 const EvalKernels& eval_shape(int i);
 

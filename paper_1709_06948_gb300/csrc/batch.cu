@@ -151,7 +151,8 @@ struct Launch {
   int shape = 0;
   EvalArgs a{};
   int n_ctas = 0;
-  bool var = false, rotate = false;
+  int vw = 1;  // table value words per slot (eval_layout)
+  bool rotate = false;
   int n_items = 0;
   int n_copies = 0;
   int64_t max_out = 0;
@@ -164,7 +165,7 @@ align_status enqueue_launch(align_batch* b, const Launch& L) {
   BCU(cudaMemsetAsync(b->ipasses.p, 0, (size_t)L.n_items * 4, s), "clear partition counts");
   BCU(cudaMemsetAsync(b->redo_count.p, 0, 4, s), "clear redo count");
   BCU(L.ek->launch_pack_batch(b->copies.as<PackCopy>(), L.n_copies, L.max_out, s), "launch pack");
-  BCU(L.ek->launch_eval(L.a, L.n_ctas, L.var, L.rotate, s), "launch eval kernel");
+  BCU(L.ek->launch_eval(L.a, L.n_ctas, L.vw, L.rotate, s), "launch eval kernel");
   BCU(L.ek->launch_compose(L.a, s), "launch compose kernel");
   BCU(L.ek->launch_argmax_finalize(L.a.items, L.n_items, s), "launch argmax");
   return ALIGN_OK;
@@ -351,7 +352,9 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   }
   if (poses_n >= INT32_MAX) return report_error(ALIGN_E_INVALID, "too many poses in one batch");
   if (n_copies > 65535) return report_error(ALIGN_E_INVALID, "too many tile copies in one batch");
-  const int T = ek.table_slots_for(maxK, b->smem_optin);
+  int vw = 1;  // table layout of the launch: the widest any pair needs
+  for (const PairPlan& pp : plans) vw = std::max(vw, eval_layout(pp.g->gc, var));
+  const int T = ek.table_slots_for(maxK, vw, b->smem_optin);
   const int n_ctas = b->n_sm * ek.ctas_per_sm;
   // ---- workspace ----
   align_status st;
@@ -459,7 +462,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   L.ek = &ek;
   L.shape = shape;
   L.n_ctas = n_ctas;
-  L.var = var;
+  L.vw = vw;
   L.rotate = rotate;
   L.n_items = n;
   L.n_copies = n_copies;
@@ -485,7 +488,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   b->last_grids.clear();
   for (const PairPlan& pp : plans) b->last_grids.push_back(pp.g);
   b->last_shape = shape;
-  const std::vector<int64_t> sig = {shape,   n,       rotate,     var,      a.passes0, T, n_ctas,
+  const std::vector<int64_t> sig = {shape,   n,       rotate,     vw,       a.passes0, T, n_ctas,
                                     poses_n, n_copies, max_out,   maxK,     (int64_t)(uintptr_t)b->pts.p,
                                     (int64_t)(uintptr_t)b->items.p};
   st = run_launch(b, L, (flags & ALIGN_BATCH_GRAPH) != 0, sig);

@@ -64,8 +64,8 @@ constexpr int kTile = kThreads * kPPT;  // points per tile
 constexpr int kDepth = MI_EVAL_DEPTH;   // tiles loaded ahead into registers
 constexpr int kMinTiles = 3;
 constexpr uint32_t kQueue = 64;         // finished runs buffered per warp (32 drained at a time)
-constexpr int kProbeBuckets = 64;       // probe budget per key (buckets of 4 slots)
-constexpr int kOvfCap = 4096;           // overflow list entries per CTA
+constexpr int kProbeBuckets = 1024;     // probe budget per key (buckets of 4 slots)
+constexpr int kOvfCap = 16384;          // overflow list entries per CTA
 constexpr int kMaxPasses = 1 << 16;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr int kGcWords = (int)(sizeof(GridConst) / 4);
@@ -166,14 +166,25 @@ __device__ __forceinline__ uint32_t lane_mask_lt() {
   return m;
 }
 
-// Layout: per-warp rings | flags (16 B) | table keys (T x 4 B) | table values (T x 12 B:
-// n, S1, S2) | histogram | grid constants | bbox | current item.  The flags sit just below
-// the keys so that the hot loop reaches them at a fixed offset from the key base.
+// Layout: per-warp rings | flags (16 B) | table keys (T x 4 B) | table values (T x kVW
+// words) | histogram | grid constants | bbox | current item.  The flags sit just below the
+// keys so that the hot loop reaches them at a fixed offset from the key base.
+//
+// Table values, kVW words per slot (chosen per launch, see eval_layout):
+//   1: n (no z sums: count feature);
+//   2: W = n * 2^ns + S1' and S2, where S1' = sum(dz + dz_bound) >= 0 is the biased z sum
+//      (S1 = S1' - n * dz_bound) and ns = GridConst::ns_shift.  While n <= nlim_pack the
+//      biased sum stays below 2^ns, so W holds both exactly; a voxel that may pass nlim_pack
+//      sends the pose to the exact path.  A third more slots than layout 3 in the same memory;
+//   3: n, S1 (two's complement), S2; a voxel above nlim (the 32-bit sums may have wrapped)
+//      sends the pose to the exact path.
+// The exact path (redo_kernel) keeps the plain count in word 0 and S1, S2 in 64-bit sums in
+// global memory.
 struct EvalSmem {
-  uint4* queue;       // per warp: kQueue finished runs (key, n, S1, S2)
+  uint4* queue;       // per warp: kQueue finished runs (key, and the run's value words), a ring
   uint32_t* flags;    // occupied count, table full, overflow entries, sums need the exact path
   uint32_t* tkey;
-  uint32_t* tval;     // 3 words per slot
+  uint32_t* tval;     // kVW words per slot
   uint32_t* hist;
   GridConst* gc;      // the current item's grid constants
   int32_t* box;       // 6
@@ -186,7 +197,7 @@ constexpr uint32_t kFlagFull = 12u;
 constexpr uint32_t kFlagOvf = 8u;        // entries in the CTA's overflow list
 constexpr uint32_t kFlagWide = 4u;
 
-__host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, uint8_t* base) {
+__host__ __device__ inline size_t eval_smem_layout(int K, int T, int vw, EvalSmem* s, uint8_t* base) {
   size_t off = 0;
   auto take = [&](size_t bytes, size_t align) {
     off = (off + align - 1) / align * align;
@@ -197,7 +208,7 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, ui
   size_t o_queue = take((size_t)kWarps * kQueue * 16, 16);
   size_t o_flags = take(16, 16);
   size_t o_key = take((size_t)T * 4, 16);
-  size_t o_vals = take((size_t)T * 12, 16);
+  size_t o_vals = take((size_t)T * 4 * vw, 16);
   size_t o_hist = take((size_t)round4(K * K) * 4, 16);
   size_t o_gc = take(sizeof(GridConst), 16);
   size_t o_box = take(6 * 4, 4);
@@ -227,11 +238,16 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, EvalSmem* s, ui
 struct VoxelConst {
   float inv_res;
   int X, Y, Z, res_mm, dz_bound;
-  uint32_t nlim;
+  uint32_t nlim;        // largest n per voxel of the layout's table sums
+  uint32_t winc;        // layout 2, per point: 2^ns + dz_bound (plus dz)
+  uint32_t wide_shift;  // layout 2: ns + b with 2^(b+1) - 2 <= nlim_pack (the drains' bound)
 };
 
+template <int kVW>
 __device__ __forceinline__ VoxelConst voxel_const(const GridConst& g) {
-  return VoxelConst{g.inv_res, g.X, g.Y, g.Z, g.res_mm, g.dz_bound, g.nlim};
+  const uint32_t nlim = kVW == 2 ? g.nlim_pack : kVW == 3 ? g.nlim : 0x7FFFFFFFu;
+  return VoxelConst{g.inv_res, g.X, g.Y, g.Z, g.res_mm, g.dz_bound, nlim,
+                    (1u << g.ns_shift) + (uint32_t)g.dz_bound, (uint32_t)g.wide_shift};
 }
 
 // Find or insert `key` in the open-addressing table: buckets of 4 key slots read with one
@@ -282,74 +298,85 @@ __device__ __noinline__ int table_slot_slow(uint32_t a_key, uint32_t key, uint32
   return -1;
 }
 
-// Add one finished run (key, n, S1, S2) to the table (fire-and-forget shared reductions).
-// A voxel whose count ends above nlim may have wrapped its 32-bit sums; the table scan
-// sends such a pose to the exact path.
-template <bool kVar>
-__device__ __forceinline__ void table_add_slot(const EvalSmem& S, const uint4& e, int slot) {
-  const uint32_t v = S.a_vals + 12u * (uint32_t)slot;
-  red_add(v, e.y);
-  if (kVar) {
+// Add one finished run (ring entry: key and the run's value words) to the table.  In the
+// packed layout the packed word is added with an atomic that returns the old value, so that
+// an add taking the voxel above nlim_pack flags the pose for the exact path.
+template <int kVW>
+__device__ __forceinline__ void table_add_slot(const EvalSmem& S, const uint4& e, int slot, const GridConst& gc) {
+  const uint32_t v = S.a_vals + 4u * kVW * (uint32_t)slot;
+  if (kVW == 2) {
+    const uint32_t ns = (uint32_t)gc.ns_shift;
+    const uint32_t old = atom_add(v, e.y);
+    if ((old >> ns) + (e.y >> ns) > gc.nlim_pack) sts32(S.a_key - kFlagWide, 1u);
     red_add(v + 4u, e.z);
-    red_add(v + 8u, e.w);
+  } else {
+    red_add(v, e.y);
+    if (kVW == 3) {
+      red_add(v + 4u, e.z);
+      red_add(v + 8u, e.w);
+    }
   }
 }
 
 // After a sweep: insert the overflow list with the full probe (all threads of the CTA).
-template <bool kVar>
-__device__ __forceinline__ void insert_overflow(const EvalSmem& S, const EvalArgs& a) {
+template <int kVW>
+__device__ __forceinline__ void insert_overflow(const EvalSmem& S, const EvalArgs& a, const GridConst& gc) {
   const uint32_t n = min(*(volatile uint32_t*)&S.flags[2], (uint32_t)a.ovf_cap);
   const uint4* ovf = a.ovf + (size_t)blockIdx.x * (uint32_t)a.ovf_cap;
   for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
     const uint4 e = ovf[i];
     const int slot = table_slot(S, e.x, (uint32_t)a.n_buckets);
     if (slot < 0) sts32(S.a_key - kFlagFull, 1u);
-    else table_add_slot<kVar>(S, e, slot);
+    else table_add_slot<kVW>(S, e, slot, gc);
   }
 }
 
-// Exact path (redo_kernel): add one run, with 64-bit side sums for voxels beyond nlim.
-template <bool kVar>
-__device__ __forceinline__ void add_run(const EvalSmem& S, const VoxelConst& vc, unsigned long long* wide, uint32_t key,
-                                        uint32_t n, int s1, uint32_t s2, uint32_t nb) {
+// Exact path (redo_kernel): add one run; the table keeps the plain count, S1 and S2 go to
+// the CTA's 64-bit sums in global memory.
+template <int kVW>
+__device__ __forceinline__ void add_run(const EvalSmem& S, unsigned long long* wide, uint32_t key, uint32_t n,
+                                        int s1, uint32_t s2, uint32_t nb) {
   if (lds32(S.a_key - kFlagFull)) return;  // table already full: the pose restarts
   const int slot = table_slot(S, key, nb);
   if (slot < 0) {
     sts32(S.a_key - kFlagFull, 1u);
     return;
   }
-  const uint32_t v = S.a_vals + 12u * (uint32_t)slot;
-  if (kVar) {
-    const uint32_t old = atom_add(v, n);
-    if (old + n <= vc.nlim) {
-      red_add(v + 4u, (uint32_t)s1);
-      red_add(v + 8u, s2);
-    } else {
-      atomicAdd(&wide[2 * slot], (unsigned long long)(long long)s1);
-      atomicAdd(&wide[2 * slot + 1], (unsigned long long)s2);
-    }
-  } else {
-    red_add(v, n);
+  red_add(S.a_vals + 4u * kVW * (uint32_t)slot, n);
+  if (kVW > 1) {
+    atomicAdd(&wide[2 * slot], (unsigned long long)(long long)s1);
+    atomicAdd(&wide[2 * slot + 1], (unsigned long long)s2);
   }
 }
 
-// The run of equal keys a thread is walking.  Points outside the grid (or outside the
-// current key partition) carry kEmptyKey and form runs of their own, which are dropped.
+// The run of equal keys a thread is walking: w is the packed word (layout 2) or n, s1 and
+// s2 the z sums (s1 only in layout 3).  Points outside the grid (or outside the current key
+// partition) carry kEmptyKey and form runs of their own, which are dropped.
 struct Run {
   uint32_t key;
-  uint32_t n;
+  uint32_t w;
   uint32_t s1;  // two's complement
   uint32_t s2;
 };
+
+// The ring entry of a run: key, then the table's value words.
+template <int kVW>
+__device__ __forceinline__ uint4 run_entry(const Run& r) {
+  return kVW == 3 ? make_uint4(r.key, r.w, r.s1, r.s2) : make_uint4(r.key, r.w, r.s2, 0u);
+}
 
 // Per-warp ring of finished runs in shared memory: lanes append what they finished at
 // this step (compacted by a ballot); once 32 are waiting the whole warp adds entries
 // 0..31 to the table and moves the rest down, so the ring never wraps.  The insert is
 // written with predicated shared-memory operations so that the drain is one straight
-// sequence; only a run whose home bucket is full branches off to the overflow list.
-template <bool kVar>
+// sequence; a run whose home bucket is full goes to the overflow list.
+//
+// Packed-word bound: `acc` ORs every old table word and every run word the lane added.
+// While no n field in it reaches 2^b (2^(b+1) - 2 <= nlim), every add kept the voxel at or
+// below nlim; the sweep's end tests acc once (the exact path takes the pose otherwise).
+template <int kVW>
 __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count,
-                                           const EvalArgs& a) {
+                                           const EvalArgs& a, uint32_t& acc) {
   const uint32_t lane = threadIdx.x & 31u;
   __syncwarp();
   uint4 e = lds128(ring + 16u * lane);  // the ring holds 64 entries: always in bounds
@@ -364,11 +391,17 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
   const uint32_t old = atom_cas_if(ins, kb + 4u * (uint32_t)f, kEmptyKey, e.x);
   if (ins && (old == kEmptyKey || old == e.x)) slot = f;
   const bool ok = valid && slot >= 0;
-  const uint32_t v = S.a_vals + 12u * (4u * b + (uint32_t)slot);
-  red_add_if(ok, v, e.y);
-  if (kVar) {
+  const uint32_t v = S.a_vals + 4u * kVW * (4u * b + (uint32_t)slot);
+  if (kVW == 2) {
+    const uint32_t old = atom_add_if(ok, v, e.y);
+    acc |= ok ? (old | e.y) : 0u;
     red_add_if(ok, v + 4u, e.z);
-    red_add_if(ok, v + 8u, e.w);
+  } else {
+    red_add_if(ok, v, e.y);
+    if (kVW == 3) {
+      red_add_if(ok, v + 4u, e.z);
+      red_add_if(ok, v + 8u, e.w);
+    }
   }
   // home bucket full (or insert race lost): the run goes to the overflow list
   const bool ov = valid && slot < 0;
@@ -387,14 +420,14 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
 }
 
 // Append the finished runs of the lanes with `done` set, then drain if 32 are waiting.
-template <bool kVar>
+template <int kVW>
 __device__ __forceinline__ void ring_push(const EvalSmem& S, uint32_t ring, uint32_t lane_lt, bool done,
-                                          const Run& r, uint32_t& fill, const EvalArgs& a) {
+                                          const Run& r, uint32_t& fill, const EvalArgs& a, uint32_t& acc) {
   const uint32_t m = __ballot_sync(kFull, done);
-  sts128_if(done, ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), make_uint4(r.key, r.n, r.s1, r.s2));
+  sts128_if(done, ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), run_entry<kVW>(r));
   fill += (uint32_t)__popc(m);
   // fill is the same in every lane; the vote lets the compiler know the branch is uniform
-  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVar>(S, ring, fill, 32u, a);
+  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVW>(S, ring, fill, 32u, a, acc);
 }
 
 struct PoseRegs {
@@ -516,29 +549,38 @@ struct ScanBox {
 
 // One occupied slot: read and clear it, then (unless `discard`) its voxel's coordinates,
 // feature symbol and joint-histogram entry.
-template <bool kVar, bool kExact>
+template <int kVW, bool kExact>
 __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& gc, const EvalItem& I,
                                            unsigned long long* wide, uint32_t* wide_count, uint32_t s, int lp,
                                            bool discard, ScanBox& bx) {
   const uint32_t k = lds32(S.a_key + 4u * s);
   // A's symbol of the voxel, requested first: its L2 latency overlaps the work below
   const int sA = discard ? 0 : (int)__ldg(I.symA + k);
-  const uint32_t v = S.a_vals + 12u * s;
-  const uint64_t n = lds32(v);
-  int64_t s1 = (int32_t)lds32(v + 4u);
-  uint64_t s2 = lds32(v + 8u);
-  if (!kExact && kVar && n > gc.nlim) sts32(S.a_key - kFlagWide, 1u);  // sums may have wrapped: exact path
-  if (kExact && kVar && n > gc.nlim) {
-    s1 += (int64_t)wide[2 * s];
-    s2 += wide[2 * s + 1];
-    wide[2 * s] = 0ull;
-    wide[2 * s + 1] = 0ull;
-    if (!discard) atomicAdd(wide_count, 1u);
+  const uint32_t v = S.a_vals + 4u * kVW * s;
+  const uint32_t w = lds32(v);
+  uint64_t n = w;
+  int64_t s1 = 0;
+  uint64_t s2 = 0;
+  if (kExact) {  // plain count in the table, S1 and S2 in the 64-bit sums
+    if (kVW > 1) {
+      s1 = (int64_t)wide[2 * s];
+      s2 = wide[2 * s + 1];
+      wide[2 * s] = 0ull;
+      wide[2 * s + 1] = 0ull;
+      if (!discard && n > gc.nlim) atomicAdd(wide_count, 1u);
+    }
+  } else if (kVW == 2) {  // packed: W = n * 2^ns + sum(dz + dz_bound)
+    n = w >> gc.ns_shift;
+    s1 = (int64_t)(w & ((1u << gc.ns_shift) - 1u)) - (int64_t)n * gc.dz_bound;
+    s2 = lds32(v + 4u);
+  } else if (kVW == 3) {
+    s1 = (int32_t)lds32(v + 4u);
+    s2 = lds32(v + 8u);
+    if (n > gc.nlim) sts32(S.a_key - kFlagWide, 1u);  // the sums may have wrapped: exact path
   }
   sts32(S.a_key + 4u * s, kEmptyKey);
-  sts32(v, 0u);
-  sts32(v + 4u, 0u);
-  sts32(v + 8u, 0u);
+#pragma unroll
+  for (int i = 0; i < kVW; ++i) sts32(v + 4u * i, 0u);
   if (discard) return;
   const uint32_t r = gc.div_x ? (uint32_t)__umul64hi(gc.div_x, k) : k;  // k / X
   const uint32_t q = gc.div_y ? (uint32_t)__umul64hi(gc.div_y, r) : r;  // r / Y
@@ -566,7 +608,7 @@ __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& g
 // Every warp scans a contiguous share of the slots and compacts the occupied ones into a
 // list (in its run ring, empty after the sweep), so that the per-voxel work runs with all
 // 32 lanes busy.  The CTA-wide occupied count is added to the occupied flag word.
-template <bool kVar, bool kExact>
+template <int kVW, bool kExact>
 __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& gc, const EvalItem& I,
                                            unsigned long long* wide, uint32_t* wide_count, int T, int lp,
                                            bool discard) {
@@ -586,7 +628,7 @@ __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& g
     occupied += (uint32_t)__popc(m);
     if (cnt >= 32u) {
       __syncwarp();
-      scan_entry<kVar, kExact>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
+      scan_entry<kVW, kExact>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
       // move the rest down (lane l reads entry l + 32 and writes entry l, which only it read)
       if ((uint32_t)lane + 32u < cnt) sts32(list + 4u * (uint32_t)lane, lds32(list + 4u * ((uint32_t)lane + 32u)));
       __syncwarp();
@@ -595,7 +637,7 @@ __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& g
   }
   __syncwarp();
   if ((uint32_t)lane < cnt)
-    scan_entry<kVar, kExact>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
+    scan_entry<kVW, kExact>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
   if (lane == 0 && occupied) red_add(S.a_key - kFlagOccupied, occupied);
   const int mn0 = __reduce_min_sync(kFull, bx.mn0), mn1 = __reduce_min_sync(kFull, bx.mn1);
   const int mn2 = __reduce_min_sync(kFull, bx.mn2), mx0 = __reduce_max_sync(kFull, bx.mx0);
@@ -606,13 +648,13 @@ __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& g
   }
 }
 
+template <int kVW>
 __device__ __forceinline__ void init_smem(const EvalSmem& S, int T, int KK) {
   const int tid = threadIdx.x;
   for (int i = tid; i < T; i += kThreads) {
     S.tkey[i] = kEmptyKey;
-    S.tval[3 * i] = 0u;
-    S.tval[3 * i + 1] = 0u;
-    S.tval[3 * i + 2] = 0u;
+#pragma unroll
+    for (int j = 0; j < kVW; ++j) S.tval[kVW * i + j] = 0u;
   }
   for (int i = tid; i < KK; i += kThreads) S.hist[i] = 0u;
   if (tid == 0) {
@@ -675,10 +717,11 @@ __device__ __forceinline__ const float4* pose_tiles(const EvalItem& I, int lp) {
 
 // One tile of this thread's stream: key, run step, ring append of the finished run.
 // `bad` collects dz + dz_bound of every in-grid point (checked against 2^dz_shift).
-template <bool kVar, bool kRot, bool kPart>
+template <int kVW, bool kRot, bool kPart>
 __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                            const PoseRegs& P, const float4* pts, int lg, uint32_t part, Run& run,
-                                           uint32_t ring, uint32_t lane_lt, uint32_t& fill, uint32_t& bad) {
+                                           uint32_t ring, uint32_t lane_lt, uint32_t& fill, uint32_t& bad,
+                                           uint32_t& acc) {
 #pragma unroll
   for (int j = 0; j < kPPT; ++j) {
     uint32_t key;
@@ -687,12 +730,14 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
     if (kPart && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != part) key = kEmptyKey;
     bad |= (uint32_t)(dz + vc.dz_bound);
     const bool done = key != run.key;
-    ring_push<kVar>(S, ring, lane_lt, done, run, fill, a);
-    run.n = (done ? 0u : run.n) + 1u;
-    if (kVar) {
-      run.s1 = (done ? 0u : run.s1) + (uint32_t)dz;
-      run.s2 = (done ? 0u : run.s2) + (uint32_t)(dz * dz);
+    ring_push<kVW>(S, ring, lane_lt, done, run, fill, a, acc);
+    if (kVW == 2) {
+      run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
+    } else {
+      run.w = (done ? 0u : run.w) + 1u;
+      if (kVW == 3) run.s1 = (done ? 0u : run.s1) + (uint32_t)dz;
     }
+    if (kVW > 1) run.s2 = (done ? 0u : run.s2) + (uint32_t)(dz * dz);
     run.key = key;
   }
 }
@@ -700,12 +745,12 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
 // One pass over all tiles of the pose: every thread streams its own points straight from
 // L2, kDepth tiles ahead.  A run is cut every `cut` tiles so that its 32-bit sums stay
 // below nlim points.  Returns the bad-dz flag.
-template <bool kVar, bool kRot, bool kPart>
+template <int kVW, bool kRot, bool kPart>
 __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                                const PoseRegs& P, const float4* src, int nt, int lg, uint32_t part,
                                                uint32_t ring, uint32_t lane_lt, int cut) {
   Run run{kEmptyKey, 0u, 0u, 0u};
-  uint32_t fill = 0u, bad = 0u;
+  uint32_t fill = 0u, bad = 0u, acc = 0u;
   float4 buf[kDepth][kPPT];  // register ring of the next kDepth tiles
 #pragma unroll
   for (int d = 0; d < kDepth; ++d)
@@ -714,48 +759,49 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs
   int t = 0;
   for (; t + 2 * kDepth <= nt; t += kDepth) {  // every prefetch in range: no guards
     if (t >= next_cut) {  // uniform; only when a stream is longer than nlim points
-      ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
+      ring_push<kVW>(S, ring, lane_lt, true, run, fill, a, acc);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
 #pragma unroll
     for (int d = 0; d < kDepth; ++d) {
-      sweep_tile<kVar, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad);
+      sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad, acc);
       load_tile(src, t + kDepth + d, buf[d]);
     }
   }
   for (; t < nt; t += kDepth) {
     if (t >= next_cut) {
-      ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
+      ring_push<kVW>(S, ring, lane_lt, true, run, fill, a, acc);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
 #pragma unroll
     for (int d = 0; d < kDepth; ++d) {
       if (t + d < nt) {
-        sweep_tile<kVar, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad);
+        sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad, acc);
         if (t + kDepth + d < nt) load_tile(src, t + kDepth + d, buf[d]);
       }
     }
   }
-  ring_push<kVar>(S, ring, lane_lt, true, run, fill, a);
-  while (fill > 0u) ring_drain<kVar>(S, ring, fill, min(fill, 32u), a);
+  ring_push<kVW>(S, ring, lane_lt, true, run, fill, a, acc);
+  while (fill > 0u) ring_drain<kVW>(S, ring, fill, min(fill, 32u), a, acc);
+  if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
   return bad;
 }
 
-template <bool kVar, bool kRot, bool kOne>
+template <int kVW, bool kRot, bool kOne>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid_constant__ EvalArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
   const int T = a.table_slots;
-  eval_smem_layout(a.K, T, &S, smem_raw);
+  eval_smem_layout(a.K, T, kVW, &S, smem_raw);
   const int tid = threadIdx.x;
   const uint32_t cap = (uint32_t)T - (uint32_t)T / 10u;  // above 90% full the table counts as crowded
   const uint32_t ring = S.a_queue + (uint32_t)(tid >> 5) * kQueue * 16u;
   const uint32_t lane_lt = lane_mask_lt();
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
 
-  init_smem(S, T, a.K * a.K);
+  init_smem<kVW>(S, T, a.K * a.K);
   __syncthreads();
   int passes = a.passes0;
   int cur = -1;  // item of the previous pose: key partitions are learned per item
@@ -771,10 +817,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
       if (I.passes0 > 0) passes = I.passes0;
     }
     const int lp = gp - I.pose_base;
-    const VoxelConst vc = voxel_const(kOne ? a.one.gc : *S.gc);
+    const VoxelConst vc = voxel_const<kVW>(kOne ? a.one.gc : *S.gc);
     const int dz_shift = kOne ? a.one.gc.dz_shift : S.gc->dz_shift;
     const int nt = I.n_tiles;
-    const int cut = max(3, (int)min(vc.nlim / (uint32_t)kPPT, (uint32_t)INT_MAX) / 3 * 3);
+    // runs are cut every `cut` tiles (a multiple of the prefetch depth, where the sweep checks)
+    const int cut = max(kDepth, (int)min(vc.nlim / (uint32_t)kPPT, (uint32_t)INT_MAX) / kDepth * kDepth);
     PoseRegs P;
     load_pose(I.poses + 12 * (size_t)lp, P);
     const float4* src = pose_tiles(I, lp) + tid;
@@ -786,21 +833,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
     for (int pass = 0; pass < pose_passes; ++pass) {
       if (!full) {
         const uint32_t bad =
-            lg == 0 ? sweep_pose<kVar, kRot, false>(S, a, vc, P, src, nt, 0, 0u, ring, lane_lt, cut)
-                    : sweep_pose<kVar, kRot, true>(S, a, vc, P, src, nt, lg, (uint32_t)pass, ring, lane_lt, cut);
+            lg == 0 ? sweep_pose<kVW, kRot, false>(S, a, vc, P, src, nt, 0, 0u, ring, lane_lt, cut)
+                    : sweep_pose<kVW, kRot, true>(S, a, vc, P, src, nt, lg, (uint32_t)pass, ring, lane_lt, cut);
         if (bad >> dz_shift) atomicOr(a.err, kErrDzBound);
       }
       __syncthreads();
       if (!full && *(volatile uint32_t*)&S.flags[2] != 0u) {  // runs whose home bucket was full
-        insert_overflow<kVar>(S, a);
+        insert_overflow<kVW>(S, a, kOne ? a.one.gc : *S.gc);
         __syncthreads();
       }
       overflowed = overflowed || S.flags[1] != 0u;
       full = full || overflowed;
-      scan_table<kVar, false>(S, kOne ? a.one.gc : *S.gc, I, wide, a.wide_count, T, lp, full);
+      scan_table<kVW, false>(S, kOne ? a.one.gc : *S.gc, I, wide, a.wide_count, T, lp, full);
       __syncthreads();
       max_occupied = max(max_occupied, S.flags[0]);
-      full = full || S.flags[3] != 0u;  // a voxel beyond the 32-bit sums: wide sums, not partitions
+      full = full || S.flags[3] != 0u;  // a voxel beyond the table sums: wide sums, not partitions
       __syncthreads();
       if (tid == 0) {
         S.flags[0] = 0u;
@@ -831,18 +878,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
 // Poses that eval_kernel could not finish: plain sweeps; each run goes straight into the
 // table with 64-bit side sums for voxels beyond the 32-bit bound; a full table restarts
 // the pose with twice the key partitions.
-template <bool kVar, bool kRot>
+template <int kVW, bool kRot>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid_constant__ EvalArgs a) {
+  constexpr bool kVar = kVW > 1;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
   const int T = a.table_slots;
-  eval_smem_layout(a.K, T, &S, smem_raw);
+  eval_smem_layout(a.K, T, kVW, &S, smem_raw);
   const int tid = threadIdx.x;
   const uint32_t nb = (uint32_t)T >> 2;
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
   const uint32_t n_redo = *(volatile const uint32_t*)a.redo_count;
   if (blockIdx.x >= n_redo) return;
-  init_smem(S, T, a.K * a.K);
+  init_smem<kVW>(S, T, a.K * a.K);
   __syncthreads();
   int passes_used = 1;
   for (uint32_t i = blockIdx.x; i < n_redo; i += gridDim.x) {
@@ -851,7 +899,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
     select_item(S, a, it);
     const EvalItem& I = a.items[it];
     const int lp = gp - I.pose_base;
-    const VoxelConst vc = voxel_const(*S.gc);
+    const VoxelConst vc = voxel_const<3>(*S.gc);  // runs with 32-bit sums, cut at nlim
     PoseRegs P;
     load_pose(I.poses + 12 * (size_t)lp, P);
     const float4* src = pose_tiles(I, lp) + tid;
@@ -861,7 +909,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
     int pass = 0;
     while (pass < passes) {
       const int lg = __ffs(passes) - 1;
-      Run run{kEmptyKey, 0u, 0u, 0u};
+      // plain runs: count n, S1 (two's complement) and S2, cut at nlim points
+      uint32_t rkey = kEmptyKey, rn = 0u, rs1 = 0u, rs2 = 0u;
       uint32_t bad = 0u;
       for (int t = 0; t < I.n_tiles; ++t) {
         float4 v[kPPT];
@@ -873,21 +922,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
           point_key<kRot>(vc, P, v[j], key, dz);
           if (lg > 0 && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != (uint32_t)pass) key = kEmptyKey;
           bad |= (uint32_t)((uint32_t)(dz + vc.dz_bound) > (uint32_t)(2 * vc.dz_bound));
-          if (key != run.key || (kVar && run.n >= vc.nlim)) {
-            if (run.key != kEmptyKey && run.n != 0u)
-              add_run<kVar>(S, vc, wide, run.key, run.n, (int)run.s1, run.s2, nb);
-            run = Run{key, 0u, 0u, 0u};
+          if (key != rkey || (kVar && rn >= vc.nlim)) {
+            if (rkey != kEmptyKey && rn != 0u) add_run<kVW>(S, wide, rkey, rn, (int)rs1, rs2, nb);
+            rkey = key;
+            rn = rs1 = rs2 = 0u;
           }
-          run.n += 1u;
-          run.s1 += (uint32_t)dz;
-          run.s2 += (uint32_t)(dz * dz);
+          rn += 1u;
+          rs1 += (uint32_t)dz;
+          rs2 += (uint32_t)(dz * dz);
         }
       }
       if (bad) atomicOr(a.err, kErrDzBound);
-      if (run.key != kEmptyKey && run.n != 0u) add_run<kVar>(S, vc, wide, run.key, run.n, (int)run.s1, run.s2, nb);
+      if (rkey != kEmptyKey && rn != 0u) add_run<kVW>(S, wide, rkey, rn, (int)rs1, rs2, nb);
       __syncthreads();
       const bool full = S.flags[1] != 0u;
-      scan_table<kVar, true>(S, *S.gc, I, wide, a.wide_count, T, lp, full);
+      scan_table<kVW, true>(S, *S.gc, I, wide, a.wide_count, T, lp, full);
       __syncthreads();
       if (tid == 0) S.flags[0] = 0u;
       if (full) {
@@ -1087,23 +1136,23 @@ __global__ void argmax_finalize_kernel(const EvalItem* items, int n_items) {
   *items[i].argmax = (b == 0ull) ? -1 : (int64_t)(0xFFFFFFFFu - (uint32_t)(b & 0xFFFFFFFFull));
 }
 
-template <bool kVar, bool kRot>
+template <int kVW, bool kRot>
 cudaError_t setup_t(int smem) {
-  cudaError_t e = cudaFuncSetAttribute(eval_kernel<kVar, kRot, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(eval_kernel<kVW, kRot, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(eval_kernel<kVar, kRot, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(eval_kernel<kVW, kRot, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(redo_kernel<kVar, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(redo_kernel<kVW, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
-template <bool kVar, bool kRot>
+template <int kVW, bool kRot>
 cudaError_t launch_eval_t(const EvalArgs& a, int n_ctas, size_t smem, cudaStream_t s) {
-  auto* k = a.item_start == nullptr ? eval_kernel<kVar, kRot, true> : eval_kernel<kVar, kRot, false>;
+  auto* k = a.item_start == nullptr ? eval_kernel<kVW, kRot, true> : eval_kernel<kVW, kRot, false>;
   k<<<n_ctas, kThreads, smem, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  redo_kernel<kVar, kRot><<<n_ctas, kThreads, smem, s>>>(a);
+  redo_kernel<kVW, kRot><<<n_ctas, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1111,9 +1160,11 @@ int eval_tile_points() { return kTile; }
 int eval_ovf_cap() { return kOvfCap; }
 int eval_min_tiles() { return kMinTiles; }
 
-size_t eval_smem_bytes(int K, int table_slots) { return eval_smem_layout(K, table_slots, nullptr, nullptr); }
+size_t eval_smem_bytes(int K, int table_slots, int vw) {
+  return eval_smem_layout(K, table_slots, vw, nullptr, nullptr);
+}
 
-int eval_table_slots_for(int K, size_t smem_budget) {
+int eval_table_slots_for(int K, int vw, size_t smem_budget) {
   if (kCtasPerSm > 1) {  // share the SM's shared memory between its resident CTAs
     int dev = 0, per_sm = 0, reserved = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -1122,15 +1173,18 @@ int eval_table_slots_for(int K, size_t smem_budget) {
       smem_budget = std::min(smem_budget, (size_t)(per_sm / kCtasPerSm - reserved));
   }
   int lo = 32;
-  while (eval_smem_bytes(K, lo + 32) <= smem_budget && lo < (1 << 16)) lo += 32;
+  while (eval_smem_bytes(K, lo + 32, vw) <= smem_budget && lo < (1 << 16)) lo += 32;
   return lo;
 }
 
-cudaError_t launch_eval(const EvalArgs& a, int n_ctas, bool var, bool rotate, cudaStream_t s) {
-  const size_t smem = eval_smem_bytes(a.K, a.table_slots);
-  if (var)
-    return rotate ? launch_eval_t<true, true>(a, n_ctas, smem, s) : launch_eval_t<true, false>(a, n_ctas, smem, s);
-  return rotate ? launch_eval_t<false, true>(a, n_ctas, smem, s) : launch_eval_t<false, false>(a, n_ctas, smem, s);
+cudaError_t launch_eval(const EvalArgs& a, int n_ctas, int vw, bool rotate, cudaStream_t s) {
+  const size_t smem = eval_smem_bytes(a.K, a.table_slots, vw);
+  switch (vw) {
+    case 1: return rotate ? launch_eval_t<1, true>(a, n_ctas, smem, s) : launch_eval_t<1, false>(a, n_ctas, smem, s);
+    case 2: return rotate ? launch_eval_t<2, true>(a, n_ctas, smem, s) : launch_eval_t<2, false>(a, n_ctas, smem, s);
+    case 3: return rotate ? launch_eval_t<3, true>(a, n_ctas, smem, s) : launch_eval_t<3, false>(a, n_ctas, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t eval_setup() {
@@ -1145,10 +1199,12 @@ cudaError_t eval_setup() {
   int smem = 0;
   e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  if ((e = setup_t<true, true>(smem)) != cudaSuccess) return e;
-  if ((e = setup_t<true, false>(smem)) != cudaSuccess) return e;
-  if ((e = setup_t<false, true>(smem)) != cudaSuccess) return e;
-  if ((e = setup_t<false, false>(smem)) != cudaSuccess) return e;
+  if ((e = setup_t<1, true>(smem)) != cudaSuccess) return e;
+  if ((e = setup_t<1, false>(smem)) != cudaSuccess) return e;
+  if ((e = setup_t<2, true>(smem)) != cudaSuccess) return e;
+  if ((e = setup_t<2, false>(smem)) != cudaSuccess) return e;
+  if ((e = setup_t<3, true>(smem)) != cudaSuccess) return e;
+  if ((e = setup_t<3, false>(smem)) != cudaSuccess) return e;
   done[dev] = true;
   return cudaSuccess;
 }

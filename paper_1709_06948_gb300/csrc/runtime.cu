@@ -56,6 +56,17 @@ namespace {
 // --------------------------------------------------------------------------------------
 // Host-side conventions (the library's own implementation of the stated convention).
 // --------------------------------------------------------------------------------------
+// R = Rz(thz) Ry(thy) Rx(thx) from the cosines and sines of the three angles, FP64, rounded
+// once to FP32.
+void rotation_fp32(double cx, double sx, double cy, double sy, double cz, double sz, float* out9) {
+  const double czsy = cz * sy;
+  const double szsy = sz * sy;
+  const double R[9] = {cz * cy, czsy * sx - sz * cx, czsy * cx + sz * sx,
+                       sz * cy, szsy * sx + cz * cx, szsy * cx - cz * sx,
+                       -sy,     cy * sx,             cy * cx};
+  for (int i = 0; i < 9; ++i) out9[i] = (float)R[i];
+}
+
 void pose_to_fp32(const float origin[3], const double* eta, float* out12) {
   // R = Rz(thz) Ry(thy) Rx(thx), FP64, rounded once; t' = t - origin.
   const double cx = std::cos(eta[3]), sx = std::sin(eta[3]);
@@ -176,9 +187,23 @@ align_status validate_desc(const align_grid_desc* d, GridConst* gc) {
   int m = 0;
   while ((1 << m) <= 2 * gc->dz_bound) ++m;
   gc->dz_shift = m;
-  // the sweep's check accepts dz in [-dz_bound, 2^m - 1 - dz_bound]
-  const uint64_t D = (uint64_t)((1 << m) - 1 - gc->dz_bound);
+  // the sweep's check accepts dz in [-dz_bound, 2^m - 1 - dz_bound], i.e. dz + dz_bound in
+  // [0, 2^m - 1].  The table packs n and the biased sum S1' = sum(dz + dz_bound) into one
+  // word n * 2^ns + S1': exact while n < 2^(32 - ns) and n * (2^m - 1) < 2^ns; ns is chosen
+  // for the largest such n, and S2 = sum(dz^2) must also fit 32 bits.
+  const uint64_t D = (uint64_t)((1 << m) - 1 - gc->dz_bound);  // largest |dz|
+  uint64_t best = 0;
+  int best_ns = m;
+  for (int ns = m; ns <= 31; ++ns) {
+    const uint64_t lim = std::min<uint64_t>((1ull << (32 - ns)) - 1, ((1ull << ns) - 1) / ((1ull << m) - 1));
+    if (lim > best) best = lim, best_ns = ns;
+  }
+  gc->ns_shift = best_ns;
   gc->nlim = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull / (D * D), 0x7FFFFFFFull / D);
+  gc->nlim_pack = (uint32_t)std::min<uint64_t>(best, gc->nlim);
+  int b = 0;
+  while (b < 30 && (2ull << (b + 1)) - 2ull <= (uint64_t)gc->nlim_pack) ++b;
+  gc->wide_shift = std::min(31, best_ns + b);
   for (int i = 0; i < 3; ++i) gc->boxA[i] = INT_MAX, gc->boxA[3 + i] = INT_MIN;
   // division of 32-bit keys by X and Y as a 64-bit multiply-high (Lemire, Kaser and Kurz,
   // "Faster remainder by direct computation", 2019: exact for every 32-bit dividend)
@@ -317,6 +342,9 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   align_status st0 = ensure_status_words(g);
   if (st0 != ALIGN_OK) return st0;
   const int n_ctas = (int)std::min<int64_t>(P, g->n_sm);
+  const bool var = g->gc.feature != ALIGN_FEAT_COUNT || out.dump != nullptr;
+  const int vw = eval_layout(g->gc, var);
+  g->table_slots = eval_shape(0).table_slots_for(K, vw, g->smem_optin);
   const size_t wide_bytes = (size_t)n_ctas * 2 * g->table_slots * sizeof(unsigned long long);
   if (g->wide.cap < wide_bytes || g->wide.p == nullptr) {
     CU(g->wide.ensure(wide_bytes), "allocate wide sums");
@@ -388,8 +416,7 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
     }
     CU(cudaEventRecord(evs[0], g->stream), "record event");
   }
-  const bool var = g->gc.feature != ALIGN_FEAT_COUNT || out.dump != nullptr;
-  CU(ek.launch_eval(a, n_ctas, var, rotate, g->stream), "launch eval kernel");
+  CU(ek.launch_eval(a, n_ctas, vw, rotate, g->stream), "launch eval kernel");
   if (g->profiling) CU(cudaEventRecord(evs[1], g->stream), "record event");
   CU(ek.launch_compose(a, g->stream), "launch compose kernel");
   CU(ek.launch_argmax_finalize(a.items, 1, g->stream), "launch argmax");
@@ -448,6 +475,7 @@ align_status collect_status(align_grid* g) {
 // Largest rotation table (rotation samples squared) of a search whose levels are built on
 // the device; larger rotation lattices take the synchronous path.
 constexpr int64_t kMaxLatticeCand = 16384;
+constexpr int kMaxAxisSamples = 32;  // rotation samples per axis of a device-built search
 
 // Centre of the next level: the sample `am` of the lattice around c with ranges r (the same
 // FP64 operations as build_lattice).
@@ -461,15 +489,6 @@ void lattice_sample(const double c[6], const double r[6], const int32_t m[6], in
   i[4] = (int32_t)(rem % m[4]); rem /= m[4];
   i[3] = (int32_t)rem;
   for (int a = 0; a < 6; ++a) out[a] = c[a] + lattice_step(r[a], m[a], i[a]);
-}
-
-// Rotation sample jr of a lattice around rotation centre c (components 3..5), as angles.
-void rotation_sample(const double c[6], const double r[6], const int32_t m[6], int32_t jr, double eta[6]) {
-  const int32_t irz = jr % m[5], iry = (jr / m[5]) % m[4], irx = jr / (m[5] * m[4]);
-  eta[0] = eta[1] = eta[2] = 0.0;
-  eta[3] = c[3] + lattice_step(r[3], m[3], irx);
-  eta[4] = c[4] + lattice_step(r[4], m[4], iry);
-  eta[5] = c[5] + lattice_step(r[5], m[5], irz);
 }
 
 // Coarse-to-fine lattice search with every level built on the device from the previous
@@ -505,8 +524,10 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
     CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
     g->lat_ev.push_back(e);
   }
-  // the previous search's copies out of the pinned buffers must be done before they change
-  CU(cudaStreamSynchronize(g->stream), "synchronize");
+  // copies out of the pinned buffers left by a search that stopped early must be done
+  // before the buffers change (a search that finished has synchronised the stream)
+  if (g->lat_pending) CU(cudaStreamSynchronize(g->stream), "synchronize");
+  g->lat_pending = true;
   Rec* rec = g->lat_rec_h.as<Rec>();
   std::vector<std::array<double, 6>> c((size_t)levels + 1), r((size_t)levels);
   for (int a = 0; a < 6; ++a) c[0][a] = c0[a], r[0][a] = r0[a];
@@ -528,22 +549,29 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
           (q.max_passes & (q.max_passes - 1)) == 0)
         g->passes_seed[0] = (int32_t)q.max_passes;
     }
-    // rotation table of level l: options = rotation samples of level l-1 (one at level 0)
+    // rotation table of level l: options = rotation samples of level l-1 (one at level 0).
+    // Per axis the angle of (option sample i, sample j) is centre + offset_i + offset_j; its
+    // cosine and sine are taken once (the same values pose_to_fp32 would compute).
     float* tab = g->lat_cand_h.as<float>() + (size_t)(l % 2) * slot;
     const int32_t n_opt = l == 0 ? 1 : n_rot;
+    double cs[3][2][kMaxAxisSamples * kMaxAxisSamples];
+    for (int ax = 0; ax < 3; ++ax) {
+      const int a = 3 + ax, ma = m[a];
+      for (int32_t io = 0; io < (l == 0 ? 1 : ma); ++io)
+        for (int32_t j = 0; j < ma; ++j) {
+          const double centre = l == 0 ? c[0][a] : c[(size_t)l - 1][a] + lattice_step(r[(size_t)l - 1][a], ma, io);
+          const double ang = centre + lattice_step(r[(size_t)l][a], ma, j);
+          cs[ax][0][io * ma + j] = std::cos(ang);
+          cs[ax][1][io * ma + j] = std::sin(ang);
+        }
+    }
     for (int32_t opt = 0; opt < n_opt; ++opt) {
-      double centre[6];
-      if (l == 0) {
-        std::memcpy(centre, c[0].data(), sizeof(centre));
-      } else {
-        rotation_sample(c[(size_t)l - 1].data(), r[(size_t)l - 1].data(), m, opt, centre);
-      }
+      const int32_t oz = opt % m[5], oy = (opt / m[5]) % m[4], ox = opt / (m[5] * m[4]);
       for (int32_t jr = 0; jr < n_rot; ++jr) {
-        double eta[6];
-        float p12[12];
-        rotation_sample(centre, r[(size_t)l].data(), m, jr, eta);
-        pose_to_fp32(g->origin, eta, p12);
-        std::memcpy(tab + ((size_t)opt * n_rot + jr) * 9, p12, 9 * sizeof(float));
+        const int32_t jz = jr % m[5], jy = (jr / m[5]) % m[4], jx = jr / (m[5] * m[4]);
+        const int ix = ox * m[3] + jx, iy = oy * m[4] + jy, iz = oz * m[5] + jz;
+        rotation_fp32(cs[0][0][ix], cs[0][1][ix], cs[1][0][iy], cs[1][1][iy], cs[2][0][iz], cs[2][1][iz],
+                      tab + ((size_t)opt * n_rot + jr) * 9);
       }
     }
     float* d_tab = g->lat_cand.as<float>() + (size_t)(l % 2) * slot;
@@ -581,6 +609,7 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
   }
   align_status st = collect_status(g);  // synchronises the stream
   if (st != ALIGN_OK) return st;
+  g->lat_pending = false;
   for (int32_t l = std::max(0, levels - 2); l < levels; ++l) {
     if (rec[l].am < 0 || rec[l].am >= P) return fail(ALIGN_E_INTERNAL, "argmax out of range");
     lattice_sample(c[(size_t)l].data(), r[(size_t)l].data(), m, rec[l].am, c[(size_t)l + 1].data());
@@ -635,7 +664,8 @@ align_status align_create_grid(const align_grid_desc* desc, void* cuda_stream, a
   g->stream = (cudaStream_t)cuda_stream;
   g->device = dev;
   g->n_sm = prop.multiProcessorCount;
-  g->table_slots = eval_shape(0).table_slots_for(gc.K, prop.sharedMemPerBlockOptin);
+  g->smem_optin = prop.sharedMemPerBlockOptin;
+  g->table_slots = eval_shape(0).table_slots_for(gc.K, eval_layout(gc, gc.feature != ALIGN_FEAT_COUNT), g->smem_optin);
   for (int i = 0; i < 6; ++i) g->boxA[i] = i < 3 ? INT_MAX : INT_MIN;
   *out = g;
   return ALIGN_OK;
@@ -648,9 +678,9 @@ align_status align_destroy_grid(align_grid* g) {
   for (DevBuf* b : {&g->symA, &g->sat, &g->xyz, &g->poses, &g->out_c, &g->out_box, &g->mi, &g->hist, &g->best,
                     &g->argmax, &g->err, &g->max_passes, &g->wide_count, &g->wide, &g->dump, &g->pts4,
                     &g->pose_src, &g->rots, &g->redo_list, &g->redo_count, &g->items, &g->ovf, &g->lat_c,
-                    &g->lat_cand})
+                    &g->lat_cand, &g->ref_pts, &g->ref_pose, &g->ref_cnt, &g->ref_s1, &g->ref_s2, &g->ref_box})
     b->release();
-  for (HostBuf* b : {&g->lat_cand_h, &g->lat_rec_h, &g->lat_c_h}) b->release();
+  for (HostBuf* b : {&g->lat_cand_h, &g->lat_rec_h, &g->lat_c_h, &g->ref_box_h}) b->release();
   for (cudaEvent_t e : g->lat_ev) cudaEventDestroy(e);
   for (auto* v : {&g->ev_pending, &g->ev_pool})
     for (auto& evs : *v)
@@ -683,15 +713,9 @@ align_status align_set_reference(align_grid* g, const float* xyzA, int64_t nA, i
   if (st != ALIGN_OK) return st;
   const GridConst& gc = g->gc;
   const size_t V = (size_t)g->V;
-  DevBuf pts, pose, cnt, s1, s2, box;
-  auto cleanup = [&]() {
-    pts.release();
-    pose.release();
-    cnt.release();
-    s1.release();
-    s2.release();
-    box.release();
-  };
+  // working buffers, kept by the grid between calls (a free would synchronise the device)
+  DevBuf &pts = g->ref_pts, &pose = g->ref_pose, &cnt = g->ref_cnt, &s1 = g->ref_s1, &s2 = g->ref_s2,
+         &box = g->ref_box;
   align_status result = ALIGN_OK;
   do {
     cudaError_t e;
@@ -705,11 +729,15 @@ align_status align_set_reference(align_grid* g, const float* xyzA, int64_t nA, i
       TRY(cudaMemcpyAsync(pts.p, xyzA, (size_t)nA * 12,
                           (flags & ALIGN_XYZ_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream),
           "copy A points");
-    float ident[12];
-    const double eta0[6] = {0, 0, 0, 0, 0, 0};
-    pose_to_fp32(g->origin, eta0, ident);
-    TRY(pose.ensure(sizeof(ident)), "allocate pose");
-    TRY(cudaMemcpyAsync(pose.p, ident, sizeof(ident), cudaMemcpyHostToDevice, g->stream), "copy pose");
+    if (!g->ref_pose_set) {  // the identity pose, rounded like every other pose
+      float ident[12];
+      const double eta0[6] = {0, 0, 0, 0, 0, 0};
+      pose_to_fp32(g->origin, eta0, ident);
+      TRY(pose.ensure(sizeof(ident)), "allocate pose");
+      TRY(cudaMemcpyAsync(pose.p, ident, sizeof(ident), cudaMemcpyHostToDevice, g->stream), "copy pose");
+      TRY(cudaStreamSynchronize(g->stream), "synchronize");
+      g->ref_pose_set = true;
+    }
     TRY(cnt.ensure(V * 4), "allocate A counts");
     TRY(s1.ensure(V * 8), "allocate A sums");
     TRY(s2.ensure(V * 8), "allocate A sums");
@@ -720,9 +748,11 @@ align_status align_set_reference(align_grid* g, const float* xyzA, int64_t nA, i
                               s1.as<unsigned long long>(), s2.as<unsigned long long>(), g->stream),
         "launch reference accumulate");
     TRY(g->symA.ensure(V), "allocate A symbols");
-    const int32_t box0[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-    TRY(box.ensure(sizeof(box0)), "allocate box");
-    TRY(cudaMemcpyAsync(box.p, box0, sizeof(box0), cudaMemcpyHostToDevice, g->stream), "init box");
+    TRY(box.ensure(sizeof(int32_t) * 6), "allocate box");
+    TRY(g->ref_box_h.ensure(sizeof(int32_t) * 12), "allocate pinned box");
+    int32_t* box_h = g->ref_box_h.as<int32_t>();
+    for (int i = 0; i < 6; ++i) box_h[i] = i < 3 ? INT_MAX : INT_MIN;
+    TRY(cudaMemcpyAsync(box.p, box_h, sizeof(int32_t) * 6, cudaMemcpyHostToDevice, g->stream), "init box");
     TRY(launch_ref_symbols(gc, cnt.as<uint32_t>(), s1.as<unsigned long long>(), s2.as<unsigned long long>(),
                            g->symA.as<uint8_t>(), box.as<int32_t>(), g->stream),
         "launch reference symbols");
@@ -730,14 +760,13 @@ align_status align_set_reference(align_grid* g, const float* xyzA, int64_t nA, i
     TRY(g->sat.ensure(std::max<size_t>(1, sat_elems) * 4), "allocate prefix sums");
     TRY(cudaMemsetAsync(g->sat.p, 0, std::max<size_t>(1, sat_elems) * 4, g->stream), "clear prefix sums");
     TRY(launch_ref_sat(gc, g->symA.as<uint8_t>(), g->sat.as<int32_t>(), g->stream), "launch prefix sums");
-    int32_t hb[6];
-    TRY(cudaMemcpyAsync(hb, box.p, sizeof(hb), cudaMemcpyDeviceToHost, g->stream), "read box");
+    int32_t* hb = box_h + 6;
+    TRY(cudaMemcpyAsync(hb, box.p, sizeof(int32_t) * 6, cudaMemcpyDeviceToHost, g->stream), "read box");
     TRY(cudaStreamSynchronize(g->stream), "synchronize");
     for (int i = 0; i < 6; ++i) g->boxA[i] = g->gc.boxA[i] = hb[i];
     g->stats[4] += (nA > 0 ? 1 : 0) + 1 + (gc.K > 1 ? 3 : 0);
 #undef TRY
   } while (0);
-  cleanup();
   if (result != ALIGN_OK) return result;
   g->has_ref = true;
   return ALIGN_OK;
@@ -888,7 +917,8 @@ align_status align_search_ex(align_grid* g, const float* xyzB, int64_t nB, int f
   std::memcpy(c, init, sizeof(c));
   std::memcpy(r, range, sizeof(r));
   const int32_t n_rot = counts[3] * counts[4] * counts[5];
-  if (levels >= 1 && (int64_t)n_rot * n_rot <= kMaxLatticeCand && n_rot <= max_rotation_copies(P, n_tiles))
+  if (levels >= 1 && (int64_t)n_rot * n_rot <= kMaxLatticeCand && n_rot <= max_rotation_copies(P, n_tiles) &&
+      counts[3] <= kMaxAxisSamples && counts[4] <= kMaxAxisSamples && counts[5] <= kMaxAxisSamples)
     return search_pipelined(g, n_tiles, c, r, counts, P, n_rot, levels, T_out, mi_out, level_best);
   std::vector<double> eta;
   std::vector<float> poses;

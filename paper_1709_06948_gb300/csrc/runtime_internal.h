@@ -87,7 +87,8 @@ struct align_grid {
   cudaStream_t stream = nullptr;
   int device = 0;
   int n_sm = 0;
-  int table_slots = 0;
+  int table_slots = 0;  // of the last launch (it depends on the table layout)
+  size_t smem_optin = 0;
   bool has_ref = false;
   int32_t boxA[6];
   mialign::DevBuf symA, sat;
@@ -96,8 +97,13 @@ struct align_grid {
   mialign::DevBuf pts4, pose_src, rots, redo_list, redo_count, items, ovf;
   // device-built lattice levels (align_search_ex): centres, rotation tables, read-backs
   mialign::DevBuf lat_c, lat_cand;
+  // reference-build working buffers (align_set_reference)
+  mialign::DevBuf ref_pts, ref_pose, ref_cnt, ref_s1, ref_s2, ref_box;
+  mialign::HostBuf ref_box_h;
+  bool ref_pose_set = false;
   mialign::HostBuf lat_cand_h, lat_rec_h, lat_c_h;
   std::vector<cudaEvent_t> lat_ev;
+  bool lat_pending = false;  // a search's copies may still be reading the pinned buffers
   int64_t n_points = 0;  // points staged in `xyz`
   // key partitions the next launch starts with, per kernel shape (its table size)
   int32_t passes_seed[mialign::kEvalShapes] = {1, 1, 1};

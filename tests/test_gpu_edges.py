@@ -205,3 +205,29 @@ def test_exact_path_does_not_escalate_partitions():
         assert np.array_equal(mi, first)
     st = align.align_eval_stats(L)
     assert st["wide_voxels"] >= 1 and st["passes"] <= 2
+
+
+@pytest.mark.parametrize("res,n_dense", [(0.5, 900), (0.5, 1500), (0.5, 2100), (0.25, 1100), (1.0, 3000),
+                                         (1.0, 4500)])
+def test_dense_voxel_near_table_limits(res, n_dense):
+    """One voxel holding about as many points as the table's per-voxel sums allow: below,
+    at and above the bound of the packed layout (fine grids) and of the three-word layout
+    (coarse grids).  Voxels past a bound go to the exact path; results stay exact."""
+    from paper_1709_06948_gb300 import align
+    rng = np.random.default_rng(41 + n_dense)
+    spec = scangen.lidar_grid(res)
+    lo = np.array([1.0, 2.0, 0.0]) + 0.01 * res
+    dense = lo + rng.uniform(0.0, 0.98 * res, (n_dense, 3))
+    rest = np.stack([rng.uniform(-30, 30, 8000), rng.uniform(-30, 30, 8000), rng.uniform(-0.5, 5, 8000)], 1)
+    xyz = np.concatenate([dense, rest]).astype(np.float32)
+    etas = np.zeros((7, 6))
+    etas[:, 0] = np.linspace(-0.3 * res, 0.3 * res, 7)
+    _compare(spec, xyz, xyz, etas)
+    G = oracle_grid(spec)
+    L = lib_grid(spec)
+    align.align_set_reference(L, xyz)
+    pose = G.round_pose(np.zeros(6))[0]
+    acc, box = align.align_accumulate(L, xyz, pose)
+    cnt, s1, s2, obox, _ = G.accumulate(xyz, pose)
+    assert np.array_equal(acc[:, 0], cnt) and np.array_equal(acc[:, 1], s1) and np.array_equal(acc[:, 2], s2)
+    assert cnt.max() >= n_dense
