@@ -252,12 +252,14 @@ align_status align_batch_stats(const align_batch* b, int64_t out[8]);
 
 /* ---------------------------------------------------------------------------------
    Serving: alignment requests (a lattice search of scan B against a resident reference
-   scan A, as align_search_ex) submitted at any time.  A worker thread runs continuous
-   batching: at every step it admits queued requests while request slots and the device
-   memory budget allow, evaluates the current lattice level of every active request in
-   one batched launch (align_eval_batch), moves each request to its next level, and
-   retires finished ones, freeing their slot and memory.  A request's result is the same
-   as align_search_ex on its grid alone.
+   scan A, as align_search_ex) submitted at any time.  Worker threads (two when
+   max_slots > 1), each with its own batch and stream, run continuous batching: at every
+   step a worker admits queued requests (first come, first served) while request slots and
+   the device memory budget allow, evaluates the current lattice level of each of its
+   active requests in one batched launch (align_eval_batch), moves each request to its next
+   level, and retires finished ones, freeing their slot and memory.  While one worker works
+   on the host, the other's launches run.  A request's result is the same as
+   align_search_ex on its grid alone.
    --------------------------------------------------------------------------------- */
 typedef struct align_server align_server;
 
@@ -292,7 +294,7 @@ align_status align_poll(align_server* s, uint64_t ticket, align_result* out);
 align_status align_wait(align_server* s, uint64_t ticket, int64_t timeout_ms, align_result* out);
 /* Seconds on the server's monotonic clock (the clock of align_result's times). */
 double align_server_now(const align_server* s);
-/* [0] batched steps, [1] requests admitted, [2] requests done, [3] most requests active
+/* [0] batched steps (all workers), [1] requests admitted, [2] requests done, [3] most requests active
    at once, [4] pose evaluations, [5] device bytes held now (estimate), [6] peak of [5],
    [7] requests waiting in the queue. */
 align_status align_server_stats(align_server* s, int64_t out[8]);

@@ -86,7 +86,7 @@ struct EvalArgs {
   uint32_t* redo_count;       // entries in redo_list (zeroed before every launch)
   uint4* ovf;                 // per CTA: ovf_cap runs (key, n, S1, S2) whose home bucket was full
   int32_t ovf_cap;
-  int32_t pad1;
+  int32_t p_begin;            // eval_kernel: first global pose of this launch (poses p_begin..P-1)
 };
 
 // One point-tile PackCopy of a batch: scan xyz (n points) -> out (n_out float4), raw
@@ -178,5 +178,7 @@ align_status check_grid_desc(const align_grid_desc* desc, GridConst* gc);
 align_status report_error(align_status st, const char* msg);
 align_status report_cuda_error(cudaError_t e, const char* what);
 void round_pose_host(const float origin[3], const double* eta6, float* pose12);
+// P poses; equal consecutive angles reuse the previous rotation (identical results).
+void round_poses_host(const float origin[3], const double* eta6, int64_t P, float* poses12);
 
 }  // namespace mialign

@@ -117,6 +117,10 @@ struct align_batch {
   int shape_fixed = -1;
   DevBuf xyz, poses, pts, pose_src, copies, items, starts, outc, box, best, mi, argmax, redo_list, redo_count, wide,
       status, ipasses, ovf;
+  // page-locked staging of the poses and their tile copies (asynchronous copies; a call's
+  // copies are done when it returns, since every call synchronises its stream)
+  mialign::HostBuf h_poses, h_src;
+  bool staged = false;  // copies out of the staging buffers may still be queued
   std::vector<align_grid*> last_grids;  // grids of the last launch (per-item partition feedback)
   int last_shape = 0;
   Sizes cap;
@@ -146,12 +150,19 @@ align_status grow(align_batch* b, DevBuf& buf, size_t& cap, size_t bytes, const 
   return ALIGN_OK;
 }
 
+// Pairs of one table layout (contiguous in the item list): one eval + redo launch each.
+struct LayoutGroup {
+  int vw = 1;         // table value words per slot (eval_layout)
+  int T = 0;          // table slots per CTA in that layout
+  int32_t p_begin = 0, p_end = 0;
+};
+
 struct Launch {
   const EvalKernels* ek = nullptr;
   int shape = 0;
-  EvalArgs a{};
+  EvalArgs a{};  // all pairs (compose, argmax); the eval launches take their group's poses
+  std::vector<LayoutGroup> groups;
   int n_ctas = 0;
-  int vw = 1;  // table value words per slot (eval_layout)
   bool rotate = false;
   int n_items = 0;
   int n_copies = 0;
@@ -165,7 +176,17 @@ align_status enqueue_launch(align_batch* b, const Launch& L) {
   BCU(cudaMemsetAsync(b->ipasses.p, 0, (size_t)L.n_items * 4, s), "clear partition counts");
   BCU(cudaMemsetAsync(b->redo_count.p, 0, 4, s), "clear redo count");
   BCU(L.ek->launch_pack_batch(b->copies.as<PackCopy>(), L.n_copies, L.max_out, s), "launch pack");
-  BCU(L.ek->launch_eval(L.a, L.n_ctas, L.vw, L.rotate, s), "launch eval kernel");
+  for (size_t k = 0; k < L.groups.size(); ++k) {
+    const LayoutGroup& lg = L.groups[k];
+    EvalArgs a = L.a;
+    a.p_begin = lg.p_begin;
+    a.P = lg.p_end;
+    a.table_slots = lg.T;
+    a.n_buckets = lg.T / 4;
+    // each group's redo kernel finishes only that group's poses
+    if (k > 0) BCU(cudaMemsetAsync(b->redo_count.p, 0, 4, s), "clear redo count");
+    BCU(L.ek->launch_eval(a, L.n_ctas, lg.vw, L.rotate, s), "launch eval kernel");
+  }
   BCU(L.ek->launch_compose(L.a, s), "launch compose kernel");
   BCU(L.ek->launch_argmax_finalize(L.a.items, L.n_items, s), "launch argmax");
   return ALIGN_OK;
@@ -200,7 +221,7 @@ align_status run_launch(align_batch* b, const Launch& L, bool use_graph, const s
   }
   BCU(cudaEventRecord(b->ev1, b->stream), "record event");
   b->stats[0] += 1;
-  b->stats[5] += 5;  // pack, eval, redo, compose, argmax
+  b->stats[5] += 3 + 2 * (int64_t)L.groups.size();  // pack, eval + redo per layout, compose, argmax
   return ALIGN_OK;
 }
 
@@ -213,11 +234,17 @@ align_status collect(align_batch* b) {
     BCU(cudaMemcpyAsync(ip.data(), b->ipasses.p, ip.size() * 4, cudaMemcpyDeviceToHost, b->stream),
         "read partition counts");
   BCU(cudaStreamSynchronize(b->stream), "synchronize");
-  // seed each grid's next launches with the partitions its poses needed (a power of two)
+  b->staged = false;
+  // seed each grid's next launches with the partitions its poses needed (a power of two);
+  // batches on other threads may share the grid (a server's workers): atomic max
   for (size_t i = 0; i < ip.size(); ++i) {
     align_grid* g = b->last_grids[i];
-    int32_t& seed = g->passes_seed[b->last_shape];
-    if (ip[i] > (uint32_t)seed && ip[i] <= (1u << 16) && (ip[i] & (ip[i] - 1)) == 0) seed = (int32_t)ip[i];
+    int32_t* seed = &g->passes_seed[b->last_shape];
+    if (ip[i] > (1u << 16) || (ip[i] & (ip[i] - 1)) != 0) continue;
+    int32_t cur = __atomic_load_n(seed, __ATOMIC_RELAXED);
+    while ((int32_t)ip[i] > cur &&
+           !__atomic_compare_exchange_n(seed, &cur, (int32_t)ip[i], false, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+    }
   }
   float ms = 0.0f;
   if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->stats[6] = (int64_t)std::llround(ms * 1000.0);
@@ -280,6 +307,8 @@ align_status align_batch_destroy(align_batch* b) {
   for (DevBuf* d : {&b->xyz, &b->poses, &b->pts, &b->pose_src, &b->copies, &b->items, &b->starts, &b->outc, &b->box,
                     &b->best, &b->mi, &b->argmax, &b->redo_list, &b->redo_count, &b->wide, &b->status, &b->ipasses, &b->ovf})
     d->release();
+  b->h_poses.release();
+  b->h_src.release();
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -352,9 +381,21 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   }
   if (poses_n >= INT32_MAX) return report_error(ALIGN_E_INVALID, "too many poses in one batch");
   if (n_copies > 65535) return report_error(ALIGN_E_INVALID, "too many tile copies in one batch");
-  int vw = 1;  // table layout of the launch: the widest any pair needs
-  for (const PairPlan& pp : plans) vw = std::max(vw, eval_layout(pp.g->gc, var));
-  const int T = ek.table_slots_for(maxK, vw, b->smem_optin);
+  // table layouts: pairs come sorted by layout (align_eval_batch), one eval launch per layout
+  std::vector<LayoutGroup> groups;
+  int T = 0;  // the largest table of the launches (sizes the 64-bit side sums)
+  for (const PairPlan& pp : plans) {
+    const int vw = eval_layout(pp.g->gc, var);
+    if (groups.empty() || groups.back().vw != vw) {
+      LayoutGroup lg;
+      lg.vw = vw;
+      lg.T = ek.table_slots_for(maxK, vw, b->smem_optin);
+      lg.p_begin = (int32_t)pp.pose_off;
+      T = std::max(T, lg.T);
+      groups.push_back(lg);
+    }
+    groups.back().p_end = (int32_t)(pp.pose_off + pp.P);
+  }
   const int n_ctas = b->n_sm * ek.ctas_per_sm;
   // ---- workspace ----
   align_status st;
@@ -385,13 +426,17 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   }
   // ---- stage inputs and tables (outside any graph) ----
   cudaStream_t s = b->stream;
-  std::vector<float> hp;
-  std::vector<int32_t> hsrc((size_t)poses_n, 0);
+  if (b->staged) BCU(cudaStreamSynchronize(b->stream), "synchronize");  // a call that stopped early
+  b->staged = true;
+  BCU(b->h_src.ensure((size_t)std::max<int64_t>(1, poses_n) * 4), "allocate pinned pose sources");
+  if (!rotate) BCU(b->h_poses.ensure((size_t)std::max<int64_t>(1, poses_n) * 48), "allocate pinned poses");
+  float* hp = b->h_poses.as<float>();
+  int32_t* hsrc = b->h_src.as<int32_t>();
+  std::memset(hsrc, 0, (size_t)poses_n * 4);
   std::vector<PackCopy> hcopies;
   std::vector<EvalItem> hitems((size_t)n);
   std::vector<int32_t> hstarts((size_t)n + 1);
   hcopies.reserve((size_t)n_copies);
-  if (!rotate) hp.resize((size_t)poses_n * 12);
   for (int i = 0; i < n; ++i) {
     PairPlan& pp = plans[(size_t)i];
     const align_pair& q = pairs[which[(size_t)i]];
@@ -441,15 +486,15 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     it.best = b->best.as<unsigned long long>() + i;
     it.argmax = b->argmax.as<int64_t>() + i;
     it.dump = nullptr;
-    it.passes0 = g->passes_seed[shape];
+    it.passes0 = __atomic_load_n(&g->passes_seed[shape], __ATOMIC_RELAXED);
     it.item_passes = b->ipasses.as<uint32_t>() + i;
     hstarts[(size_t)i] = (int32_t)pp.pose_off;
   }
   hstarts[(size_t)n] = (int32_t)poses_n;
   if (!rotate && poses_n > 0)
-    BCU(cudaMemcpyAsync(b->poses.p, hp.data(), (size_t)poses_n * 48, cudaMemcpyHostToDevice, s), "copy poses");
+    BCU(cudaMemcpyAsync(b->poses.p, hp, (size_t)poses_n * 48, cudaMemcpyHostToDevice, s), "copy poses");
   if (poses_n > 0)
-    BCU(cudaMemcpyAsync(b->pose_src.p, hsrc.data(), (size_t)poses_n * 4, cudaMemcpyHostToDevice, s),
+    BCU(cudaMemcpyAsync(b->pose_src.p, hsrc, (size_t)poses_n * 4, cudaMemcpyHostToDevice, s),
         "copy pose sources");
   BCU(cudaMemcpyAsync(b->copies.p, hcopies.data(), hcopies.size() * sizeof(PackCopy), cudaMemcpyHostToDevice, s),
       "copy copy table");
@@ -462,8 +507,8 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   L.ek = &ek;
   L.shape = shape;
   L.n_ctas = n_ctas;
-  L.vw = vw;
   L.rotate = rotate;
+  L.groups = groups;
   L.n_items = n;
   L.n_copies = n_copies;
   L.max_out = max_out;
@@ -488,9 +533,10 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   b->last_grids.clear();
   for (const PairPlan& pp : plans) b->last_grids.push_back(pp.g);
   b->last_shape = shape;
-  const std::vector<int64_t> sig = {shape,   n,       rotate,     vw,       a.passes0, T, n_ctas,
-                                    poses_n, n_copies, max_out,   maxK,     (int64_t)(uintptr_t)b->pts.p,
-                                    (int64_t)(uintptr_t)b->items.p};
+  std::vector<int64_t> sig = {shape,   n,       rotate,     a.passes0, T, n_ctas,
+                              poses_n, n_copies, max_out,   maxK,      (int64_t)(uintptr_t)b->pts.p,
+                              (int64_t)(uintptr_t)b->items.p};
+  for (const LayoutGroup& lg : L.groups) sig.insert(sig.end(), {lg.vw, lg.T, lg.p_begin, lg.p_end});
   st = run_launch(b, L, (flags & ALIGN_BATCH_GRAPH) != 0, sig);
   if (st != ALIGN_OK) return st;
   b->stats[3] = shape;
@@ -530,7 +576,7 @@ extern "C" align_status align_eval_batch(align_batch* b, const align_pair* pairs
     pp.P = q.P;
     if (q.eta6) {
       pp.hposes.resize((size_t)q.P * 12);
-      for (int64_t p = 0; p < q.P; ++p) round_pose_host(q.grid->origin, q.eta6 + 6 * p, &pp.hposes[(size_t)p * 12]);
+      round_poses_host(q.grid->origin, q.eta6, q.P, pp.hposes.data());
     } else if (!poses_dev) {
       pp.hposes.assign(q.poses12, q.poses12 + (size_t)q.P * 12);
     }
@@ -551,6 +597,24 @@ extern "C" align_status align_eval_batch(align_batch* b, const align_pair* pairs
   if (plans.empty()) {
     BCU(cudaStreamSynchronize(b->stream), "synchronize");
     return ALIGN_OK;
+  }
+  {  // pairs of one table layout are evaluated by one launch: order the pairs by layout
+    bool var = false;
+    for (const PairPlan& pp : plans) var = var || pp.g->gc.feature != ALIGN_FEAT_COUNT;
+    std::vector<size_t> order(plans.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+      return eval_layout(plans[x].g->gc, var) < eval_layout(plans[y].g->gc, var);
+    });
+    std::vector<PairPlan> sorted;
+    std::vector<int32_t> sorted_which;
+    sorted.reserve(plans.size());
+    for (size_t k : order) {
+      sorted.push_back(std::move(plans[k]));
+      sorted_which.push_back(which[k]);
+    }
+    plans.swap(sorted);
+    which.swap(sorted_which);
   }
   // kernel shape: fixed, tuned (cached per batch class) or the default
   int shape = b->shape_fixed >= 0 ? b->shape_fixed : 0;

@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
   int passes = a.passes0;
   int cur = -1;  // item of the previous pose: key partitions are learned per item
 
-  for (int gp = blockIdx.x; gp < a.P; gp += gridDim.x) {
+  for (int gp = a.p_begin + blockIdx.x; gp < a.P; gp += gridDim.x) {
     const int it = kOne ? 0 : item_of(a, gp);
     select_item(S, a, it);
     const EvalItem& I = item_at<kOne>(a, it);

@@ -67,6 +67,24 @@ void rotation_fp32(double cx, double sx, double cy, double sy, double cz, double
   for (int i = 0; i < 9; ++i) out9[i] = (float)R[i];
 }
 
+void pose_to_fp32(const float origin[3], const double* eta, float* out12);
+
+// Many poses, each as pose_to_fp32; a pose whose three angles equal the previous pose's
+// (bit for bit) takes the previous pose's rotation, so lattices listed rotation-major pay
+// the cosines and sines once per rotation.
+void poses_to_fp32(const float origin[3], const double* eta6, int64_t P, float* poses12) {
+  for (int64_t p = 0; p < P; ++p) {
+    const double* e = eta6 + 6 * p;
+    float* out = poses12 + 12 * p;
+    if (p > 0 && std::memcmp(e + 3, e - 3, 3 * sizeof(double)) == 0) {
+      std::memcpy(out, out - 12, 9 * sizeof(float));
+      for (int i = 0; i < 3; ++i) out[9 + i] = (float)(e[i] - (double)origin[i]);
+    } else {
+      pose_to_fp32(origin, e, out);
+    }
+  }
+}
+
 void pose_to_fp32(const float origin[3], const double* eta, float* out12) {
   // R = Rz(thz) Ry(thy) Rx(thx), FP64, rounded once; t' = t - origin.
   const double cx = std::cos(eta[3]), sx = std::sin(eta[3]);
@@ -699,7 +717,7 @@ align_status align_grid_info(const align_grid* g, int32_t* n_symbols, int64_t* n
 align_status align_round_poses(const float origin[3], const double* eta6, int64_t P, float* poses12) {
   if (!origin) return fail(ALIGN_E_INVALID, "origin is NULL");
   if (P < 0 || (P > 0 && (!eta6 || !poses12))) return fail(ALIGN_E_INVALID, "bad pose arrays");
-  for (int64_t p = 0; p < P; ++p) pose_to_fp32(origin, eta6 + 6 * p, poses12 + 12 * p);
+  poses_to_fp32(origin, eta6, P, poses12);
   return ALIGN_OK;
 }
 
@@ -805,7 +823,7 @@ static align_status eval_common(align_grid* g, const float* xyzB, int64_t nB, in
       h_poses = poses12;
     } else {
       tmp.resize((size_t)P * 12);
-      for (int64_t p = 0; p < P; ++p) pose_to_fp32(g->origin, eta6 + 6 * p, &tmp[(size_t)p * 12]);
+      poses_to_fp32(g->origin, eta6, P, tmp.data());
       h_poses = tmp.data();
     }
     for (int64_t i = 0; i < P * 12; ++i)
@@ -1200,4 +1218,7 @@ align_status check_grid_desc(const align_grid_desc* desc, GridConst* gc) { retur
 align_status report_error(align_status st, const char* msg) { return fail(st, "%s", msg); }
 align_status report_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 void round_pose_host(const float origin[3], const double* eta6, float* pose12) { pose_to_fp32(origin, eta6, pose12); }
+void round_poses_host(const float origin[3], const double* eta6, int64_t P, float* poses12) {
+  poses_to_fp32(origin, eta6, P, poses12);
+}
 }  // namespace mialign

@@ -1,12 +1,15 @@
 // server.cu — serving alignment requests with continuous batching.
 //
-// A worker thread owns a batch (align_eval_batch) and runs steps: admit queued requests
-// while slots and the device memory budget allow (first come, first served), evaluate the
-// current lattice level of every active request in one batched launch, then advance each
-// request to its next level (centre <- best pose, ranges halve, as align_search_ex) and
-// retire the finished ones.  Requests therefore join and leave between steps, and the
-// work of all active requests overlaps in the same launches.  Reference scans stay
-// resident as grids owned by the server.
+// Worker threads (two, or one with a single slot) each own a batch (align_eval_batch, with
+// its own stream and workspace) and run steps: admit queued requests while slots and the
+// device memory budget allow (first come, first served; a worker admits only while it
+// holds no more requests than the other), evaluate the current lattice level of each of
+// its active requests in one batched launch, then advance each request to its next level
+// (centre <- best pose, ranges halve, as align_search_ex) and retire the finished ones.
+// Requests therefore join and leave between steps, the work of all of a worker's requests
+// overlaps in the same launches, and while one worker prepares its next step or reads its
+// results back on the host, the other's launches keep the device busy.  Reference scans
+// stay resident as grids owned by the server.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -73,15 +76,16 @@ struct align_server {
   std::condition_variable cv;       // worker: new requests or stop
   std::condition_variable cv_done;  // clients: a request finished
   std::deque<Req*> queue;
-  std::vector<Req*> active;
+  std::vector<std::vector<Req*>> active;  // per worker
+  int32_t n_active = 0;                  // over all workers
   std::unordered_map<uint64_t, Req*> done;
   std::unordered_map<uint64_t, int> pending;  // ticket -> 1 while queued or active
   std::vector<Ref> refs;
   size_t used = 0, peak = 0;
   uint64_t next_ticket = 1;
   bool stop = false;
-  align_batch* batch = nullptr;
-  std::thread worker;
+  std::vector<align_batch*> batches;  // per worker
+  std::vector<std::thread> workers;
   int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
   double now() const {
@@ -109,27 +113,36 @@ void finish_locked(align_server* s, Req* r, int32_t status) {
   s->pending.erase(r->ticket);
   s->done[r->ticket] = r;
   s->stats[2] += 1;
+  s->n_active -= 1;
   s->cv_done.notify_all();
+  s->cv.notify_all();  // a slot and memory are free: any worker may admit
 }
 
-void admit_locked(align_server* s) {
-  while (!s->queue.empty() && (int32_t)s->active.size() < s->max_slots) {
+// Admit queued requests into worker w while the slots and the budget allow and w holds no
+// more requests than any other worker.
+void admit_locked(align_server* s, size_t w) {
+  std::vector<Req*>& mine = s->active[w];
+  while (!s->queue.empty() && s->n_active < s->max_slots) {
+    size_t least = mine.size();
+    for (const auto& other : s->active) least = std::min(least, other.size());
+    if (mine.size() > least) break;  // another worker has fewer: it admits next
     Req* r = s->queue.front();
-    if (s->used + r->bytes > s->budget && !s->active.empty()) break;  // wait for memory
+    if (s->used + r->bytes > s->budget && s->n_active > 0) break;  // wait for memory
     s->queue.pop_front();
     s->used += r->bytes;
     s->peak = std::max(s->peak, s->used);
     r->t_start = s->now();
-    s->active.push_back(r);
+    mine.push_back(r);
+    s->n_active += 1;
     s->stats[1] += 1;
   }
-  s->stats[3] = std::max<int64_t>(s->stats[3], (int64_t)s->active.size());
+  s->stats[3] = std::max<int64_t>(s->stats[3], (int64_t)s->n_active);
   s->stats[5] = (int64_t)s->used;
   s->stats[6] = (int64_t)s->peak;
   s->stats[7] = (int64_t)s->queue.size();
 }
 
-void worker_main(align_server* s) {
+void worker_main(align_server* s, size_t w) {
   cudaSetDevice(s->device);
   std::vector<align_pair> pairs;
   for (;;) {
@@ -138,11 +151,11 @@ void worker_main(align_server* s) {
       std::unique_lock<std::mutex> lk(s->mu);
       for (;;) {
         if (s->stop) return;
-        admit_locked(s);
-        if (!s->active.empty()) break;
+        admit_locked(s, w);
+        if (!s->active[w].empty()) break;
         s->cv.wait(lk);
       }
-      act = s->active;
+      act = s->active[w];
     }
     // upload the points of newly admitted requests; build every request's lattice level
     int32_t step_status = ALIGN_OK;
@@ -176,7 +189,7 @@ void worker_main(align_server* s) {
       q.argmax_out = &r->am;
     }
     if (step_status == ALIGN_OK)
-      step_status = align_eval_batch(s->batch, pairs.data(), (int32_t)pairs.size(), ALIGN_XYZ_DEVICE);
+      step_status = align_eval_batch(s->batches[w], pairs.data(), (int32_t)pairs.size(), ALIGN_XYZ_DEVICE);
     std::lock_guard<std::mutex> lk(s->mu);
     s->stats[0] += 1;
     std::vector<Req*> still;
@@ -196,7 +209,7 @@ void worker_main(align_server* s) {
       if (++r->level >= r->levels) finish_locked(s, r, ALIGN_OK);
       else still.push_back(r);
     }
-    s->active.swap(still);
+    s->active[w].swap(still);
   }
 }
 
@@ -217,15 +230,31 @@ align_status align_server_create(size_t hbm_budget_bytes, int32_t max_slots, ali
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;
   s->t0 = std::chrono::steady_clock::now();
-  align_status st = align_batch_create(nullptr, &s->batch);
-  if (st != ALIGN_OK) return st;
+  const size_t n_workers = max_slots > 1 ? 2 : 1;
+  for (size_t w = 0; w < n_workers; ++w) {
+    align_batch* b = nullptr;
+    align_status st = align_batch_create(nullptr, &b);  // its own stream
+    if (st != ALIGN_OK) {
+      for (align_batch* q : s->batches) align_batch_destroy(q);
+      return st;
+    }
+    s->batches.push_back(b);
+  }
+  s->active.assign(n_workers, {});
   align_server* raw = s.release();
   try {
-    raw->worker = std::thread(worker_main, raw);
+    for (size_t w = 0; w < n_workers; ++w) raw->workers.emplace_back(worker_main, raw, w);
   } catch (...) {
-    align_batch_destroy(raw->batch);
+    {
+      std::lock_guard<std::mutex> lk(raw->mu);
+      raw->stop = true;
+      raw->cv.notify_all();
+    }
+    for (std::thread& t : raw->workers)
+      if (t.joinable()) t.join();
+    for (align_batch* q : raw->batches) align_batch_destroy(q);
     delete raw;
-    return report_error(ALIGN_E_INTERNAL, "could not start the worker thread");
+    return report_error(ALIGN_E_INTERNAL, "could not start the worker threads");
   }
   *out = raw;
   return ALIGN_OK;
@@ -305,7 +334,7 @@ align_status align_submit(align_server* s, const align_request* req, uint64_t* t
   s->pending[raw->ticket] = 1;
   s->queue.push_back(raw);
   s->stats[7] = (int64_t)s->queue.size();
-  s->cv.notify_one();
+  s->cv.notify_all();
   return ALIGN_OK;
 }
 
@@ -368,13 +397,15 @@ align_status align_server_destroy(align_server* s) {
     s->stop = true;
     s->cv.notify_all();
   }
-  if (s->worker.joinable()) s->worker.join();
+  for (std::thread& t : s->workers)
+    if (t.joinable()) t.join();
   cudaSetDevice(s->device);
   for (Req* r : s->queue) delete r;
-  for (Req* r : s->active) delete r;
+  for (auto& act : s->active)
+    for (Req* r : act) delete r;
   for (auto& kv : s->done) delete kv.second;
   for (Ref& f : s->refs) align_destroy_grid(f.grid);
-  align_batch_destroy(s->batch);
+  for (align_batch* b : s->batches) align_batch_destroy(b);
   delete s;
   return ALIGN_OK;
 }
