@@ -235,10 +235,19 @@ def run_batched(align, steps):
     for g, B, etas in items[:2]:
         align.align_eval_mi(g, B, eta6=etas)
     loop = []
-    for _ in range(max(1, min(steps, 3))):
+    loop_reps = max(1, min(steps, 3))
+    for g in grids:
+        align.align_profile(g, 1)
+    for _ in range(loop_reps):
         t0 = time.perf_counter()
         single = [align.align_eval_mi(g, B, eta6=etas)[:2] for g, B, etas in items]
         loop.append(time.perf_counter() - t0)
+    loop_dev_ms = 0.0  # eval + compose kernels, CUDA events per launch
+    for g in grids:
+        ev_ms, comp_ms, _ = align.align_profile(g, 2)
+        align.align_profile(g, 0)
+        loop_dev_ms += ev_ms + comp_ms
+    loop_dev_ms /= loop_reps
     same = same and all(np.array_equal(a[0], r[0]) and a[1] == r[1] for a, r in zip(single, res))
     P = sum(len(e) for _, _, e in items)
     st = align.align_batch_stats(b)
@@ -254,6 +263,7 @@ def run_batched(align, steps):
            "ms_per_call_wall": statistics.median(wall) * 1e3,
            "plain_loop_pose_evals_per_s_wall": P / statistics.median(loop),
            "plain_loop_ms_wall": statistics.median(loop) * 1e3,
+           "plain_loop_eval_compose_ms_device": loop_dev_ms,
            "speedup_vs_plain_loop_wall": statistics.median(loop) / statistics.median(wall),
            "tuned_shape": st["shape"], "table_slots": st["table_slots"], "graph_replays": st["graph_replays"],
            "graph_captures": st["graph_captures"], "tuner_trials": st["tuner_trials"],

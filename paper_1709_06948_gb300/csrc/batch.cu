@@ -150,18 +150,14 @@ align_status grow(align_batch* b, DevBuf& buf, size_t& cap, size_t bytes, const 
   return ALIGN_OK;
 }
 
-// Pairs of one table layout (contiguous in the item list): one eval + redo launch each.
-struct LayoutGroup {
-  int vw = 1;         // table value words per slot (eval_layout)
-  int T = 0;          // table slots per CTA in that layout
-  int32_t p_begin = 0, p_end = 0;
-};
-
 struct Launch {
   const EvalKernels* ek = nullptr;
   int shape = 0;
-  EvalArgs a{};  // all pairs (compose, argmax); the eval launches take their group's poses
-  std::vector<LayoutGroup> groups;
+  EvalArgs a{};  // all pairs (compose, argmax)
+  // one single-pair eval + redo launch per pair: its arguments (the pair in the parameter
+  // bank, its poses p_begin..P-1 of the batch) and its table layout
+  std::vector<EvalArgs> evals;
+  std::vector<int> vws;
   int n_ctas = 0;
   bool rotate = false;
   int n_items = 0;
@@ -176,16 +172,10 @@ align_status enqueue_launch(align_batch* b, const Launch& L) {
   BCU(cudaMemsetAsync(b->ipasses.p, 0, (size_t)L.n_items * 4, s), "clear partition counts");
   BCU(cudaMemsetAsync(b->redo_count.p, 0, 4, s), "clear redo count");
   BCU(L.ek->launch_pack_batch(b->copies.as<PackCopy>(), L.n_copies, L.max_out, s), "launch pack");
-  for (size_t k = 0; k < L.groups.size(); ++k) {
-    const LayoutGroup& lg = L.groups[k];
-    EvalArgs a = L.a;
-    a.p_begin = lg.p_begin;
-    a.P = lg.p_end;
-    a.table_slots = lg.T;
-    a.n_buckets = lg.T / 4;
-    // each group's redo kernel finishes only that group's poses
+  for (size_t k = 0; k < L.evals.size(); ++k) {
+    // each pair's redo kernel finishes only that pair's poses
     if (k > 0) BCU(cudaMemsetAsync(b->redo_count.p, 0, 4, s), "clear redo count");
-    BCU(L.ek->launch_eval(a, L.n_ctas, lg.vw, L.rotate, s), "launch eval kernel");
+    BCU(L.ek->launch_eval(L.evals[k], L.n_ctas, L.vws[k], L.rotate, s), "launch eval kernel");
   }
   BCU(L.ek->launch_compose(L.a, s), "launch compose kernel");
   BCU(L.ek->launch_argmax_finalize(L.a.items, L.n_items, s), "launch argmax");
@@ -221,7 +211,7 @@ align_status run_launch(align_batch* b, const Launch& L, bool use_graph, const s
   }
   BCU(cudaEventRecord(b->ev1, b->stream), "record event");
   b->stats[0] += 1;
-  b->stats[5] += 3 + 2 * (int64_t)L.groups.size();  // pack, eval + redo per layout, compose, argmax
+  b->stats[5] += 3 + 2 * (int64_t)L.evals.size();  // pack, eval + redo per pair, compose, argmax
   return ALIGN_OK;
 }
 
@@ -381,20 +371,13 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   }
   if (poses_n >= INT32_MAX) return report_error(ALIGN_E_INVALID, "too many poses in one batch");
   if (n_copies > 65535) return report_error(ALIGN_E_INVALID, "too many tile copies in one batch");
-  // table layouts: pairs come sorted by layout (align_eval_batch), one eval launch per layout
-  std::vector<LayoutGroup> groups;
+  // per pair: its table layout and table size (one eval launch per pair)
+  std::vector<int> vws, Ts;
   int T = 0;  // the largest table of the launches (sizes the 64-bit side sums)
   for (const PairPlan& pp : plans) {
-    const int vw = eval_layout(pp.g->gc, var);
-    if (groups.empty() || groups.back().vw != vw) {
-      LayoutGroup lg;
-      lg.vw = vw;
-      lg.T = ek.table_slots_for(maxK, vw, b->smem_optin);
-      lg.p_begin = (int32_t)pp.pose_off;
-      T = std::max(T, lg.T);
-      groups.push_back(lg);
-    }
-    groups.back().p_end = (int32_t)(pp.pose_off + pp.P);
+    vws.push_back(eval_layout(pp.g->gc, var));
+    Ts.push_back(ek.table_slots_for(pp.g->gc.K, vws.back(), b->smem_optin));
+    T = std::max(T, Ts.back());
   }
   const int n_ctas = b->n_sm * ek.ctas_per_sm;
   // ---- workspace ----
@@ -508,7 +491,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   L.shape = shape;
   L.n_ctas = n_ctas;
   L.rotate = rotate;
-  L.groups = groups;
+  L.vws = vws;
   L.n_items = n;
   L.n_copies = n_copies;
   L.max_out = max_out;
@@ -530,13 +513,30 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   a.redo_count = b->redo_count.as<uint32_t>();
   a.ovf = b->ovf.as<uint4>();
   a.ovf_cap = ek.ovf_cap();
+  for (int i = 0; i < n; ++i) {
+    EvalArgs ai = a;
+    ai.one = hitems[(size_t)i];
+    ai.items = b->items.as<EvalItem>() + i;  // the redo kernel reads its one item here
+    ai.item_start = nullptr;
+    ai.n_items = 1;
+    ai.p_begin = (int32_t)plans[(size_t)i].pose_off;
+    ai.P = (int32_t)(plans[(size_t)i].pose_off + plans[(size_t)i].P);
+    ai.K = plans[(size_t)i].g->gc.K;
+    ai.table_slots = Ts[(size_t)i];
+    ai.n_buckets = Ts[(size_t)i] / 4;
+    L.evals.push_back(ai);
+  }
   b->last_grids.clear();
   for (const PairPlan& pp : plans) b->last_grids.push_back(pp.g);
   b->last_shape = shape;
+  // a graph replays the kernels' parameters as captured, the pairs' items included
+  uint64_t h = 1469598103934665603ull;
+  const unsigned char* hb = reinterpret_cast<const unsigned char*>(hitems.data());
+  for (size_t k = 0; k < hitems.size() * sizeof(EvalItem); ++k) h = (h ^ hb[k]) * 1099511628211ull;
   std::vector<int64_t> sig = {shape,   n,       rotate,     a.passes0, T, n_ctas,
                               poses_n, n_copies, max_out,   maxK,      (int64_t)(uintptr_t)b->pts.p,
-                              (int64_t)(uintptr_t)b->items.p};
-  for (const LayoutGroup& lg : L.groups) sig.insert(sig.end(), {lg.vw, lg.T, lg.p_begin, lg.p_end});
+                              (int64_t)(uintptr_t)b->items.p, (int64_t)h};
+  for (size_t i = 0; i < vws.size(); ++i) sig.insert(sig.end(), {vws[i], Ts[i]});
   st = run_launch(b, L, (flags & ALIGN_BATCH_GRAPH) != 0, sig);
   if (st != ALIGN_OK) return st;
   b->stats[3] = shape;
@@ -597,24 +597,6 @@ extern "C" align_status align_eval_batch(align_batch* b, const align_pair* pairs
   if (plans.empty()) {
     BCU(cudaStreamSynchronize(b->stream), "synchronize");
     return ALIGN_OK;
-  }
-  {  // pairs of one table layout are evaluated by one launch: order the pairs by layout
-    bool var = false;
-    for (const PairPlan& pp : plans) var = var || pp.g->gc.feature != ALIGN_FEAT_COUNT;
-    std::vector<size_t> order(plans.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
-      return eval_layout(plans[x].g->gc, var) < eval_layout(plans[y].g->gc, var);
-    });
-    std::vector<PairPlan> sorted;
-    std::vector<int32_t> sorted_which;
-    sorted.reserve(plans.size());
-    for (size_t k : order) {
-      sorted.push_back(std::move(plans[k]));
-      sorted_which.push_back(which[k]);
-    }
-    plans.swap(sorted);
-    which.swap(sorted_which);
   }
   // kernel shape: fixed, tuned (cached per batch class) or the default
   int shape = b->shape_fixed >= 0 ? b->shape_fixed : 0;
