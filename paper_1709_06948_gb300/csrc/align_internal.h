@@ -148,9 +148,12 @@ const EvalKernels& eval_shape(int i);
 // to the previous level's argmax sample when am_prev is set (else c_prev itself).  Pose p:
 // rotation cand[opt][p / n_trans] (opt = the previous argmax's rotation sample, 0 without
 // one), translation t' = fp32(centre_t + offset_t - origin_t) in FP64.
+constexpr int kLatticeMaxAxis = 32;  // samples per pose component of a device-built level
 struct LatticeLevel {
-  double r[6];              // this level's ranges
-  double r_prev[6];         // the previous level's ranges
+  // offset_i = range * (2i - (m - 1)) / (m - 1) of every sample (0 for one sample), computed
+  // by the host with the same FP64 operations as its own lattice construction
+  double off[6][kLatticeMaxAxis];       // this level's offsets
+  double off_prev[6][kLatticeMaxAxis];  // the previous level's offsets
   int32_t m[6];             // samples per pose component (tx, ty, tz, rx, ry, rz; the same every level)
   float origin[3];
   int32_t n_rot;            // rotation samples m[3] * m[4] * m[5]

@@ -967,39 +967,47 @@ __device__ __forceinline__ int stream_of(int tid) { return (tid & 31) * kWarps +
 
 // xyz -> float4 tiles, optionally one rotated copy per rotation.  Tile t, position
 // j*kThreads + s holds point s*L + kPPT*t + j of B (L = kPPT * tiles): stream s visits
-// consecutive points of B, kPPT per tile.
-__global__ void pack_points_kernel(const float* __restrict__ xyz, int64_t n, int64_t n_out,
-                                   const float* __restrict__ rots, float4* out) {
-  const int r = blockIdx.y;
+// consecutive points of B, kPPT per tile.  Block (t, g) writes tile t of the copies of
+// rotations g*kPackRot ... : each point is gathered once and rotated for all of them, and
+// every copy's tile is written with coalesced stores.
+constexpr int kPackRot = 8;
+constexpr int kPackThreads = 256;
+
+__global__ void __launch_bounds__(kPackThreads) pack_points_kernel(const float* __restrict__ xyz, int64_t n,
+                                                                   int64_t n_out, const float* __restrict__ rots,
+                                                                   int n_rot, float4* out) {
   const float nan = __int_as_float(0x7fc00000);
   const float inf = __int_as_float(0x7f800000);
-  float R[9];
-  if (rots != nullptr)
-    for (int i = 0; i < 9; ++i) R[i] = rots[9 * r + i];
-  float4* o = out + (size_t)r * n_out;
   const int64_t L = n_out / kThreads;  // points per stream
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_out; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = i / kTile;
-    const int pos = (int)(i - t * kTile);
-    const int j = pos / kThreads;
-    const int64_t src = (int64_t)stream_of(pos - j * kThreads) * L + (int64_t)kPPT * t + j;
-    // padding: NaN for raw tiles (the in-kernel rotation keeps NaN), +inf for rotated copies
-    const float pad = rots != nullptr ? inf : nan;
-    float4 v = make_float4(pad, pad, pad, 0.0f);
-    if (src < n) {
-      const float x = xyz[3 * src], y = xyz[3 * src + 1], z = xyz[3 * src + 2];
-      if (rots != nullptr) {
-        rotate_point(R, x, y, z, v.x, v.y, v.z);
-        // a non-finite coordinate can only come from a non-finite point (or an overflow),
-        // which the voxel map drops under every pose; +inf keeps it dropped
-        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) v = make_float4(inf, inf, inf, 0.0f);
-      } else {
-        v.x = x;
-        v.y = y;
-        v.z = z;
+  const int64_t t = blockIdx.x;
+  const int r0 = (int)blockIdx.y * kPackRot;
+  const int r1 = rots != nullptr ? min(n_rot, r0 + kPackRot) : 1;
+  for (int slot = threadIdx.x; slot < kTile; slot += blockDim.x) {
+    const int j = slot / kThreads;
+    const int64_t src = (int64_t)stream_of(slot - j * kThreads) * L + (int64_t)kPPT * t + j;
+    const bool have = src < n;
+    const float x = have ? xyz[3 * src] : 0.0f, y = have ? xyz[3 * src + 1] : 0.0f, z = have ? xyz[3 * src + 2] : 0.0f;
+    const int64_t i = t * kTile + slot;
+    for (int r = r0; r < r1; ++r) {
+      // padding: NaN for raw tiles (the in-kernel rotation keeps NaN), +inf for rotated copies
+      float4 v = rots != nullptr ? make_float4(inf, inf, inf, 0.0f) : make_float4(nan, nan, nan, 0.0f);
+      if (have) {
+        if (rots != nullptr) {
+          float R[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) R[k] = __ldg(rots + 9 * r + k);
+          rotate_point(R, x, y, z, v.x, v.y, v.z);
+          // a non-finite coordinate can only come from a non-finite point (or an overflow),
+          // which the voxel map drops under every pose; +inf keeps it dropped
+          if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) v = make_float4(inf, inf, inf, 0.0f);
+        } else {
+          v.x = x;
+          v.y = y;
+          v.z = z;
+        }
       }
+      store_point(out + (size_t)r * n_out, i, v.x, v.y, v.z);
     }
-    store_point(o, i, v.x, v.y, v.z);
   }
 }
 
@@ -1221,12 +1229,11 @@ cudaError_t launch_pack_batch(const PackCopy* copies, int n_copies, int64_t max_
 
 cudaError_t launch_pack_points(const float* xyz, int64_t n, int64_t n_out, const float* rots, int n_rot, float4* out,
                                cudaStream_t s) {
-  const int threads = 256;
-  int64_t bx = (n_out + threads - 1) / threads;
-  if (bx > 2048) bx = 2048;
-  if (bx < 1) bx = 1;
-  dim3 grid((unsigned)bx, (unsigned)(rots != nullptr && n_rot > 0 ? n_rot : 1));
-  pack_points_kernel<<<grid, threads, 0, s>>>(xyz, n, n_out, rots, out);
+  const int64_t n_tiles = n_out / kTile;
+  const int groups = rots != nullptr && n_rot > 0 ? (n_rot + kPackRot - 1) / kPackRot : 1;
+  if (n_tiles < 1 || n_tiles > INT_MAX || groups > 65535) return cudaErrorInvalidValue;
+  pack_points_kernel<<<dim3((unsigned)n_tiles, (unsigned)groups), kPackThreads, 0, s>>>(xyz, n, n_out, rots,
+                                                                                         n_rot, out);
   return cudaGetLastError();
 }
 

@@ -3,11 +3,12 @@
 //
 // A level's centre is the pose the previous level chose (its argmax, read here from device
 // memory); its samples are centre + offset per axis, offset_i = range*(2i - (m-1))/(m-1)
-// (one sample: the centre); pose index order rx, ry, rz, tx, ty, tz with tz fastest.  The FP64
-// operations are the same IEEE operations, in the same order, as the host's lattice
-// construction and pose rounding (t' = fp32(eta_t - origin)); the rotations, which need
-// cos/sin, arrive from the host as a table of FP32 matrices, one per (rotation sample of the
-// previous level, rotation sample of this level).
+// (one sample: the centre); pose index order rx, ry, rz, tx, ty, tz with tz fastest.  The
+// offsets come from the host (its own FP64 values), and the sums and the rounding
+// t' = fp32(eta_t - origin) are the same IEEE operations, in the same order, as the host's
+// lattice construction and pose rounding; the rotations, which need cos/sin, arrive from the
+// host as a table of FP32 matrices, one per (rotation sample of the previous level, rotation
+// sample of this level).
 #include <algorithm>
 
 #include "align_internal.h"
@@ -15,11 +16,6 @@
 namespace mialign {
 
 namespace {
-
-__device__ __forceinline__ double lattice_offset(double range, int32_t m, int32_t i) {
-  if (m < 2) return 0.0;
-  return __ddiv_rn(__dmul_rn(range, (double)(2 * i - (m - 1))), (double)(m - 1));
-}
 
 // Lattice index -> sample index of each pose component (i[0..5] for tx, ty, tz, rx, ry, rz;
 // index order rx, ry, rz, tx, ty, tz with tz fastest).
@@ -45,7 +41,7 @@ __global__ void lattice_level_kernel(const __grid_constant__ LatticeLevel L) {
     }
     int32_t i[6];
     lattice_indices(am, L.m, i);
-    for (int a = 0; a < 6; ++a) c[a] = __dadd_rn(L.c_prev[a], lattice_offset(L.r_prev[a], L.m[a], i[a]));
+    for (int a = 0; a < 6; ++a) c[a] = __dadd_rn(L.c_prev[a], L.off_prev[a][i[a]]);
     opt = (int32_t)(am / n_trans);
   } else {
     for (int a = 0; a < 6; ++a) c[a] = L.c_prev[a];
@@ -59,7 +55,7 @@ __global__ void lattice_level_kernel(const __grid_constant__ LatticeLevel L) {
     float* out = L.poses + 12 * p;
     for (int k = 0; k < 9; ++k) out[k] = cand[9 * jr + k];
     for (int a = 0; a < 3; ++a) {
-      const double e = __dadd_rn(c[a], lattice_offset(L.r[a], L.m[a], j[a]));
+      const double e = __dadd_rn(c[a], L.off[a][j[a]]);
       out[9 + a] = __double2float_rn(__dsub_rn(e, (double)L.origin[a]));
     }
     L.pose_src[p] = jr;

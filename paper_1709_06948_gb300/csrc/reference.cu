@@ -57,21 +57,49 @@ __global__ void ref_symbols_kernel(const GridConst gc, const uint32_t* __restric
 }
 
 // sat[a-1][z][y][x] = #{ voxels (x', y', z') with x' < x, y' < y, z' < z and symA == a }.
-// Pass 0: running sums along x per (a, z, y) row; pass 1 along y; pass 2 along z.
-__global__ void ref_sat_x_kernel(const GridConst gc, const uint8_t* __restrict__ symA, int32_t* sat) {
+// Pass 0: running sums along x per (a, z, y) row (a warp per row: inclusive warp scans over
+// 32-voxel chunks, coalesced); pass 1 along y and pass 2 along z (a thread per column, rows
+// read kChunk at a time so that the loads of a chunk are in flight together).
+constexpr int kChunk = 8;
+
+__global__ void ref_sat_x_kernel(const GridConst gc, const uint8_t* __restrict__ symA, int32_t* __restrict__ sat) {
   const int X = gc.X, Y = gc.Y, Z = gc.Z, X1 = X + 1, Y1 = Y + 1, Z1 = Z + 1;
   const int64_t rows = (int64_t)(gc.K - 1) * Z * Y;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
     const int y = (int)(r % Y);
     const int z = (int)((r / Y) % Z);
     const int a = (int)(r / ((int64_t)Y * Z)) + 1;
     int32_t* out = sat + (((size_t)(a - 1) * Z1 + (z + 1)) * Y1 + (y + 1)) * X1;
     const uint8_t* in = symA + ((size_t)z * Y + y) * X;
-    int32_t acc = 0;
-    out[0] = 0;
-    for (int x = 0; x < X; ++x) {
-      acc += (in[x] == a) ? 1 : 0;
-      out[x + 1] = acc;
+    if (lane == 0) out[0] = 0;
+    int32_t carry = 0;
+    for (int x0 = 0; x0 < X; x0 += 32) {
+      const int x = x0 + lane;
+      int32_t v = (x < X && in[x] == a) ? 1 : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t u = __shfl_up_sync(0xFFFFFFFFu, v, d);
+        if (lane >= d) v += u;
+      }
+      if (x < X) out[x + 1] = carry + v;
+      carry += __shfl_sync(0xFFFFFFFFu, v, 31);
+    }
+  }
+}
+
+// Running sums down a column of n entries `stride` apart (entry 0 stays as it is).
+__device__ __forceinline__ void column_scan(int32_t* __restrict__ base, int n, size_t stride) {
+  int32_t acc = 0;
+  for (int i0 = 1; i0 < n; i0 += kChunk) {
+    int32_t v[kChunk];
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) v[k] = (i0 + k < n) ? base[(size_t)(i0 + k) * stride] : 0;
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      acc += v[k];
+      if (i0 + k < n) base[(size_t)(i0 + k) * stride] = acc;
     }
   }
 }
@@ -83,12 +111,7 @@ __global__ void ref_sat_y_kernel(const GridConst gc, int32_t* sat) {
     const int x = (int)(c % X1);
     const int z = (int)((c / X1) % gc.Z) + 1;
     const int a = (int)(c / ((int64_t)X1 * gc.Z));
-    int32_t* base = sat + ((size_t)a * Z1 + z) * Y1 * X1 + x;
-    int32_t acc = 0;
-    for (int y = 1; y < Y1; ++y) {
-      acc += base[(size_t)y * X1];
-      base[(size_t)y * X1] = acc;
-    }
+    column_scan(sat + ((size_t)a * Z1 + z) * Y1 * X1 + x, Y1, (size_t)X1);
   }
 }
 
@@ -99,12 +122,7 @@ __global__ void ref_sat_z_kernel(const GridConst gc, int32_t* sat) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cols; c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t xy = c % ((int64_t)Y1 * X1);
     const int a = (int)(c / ((int64_t)Y1 * X1));
-    int32_t* base = sat + (size_t)a * Z1 * plane + xy;
-    int32_t acc = 0;
-    for (int z = 1; z < Z1; ++z) {
-      acc += base[(size_t)z * plane];
-      base[(size_t)z * plane] = acc;
-    }
+    column_scan(sat + (size_t)a * Z1 * plane + xy, Z1, plane);
   }
 }
 
@@ -134,7 +152,7 @@ cudaError_t launch_ref_symbols(const GridConst& gc, const uint32_t* cnt, const u
 cudaError_t launch_ref_sat(const GridConst& gc, const uint8_t* symA, int32_t* sat, cudaStream_t s) {
   if (gc.K <= 1) return cudaSuccess;
   const int64_t rows = (int64_t)(gc.K - 1) * gc.Z * gc.Y;
-  ref_sat_x_kernel<<<blocks_for(rows, 128), 128, 0, s>>>(gc, symA, sat);
+  ref_sat_x_kernel<<<blocks_for(rows * 32, 256), 256, 0, s>>>(gc, symA, sat);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t cy = (int64_t)(gc.K - 1) * gc.Z * (gc.X + 1);

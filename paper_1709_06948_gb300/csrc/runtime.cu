@@ -597,9 +597,11 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
        "copy rotation table");
     LatticeLevel L{};
     for (int a = 0; a < 6; ++a) {
-      L.r[a] = r[(size_t)l][a];
-      L.r_prev[a] = l > 0 ? r[(size_t)l - 1][a] : 0.0;
       L.m[a] = m[a];
+      for (int32_t i = 0; i < m[a]; ++i) {
+        L.off[a][i] = lattice_step(r[(size_t)l][a], m[a], i);
+        L.off_prev[a][i] = l > 0 ? lattice_step(r[(size_t)l - 1][a], m[a], i) : 0.0;
+      }
     }
     for (int a = 0; a < 3; ++a) L.origin[a] = g->origin[a];
     L.n_rot = n_rot;
@@ -936,7 +938,7 @@ align_status align_search_ex(align_grid* g, const float* xyzB, int64_t nB, int f
   std::memcpy(r, range, sizeof(r));
   const int32_t n_rot = counts[3] * counts[4] * counts[5];
   if (levels >= 1 && (int64_t)n_rot * n_rot <= kMaxLatticeCand && n_rot <= max_rotation_copies(P, n_tiles) &&
-      counts[3] <= kMaxAxisSamples && counts[4] <= kMaxAxisSamples && counts[5] <= kMaxAxisSamples)
+      *std::max_element(counts, counts + 6) <= std::min(kMaxAxisSamples, kLatticeMaxAxis))
     return search_pipelined(g, n_tiles, c, r, counts, P, n_rot, levels, T_out, mi_out, level_best);
   std::vector<double> eta;
   std::vector<float> poses;
