@@ -181,7 +181,8 @@ align_status align_profile(align_grid* grid, int32_t mode, double out[3]);
 
 /* align_reference_noalloc — A's feature map and bbox without allocating anything.
    The paper has no counterpart; this is a library convenience.  align_set_reference
-   allocates working arrays on every call, which some callers cannot do: processes whose
+   allocates working arrays (kept by the grid between calls), which some callers cannot
+   do at all: processes whose
    device memory belongs to another allocator under a fixed budget, and latency-bound
    loops in which a device allocation (it may synchronise the device) is not allowed.
    This entry point computes the same symbols and bbox as align_set_reference followed

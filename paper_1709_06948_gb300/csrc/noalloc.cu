@@ -1,7 +1,8 @@
 // noalloc.cu — reference-scan voxelization without any device allocation.
 //
 // align_set_reference allocates its working arrays (per-voxel counts and z sums) with
-// cudaMalloc on every call.  Some callers cannot do that: a process whose device memory
+// cudaMalloc, and a grid keeps them between calls.  Some callers cannot allocate at all: a
+// process whose device memory
 // is handed out by another framework's allocator under a fixed budget, or a
 // latency-bound loop in which an allocation (cudaMalloc may synchronise the device and
 // take milliseconds) is not allowed.  align_reference_noalloc gives them the same
