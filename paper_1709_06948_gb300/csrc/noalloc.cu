@@ -2,10 +2,9 @@
 //
 // align_set_reference allocates its working arrays (per-voxel counts and z sums) with
 // cudaMalloc, and a grid keeps them between calls.  Some callers cannot allocate at all: a
-// process whose device memory
-// is handed out by another framework's allocator under a fixed budget, or a
-// latency-bound loop in which an allocation (cudaMalloc may synchronise the device and
-// take milliseconds) is not allowed.  align_reference_noalloc gives them the same
+// process whose device memory is handed out by another framework's allocator under a fixed
+// budget, or a latency-bound loop in which an allocation (cudaMalloc may synchronise the
+// device and take milliseconds) is not allowed.  align_reference_noalloc gives them the same
 // A-side result (feature symbol per voxel and occupied bounding box) using a working
 // area that is a fixed array in the library's own device memory.
 //
