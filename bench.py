@@ -206,7 +206,7 @@ SERVE_REQUESTS = 400
 SERVE_RATE_HZ = 200.0
 SERVE_RANGE = np.array([3.0, 3.0, 0.5, math.radians(2.0), math.radians(2.0), math.radians(10.0)])
 SERVE_RES = (0.25, 0.5, 0.75, 1.0)
-SERVE_SLOTS = 16
+SERVE_SLOTS = 8
 
 
 def run_batched(align, steps):
@@ -328,14 +328,14 @@ def run_large(align, steps):
     return out
 
 
-def run_serving(align):
+def run_serving(align, slots=SERVE_SLOTS):
     """Poisson arrivals (200 req/s) of alignment requests against 16 resident references;
     continuous batching server vs the plain loop (one request at a time, one launch per
     lattice level) on the same requests and arrival times."""
     rng = np.random.default_rng(scangen.SEED_BASE + 5)
     scenes = [scangen.lidar_pair(seed=scangen.SEED_BASE + 200 + k, az_step_deg=0.15) for k in range(4)]
     refs = [(k, res) for k in range(4) for res in SERVE_RES]  # 16 references
-    srv = align.align_server_create(96 << 30, SERVE_SLOTS)
+    srv = align.align_server_create(96 << 30, slots)
     ids, grids = [], []
     for k, res in refs:
         spec = scangen.lidar_grid(res)
@@ -403,7 +403,7 @@ def run_serving(align):
            "plain_loop_p99_ms": float(np.percentile(plat, 99) * 1e3),
            "plain_loop_requests_per_s": len(reqs) / (finish - arrivals[0]),
            "plain_loop_mean_service_ms": float(np.mean(service) * 1e3),
-           "steps": st["steps"], "max_active": st["max_active"], "peak_bytes": st["bytes_peak"],
+           "slots": slots, "steps": st["steps"], "max_active": st["max_active"], "peak_bytes": st["bytes_peak"],
            "results_identical_to_plain_loop": bool(same),
            "median_xy_error_m": float(np.median(err)),
            "plain_loop_latency_basis": "measured service times, FIFO queue at the same arrival times"}
@@ -565,7 +565,7 @@ def run_ours(args):
         if not args.no_batched:
             line["batched"] = run_batched(align, max(3, min(args.steps, 10)))
         if not args.no_serving:
-            line["serving"] = run_serving(align)
+            line["serving"] = run_serving(align, args.serve_slots)
         if not args.no_large:
             line["large"] = run_large(align, 2)
     if rank == 0:
@@ -701,6 +701,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the served-requests leg")
     ap.add_argument("--no-refine", action="store_true", help="skip the Nelder-Mead refinement leg")
     ap.add_argument("--no-large", action="store_true", help="skip the large-grid leg")
+    ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS, help="request slots of the served leg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -321,8 +321,8 @@ __device__ __forceinline__ void table_add_slot(const EvalSmem& S, const uint4& e
 // After a sweep: insert the overflow list with the full probe (all threads of the CTA).
 template <int kVW>
 __device__ __forceinline__ void insert_overflow(const EvalSmem& S, const EvalArgs& a, const GridConst& gc) {
-  const uint32_t n = min(*(volatile uint32_t*)&S.flags[2], (uint32_t)a.ovf_cap);
-  const uint4* ovf = a.ovf + (size_t)blockIdx.x * (uint32_t)a.ovf_cap;
+  const uint32_t n = min(*(volatile uint32_t*)&S.flags[2], (uint32_t)kOvfCap);
+  const uint4* ovf = a.ovf + (size_t)blockIdx.x * kOvfCap;
   for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
     const uint4 e = ovf[i];
     const int slot = table_slot(S, e.x, (uint32_t)a.n_buckets);
@@ -374,13 +374,15 @@ __device__ __forceinline__ uint4 run_entry(const Run& r) {
 // Packed-word bound: `acc` ORs every old table word and every run word the lane added.
 // While no n field in it reaches 2^b (2^(b+1) - 2 <= nlim), every add kept the voxel at or
 // below nlim; the sweep's end tests acc once (the exact path takes the pose otherwise).
-template <int kVW>
-__device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count,
+// kCount32: a drain of 32 entries (during the sweep); otherwise `count` (the last drain).
+template <int kVW, bool kCount32>
+__device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count_arg,
                                            const EvalArgs& a, uint32_t& acc) {
+  const uint32_t count = kCount32 ? 32u : count_arg;
   const uint32_t lane = threadIdx.x & 31u;
   __syncwarp();
   uint4 e = lds128(ring + 16u * lane);  // the ring holds 64 entries: always in bounds
-  if (lane >= count) e.x = kEmptyKey;
+  if (!kCount32 && lane >= count) e.x = kEmptyKey;
   const bool valid = e.x != kEmptyKey;
   const uint32_t b = __umulhi(e.x * 0x9E3779B1u, (uint32_t)a.n_buckets);
   const uint32_t kb = S.a_key + 16u * b;
@@ -406,8 +408,8 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
   // home bucket full (or insert race lost): the run goes to the overflow list
   const bool ov = valid && slot < 0;
   const uint32_t i = atom_add_if(ov, S.a_key - kFlagOvf, 1u);
-  const bool ov_ok = ov && i < (uint32_t)a.ovf_cap;
-  stg128_if(ov_ok, a.ovf + ((size_t)blockIdx.x * (uint32_t)a.ovf_cap + (ov_ok ? i : 0u)), e);
+  const bool ov_ok = ov && i < (uint32_t)kOvfCap;
+  stg128_if(ov_ok, a.ovf + ((size_t)blockIdx.x * kOvfCap + (ov_ok ? i : 0u)), e);
   sts32_if(ov && !ov_ok, S.a_key - kFlagFull, 1u);
   // move the entries beyond `count` down, one word at a time (lane l reads entry l + count
   // and writes entry l, which only it has read; entry l + count < 64 for count <= 32)
@@ -427,7 +429,7 @@ __device__ __forceinline__ void ring_push(const EvalSmem& S, uint32_t ring, uint
   sts128_if(done, ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), run_entry<kVW>(r));
   fill += (uint32_t)__popc(m);
   // fill is the same in every lane; the vote lets the compiler know the branch is uniform
-  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVW>(S, ring, fill, 32u, a, acc);
+  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVW, true>(S, ring, fill, 32u, a, acc);
 }
 
 struct PoseRegs {
@@ -484,6 +486,21 @@ __device__ __forceinline__ void load_tile(const float4* src, int t, float4* v) {
     v[j].z = __ldg(z + threadIdx.x + j * kThreads);
   }
 }
+
+// The same load from per-thread pointers into a tile: xy at xy[j*kThreads], z at
+// z[j*kThreads].  The sweep advances the pointers from tile to tile, so that the
+// addresses of the tiles it prefetches are constant offsets from them.
+__device__ __forceinline__ void load_tile_at(const float2* xy, const float* z, float4* v) {
+#pragma unroll
+  for (int j = 0; j < kPPT; ++j) {
+    const float2 p = __ldg(xy + j * kThreads);
+    v[j].x = p.x;
+    v[j].y = p.y;
+    v[j].z = __ldg(z + j * kThreads);
+  }
+}
+constexpr int kTileXY = 2 * kTile;  // tile stride in float2 (kTile float4 slots)
+constexpr int kTileZ = 4 * kTile;   // tile stride in float
 
 // Store point `i` (position within its tile copy) in the tile layout above.
 __device__ __forceinline__ void store_point(float4* out, int64_t i, float x, float y, float z) {
@@ -752,9 +769,14 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs
   Run run{kEmptyKey, 0u, 0u, 0u};
   uint32_t fill = 0u, bad = 0u, acc = 0u;
   float4 buf[kDepth][kPPT];  // register ring of the next kDepth tiles
+  // this thread's slot of tile 0 (x,y and z); tile t is kTileXY / kTileZ further on
+  const float2* xy = reinterpret_cast<const float2*>(src - threadIdx.x) + threadIdx.x;
+  const float* zz = reinterpret_cast<const float*>(src - threadIdx.x) + 2 * kTile + threadIdx.x;
 #pragma unroll
   for (int d = 0; d < kDepth; ++d)
-    if (d < nt) load_tile(src, d, buf[d]);
+    if (d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
+  xy += kDepth * kTileXY;  // the next tile to load: t + kDepth
+  zz += kDepth * kTileZ;
   int next_cut = cut;
   int t = 0;
   for (; t + 2 * kDepth <= nt; t += kDepth) {  // every prefetch in range: no guards
@@ -766,8 +788,10 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs
 #pragma unroll
     for (int d = 0; d < kDepth; ++d) {
       sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad, acc);
-      load_tile(src, t + kDepth + d, buf[d]);
+      load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
     }
+    xy += kDepth * kTileXY;
+    zz += kDepth * kTileZ;
   }
   for (; t < nt; t += kDepth) {
     if (t >= next_cut) {
@@ -779,12 +803,14 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs
     for (int d = 0; d < kDepth; ++d) {
       if (t + d < nt) {
         sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad, acc);
-        if (t + kDepth + d < nt) load_tile(src, t + kDepth + d, buf[d]);
+        if (t + kDepth + d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
       }
     }
+    xy += kDepth * kTileXY;
+    zz += kDepth * kTileZ;
   }
   ring_push<kVW>(S, ring, lane_lt, true, run, fill, a, acc);
-  while (fill > 0u) ring_drain<kVW>(S, ring, fill, min(fill, 32u), a, acc);
+  while (fill > 0u) ring_drain<kVW, false>(S, ring, fill, min(fill, 32u), a, acc);
   if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
   return bad;
 }
