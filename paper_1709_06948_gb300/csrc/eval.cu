@@ -405,18 +405,21 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
       red_add_if(ok, v + 8u, e.w);
     }
   }
-  // home bucket full (or insert race lost): the run goes to the overflow list
+  // home bucket full (or insert race lost): the run goes to the overflow list (rare at
+  // the table's load: the warp skips this unless one of its lanes needs it)
   const bool ov = valid && slot < 0;
-  const uint32_t i = atom_add_if(ov, S.a_key - kFlagOvf, 1u);
-  const bool ov_ok = ov && i < (uint32_t)kOvfCap;
-  stg128_if(ov_ok, a.ovf + ((size_t)blockIdx.x * kOvfCap + (ov_ok ? i : 0u)), e);
-  sts32_if(ov && !ov_ok, S.a_key - kFlagFull, 1u);
-  // move the entries beyond `count` down, one word at a time (lane l reads entry l + count
-  // and writes entry l, which only it has read; entry l + count < 64 for count <= 32)
+  if (__any_sync(kFull, ov)) {
+    const uint32_t i = atom_add_if(ov, S.a_key - kFlagOvf, 1u);
+    const bool ov_ok = ov && i < (uint32_t)kOvfCap;
+    stg128_if(ov_ok, a.ovf + ((size_t)blockIdx.x * kOvfCap + (ov_ok ? i : 0u)), e);
+    sts32_if(ov && !ov_ok, S.a_key - kFlagFull, 1u);
+  }
+  // move the entries beyond `count` down (lane l reads entry l + count and writes entry l,
+  // which only it has read; entry l + count < 64 for count <= 32)
   const bool mv = lane + count < fill;
-  const uint32_t dst = ring + 16u * lane, src = dst + 16u * count;
-#pragma unroll
-  for (uint32_t w = 0; w < 16u; w += 4u) sts32_if(mv, dst + w, lds32(src + w));
+  const uint32_t dst = ring + 16u * lane;
+  const uint4 moved = lds128(dst + 16u * count);
+  sts128_if(mv, dst, moved);
   __syncwarp();
   fill -= count;
 }
@@ -450,7 +453,8 @@ __device__ __forceinline__ void point_key(const VoxelConst& vc, const PoseRegs& 
   } else {
     // Pre-rotated copies hold finite values or +inf (pack_points_kernel), and host poses
     // are finite, so g is never NaN: a saturating floor and unsigned compares decide
-    // "inside" exactly as the float compares would.
+    // "inside" exactly as the float compares would.  dz is meaningful only inside the grid
+    // (outside, the point's run has kEmptyKey and is dropped with its sums).
     const float gx = __fadd_rn(p.x, P.t[0]);
     const float gy = __fadd_rn(p.y, P.t[1]);
     const float gz = __fadd_rn(p.z, P.t[2]);
@@ -459,7 +463,7 @@ __device__ __forceinline__ void point_key(const VoxelConst& vc, const PoseRegs& 
     const uint32_t kz = (uint32_t)__float2int_rd(__fmul_rn(gz, vc.inv_res));
     const bool in = (kx < (uint32_t)vc.X) & (ky < (uint32_t)vc.Y) & (kz < (uint32_t)vc.Z);
     const uint32_t zq = (uint32_t)__float2int_rn(__fmul_rn(gz, 1000.0f));
-    dz = in ? (int)(zq - kz * (uint32_t)vc.res_mm) : 0;
+    dz = (int)(zq - kz * (uint32_t)vc.res_mm);
     key = in ? (kz * (uint32_t)vc.Y + ky) * (uint32_t)vc.X + kx : kEmptyKey;
   }
 }
@@ -732,20 +736,19 @@ __device__ __forceinline__ const float4* pose_tiles(const EvalItem& I, int lp) {
   return I.src + (size_t)src * I.src_stride;
 }
 
-// One tile of this thread's stream: key, run step, ring append of the finished run.
-// `bad` collects dz + dz_bound of every in-grid point (checked against 2^dz_shift).
+// One tile of this thread's stream: key, run step, ring append of the finished run.  No
+// per-point check of dz: the grid constants guarantee 0 <= dz <= res_mm for every point
+// inside the grid (validate_desc).
 template <int kVW, bool kRot, bool kPart>
 __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                            const PoseRegs& P, const float4* pts, int lg, uint32_t part, Run& run,
-                                           uint32_t ring, uint32_t lane_lt, uint32_t& fill, uint32_t& bad,
-                                           uint32_t& acc) {
+                                           uint32_t ring, uint32_t lane_lt, uint32_t& fill, uint32_t& acc) {
 #pragma unroll
   for (int j = 0; j < kPPT; ++j) {
     uint32_t key;
     int dz;
     point_key<kRot>(vc, P, pts[j], key, dz);
     if (kPart && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != part) key = kEmptyKey;
-    bad |= (uint32_t)(dz + vc.dz_bound);
     const bool done = key != run.key;
     ring_push<kVW>(S, ring, lane_lt, done, run, fill, a, acc);
     if (kVW == 2) {
@@ -761,13 +764,13 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
 
 // One pass over all tiles of the pose: every thread streams its own points straight from
 // L2, kDepth tiles ahead.  A run is cut every `cut` tiles so that its 32-bit sums stay
-// below nlim points.  Returns the bad-dz flag.
+// below nlim points.
 template <int kVW, bool kRot, bool kPart>
-__device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
+__device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                                const PoseRegs& P, const float4* src, int nt, int lg, uint32_t part,
                                                uint32_t ring, uint32_t lane_lt, int cut) {
   Run run{kEmptyKey, 0u, 0u, 0u};
-  uint32_t fill = 0u, bad = 0u, acc = 0u;
+  uint32_t fill = 0u, acc = 0u;
   float4 buf[kDepth][kPPT];  // register ring of the next kDepth tiles
   // this thread's slot of tile 0 (x,y and z); tile t is kTileXY / kTileZ further on
   const float2* xy = reinterpret_cast<const float2*>(src - threadIdx.x) + threadIdx.x;
@@ -787,7 +790,7 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs
     }
 #pragma unroll
     for (int d = 0; d < kDepth; ++d) {
-      sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad, acc);
+      sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, acc);
       load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
     }
     xy += kDepth * kTileXY;
@@ -802,7 +805,7 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs
 #pragma unroll
     for (int d = 0; d < kDepth; ++d) {
       if (t + d < nt) {
-        sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, bad, acc);
+        sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, acc);
         if (t + kDepth + d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
       }
     }
@@ -812,7 +815,6 @@ __device__ __forceinline__ uint32_t sweep_pose(const EvalSmem& S, const EvalArgs
   ring_push<kVW>(S, ring, lane_lt, true, run, fill, a, acc);
   while (fill > 0u) ring_drain<kVW, false>(S, ring, fill, min(fill, 32u), a, acc);
   if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
-  return bad;
 }
 
 template <int kVW, bool kRot, bool kOne>
@@ -844,7 +846,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
     }
     const int lp = gp - I.pose_base;
     const VoxelConst vc = voxel_const<kVW>(kOne ? a.one.gc : *S.gc);
-    const int dz_shift = kOne ? a.one.gc.dz_shift : S.gc->dz_shift;
     const int nt = I.n_tiles;
     // runs are cut every `cut` tiles (a multiple of the prefetch depth, where the sweep checks)
     const int cut = max(kDepth, (int)min(vc.nlim / (uint32_t)kPPT, (uint32_t)INT_MAX) / kDepth * kDepth);
@@ -858,10 +859,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
     bool overflowed = false;  // ... because its keys did not fit: more partitions help
     for (int pass = 0; pass < pose_passes; ++pass) {
       if (!full) {
-        const uint32_t bad =
-            lg == 0 ? sweep_pose<kVW, kRot, false>(S, a, vc, P, src, nt, 0, 0u, ring, lane_lt, cut)
-                    : sweep_pose<kVW, kRot, true>(S, a, vc, P, src, nt, lg, (uint32_t)pass, ring, lane_lt, cut);
-        if (bad >> dz_shift) atomicOr(a.err, kErrDzBound);
+        if (lg == 0) sweep_pose<kVW, kRot, false>(S, a, vc, P, src, nt, 0, 0u, ring, lane_lt, cut);
+        else sweep_pose<kVW, kRot, true>(S, a, vc, P, src, nt, lg, (uint32_t)pass, ring, lane_lt, cut);
       }
       __syncthreads();
       if (!full && *(volatile uint32_t*)&S.flags[2] != 0u) {  // runs whose home bucket was full
@@ -947,7 +946,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
           int dz;
           point_key<kRot>(vc, P, v[j], key, dz);
           if (lg > 0 && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != (uint32_t)pass) key = kEmptyKey;
-          bad |= (uint32_t)((uint32_t)(dz + vc.dz_bound) > (uint32_t)(2 * vc.dz_bound));
+          // dz is meaningful inside the grid only (the bound holds there; a cheap assertion)
+          bad |= (uint32_t)(key != kEmptyKey && (uint32_t)(dz + vc.dz_bound) > (uint32_t)(2 * vc.dz_bound));
           if (key != rkey || (kVar && rn >= vc.nlim)) {
             if (rkey != kEmptyKey && rn != 0u) add_run<kVW>(S, wide, rkey, rn, (int)rs1, rs2, nb);
             rkey = key;

@@ -198,9 +198,16 @@ align_status validate_desc(const align_grid_desc* d, GridConst* gc) {
     if (j > 0 && gc->var_thresh[j] < gc->var_thresh[j - 1])
       return fail(ALIGN_E_INVALID, "var_thresh must be ascending");
   }
-  // |dz| bound: voxel edge, rounding to the mm, and the drift of k_z * res_mm against
-  // 1000 * k_z * res when res is not exactly a whole number of mm in binary.
+  // z offsets: for a point inside the grid (0 <= fl(g_z * inv_res) < Z), the FP32 errors of
+  // inv_res = fl(1/res), fl(g_z * inv_res) and fl(g_z * 1000) together with the drift of
+  // k_z * res_mm against 1000 * k_z * res move 1000 * g_z by at most
+  // Z * res_mm * 2.2 * 2^-24 + Z * |1000 res - res_mm| + 2^-24 * (Z * res_mm + 1) < 1/2 mm
+  // under the two limits below, so zq = round(g_z * 1000) lies in [k_z, k_z + 1] * res_mm
+  // and 0 <= dz <= res_mm: the sweep needs no per-point check.
+  if ((int64_t)gc->Z * res_mm >= (int64_t(1) << 20))
+    return fail(ALIGN_E_INVALID, "the grid is too tall: Z * res must stay below 1,048 m");
   const double drift = std::fabs(mm - (double)res_mm) * (double)gc->Z;
+  if (drift >= 0.25) return fail(ALIGN_E_INVALID, "res_m is too far from a whole number of mm for Z layers");
   gc->dz_bound = (int32_t)(res_mm + 4 + (int64_t)std::ceil(drift));
   int m = 0;
   while ((1 << m) <= 2 * gc->dz_bound) ++m;

@@ -75,6 +75,7 @@ def test_no_gpu_fails_loudly():
     dict(res_m=0.0), dict(res_m=0.0004), dict(res_m=0.3333), dict(dims=(0, 4, 4)), dict(dims=(1 << 21, 4, 4)),
     dict(feature=5), dict(var_levels=0), dict(var_levels=64), dict(feature=2, count_levels=8, var_levels=8),
     dict(var_thresh=[5, 3] + [0] * 12),
+    dict(dims=(8, 8, 2098)),  # 2,098 layers of 0.5 m: z above 2^20 mm, beyond the exact z-offset bound
 ])
 def test_invalid_grid_rejected_before_gpu(bad):
     from paper_1709_06948_gb300 import align
