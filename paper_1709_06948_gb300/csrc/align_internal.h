@@ -35,6 +35,8 @@ struct GridConst {
   int32_t ns_shift;       // ns, the shift of n in the packed word
   int32_t wide_shift;     // ns + b, b the largest with 2^(b+1) - 2 <= nlim_pack: two n fields
                           // below 2^b sum to at most nlim_pack
+  int32_t sym32;          // nlim < 2^16 and every var_thresh < 2^32 (the table scan's symbol
+                          // test then multiplies 32-bit values)
   int32_t boxA[6];        // A's occupied bbox (xmin > xmax when empty)
   uint64_t div_x, div_y;  // floor((2^64 - 1) / X) + 1 (0 when X == 1): k / X = umulhi64(div_x, k) for k < 2^32
   uint32_t count_thresh[kMaxLevels];

@@ -545,14 +545,23 @@ __device__ __forceinline__ int feature_symbol_small(const GridConst& gc, uint32_
   }
   if (gc.feature != 0) {  // variance level: #{j : n*S2 - S1^2 >= vt[j] * n^2}
     const uint64_t spread = (uint64_t)n * s2 - (uint64_t)((int64_t)s1 * s1);  // >= 0 (Cauchy-Schwarz)
-    const uint64_t n2 = (uint64_t)n * n;
     int lo = 0, hi = gc.Lv - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      const uint64_t t = (uint64_t)gc.var_thresh[mid];  // thresholds are >= 0
-      const bool reached = __umul64hi(t, n2) == 0ull && t * n2 <= spread;
-      if (reached) lo = mid + 1;
-      else hi = mid;
+    if (gc.sym32) {  // n < 2^16 and every threshold < 2^32: t * n^2 is one 32 x 32-bit product
+      const uint32_t n2 = n * n;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((uint64_t)(uint32_t)gc.var_thresh[mid] * n2 <= spread) lo = mid + 1;
+        else hi = mid;
+      }
+    } else {
+      const uint64_t n2 = (uint64_t)n * n;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const uint64_t t = (uint64_t)gc.var_thresh[mid];  // thresholds are >= 0
+        const bool reached = __umul64hi(t, n2) == 0ull && t * n2 <= spread;
+        if (reached) lo = mid + 1;
+        else hi = mid;
+      }
     }
     lv = lo;
   }

@@ -229,6 +229,9 @@ align_status validate_desc(const align_grid_desc* d, GridConst* gc) {
   int b = 0;
   while (b < 30 && (2ull << (b + 1)) - 2ull <= (uint64_t)gc->nlim_pack) ++b;
   gc->wide_shift = std::min(31, best_ns + b);
+  gc->sym32 = gc->nlim < 65536u ? 1 : 0;
+  for (int j = 0; j + 1 < Lv; ++j)
+    if (gc->var_thresh[j] >= (int64_t(1) << 32)) gc->sym32 = 0;
   for (int i = 0; i < 3; ++i) gc->boxA[i] = INT_MAX, gc->boxA[3 + i] = INT_MIN;
   // division of 32-bit keys by X and Y as a 64-bit multiply-high (Lemire, Kaser and Kurz,
   // "Faster remainder by direct computation", 2019: exact for every 32-bit dividend)
