@@ -771,6 +771,24 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
   }
 }
 
+// The run step of one point whose key and dz are known: append the finished run, extend or
+// restart the run.
+template <int kVW>
+__device__ __forceinline__ void run_step(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc, uint32_t key,
+                                         int dz, Run& run, uint32_t ring, uint32_t lane_lt, uint32_t& fill,
+                                         uint32_t& acc) {
+  const bool done = key != run.key;
+  ring_push<kVW>(S, ring, lane_lt, done, run, fill, a, acc);
+  if (kVW == 2) {
+    run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
+  } else {
+    run.w = (done ? 0u : run.w) + 1u;
+    if (kVW == 3) run.s1 = (done ? 0u : run.s1) + (uint32_t)dz;
+  }
+  if (kVW > 1) run.s2 = (done ? 0u : run.s2) + (uint32_t)(dz * dz);
+  run.key = key;
+}
+
 // One pass over all tiles of the pose: every thread streams its own points straight from
 // L2, kDepth tiles ahead.  A run is cut every `cut` tiles so that its 32-bit sums stay
 // below nlim points.
@@ -797,11 +815,24 @@ __device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a,
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
+    // the keys of the kDepth buffered tiles first (independent of one another), then the
+    // next loads into the freed buffers, then the run steps in stream order
+    uint32_t keys[kDepth][kPPT];
+    int dzs[kDepth][kPPT];
 #pragma unroll
-    for (int d = 0; d < kDepth; ++d) {
-      sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, acc);
-      load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
-    }
+    for (int d = 0; d < kDepth; ++d)
+#pragma unroll
+      for (int j = 0; j < kPPT; ++j) {
+        point_key<kRot>(vc, P, buf[d][j], keys[d][j], dzs[d][j]);
+        if (kPart && keys[d][j] != kEmptyKey && ((keys[d][j] * 0x85EBCA77u) >> (32 - lg)) != part)
+          keys[d][j] = kEmptyKey;
+      }
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d)
+#pragma unroll
+      for (int j = 0; j < kPPT; ++j) run_step<kVW>(S, a, vc, keys[d][j], dzs[d][j], run, ring, lane_lt, fill, acc);
     xy += kDepth * kTileXY;
     zz += kDepth * kTileZ;
   }
