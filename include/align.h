@@ -66,7 +66,7 @@ typedef enum {
   ALIGN_E_OOM = -2,        /* device or pinned host allocation failed */
   ALIGN_E_CUDA = -3,       /* CUDA runtime error, or no usable GPU */
   ALIGN_E_BUSY = -4,       /* server admission refused (queue full / over budget) */
-  ALIGN_E_TIMEOUT = -5,    /* a bounded device or host wait gave up */
+  ALIGN_E_TIMEOUT = -5,    /* a bounded wait gave up (align_wait) */
   ALIGN_E_NOREF = -6,      /* align_set_reference has not been called on this grid */
   ALIGN_E_INTERNAL = -7    /* a kernel reported a violated internal bound */
 } align_status;

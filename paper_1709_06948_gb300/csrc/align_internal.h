@@ -15,7 +15,7 @@ constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 // Error bits written by kernels into the grid's error word.
 enum : uint32_t {
   kErrDzBound = 1u,       // |dz| above the bound the 32-bit sums were sized for
-  kErrWaitTimeout = 2u,   // a bounded mbarrier wait gave up
+  // 2u: unused (an earlier bounded-wait bit)
   kErrPassLimit = 4u,     // key partitioning could not make the table fit
   kErrLattice = 8u,       // a device-built lattice level found its previous argmax out of range
 };

@@ -240,7 +240,6 @@ align_status collect(align_batch* b) {
   if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->stats[6] = (int64_t)std::llround(ms * 1000.0);
   // reset the error word, the partition maximum and the wide-voxel count (per launch)
   BCU(cudaMemsetAsync(b->status.p, 0, 12, b->stream), "reset status");
-  if (v[0] & kErrWaitTimeout) return report_error(ALIGN_E_TIMEOUT, "a bounded device wait gave up");
   if (v[0] & kErrDzBound) return report_error(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");
   if (v[0] & kErrPassLimit) return report_error(ALIGN_E_INTERNAL, "key partitioning limit reached");
   return ALIGN_OK;

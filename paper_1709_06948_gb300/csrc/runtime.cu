@@ -493,7 +493,6 @@ align_status collect_status(align_grid* g) {
     g->passes_seed[0] = (int32_t)vals[1];
   g->stats[0] = vals[1];
   g->stats[1] = vals[2];
-  if (vals[0] & kErrWaitTimeout) return fail(ALIGN_E_TIMEOUT, "a bounded device wait gave up");
   if (vals[0] & kErrDzBound) return fail(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");
   if (vals[0] & kErrPassLimit) return fail(ALIGN_E_INTERNAL, "key partitioning limit reached");
   if (vals[0] & kErrLattice) return fail(ALIGN_E_INTERNAL, "a lattice level found its argmax out of range");
