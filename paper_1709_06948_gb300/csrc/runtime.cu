@@ -624,6 +624,7 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
     L.rots = g->rots.as<float>();
     L.err = g->err.as<uint32_t>();
     CU(launch_lattice_level(L, g->stream), "launch lattice level");
+    g->stats[4] += 1;
     EvalOut o{};
     o.mi = g->mi.as<float>();
     o.argmax = g->argmax.as<int64_t>();
