@@ -137,17 +137,30 @@ def measured_peaks():
         return None
 
 
+def code_digest(path):
+    """sha256 of a source file's code: `//` comments, trailing blanks and empty lines
+    removed (a comment-only edit leaves the kernel, and its profile, unchanged)."""
+    lines = []
+    with open(path, encoding="utf-8") as f:
+        for line in f:
+            i = line.find("//")
+            line = (line[:i] if i >= 0 else line).rstrip()
+            if line:
+                lines.append(line)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def committed_traffic():
     """Per-launch DRAM bytes of the eval kernel from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    taken on the current kernel code (else None)."""
     path = os.path.join(ROOT, "profiles", "eval_kernel_lidar120k.md")
     src = os.path.join(ROOT, "paper_1709_06948_gb300", "csrc", "eval.cu")
     try:
         text = open(path).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        digest = code_digest(src)
     except Exception:
         return None
-    m_sha = re.search(r"eval\.cu sha256:\s*([0-9a-f]{64})", text)
+    m_sha = re.search(r"eval\.cu code sha256[^:]*:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_b or m_sha.group(1) != digest:
         return None

@@ -8,20 +8,21 @@
 // tile, the points s*L, s*L+1, ... of B's given order (L = kPPT * tiles), so each thread
 // walks a stretch of consecutive scan points (stream_of: which stream a thread walks).
 //
-// eval_kernel: persistent, one CTA per SM, one pose at a time per CTA; the poses of all
-// items are one list, and each pose brings its item's grid constants.  Every thread
-// streams its own points straight from L2, four tiles ahead, computes the voxel key and
-// dz (device_common.cuh) and keeps the run of equal keys it is walking in registers
-// (n, S1, S2).  Finished runs go to a per-warp ring in shared memory; 32 at a time the
-// whole warp adds them into a shared-memory open-addressing hash table (buckets of 4
-// keys, 32-bit shared atomics).  After the sweep one pass over the table gives the
-// feature symbols, B's occupied bbox and the partial joint histogram c[a][b >= 1] of the
-// occupied voxels inside A's bbox.
+// eval_kernel: persistent, one CTA per SM, one pose at a time per CTA; a launch covers the
+// poses of one scan pair (grid constants in the kernel parameters) or, in the multi-pair
+// mode, of several pairs, each pose bringing its pair's constants.  Every thread streams
+// its own points straight from L2, four tiles ahead, computes the voxel keys and z
+// offsets of the buffered tiles, then keeps the run of equal keys it is walking in
+// registers (the table layout's value words: n and the z sums).  Finished runs go to a
+// per-warp ring in shared memory; 32 at a time the whole warp adds them into a
+// shared-memory open-addressing hash table (buckets of 4 keys, 32-bit shared atomics).
+// After the sweep one pass over the table gives the feature symbols, B's occupied bbox
+// and the partial joint histogram c[a][b >= 1] of the occupied voxels inside A's bbox.
 //  - A pose with more occupied voxels than fit the table, or with a voxel so full that
-//    its 32-bit sums may have wrapped, is finished by redo_kernel: plain sweeps with the
-//    keys split into 2, 4, ... hash partitions, each run added at once, and 64-bit side
-//    sums in global memory for voxels beyond the 32-bit bound.  A crowded table makes the
-//    CTA sweep its following poses in twice as many partitions.
+//    its table sums may have wrapped, is finished by redo_kernel: plain sweeps with the
+//    keys split into 2, 4, ... hash partitions, each run added at once, the plain count in
+//    the table and S1, S2 in 64-bit sums in global memory.  A crowded table makes the CTA
+//    sweep its following poses in twice as many partitions.
 //
 // compose_kernel: per pose, the overlap box (Algorithm 1), A's symbol counts over it from
 // per-symbol prefix sums, the phi column h[a][0], then Eqs. 2-5 in FP32 with a fixed
