@@ -528,7 +528,6 @@ void lattice_sample(const double c[6], const double r[6], const int32_t m[6], in
 align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6], const double r0[6],
                               const int32_t m[6], int64_t P, int32_t n_rot, int32_t levels, double T_out[6],
                               float* mi_out, int64_t* level_best) {
-  const int64_t n_trans = P / n_rot;
   const size_t slot = (size_t)n_rot * n_rot * 9;  // floats of one level's rotation table
   struct Rec {
     int64_t am;
@@ -655,7 +654,6 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
     const uint32_t u = (ord & 0x80000000u) ? (ord & 0x7FFFFFFFu) : ~ord;
     std::memcpy(mi_out, &u, 4);
   }
-  (void)n_trans;
   return ALIGN_OK;
 }
 
