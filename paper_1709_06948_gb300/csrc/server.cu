@@ -86,6 +86,9 @@ struct align_server {
   bool stop = false;
   std::vector<align_batch*> batches;  // per worker
   std::vector<std::thread> workers;
+  // device buffers of retired requests' points, kept for reuse: freeing device memory
+  // synchronises the whole device (the other worker's launches included)
+  std::vector<mialign::DevBuf> spare;
   int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
   double now() const {
@@ -109,7 +112,11 @@ void finish_locked(align_server* s, Req* r, int32_t status) {
   r->status = status;
   r->t_done = s->now();
   s->used -= std::min(s->used, r->bytes);
-  r->dev_xyz.release();
+  if (r->dev_xyz.p) {  // back to the spare buffers (at most max_slots are kept)
+    if ((int32_t)s->spare.size() < s->max_slots) s->spare.push_back(r->dev_xyz);
+    else r->dev_xyz.release();
+    r->dev_xyz = DevBuf{};
+  }
   s->pending.erase(r->ticket);
   s->done[r->ticket] = r;
   s->stats[2] += 1;
@@ -165,6 +172,15 @@ void worker_main(align_server* s, size_t w) {
       align_grid* g = s->refs[(size_t)r->ref].grid;
       if (!r->uploaded) {
         if (r->nB > 0) {
+          {  // a spare buffer large enough, if there is one
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (size_t k = 0; k < s->spare.size(); ++k)
+              if (s->spare[k].cap >= (size_t)r->nB * 12) {
+                r->dev_xyz = s->spare[k];
+                s->spare.erase(s->spare.begin() + (ptrdiff_t)k);
+                break;
+              }
+          }
           cudaError_t e = r->dev_xyz.ensure((size_t)r->nB * 12);
           if (e == cudaSuccess) e = cudaMemcpy(r->dev_xyz.p, r->xyz.data(), (size_t)r->nB * 12, cudaMemcpyHostToDevice);
           if (e != cudaSuccess) {
@@ -402,8 +418,12 @@ align_status align_server_destroy(align_server* s) {
   cudaSetDevice(s->device);
   for (Req* r : s->queue) delete r;
   for (auto& act : s->active)
-    for (Req* r : act) delete r;
+    for (Req* r : act) {
+      r->dev_xyz.release();
+      delete r;
+    }
   for (auto& kv : s->done) delete kv.second;
+  for (DevBuf& b : s->spare) b.release();
   for (Ref& f : s->refs) align_destroy_grid(f.grid);
   for (align_batch* b : s->batches) align_batch_destroy(b);
   delete s;
