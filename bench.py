@@ -212,7 +212,7 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------------------
-# batched pairs (many pairs in one persistent launch) and served requests
+# batched pairs (many pairs in one captured launch sequence) and served requests
 # --------------------------------------------------------------------------------------
 BATCH_PAIRS = 64
 SERVE_REQUESTS = 400
@@ -224,7 +224,7 @@ SERVE_SLOTS = 8
 
 def run_batched(align, steps):
     """64 pairs (20k-130k points, 0.25/0.5/1 m grids), each with its own 4,096-pose lattice,
-    in one persistent launch (graph replay, tuned kernel shape); against one align_eval_mi
+    in one launch sequence (graph replay, tuned kernel shape); against one align_eval_mi
     launch per pair on the same inputs."""
     pairs = scangen.batched_pairs(BATCH_PAIRS)
     grids, items = [], []
@@ -267,7 +267,7 @@ def run_batched(align, steps):
     dev_s = statistics.median(dev_us) / 1e6
     out = {"workload": f"{BATCH_PAIRS} pairs, points log-uniform 20k-130k, grids 0.25/0.5/1 m cycled "
                        "(320x320x32, 160x160x16, 80x80x8), z-variance 16 symbols, 4,096 lattice poses each, "
-                       "one persistent launch replayed as a CUDA graph",
+                       "one launch sequence replayed as a CUDA graph",
            "points": [int(p.xyzB.shape[0]) for p in pairs][:8] + ["..."],
            "poses_per_launch": P,
            "pose_evals_per_s_device": P / dev_s,

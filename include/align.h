@@ -204,8 +204,9 @@ align_status align_reference_noalloc(const align_grid_desc* desc, const float* x
 
 /* ---------------------------------------------------------------------------------
    Batching: many scan pairs, each with its own grid (reference scan A resident) and its
-   own pose batch, evaluated in one persistent launch (Algorithm 1's MI evaluation for
-   every pair and pose; Eqs. 1-5).  Results are identical to align_eval_mi on each pair.
+   own pose batch, evaluated in one launch sequence on the batch's stream, capturable as
+   one CUDA graph (Algorithm 1's MI evaluation for every pair and pose; Eqs. 1-5).  Results
+   are identical to align_eval_mi on each pair.
    --------------------------------------------------------------------------------- */
 typedef struct align_pair {
   align_grid* grid;        /* reference set; every grid of a batch on the batch's device */
@@ -235,8 +236,10 @@ enum {
 align_status align_batch_create(void* cuda_stream, align_batch** out);
 align_status align_batch_destroy(align_batch* b);
 
-/* Evaluate every pair's poses in one persistent launch (plus packing, composition and
-   argmax launches).  Inputs are copied into the batch's workspace first, so the caller's
+/* Evaluate every pair's poses in one launch sequence: one packing launch for all pairs,
+   then per pair the persistent eval kernel (and its exact-path kernel) with the pair's own
+   table layout, then one composition and one argmax launch for all pairs.  Inputs are
+   copied into the batch's workspace first, so the caller's
    buffers may be reused when the call returns; the call waits for the results.  Pairs
    with P == 0 get argmax -1.  ALIGN_E_INVALID for bad arguments, ALIGN_E_NOREF if a grid
    has no reference, ALIGN_E_OOM / ALIGN_E_CUDA as usual. */

@@ -388,7 +388,7 @@ def align_reference_noalloc(desc_kw: dict, xyzA, symA_out, boxA_out, stream=None
 
 
 # ---------------------------------------------------------------------------------------
-# batching: many scan pairs in one persistent launch
+# batching: many scan pairs in one launch sequence (one CUDA graph when captured)
 # ---------------------------------------------------------------------------------------
 def _stream_raw(stream):
     stream_obj = stream
