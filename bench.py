@@ -39,13 +39,13 @@ UNIT = "pose-evals/s"
 LEVELS = 6
 COUNTS = (8, 8, 2, 2, 2, 8)
 RANGE = np.array([2.0, 2.0, 0.25, math.radians(1.0), math.radians(1.0), math.radians(5.0)])
-# Algorithmic work of the voxel map per (point, pose) and of the accumulation per in-grid
-# (point, pose), in 32-bit lane operations (see the design notes for the count).
-OPS_MAP = 29
-OPS_ACC = 4
-SM_COUNT_NOMINAL = 152
-LANES_PER_SM = 128
-SM_MAX_MHZ_NOMINAL = 2070.0
+# Algorithmic ALU work per (point, pose) in 32-bit lane operations: transform, voxel key,
+# dz and bounds, with the 9-operation rotation (OPS_MAP) and with the rotation amortised
+# across the translations that share it (OPS_MAP_AMORTISED).  Shared-memory atomics: three
+# per occupied voxel of a pose (n, S1, S2).
+OPS_MAP = 24
+OPS_MAP_AMORTISED = 15
+ATOMICS_PER_VOXEL = 3
 
 
 def workload_config(pair, levels):
@@ -167,6 +167,48 @@ def committed_traffic():
     return float(m_b.group(1))
 
 
+def host_cpu():
+    """Host CPU model and core count (for the CPU baseline)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
+def measure_peaks(align, gpu_id, reps=5):
+    """Measured throughput peaks of this GPU (align_microbench), with the SM clock sampled
+    while they run."""
+    import torch
+    buf = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.3)
+    t0 = time.time()
+    r = {}
+    for k, name in align.MICROBENCH_KINDS.items():
+        for _ in range(3):  # repeat the set so the sampler sees every kind under load
+            rate, ms, ops = align.align_microbench(k, buf, reps=reps)
+            if name not in r or rate > r[name]["per_s"]:
+                r[name] = {"per_s": rate, "ms": ms, "ops": ops}
+    t1 = time.time()
+    clocks = sampler.stop(t0, t1)
+    del buf
+    alu = max(r["fp32 ffma lane-ops"]["per_s"], r["int32 add/xor lane-ops"]["per_s"])
+    return {"alu_lane_ops_per_s": alu, "keymix_lane_ops_per_s": r["voxel-map mix lane-ops"]["per_s"],
+            "smem_red_random_per_s": r["shared red.add (random words)"]["per_s"],
+            "smem_atom_random_per_s": r["shared atom.add (random words)"]["per_s"],
+            "l2_atomic_per_s": r["L2 atomic add (random words)"]["per_s"],
+            "all": {k: v["per_s"] for k, v in r.items()}, "clocks": clocks,
+            "how": f"align_microbench, fastest of {reps} runs x 3 rounds, 2 x 1,024-thread CTAs per SM, "
+                   "CUDA events"}
+
+
 # --------------------------------------------------------------------------------------
 # CPU oracle (reference arm and the cpu_baseline leg)
 # --------------------------------------------------------------------------------------
@@ -190,7 +232,7 @@ def run_reference(args):
     import oracle
     pair = scangen.lidar_pair()
     cores = oracle.host_cores()
-    sample = 128
+    sample = 4096
     for _ in range(args.warmup):
         oracle_rate(pair, sample, cores)
     times = []
@@ -199,8 +241,8 @@ def run_reference(args):
         times.append(dt)
     total = sum(times)
     value = sample * args.steps / total
-    desc = (f"{sample} level-0 lattice poses of the 120k-point pair per step, oracle (dense per-pose arrays, "
-            f"FP64 MI) on {cores} host threads")
+    desc = (f"all {sample} level-0 lattice poses of the 120k-point pair per step (one of the 6 levels of a "
+            f"search step), oracle (dense per-pose arrays, FP64 MI) on {cores} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -473,7 +515,7 @@ def run_ours(args):
     # in-grid point count of B at the lattice centre (for the accumulation op count)
     ident = align.align_round_poses(spec.origin, np.zeros((1, 6)))[0]
     acc, _ = align.align_accumulate(L, pair.xyzB, ident)
-    n_in = int(acc[:, 0].sum())
+    occ = int(np.count_nonzero(acc[:, 0]))
     del acc
 
     dev_props = torch.cuda.get_device_properties(local)
@@ -522,11 +564,14 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e2e_s = 0.0
     for _ in range(e2e_steps):
+        flush.zero_()  # the same cold L2 as the device-timed steps; not timed
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         align.align_set_reference(L, A_h)
-        align.align_search(L, B_h, init, RANGE, levels=LEVELS)
-    e2e_s = time.perf_counter() - t0
+        align.align_search(L, B_h, init, RANGE, levels=LEVELS)  # returns T on the host: synchronised
+        e2e_s += time.perf_counter() - t0
     if dist is not None:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -535,20 +580,43 @@ def run_ours(args):
     h2d = (pair.xyzA.shape[0] + pair.xyzB.shape[0]) * 12 + LEVELS * P * 48
     d2h = 24 + LEVELS * (8 + 12 + 4)
 
+    # ---- measured peaks (micro-benchmarks on this GPU, clocks sampled while they run) ----
+    peaks = measure_peaks(align, gpu_id) if not args.no_peaks else None
+
     # ---- roofline of the dominant kernel (eval) ----
     eval_ms = prof[0] / max(prof[2], 1)
     nB = pair.xyzB.shape[0]
-    ops_per_launch = P * (nB * OPS_MAP + n_in * OPS_ACC)
+    ops_per_launch = P * nB * OPS_MAP
     achieved = ops_per_launch / (eval_ms / 1000.0) / 1e12
-    sm_count = dev_props.multi_processor_count
-    peak = sm_count * LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved_am = P * nB * OPS_MAP_AMORTISED / (eval_ms / 1000.0) / 1e12
     traffic = committed_traffic()
+    if peaks is not None:
+        peak = peaks["alu_lane_ops_per_s"] / 1e12
+        basis = (f"measured: fastest of FP32 FFMA and INT32 add/xor issue micro-benchmarks on this GPU at "
+                 f"{peaks['clocks']['sm_mhz']} MHz median SM clock (of measured peak)")
+    else:
+        peak = dev_props.multi_processor_count * 128 * 2070.0e6 / 1e12
+        basis = "derived: SMs x 128 lanes x 2,070 MHz (of derived peak; micro-benchmarks skipped)"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "eval_kernel", "eval_kernel_ms": eval_ms,
                 "ops_per_launch": ops_per_launch,
-                "peak_basis": f"{sm_count} SMs x {LANES_PER_SM} int32/fp32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz "
-                              "(nominal max SM clock; of derived peak, no measured ALU peak exists)",
+                "ops_basis": f"{OPS_MAP} lane-ops per (point, pose) x {nB} points x {P} poses",
+                "achieved_amortised": achieved_am, "frac_amortised": achieved_am / peak,
+                "amortised_basis": f"{OPS_MAP_AMORTISED} lane-ops per (point, pose): the rotation shared by the "
+                                   "translations of a lattice (the kernel reads pre-rotated copies)",
+                "peak_basis": basis,
                 "kernel_share_of_step": (prof[0] / total_ms) if total_ms > 0 else None}
+    if peaks is not None:
+        atom = P * occ * ATOMICS_PER_VOXEL / (eval_ms / 1000.0)
+        roofline["shared_atomics"] = {
+            "achieved_per_s": atom, "peak_per_s": peaks["smem_red_random_per_s"],
+            "frac": atom / peaks["smem_red_random_per_s"],
+            "basis": f"{ATOMICS_PER_VOXEL} atomics per occupied voxel x {occ} occupied voxels (lattice centre) x "
+                     f"{P} poses; peak: shared red.add on random words (measured)"}
+        roofline["mix_peak"] = {"lane_ops_per_s": peaks["keymix_lane_ops_per_s"],
+                                "frac": achieved * 1e12 / peaks["keymix_lane_ops_per_s"],
+                                "basis": "the voxel map's own instruction mix (with float-to-int conversions) "
+                                         "as a micro-benchmark"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -557,6 +625,8 @@ def run_ours(args):
             "gpu_launches": int(launches), "clocks": clocks,
             "result_check": ({"T": [float(x) for x in T], "T_true": [float(x) for x in pair.T], "mi": mi}
                              if args.mode == "search" else {"argmax": int(am_dev.item()), "mi_max": float(mi_dev.max())})}
+    if peaks is not None:
+        line["peaks"] = peaks
     if args.mode == "eval":
         line["config"]["workload"] = (f"lidar-120k eval: set_reference + one align_eval_mi of {P} lattice poses "
                                       "(device-resident inputs and outputs)")
@@ -566,11 +636,16 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.mode == "search":
         import oracle
         cores = oracle.host_cores()
-        n_sample = 4096
-        rate, dt = oracle_rate(pair, n_sample, cores)
+        n_all, n_one = 4096, 2048
+        rate, dt = oracle_rate(pair, n_all, cores)
+        rate1, dt1 = oracle_rate(pair, n_one, 1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{n_sample} level-0 lattice poses (of 4,096) on the same pair, "
-                                          f"{dt:.1f} s wall on {cores} threads (MI evaluations only)"}
+                                "sample": f"{n_all} level-0 lattice poses (of 4,096) on the same pair, "
+                                          f"{dt:.1f} s wall on {cores} threads (MI evaluations only)",
+                                "one_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                                             "sample": f"the first {n_one} of those poses on 1 thread, "
+                                                       f"{dt1:.1f} s wall"},
+                                "host": host_cpu()}
     if rank == 0 and ws == 1 and args.mode == "search" and not args.no_refine:
         line["refine"] = run_refine(align, pair, L, np.array(T, dtype=np.float64))
     L.close()
@@ -695,6 +770,19 @@ def run_surface(args):
     return 0
 
 
+def run_peaks(args):
+    """The measured peaks alone (one JSON line)."""
+    import torch
+    from paper_1709_06948_gb300 import align
+    torch.cuda.set_device(0)
+    props = torch.cuda.get_device_properties(0)
+    uuid = getattr(props, "uuid", None)
+    gpu_id = None if uuid is None else (str(uuid) if str(uuid).startswith("GPU-") else "GPU-" + str(uuid))
+    print(json.dumps({"mode": "peaks", "gpu": props.name, "sms": props.multi_processor_count,
+                      "peaks": measure_peaks(align, gpu_id)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -702,11 +790,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="search", choices=["search", "eval", "accuracy", "surface"],
+    ap.add_argument("--mode", default="search", choices=["search", "eval", "accuracy", "surface", "peaks"],
                     help="search: reference build + 6-level search per step (default); "
                          "eval: reference build + one align_eval_mi of --poses poses per step; "
                          "accuracy: final error vs initial error (synthetic Figs. 4-5); "
-                         "surface: MI cost surfaces around the truth (synthetic Fig. 6)")
+                         "surface: MI cost surfaces around the truth (synthetic Fig. 6); "
+                         "peaks: the throughput micro-benchmarks alone")
     ap.add_argument("--pairs", type=int, default=4, help="accuracy mode: pairs per initial error")
     ap.add_argument("--surface-out", default=None, help="surface mode: prefix of .npy files for the surfaces")
     ap.add_argument("--poses", type=int, default=4096)
@@ -715,6 +804,7 @@ def main():
     ap.add_argument("--no-refine", action="store_true", help="skip the Nelder-Mead refinement leg")
     ap.add_argument("--no-large", action="store_true", help="skip the large-grid leg")
     ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS, help="request slots of the served leg")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the peak micro-benchmarks")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -724,6 +814,8 @@ def main():
         return run_accuracy(args)
     if args.mode == "surface":
         return run_surface(args)
+    if args.mode == "peaks":
+        return run_peaks(args)
     return run_ours(args)
 
 

@@ -172,12 +172,34 @@ align_status align_refine_nm(align_grid* grid, const float* xyzB, int64_t nB, in
    launch, [4] kernels launched by this grid since creation. */
 align_status align_eval_stats(align_grid* grid, int64_t out[5]);
 
+/* Poses of the last evaluation on this grid (align_eval_mi, align_accumulate or the last
+   level of a search) that the exact path finished: poses whose voxels did not fit the
+   shared-memory table at the partition count in use, or whose per-voxel sums could exceed
+   the table's 32-bit words.  Their results are the same as every other pose's; this
+   listing serves parity checks.  Waits for the grid's stream.  *n_out: how many there were;
+   out (host, may be NULL when cap is 0): the first min(cap, *n_out) pose indices, ascending. */
+align_status align_eval_redo_poses(align_grid* grid, int64_t* out, int64_t cap, int64_t* n_out);
+
 /* Kernel timing with CUDA events recorded on the grid's stream around every eval
    kernel and every compose+argmax pair.  mode 1: enable and reset the totals;
    mode 0: disable; mode 2: only read.  out (may be NULL): [0] total eval-kernel ms,
    [1] total compose+argmax ms, [2] eval launches timed.  Every call of this function
    first waits for the launches recorded so far and adds them to the totals. */
 align_status align_profile(align_grid* grid, int32_t mode, double out[3]);
+
+/* Micro-benchmarks of this GPU's throughputs that bound the MI evaluation (the measured
+   denominators of its roofline; not part of the method).  kind:
+     0  FP32 FFMA lane operations          1  INT32 add/xor lane operations
+     2  the voxel map's own per-point mix (FADD, FMUL, float-to-int floor, compares, IMAD)
+     3  shared 32-bit red.add, one bank per lane      4  the same with atom.add (returns)
+     5  shared 32-bit red.add, random words of 32 KiB 6  the same with atom.add
+     7  L2 32-bit atomic adds on random words of an L2-resident region (up to 16 MiB)
+   dev_buf: a device buffer of buf_bytes >= 1 MiB the kernels may overwrite (caller-owned).
+   The work runs on cuda_stream (NULL = legacy default stream) `reps` times after one
+   warm-up; out[0] = operations per second of the fastest run, out[1] = its milliseconds,
+   out[2] = operations per run.  Synchronises the stream. */
+align_status align_microbench(int32_t kind, void* dev_buf, int64_t buf_bytes, int32_t reps, void* cuda_stream,
+                              double out[3]);
 
 /* align_reference_noalloc — A's feature map and bbox without allocating anything.
    The paper has no counterpart; this is a library convenience.  align_set_reference
@@ -196,7 +218,9 @@ align_status align_profile(align_grid* grid, int32_t mode, double out[3]);
      cuda_stream: stream to enqueue on (NULL = legacy default stream).
    The call is asynchronous: outputs are ready when the stream reaches this point.  The
    first call on a device looks up the working area's device address (once per device,
-   with that device current); make that first call before any stream capture.  All calls
+   with that device current); make that first call before any stream capture.  The address
+   belongs to the device's CUDA context: after a cudaDeviceReset the next call looks it up
+   again (so that call, too, should come before any stream capture).  All calls
    on a device share the working area (each clears what it uses first), so calls whose
    work overlaps on the GPU race; issue them one after another. */
 align_status align_reference_noalloc(const align_grid_desc* desc, const float* xyzA, int64_t nA,

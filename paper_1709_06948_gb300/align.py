@@ -28,7 +28,7 @@ _STATUS_NAMES = {0: "ALIGN_OK", 1: "ALIGN_NOT_READY", -1: "ALIGN_E_INVALID", -2:
 # Every entry point include/align.h declares (checked by the tests against the .so).
 EXPORTS = ["align_create_grid", "align_destroy_grid", "align_grid_info", "align_set_reference",
            "align_get_reference", "align_round_poses", "align_eval_mi", "align_accumulate", "align_search",
-           "align_search_ex", "align_eval_stats", "align_profile", "align_reference_noalloc", "align_batch_create",
+           "align_search_ex", "align_eval_stats", "align_eval_redo_poses", "align_profile", "align_microbench", "align_reference_noalloc", "align_batch_create",
            "align_batch_destroy", "align_eval_batch", "align_batch_set_shape", "align_batch_stats",
            "align_server_create", "align_server_add_reference", "align_submit", "align_poll", "align_wait",
            "align_server_now", "align_server_stats", "align_server_destroy", "align_refine_nm", "align_last_error"]
@@ -92,8 +92,10 @@ def load(build_if_missing: bool = True):
         "align_search": [P, P, i64, C.c_int, P, P, i32, P, P],
         "align_search_ex": [P, P, i64, C.c_int, P, P, P, i32, P, P, P],
         "align_eval_stats": [P, P],
+        "align_eval_redo_poses": [P, P, i64, P],
         "align_profile": [P, i32, P],
         "align_reference_noalloc": [P, P, i64, P, P, P],
+        "align_microbench": [i32, P, i64, i32, P, P],
         "align_batch_create": [P, P],
         "align_batch_destroy": [P],
         "align_eval_batch": [P, P, i32, C.c_int],
@@ -145,6 +147,17 @@ def _host(a, dtype, shape_tail=None):
     if shape_tail is not None:
         a = a.reshape(-1, *shape_tail) if a.size else a.reshape(0, *shape_tail)
     return a
+
+
+def _device_out(t, dtypes, numel, name):
+    """Check a caller-owned CUDA output tensor: contiguous, of one of `dtypes`, with at least
+    `numel` elements (the library writes that many)."""
+    dtypes = dtypes if isinstance(dtypes, (tuple, list)) else (dtypes,)
+    if not _is_torch_cuda(t):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes or not t.is_contiguous() or t.numel() < numel:
+        raise ValueError(f"{name} must be a contiguous {'/'.join(str(x) for x in dtypes)} CUDA tensor "
+                         f"of at least {numel} elements")
 
 
 def _points_arg(xyz):
@@ -275,7 +288,14 @@ def align_eval_mi(grid: Grid, xyzB, poses12=None, eta6=None, with_hist=False, ou
         poses_ptr = None
         eta_ptr = eh.ctypes.data_as(C.c_void_p)
     if out is not None:
+        import torch
         mi_t, am_t, hist_t = out
+        _device_out(mi_t, torch.float32, P, "mi out")
+        if am_t is not None:
+            _device_out(am_t, torch.int64, 1, "argmax out")
+        if hist_t is not None:
+            _device_out(hist_t, (torch.int32, torch.uint32) if hasattr(torch, "uint32") else torch.int32,
+                        P * grid.K * grid.K, "hist out")
         flags |= ALIGN_OUT_DEVICE
         _check(lib.align_eval_mi(grid.handle, pptr, n, flags, poses_ptr, eta_ptr, P, C.c_void_p(mi_t.data_ptr()),
                                  None if am_t is None else C.c_void_p(am_t.data_ptr()),
@@ -349,12 +369,40 @@ def align_eval_stats(grid: Grid):
             "kernel_launches": int(out[4])}
 
 
+def align_eval_redo_poses(grid: Grid) -> np.ndarray:
+    """Pose indices of the last evaluation that the exact path finished (ascending)."""
+    lib = load()
+    n = C.c_int64(0)
+    _check(lib.align_eval_redo_poses(grid.handle, None, 0, C.byref(n)))
+    out = np.zeros(max(int(n.value), 1), dtype=np.int64)
+    _check(lib.align_eval_redo_poses(grid.handle, out.ctypes.data_as(C.c_void_p), int(n.value), C.byref(n)))
+    return out[:int(n.value)]
+
+
 def align_profile(grid: Grid, mode: int):
     """mode 1: enable + reset, 0: disable, 2: read.  Returns (eval ms total, compose ms total,
     eval launches timed)."""
     out = np.zeros(3, dtype=np.float64)
     _check(load().align_profile(grid.handle, int(mode), out.ctypes.data_as(C.c_void_p)))
     return float(out[0]), float(out[1]), int(out[2])
+
+
+MICROBENCH_KINDS = {0: "fp32 ffma lane-ops", 1: "int32 add/xor lane-ops", 2: "voxel-map mix lane-ops",
+                    3: "shared red.add (one bank per lane)", 4: "shared atom.add (one bank per lane)",
+                    5: "shared red.add (random words)", 6: "shared atom.add (random words)",
+                    7: "L2 atomic add (random words)"}
+
+
+def align_microbench(kind: int, buf, reps: int = 5, stream=None):
+    """(operations/s of the fastest run, its ms, operations per run) of micro-benchmark `kind`
+    (MICROBENCH_KINDS) run on the caller's CUDA scratch tensor `buf` (>= 1 MiB)."""
+    if not _is_torch_cuda(buf) or not buf.is_contiguous():
+        raise ValueError("buf must be a contiguous CUDA tensor")
+    raw, _ = _stream_raw(stream)
+    out = np.zeros(3, dtype=np.float64)
+    _check(load().align_microbench(int(kind), C.c_void_p(buf.data_ptr()), int(buf.numel() * buf.element_size()),
+                                   int(reps), C.c_void_p(raw), out.ctypes.data_as(C.c_void_p)))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def align_reference_noalloc(desc_kw: dict, xyzA, symA_out, boxA_out, stream=None):
@@ -378,13 +426,19 @@ def align_reference_noalloc(desc_kw: dict, xyzA, symA_out, boxA_out, stream=None
     d.var_thresh = None if vt is None else vt.ctypes.data
     if not (_is_torch_cuda(xyzA) and _is_torch_cuda(symA_out) and _is_torch_cuda(boxA_out)):
         raise ValueError("align_reference_noalloc takes CUDA tensors only")
+    import torch
+    xptr, nA, _, _ = _points_arg(xyzA)  # contiguous (n, 3) float32
+    V = int(d.dims[0]) * int(d.dims[1]) * int(d.dims[2])
+    _device_out(symA_out, torch.uint8, V, "symA_out")
+    _device_out(boxA_out, torch.int32, 6, "boxA_out")
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in (xyzA, symA_out, boxA_out)):
+        raise ValueError("align_reference_noalloc: tensors must be on the current device")
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream()
     raw = stream if isinstance(stream, int) else int(stream.cuda_stream)
-    _check(lib.align_reference_noalloc(C.byref(d), C.c_void_p(xyzA.data_ptr()), int(xyzA.shape[0]),
-                                       C.c_void_p(symA_out.data_ptr()), C.c_void_p(boxA_out.data_ptr()),
-                                       C.c_void_p(raw)))
+    _check(lib.align_reference_noalloc(C.byref(d), xptr, nA, C.c_void_p(symA_out.data_ptr()),
+                                       C.c_void_p(boxA_out.data_ptr()), C.c_void_p(raw)))
 
 
 # ---------------------------------------------------------------------------------------
@@ -486,7 +540,11 @@ def align_eval_batch(batch: Batch, pairs, graph=False, tune=False, out=None):
             arr[i].poses12 = ph.ctypes.data
             arr[i].P = int(ph.shape[0])
         if out is not None:
+            import torch
             mi_t, am_t = out[i]
+            _device_out(mi_t, torch.float32, int(arr[i].P), "mi out")
+            if am_t is not None:
+                _device_out(am_t, torch.int64, 1, "argmax out")
             arr[i].mi_out = mi_t.data_ptr()
             arr[i].argmax_out = None if am_t is None else am_t.data_ptr()
             results.append((mi_t, am_t))

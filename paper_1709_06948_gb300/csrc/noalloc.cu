@@ -13,6 +13,8 @@
 // process exits.  All calls on a device share it and it keeps the last call's contents,
 // so each call clears the part it uses first, and calls whose work overlaps on the GPU
 // (different streams, or different host threads) race and must not be issued.
+#include <cuda.h>  // driver types for the context lookups (entry points via the runtime)
+
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -34,10 +36,50 @@ constexpr size_t kScratchBytes = kCntBytes + 2 * kSumBytes + 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Device address of g_noalloc_scratch per device, looked up once (with that device
-// current).  In host code the symbol itself is only a host-side stand-in.
+// current).  In host code the symbol itself is only a host-side stand-in.  The address
+// belongs to the device's current context: a cudaDeviceReset destroys that context and the
+// next one may place the array elsewhere, so the lookup is keyed by the context's unique id
+// (cuCtxGetId, never reused within a process) and repeated when the id changes.
 constexpr int kMaxDevices = 64;
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;
+  void* addr = nullptr;
+};
 std::mutex g_addr_mutex;
-void* g_addr[kMaxDevices] = {};
+ScratchSlot g_slot[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique id of the calling thread's current context on device `dev` (the runtime's primary
+// context, made current first if no context is).  Driver entry points come through the
+// runtime, so the library needs no link against the driver library.
+align_status current_context_id(int dev, unsigned long long* id) {
+  if (g_ctx_get_current == nullptr || g_ctx_get_id == nullptr) {
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+    if (e != cudaSuccess) return report_cuda_error(e, "cudaGetDriverEntryPointByVersion");
+    if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+      return report_error(ALIGN_E_CUDA, "driver entry points cuCtxGetCurrent/cuCtxGetId not found");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f1);
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return report_error(ALIGN_E_CUDA, "cuCtxGetCurrent failed");
+  if (ctx == nullptr) {  // no context current yet: cudaSetDevice initialises the primary context
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return report_cuda_error(e, "cudaSetDevice");
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr)
+      return report_error(ALIGN_E_CUDA, "no current CUDA context");
+  }
+  if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return report_error(ALIGN_E_CUDA, "cuCtxGetId failed");
+  return ALIGN_OK;
+}
 
 __global__ void noalloc_clear_kernel(unsigned char* base, int64_t V, Pose12 pose, int32_t* box) {
   uint32_t* cnt = reinterpret_cast<uint32_t*>(base);
@@ -63,13 +105,18 @@ align_status scratch_address(void** out) {
   if (e != cudaSuccess) return report_cuda_error(e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return report_error(ALIGN_E_INVALID, "device index beyond 63");
   std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (g_addr[dev] == nullptr) {
+  unsigned long long ctx_id = 0;
+  align_status st = current_context_id(dev, &ctx_id);
+  if (st != ALIGN_OK) return st;
+  ScratchSlot& slot = g_slot[dev];
+  if (slot.addr == nullptr || slot.ctx_id != ctx_id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return report_cuda_error(e, "cudaGetSymbolAddress(noalloc scratch)");
-    g_addr[dev] = p;
+    slot.addr = p;
+    slot.ctx_id = ctx_id;
   }
-  *out = g_addr[dev];
+  *out = slot.addr;
   return ALIGN_OK;
 }
 

@@ -1172,6 +1172,26 @@ align_status align_eval_stats(align_grid* g, int64_t out[5]) {
   return ALIGN_OK;
 }
 
+align_status align_eval_redo_poses(align_grid* g, int64_t* out, int64_t cap, int64_t* n_out) {
+  align_status st = check_grid(g);
+  if (st != ALIGN_OK) return st;
+  if (!n_out || cap < 0 || (cap > 0 && !out)) return fail(ALIGN_E_INVALID, "bad output arguments");
+  *n_out = 0;
+  if (g->redo_count.p == nullptr || g->redo_list.p == nullptr) return ALIGN_OK;  // nothing evaluated yet
+  uint32_t n = 0;
+  CU(cudaMemcpyAsync(&n, g->redo_count.p, 4, cudaMemcpyDeviceToHost, g->stream), "read redo count");
+  CU(cudaStreamSynchronize(g->stream), "synchronize");
+  *n_out = n;
+  const int64_t k = std::min<int64_t>(cap, n);
+  if (k > 0) {
+    std::vector<uint32_t> idx((size_t)k);
+    CU(cudaMemcpy(idx.data(), g->redo_list.p, (size_t)k * 4, cudaMemcpyDeviceToHost), "read redo list");
+    std::sort(idx.begin(), idx.end());
+    for (int64_t i = 0; i < k; ++i) out[i] = idx[(size_t)i];
+  }
+  return ALIGN_OK;
+}
+
 align_status align_profile(align_grid* g, int32_t mode, double out[3]) {
   align_status st = check_grid(g);
   if (st != ALIGN_OK) return st;

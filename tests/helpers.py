@@ -26,8 +26,16 @@ def mi_tolerance() -> float:
     return 1e-5
 
 
-def check_argmax(gpu_idx: int, mi_oracle: np.ndarray, tie_band: float = 2e-5):
-    """The GPU's argmax must be the oracle's, unless the two poses are within the FP32 band."""
+def lowest_argmax(mi) -> int:
+    """Index of the largest value, the lowest one on ties (Eq. 1's rule), or -1 if empty."""
+    mi = np.asarray(mi)
+    return int(np.flatnonzero(mi == mi.max())[0]) if mi.size else -1
+
+
+def check_argmax(gpu_idx: int, mi_oracle: np.ndarray, mi_gpu: np.ndarray, tie_band: float = 2e-5):
+    """The GPU's argmax is exactly the lowest-index maximum of its own FP32 MI array, and it is
+    the oracle's argmax unless the two poses lie within the FP32-versus-FP64 band."""
+    assert gpu_idx == lowest_argmax(mi_gpu), (gpu_idx, lowest_argmax(mi_gpu))
     o = int(oracle.argmax(mi_oracle))
     if gpu_idx == o:
         return True

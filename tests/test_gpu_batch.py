@@ -67,7 +67,7 @@ def test_batch_matches_oracle_and_single(cases):
         mo = c.oracle_mi()
         assert mi.shape == (len(c.etas),)
         assert np.max(np.abs(mi.astype(np.float64) - mo)) <= mi_tolerance()
-        check_argmax(am, mo)
+        check_argmax(am, mo, mi)
         mi1, am1, _ = align.align_eval_mi(c.L, c.xyzB, eta6=c.etas)
         assert np.array_equal(mi, mi1) and am == am1
     st = align.align_batch_stats(b)

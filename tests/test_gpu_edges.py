@@ -28,7 +28,7 @@ def _compare(spec, xyzA, xyzB, etas, **grid_over):
     assert np.array_equal(hist, ho)
     assert np.max(np.abs(mi.astype(np.float64) - mo)) <= mi_tolerance()
     if len(etas):
-        check_argmax(am, mo)
+        check_argmax(am, mo, mi)
     return mi, am, align.align_eval_stats(L)
 
 

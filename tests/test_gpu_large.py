@@ -1,16 +1,19 @@
 """The large workload (128-beam scans of ~260k points, 400x400x40 grid at 0.2 m = 6.4M
 voxels, joint count x z-variance feature with 57 symbols, key-partitioned tables) against
-the oracle on sampled poses of its 32,768-pose lattice: histograms bit-exact, MI within
-1e-5 nats.  The launch evaluates the whole lattice as the benchmark does."""
+the oracle: the whole 32,768-pose lattice is evaluated in one launch, as the benchmark
+does, and 1,024 of its poses are compared element by element (histograms bit-exact, MI
+within 1e-5 nats).  The compared set always holds the launch's argmax and every pose that
+the exact path finished, besides a seeded random sample."""
 import numpy as np
 import pytest
 
 import oracle
 import scangen
-from tests.helpers import lib_grid, mi_tolerance, oracle_grid
+from tests.helpers import lib_grid, lowest_argmax, mi_tolerance, oracle_grid
 
 pytestmark = pytest.mark.gpu
 NT = oracle.host_cores()
+N_COMPARED = 1024
 
 
 @pytest.fixture(scope="module")
@@ -18,7 +21,7 @@ def large():
     return scangen.large_pair()
 
 
-def test_large_lattice_sampled_poses_match_oracle(large):
+def test_large_lattice_matches_oracle(large):
     import torch
     from paper_1709_06948_gb300 import align
     spec = large.grid
@@ -30,15 +33,26 @@ def test_large_lattice_sampled_poses_match_oracle(large):
     mi = torch.empty(P, device="cuda")
     am = torch.empty(1, dtype=torch.int64, device="cuda")
     hist = torch.empty((P, L.K, L.K), dtype=torch.int32, device="cuda")
-    align.align_eval_mi(L, torch.from_numpy(large.xyzB).cuda(), poses12=torch.from_numpy(poses).cuda(),
-                        out=(mi, am, hist))
+    B = torch.from_numpy(large.xyzB).cuda()
+    align.align_eval_mi(L, B, poses12=torch.from_numpy(poses).cuda(), out=(mi, am, hist))
     torch.cuda.synchronize()
+    redo = align.align_eval_redo_poses(L)  # poses the exact path finished in this launch
+    mi_h = mi.cpu().numpy()
+    am_h = int(am.item())
+    assert am_h == lowest_argmax(mi_h)
     align.align_eval_mi(L, large.xyzB, eta6=etas[:304])  # a synchronising call collects the counters
     assert align.align_eval_stats(L)["passes"] > 1  # the tables were partitioned
+    rng = np.random.default_rng(81)
+    must = np.unique(np.concatenate([[am_h], redo]))
+    rest = np.setdiff1d(np.arange(P), must)
+    sample = np.sort(np.concatenate([must, rng.choice(rest, max(0, N_COMPARED - len(must)), replace=False)]))
     G = oracle_grid(spec)
     symA, boxA = G.reference(large.xyzA)
-    rng = np.random.default_rng(81)
-    sample = np.sort(rng.choice(P, 6, replace=False))
     mo, ho, _ = G.eval_mi(symA, boxA, large.xyzB, poses[sample], nthreads=NT, with_hist=True)
-    assert np.array_equal(hist[torch.from_numpy(sample).cuda()].cpu().numpy().view(np.uint32), ho)
-    assert np.max(np.abs(mi.cpu().numpy()[sample].astype(np.float64) - mo)) <= mi_tolerance()
+    hist_s = hist[torch.from_numpy(sample).cuda()].cpu().numpy().view(np.uint32)
+    bad = [int(sample[i]) for i in range(len(sample)) if not np.array_equal(hist_s[i], ho[i])]
+    assert not bad, f"histograms differ at poses {bad[:10]}"
+    assert np.max(np.abs(mi_h[sample].astype(np.float64) - mo)) <= mi_tolerance()
+    # the oracle's maximum over the compared poses is the GPU's argmax (within the FP32 band)
+    o = int(sample[oracle.argmax(mo)])
+    assert o == am_h or abs(mo[np.searchsorted(sample, am_h)] - mo.max()) <= 2e-5

@@ -345,6 +345,51 @@ def test_lattice_order_and_values():
     assert np.allclose(L3[:, 0], [c[0] - r[0], c[0], c[0] + r[0]]) and np.all(L3[:, 1:] == c[1:])
 
 
+def test_argmax_ties_go_to_the_lowest_index():
+    """Eq. 1 with the tie rule of the C ABI: of several equal maxima the first one wins.
+    MI is piecewise constant in the pose, so exact ties are common on a lattice."""
+    assert oracle.argmax([0.1, 0.5, 0.2, 0.5, 0.5]) == 1
+    assert oracle.argmax([0.3, 0.3, 0.3]) == 0
+    assert oracle.argmax([-1.0, -0.5, -0.5]) == 1
+    assert oracle.argmax([0.0] * 7 + [1e-300]) == 7
+    assert oracle.argmax(np.repeat([0.2, 0.7, 0.7, 0.1], 5)) == 5
+    assert oracle.argmax([2.0]) == 0
+    assert oracle.argmax(np.zeros(0)) == -1
+
+
+def test_search_schedule_hand_computed():
+    """The lattice search level by level: the lattice around the current centre with the
+    current ranges, centre <- its best sample (lowest index on ties), ranges halved.  The
+    per-level lattices are written out here with hand-computed offsets (three samples per
+    searched axis: -r, 0, +r with r = 1, 0.5, 0.25 m in x and y, 0.08, 0.04, 0.02 rad in yaw)."""
+    T = np.array([0.35, -0.6, 0.0, 0.0, 0.0, math.radians(3.0)])
+    pair = scangen.tiny_pair(T=T)
+    G = oracle_grid(pair.grid)
+    symA, boxA = G.reference(pair.xyzA)
+    nt = oracle.host_cores()
+    offs_t = [[-1.0, 0.0, 1.0], [-0.5, 0.0, 0.5], [-0.25, 0.0, 0.25]]
+    offs_yaw = [[-0.08, 0.0, 0.08], [-0.04, 0.0, 0.04], [-0.02, 0.0, 0.02]]
+    c = np.zeros(6)
+    centres, bests = [], []
+    for lvl in range(3):
+        # pose order: rotation samples outermost (only yaw varies here), then tx, then ty
+        etas = np.array([[c[0] + offs_t[lvl][ix], c[1] + offs_t[lvl][iy], c[2], c[3], c[4],
+                          c[5] + offs_yaw[lvl][iz]]
+                         for iz in range(3) for ix in range(3) for iy in range(3)])
+        mi, _, _ = G.eval_mi(symA, boxA, pair.xyzB, G.round_pose(etas), nthreads=nt)
+        b = int(np.flatnonzero(mi == mi.max())[0])
+        bests.append(b)
+        c = etas[b].copy()
+        centres.append(c)
+    Tout, mi_out, lb = G.search(symA, boxA, pair.xyzB, np.zeros(6), np.array([1.0, 1.0, 0.0, 0.0, 0.0, 0.08]),
+                                counts=(3, 3, 1, 1, 1, 3), levels=3, nthreads=nt)
+    assert lb.tolist() == bests
+    assert Tout.tolist() == centres[-1].tolist()
+    assert len({tuple(x) for x in centres}) > 1  # the centre moved: the schedule was exercised
+    mo, _, _ = G.eval_mi(symA, boxA, pair.xyzB, G.round_pose(centres[-1][None]), nthreads=1)
+    assert mi_out == mo[0]
+
+
 def test_search_recovers_tiny_within_final_step():
     T = np.array([0.35, -0.6, 0.1, math.radians(1.0), math.radians(-1.5), math.radians(3.0)])
     pair = scangen.tiny_pair(T=T)

@@ -47,6 +47,51 @@ def test_noalloc_matches_set_reference_on_consecutive_calls():
         assert (sym > 0).sum() > 100
 
 
+def test_noalloc_allocates_nothing():
+    """After one warm-up call (which looks up the working area's address), further calls leave
+    the device's free memory unchanged: nothing is allocated on the caller's behalf."""
+    import torch
+    from paper_1709_06948_gb300 import align
+    tiny = scangen.tiny_pair(seed=scangen.SEED_BASE + 62)
+    spec = tiny.grid
+    X, Y, Z = spec.dims
+    desc = dict(origin=spec.origin, res_m=spec.res_m, dims=spec.dims, feature=spec.feature,
+                count_levels=spec.count_levels, var_levels=spec.var_levels)
+    xyz = torch.from_numpy(np.ascontiguousarray(tiny.xyzA, np.float32)).cuda()
+    sym = torch.empty(X * Y * Z, dtype=torch.uint8, device="cuda")
+    box = torch.empty(6, dtype=torch.int32, device="cuda")
+    align.align_reference_noalloc(desc, xyz, sym, box)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        align.align_reference_noalloc(desc, xyz, sym, box)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    sym_ref, box_ref = _existing(spec, tiny.xyzA)
+    assert np.array_equal(sym.cpu().numpy(), sym_ref) and box.cpu().numpy().tolist() == box_ref.tolist()
+
+
+def test_noalloc_checks_its_buffers():
+    import torch
+    from paper_1709_06948_gb300 import align
+    tiny = scangen.tiny_pair(seed=scangen.SEED_BASE + 63)
+    spec = tiny.grid
+    X, Y, Z = spec.dims
+    desc = dict(origin=spec.origin, res_m=spec.res_m, dims=spec.dims, feature=spec.feature,
+                count_levels=spec.count_levels, var_levels=spec.var_levels)
+    xyz = torch.from_numpy(np.ascontiguousarray(tiny.xyzA, np.float32)).cuda()
+    box = torch.empty(6, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):  # symA shorter than the grid
+        align.align_reference_noalloc(desc, xyz, torch.empty(X * Y * Z - 1, dtype=torch.uint8, device="cuda"), box)
+    with pytest.raises(ValueError):  # wrong dtype of the points
+        align.align_reference_noalloc(desc, xyz.double(), torch.empty(X * Y * Z, dtype=torch.uint8, device="cuda"),
+                                      box)
+    with pytest.raises(ValueError):  # box of 5 entries
+        align.align_reference_noalloc(desc, xyz, torch.empty(X * Y * Z, dtype=torch.uint8, device="cuda"),
+                                      box[:5])
+
+
 def test_noalloc_rejects_grids_beyond_its_working_area():
     import torch
     from paper_1709_06948_gb300 import align
