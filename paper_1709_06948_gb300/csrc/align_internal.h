@@ -89,6 +89,10 @@ struct EvalArgs {
   uint4* ovf;                 // per CTA: ovf_cap runs (key, n, S1, S2) whose home bucket was full
   int32_t ovf_cap;
   int32_t p_begin;            // eval_kernel: first global pose of this launch (poses p_begin..P-1)
+  // Pose pairs (one item, pre-rotated tiles): n_units units of two pose indices each, the
+  // second -1 for a single pose.  nullptr: one pose per CTA step (eval_kernel).
+  const int32_t* units;
+  int32_t n_units;
 };
 
 // One point-tile PackCopy of a batch: scan xyz (n points) -> out (n_out float4), raw
@@ -114,15 +118,16 @@ struct EvalKernels {
   int (*tile_points)();
   int (*ovf_cap)();  // overflow-list entries per CTA (EvalArgs::ovf holds CTAs x this many)
   int (*min_tiles)();
-  // vw: table value words per slot (eval_layout)
-  size_t (*smem_bytes)(int K, int table_slots, int vw);
-  int (*table_slots_for)(int K, int vw, size_t smem_budget);
+  // vw: table value words per slot (eval_layout); np: poses swept together (2 for pairs)
+  size_t (*smem_bytes)(int K, int table_slots, int vw, int np);
+  int (*table_slots_for)(int K, int vw, size_t smem_budget, int np);
   // Raise the kernels' dynamic shared-memory limit on the current device (once per device,
   // before any launch or stream capture).
   cudaError_t (*setup)();
   // vw: table layout (eval_layout); rotate: tiles hold raw xyz (the kernel applies each
   // pose's rotation) instead of pre-rotated copies.  Launches the eval and redo kernels.  A
-  // launch with item_start == nullptr is a single-item launch (its item is read from `one`).
+  // launch with item_start == nullptr is a single-item launch (its item is read from `one`);
+  // one with units != nullptr evaluates pose pairs (single item, pre-rotated tiles only).
   cudaError_t (*launch_eval)(const EvalArgs& a, int n_ctas, int vw, bool rotate, cudaStream_t s);
   // xyz (n x 3 fp32) -> n_out float4 with NaN padding; with rots (n_rot x 9), one
   // pre-rotated copy u = R p per rotation (same FMA order as the voxel map).

@@ -375,7 +375,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   int T = 0;  // the largest table of the launches (sizes the 64-bit side sums)
   for (const PairPlan& pp : plans) {
     vws.push_back(eval_layout(pp.g->gc, var));
-    Ts.push_back(ek.table_slots_for(pp.g->gc.K, vws.back(), b->smem_optin));
+    Ts.push_back(ek.table_slots_for(pp.g->gc.K, vws.back(), b->smem_optin, 1));
     T = std::max(T, Ts.back());
   }
   const int n_ctas = b->n_sm * ek.ctas_per_sm;

@@ -63,6 +63,10 @@ constexpr int kTile = kThreads * kPPT;  // points per tile
 #define MI_EVAL_DEPTH 4
 #endif
 constexpr int kDepth = MI_EVAL_DEPTH;   // tiles loaded ahead into registers
+#ifndef MI_EVAL_PAIR_DEPTH
+#define MI_EVAL_PAIR_DEPTH (MI_EVAL_PPT >= 2 ? 1 : 2)
+#endif
+constexpr int kPairDepth = MI_EVAL_PAIR_DEPTH;  // the same for the pose-pair sweep (two runs per thread)
 constexpr int kMinTiles = 3;
 constexpr uint32_t kQueue = 64;         // finished runs buffered per warp (32 drained at a time)
 constexpr int kProbeBuckets = 1024;     // probe budget per key (buckets of 4 slots)
@@ -186,10 +190,11 @@ struct EvalSmem {
   uint32_t* flags;    // occupied count, table full, overflow entries, sums need the exact path
   uint32_t* tkey;
   uint32_t* tval;     // kVW words per slot
-  uint32_t* hist;
+  uint32_t* hist;     // np partial histograms of hist_stride words
   GridConst* gc;      // the current item's grid constants
-  int32_t* box;       // 6
+  int32_t* box;       // np x 6
   int32_t* item;      // the item whose constants are loaded
+  uint32_t hist_stride;
   // shared-window addresses
   uint32_t a_queue, a_key, a_vals, a_hist, a_box;
 };
@@ -198,7 +203,8 @@ constexpr uint32_t kFlagFull = 12u;
 constexpr uint32_t kFlagOvf = 8u;        // entries in the CTA's overflow list
 constexpr uint32_t kFlagWide = 4u;
 
-__host__ __device__ inline size_t eval_smem_layout(int K, int T, int vw, EvalSmem* s, uint8_t* base) {
+// np: poses swept together (1, or 2 for a pose pair): one partial histogram and one bbox each.
+__host__ __device__ inline size_t eval_smem_layout(int K, int T, int vw, int np, EvalSmem* s, uint8_t* base) {
   size_t off = 0;
   auto take = [&](size_t bytes, size_t align) {
     off = (off + align - 1) / align * align;
@@ -210,9 +216,9 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, int vw, EvalSme
   size_t o_flags = take(16, 16);
   size_t o_key = take((size_t)T * 4, 16);
   size_t o_vals = take((size_t)T * 4 * vw, 16);
-  size_t o_hist = take((size_t)round4(K * K) * 4, 16);
+  size_t o_hist = take((size_t)np * round4(K * K) * 4, 16);
   size_t o_gc = take(sizeof(GridConst), 16);
-  size_t o_box = take(6 * 4, 4);
+  size_t o_box = take((size_t)np * 6 * 4, 4);
   size_t o_item = take(4, 4);
   if (s) {
     s->queue = (uint4*)(base + o_queue);
@@ -223,6 +229,7 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, int vw, EvalSme
     s->gc = (GridConst*)(base + o_gc);
     s->box = (int32_t*)(base + o_box);
     s->item = (int32_t*)(base + o_item);
+    s->hist_stride = (uint32_t)round4(K * K);
 #ifdef __CUDA_ARCH__
     const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(base);
     s->a_queue = a0 + (uint32_t)o_queue;
@@ -251,48 +258,79 @@ __device__ __forceinline__ VoxelConst voxel_const(const GridConst& g) {
                     (1u << g.ns_shift) + (uint32_t)g.dz_bound, (uint32_t)g.wide_shift};
 }
 
-// Find or insert `key` in the open-addressing table: buckets of 4 key slots read with one
-// 16-byte load, probed linearly; slots of a bucket fill in order, so a bucket with a free
-// slot ends the search.  Returns -1 when kProbeBuckets buckets were searched in vain (the
-// pose then counts as overflowing the table).  The home bucket is tried in straight-line
-// code; the loop over further buckets is a separate (rarely called) function.
+// The table: buckets of 4 key slots (one 16-byte load each).  With kTwo (the pair kernel,
+// whose table holds two poses' voxels) it is two-choice ("d-left"): a key's
+// candidate buckets are b1 in the left half and b2 in the right half of the table, and a new
+// key goes to the one with fewer keys (b1 on a tie).  Slots of a bucket fill in order and
+// never empty during a sweep, so a bucket's key count is the index of its first free slot,
+// and two inserters of the same key can never settle in different buckets: an inserter
+// places the key only in a slot that was empty when it read both buckets without finding
+// the key, and it reads both before it chooses.  A key whose two buckets are full (or whose
+// insert lost a race) goes to the overflow list; table_slot then places it by a linear probe
+// that starts after b2, the same sequence for every inserter of that key.
+__device__ __forceinline__ void table_buckets(uint32_t key, uint32_t nb, uint32_t& b1, uint32_t& b2) {
+  const uint32_t half = nb >> 1;
+  b1 = __umulhi(key * 0x9E3779B1u, half);
+  b2 = half + __umulhi(key * 0xC2B2AE35u, nb - half);
+}
+// Lowest slot of bucket k4 holding `key` (-1: none), and the bucket's key count.
+__device__ __forceinline__ int bucket_hit(const uint4& k4, uint32_t key) {
+  return (k4.x == key) ? 0 : (k4.y == key) ? 1 : (k4.z == key) ? 2 : (k4.w == key) ? 3 : -1;
+}
+__device__ __forceinline__ uint32_t bucket_fill(const uint4& k4) {
+  return (uint32_t)(k4.x != kEmptyKey) + (uint32_t)(k4.y != kEmptyKey) + (uint32_t)(k4.z != kEmptyKey) +
+         (uint32_t)(k4.w != kEmptyKey);
+}
+
+// Find or insert `key` (any thread, after the sweep's drains): returns the slot, or -1 when
+// kProbeBuckets buckets past b2 were searched in vain (the pose then counts as overflowing).
+// kTwo == false: one candidate bucket per key over the whole table (the single-pose kernel,
+// whose table is about a third full), linear probing from it when it is full.
 __device__ __noinline__ int table_slot_slow(uint32_t a_key, uint32_t key, uint32_t nb, uint32_t b);
+template <bool kTwo>
 __device__ __forceinline__ int table_slot(const EvalSmem& S, uint32_t key, uint32_t nb) {
-  const uint32_t b = __umulhi(key * 0x9E3779B1u, nb);
-  const uint4 k4 = lds128(S.a_key + 16u * b);
-  const uint32_t hit = (uint32_t)(k4.x == key) | ((uint32_t)(k4.y == key) << 1) | ((uint32_t)(k4.z == key) << 2) |
-                       ((uint32_t)(k4.w == key) << 3);
-  const uint32_t emp = (uint32_t)(k4.x == kEmptyKey) | ((uint32_t)(k4.y == kEmptyKey) << 1) |
-                       ((uint32_t)(k4.z == kEmptyKey) << 2) | ((uint32_t)(k4.w == kEmptyKey) << 3);
-  int slot = -1;
-  if (hit) {
-    slot = (int)(4 * b) + __ffs(hit) - 1;
-  } else if (emp) {
-    const uint32_t s = 4 * b + (uint32_t)(__ffs(emp) - 1);
-    const uint32_t old = atom_cas(S.a_key + 4u * s, kEmptyKey, key);
-    if (old == kEmptyKey || old == key) slot = (int)s;
+  if constexpr (!kTwo) {
+    const uint32_t b = __umulhi(key * 0x9E3779B1u, nb);
+    const uint4 k4 = lds128(S.a_key + 16u * b);
+    const int h = bucket_hit(k4, key);
+    if (h >= 0) return (int)(4 * b) + h;
+    const uint32_t f = bucket_fill(k4);
+    if (f < 4u) {
+      const uint32_t s = 4 * b + f;
+      const uint32_t old = atom_cas(S.a_key + 4u * s, kEmptyKey, key);
+      if (old == kEmptyKey || old == key) return (int)s;
+    }
+    return table_slot_slow(S.a_key, key, nb, b);
   }
-  if (slot < 0) slot = table_slot_slow(S.a_key, key, nb, b);
-  return slot;
+  uint32_t b1, b2;
+  table_buckets(key, nb, b1, b2);
+#pragma unroll 1
+  for (int tries = 0; tries < 9; ++tries) {  // each lost race means one more key in b1 or b2
+    const uint4 ka = lds128(S.a_key + 16u * b1);
+    const uint4 kb = lds128(S.a_key + 16u * b2);
+    const int ha = bucket_hit(ka, key), hb = bucket_hit(kb, key);
+    if (ha >= 0) return (int)(4 * b1) + ha;
+    if (hb >= 0) return (int)(4 * b2) + hb;
+    const uint32_t fa = bucket_fill(ka), fb = bucket_fill(kb);
+    if (fa == 4u && fb == 4u) break;  // both full: the key can never enter b1 or b2
+    const uint32_t s = fa <= fb ? 4 * b1 + fa : 4 * b2 + fb;
+    const uint32_t old = atom_cas(S.a_key + 4u * s, kEmptyKey, key);
+    if (old == kEmptyKey || old == key) return (int)s;
+  }
+  return table_slot_slow(S.a_key, key, nb, b2 + 1 == nb ? 0u : b2 + 1);
 }
 __device__ __noinline__ int table_slot_slow(uint32_t a_key, uint32_t key, uint32_t nb, uint32_t b) {
 #pragma unroll 1
   for (int i = 0; i < kProbeBuckets; ++i) {
     const uint4 k4 = lds128(a_key + 16u * b);
-    if (k4.x == key) return (int)(4 * b);
-    if (k4.y == key) return (int)(4 * b + 1);
-    if (k4.z == key) return (int)(4 * b + 2);
-    if (k4.w == key) return (int)(4 * b + 3);
-    const int e = (k4.x == kEmptyKey)   ? 0
-                  : (k4.y == kEmptyKey) ? 1
-                  : (k4.z == kEmptyKey) ? 2
-                  : (k4.w == kEmptyKey) ? 3
-                                        : -1;
-    if (e >= 0) {
-      const uint32_t s = 4 * b + (uint32_t)e;
+    const int h = bucket_hit(k4, key);
+    if (h >= 0) return (int)(4 * b) + h;
+    const uint32_t f = bucket_fill(k4);
+    if (f < 4u) {
+      const uint32_t s = 4 * b + f;
       const uint32_t old = atom_cas(a_key + 4u * s, kEmptyKey, key);
       if (old == kEmptyKey || old == key) return (int)s;
-      continue;  // another lane took that slot: read the bucket again
+      continue;  // another thread took that slot: read the bucket again
     }
     b = (b + 1 == nb) ? 0u : b + 1;
   }
@@ -320,13 +358,13 @@ __device__ __forceinline__ void table_add_slot(const EvalSmem& S, const uint4& e
 }
 
 // After a sweep: insert the overflow list with the full probe (all threads of the CTA).
-template <int kVW>
+template <int kVW, bool kTwo>
 __device__ __forceinline__ void insert_overflow(const EvalSmem& S, const EvalArgs& a, const GridConst& gc) {
   const uint32_t n = min(*(volatile uint32_t*)&S.flags[2], (uint32_t)kOvfCap);
   const uint4* ovf = a.ovf + (size_t)blockIdx.x * kOvfCap;
   for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
     const uint4 e = ovf[i];
-    const int slot = table_slot(S, e.x, (uint32_t)a.n_buckets);
+    const int slot = table_slot<kTwo>(S, e.x, (uint32_t)a.n_buckets);
     if (slot < 0) sts32(S.a_key - kFlagFull, 1u);
     else table_add_slot<kVW>(S, e, slot, gc);
   }
@@ -338,7 +376,7 @@ template <int kVW>
 __device__ __forceinline__ void add_run(const EvalSmem& S, unsigned long long* wide, uint32_t key, uint32_t n,
                                         int s1, uint32_t s2, uint32_t nb) {
   if (lds32(S.a_key - kFlagFull)) return;  // table already full: the pose restarts
-  const int slot = table_slot(S, key, nb);
+  const int slot = table_slot<false>(S, key, nb);
   if (slot < 0) {
     sts32(S.a_key - kFlagFull, 1u);
     return;
@@ -376,7 +414,7 @@ __device__ __forceinline__ uint4 run_entry(const Run& r) {
 // While no n field in it reaches 2^b (2^(b+1) - 2 <= nlim), every add kept the voxel at or
 // below nlim; the sweep's end tests acc once (the exact path takes the pose otherwise).
 // kCount32: a drain of 32 entries (during the sweep); otherwise `count` (the last drain).
-template <int kVW, bool kCount32>
+template <int kVW, bool kCount32, bool kTwo>
 __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count_arg,
                                            const EvalArgs& a, uint32_t& acc) {
   const uint32_t count = kCount32 ? 32u : count_arg;
@@ -385,16 +423,33 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
   uint4 e = lds128(ring + 16u * lane);  // the ring holds 64 entries: always in bounds
   if (!kCount32 && lane >= count) e.x = kEmptyKey;
   const bool valid = e.x != kEmptyKey;
-  const uint32_t b = __umulhi(e.x * 0x9E3779B1u, (uint32_t)a.n_buckets);
-  const uint32_t kb = S.a_key + 16u * b;
-  const uint4 k4 = lds128(kb);
-  int slot = (k4.x == e.x) ? 0 : (k4.y == e.x) ? 1 : (k4.z == e.x) ? 2 : (k4.w == e.x) ? 3 : -1;
-  const int f = (k4.x == kEmptyKey) ? 0 : (k4.y == kEmptyKey) ? 1 : (k4.z == kEmptyKey) ? 2 : (k4.w == kEmptyKey) ? 3 : -1;
-  const bool ins = valid && slot < 0 && f >= 0;
-  const uint32_t old = atom_cas_if(ins, kb + 4u * (uint32_t)f, kEmptyKey, e.x);
-  if (ins && (old == kEmptyKey || old == e.x)) slot = f;
+  int slot;
+  uint32_t s_new;
+  bool ins;
+  if constexpr (kTwo) {
+    uint32_t b1, b2;
+    table_buckets(e.x, (uint32_t)a.n_buckets, b1, b2);
+    const uint4 ka = lds128(S.a_key + 16u * b1);
+    const uint4 kb = lds128(S.a_key + 16u * b2);
+    const int ha = bucket_hit(ka, e.x), hb = bucket_hit(kb, e.x);
+    const uint32_t fa = bucket_fill(ka), fb = bucket_fill(kb);
+    slot = ha >= 0 ? (int)(4 * b1) + ha : hb >= 0 ? (int)(4 * b2) + hb : -1;
+    // a new key: the emptier bucket's first free slot
+    s_new = fa <= fb ? 4 * b1 + fa : 4 * b2 + fb;
+    ins = valid && slot < 0 && (fa < 4u || fb < 4u);
+  } else {
+    const uint32_t b = __umulhi(e.x * 0x9E3779B1u, (uint32_t)a.n_buckets);
+    const uint4 k4 = lds128(S.a_key + 16u * b);
+    const int h = bucket_hit(k4, e.x);
+    const uint32_t f = bucket_fill(k4);
+    slot = h >= 0 ? (int)(4 * b) + h : -1;
+    s_new = 4 * b + f;
+    ins = valid && slot < 0 && f < 4u;
+  }
+  const uint32_t old = atom_cas_if(ins, S.a_key + 4u * s_new, kEmptyKey, e.x);
+  if (ins && (old == kEmptyKey || old == e.x)) slot = (int)s_new;
   const bool ok = valid && slot >= 0;
-  const uint32_t v = S.a_vals + 4u * kVW * (4u * b + (uint32_t)slot);
+  const uint32_t v = S.a_vals + 4u * kVW * (uint32_t)slot;
   if (kVW == 2) {
     const uint32_t old = atom_add_if(ok, v, e.y);
     acc |= ok ? (old | e.y) : 0u;
@@ -406,7 +461,7 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
       red_add_if(ok, v + 8u, e.w);
     }
   }
-  // home bucket full (or insert race lost): the run goes to the overflow list (rare at
+  // both buckets full (or insert race lost): the run goes to the overflow list (rare at
   // the table's load: the warp skips this unless one of its lanes needs it)
   const bool ov = valid && slot < 0;
   if (__any_sync(kFull, ov)) {
@@ -426,14 +481,14 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
 }
 
 // Append the finished runs of the lanes with `done` set, then drain if 32 are waiting.
-template <int kVW>
+template <int kVW, bool kTwo>
 __device__ __forceinline__ void ring_push(const EvalSmem& S, uint32_t ring, uint32_t lane_lt, bool done,
                                           const Run& r, uint32_t& fill, const EvalArgs& a, uint32_t& acc) {
   const uint32_t m = __ballot_sync(kFull, done);
   sts128_if(done, ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), run_entry<kVW>(r));
   fill += (uint32_t)__popc(m);
   // fill is the same in every lane; the vote lets the compiler know the branch is uniform
-  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVW, true>(S, ring, fill, 32u, a, acc);
+  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVW, true, kTwo>(S, ring, fill, 32u, a, acc);
 }
 
 struct PoseRegs {
@@ -571,20 +626,41 @@ __device__ __forceinline__ int feature_symbol_small(const GridConst& gc, uint32_
   return 1 + lc * gc.Lv + lv;
 }
 
-// Read (and clear) the table after a sweep: symbols, bbox and histogram unless `discard`.
-// The CTA-wide occupied count is added to S.flags[0].
-// Bbox accumulators of a warp's share of the table scan.
+// Bbox accumulators of a warp's share of the table scan, one box per pose of the sweep.
+template <int kNP>
 struct ScanBox {
-  int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX, mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
+  int mn[kNP][3], mx[kNP][3];
+  __device__ ScanBox() {
+#pragma unroll
+    for (int a = 0; a < kNP; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) mn[a][i] = INT_MAX, mx[a][i] = INT_MIN;
+  }
+  // add voxel (kx, ky, kz) to the box of pose pa (branch-free for two poses)
+  __device__ __forceinline__ void add(uint32_t pa, int kx, int ky, int kz) {
+    const int k[3] = {kx, ky, kz};
+#pragma unroll
+    for (int a = 0; a < kNP; ++a) {
+      const bool mine = kNP == 1 || pa == (uint32_t)a;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        mn[a][i] = mine ? min(mn[a][i], k[i]) : mn[a][i];
+        mx[a][i] = mine ? max(mx[a][i], k[i]) : mx[a][i];
+      }
+    }
+  }
 };
 
 // One occupied slot: read and clear it, then (unless `discard`) its voxel's coordinates,
-// feature symbol and joint-histogram entry.
-template <int kVW, bool kExact>
+// feature symbol and joint-histogram entry.  With kNP == 2 the key's top bit names the pose
+// of the pair (the keys of the second pose carry bit 31).
+template <int kVW, bool kExact, int kNP>
 __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& gc, const EvalItem& I,
                                            unsigned long long* wide, uint32_t* wide_count, uint32_t s, int lp,
-                                           bool discard, ScanBox& bx) {
-  const uint32_t k = lds32(S.a_key + 4u * s);
+                                           bool discard, ScanBox<kNP>& bx) {
+  const uint32_t kk = lds32(S.a_key + 4u * s);
+  const uint32_t pa = kNP == 2 ? kk >> 31 : 0u;
+  const uint32_t k = kNP == 2 ? kk & 0x7FFFFFFFu : kk;
   // A's symbol of the voxel, requested first: its L2 latency overlaps the work below
   const int sA = discard ? 0 : (int)__ldg(I.symA + k);
   const uint32_t v = S.a_vals + 4u * kVW * s;
@@ -618,8 +694,7 @@ __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& g
   const int kx = (int)(k - r * (uint32_t)gc.X);
   const int ky = (int)(r - q * (uint32_t)gc.Y);
   const int kz = (int)q;
-  bx.mn0 = min(bx.mn0, kx); bx.mn1 = min(bx.mn1, ky); bx.mn2 = min(bx.mn2, kz);
-  bx.mx0 = max(bx.mx0, kx); bx.mx1 = max(bx.mx1, ky); bx.mx2 = max(bx.mx2, kz);
+  bx.add(pa, kx, ky, kz);
   // The fast path redoes any pose with a voxel above nlim (flag above), so its symbols only
   // need the 64-bit test; the exact path takes the 128-bit one where needed.
   const int sB = (kExact && n > gc.nlim)
@@ -627,19 +702,19 @@ __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& g
                      : feature_symbol_small(gc, (uint32_t)n, (int32_t)s1, (uint32_t)s2);
   if (kx >= gc.boxA[0] && kx <= gc.boxA[3] && ky >= gc.boxA[1] && ky <= gc.boxA[4] && kz >= gc.boxA[2] &&
       kz <= gc.boxA[5])
-    red_add(S.a_hist + 4u * (uint32_t)(sA * gc.K + sB), 1u);
-  if (I.dump != nullptr && lp == 0) {
+    red_add(S.a_hist + 4u * (pa * S.hist_stride + (uint32_t)(sA * gc.K + sB)), 1u);
+  if (I.dump != nullptr && lp == 0 && pa == 0u) {
     I.dump[3 * (size_t)k] = (int64_t)n;
     I.dump[3 * (size_t)k + 1] = s1;
     I.dump[3 * (size_t)k + 2] = (int64_t)s2;
   }
 }
 
-// Read (and clear) the table after a sweep: symbols, bbox and histogram unless `discard`.
+// Read (and clear) the table after a sweep: symbols, bboxes and histograms unless `discard`.
 // Every warp scans a contiguous share of the slots and compacts the occupied ones into a
 // list (in its run ring, empty after the sweep), so that the per-voxel work runs with all
 // 32 lanes busy.  The CTA-wide occupied count is added to the occupied flag word.
-template <int kVW, bool kExact>
+template <int kVW, bool kExact, int kNP>
 __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& gc, const EvalItem& I,
                                            unsigned long long* wide, uint32_t* wide_count, int T, int lp,
                                            bool discard) {
@@ -648,7 +723,7 @@ __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& g
   const uint32_t list = S.a_queue + (uint32_t)warp * kQueue * 16u;
   const int per = (T + kWarps * 32 - 1) / (kWarps * 32) * 32;
   const int beg = warp * per, end = min(T, beg + per);
-  ScanBox bx;
+  ScanBox<kNP> bx;
   uint32_t cnt = 0, occupied = 0;
   for (int base = beg; base < end; base += 32) {
     const int s = base + lane;
@@ -659,7 +734,7 @@ __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& g
     occupied += (uint32_t)__popc(m);
     if (cnt >= 32u) {
       __syncwarp();
-      scan_entry<kVW, kExact>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
+      scan_entry<kVW, kExact, kNP>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
       // move the rest down (lane l reads entry l + 32 and writes entry l, which only it read)
       if ((uint32_t)lane + 32u < cnt) sts32(list + 4u * (uint32_t)lane, lds32(list + 4u * ((uint32_t)lane + 32u)));
       __syncwarp();
@@ -668,54 +743,65 @@ __device__ __forceinline__ void scan_table(const EvalSmem& S, const GridConst& g
   }
   __syncwarp();
   if ((uint32_t)lane < cnt)
-    scan_entry<kVW, kExact>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
+    scan_entry<kVW, kExact, kNP>(S, gc, I, wide, wide_count, lds32(list + 4u * (uint32_t)lane), lp, discard, bx);
   if (lane == 0 && occupied) red_add(S.a_key - kFlagOccupied, occupied);
-  const int mn0 = __reduce_min_sync(kFull, bx.mn0), mn1 = __reduce_min_sync(kFull, bx.mn1);
-  const int mn2 = __reduce_min_sync(kFull, bx.mn2), mx0 = __reduce_max_sync(kFull, bx.mx0);
-  const int mx1 = __reduce_max_sync(kFull, bx.mx1), mx2 = __reduce_max_sync(kFull, bx.mx2);
-  if (lane == 0 && !discard && mn0 != INT_MAX) {
-    red_min_s32(S.a_box, mn0); red_min_s32(S.a_box + 4, mn1); red_min_s32(S.a_box + 8, mn2);
-    red_max_s32(S.a_box + 12, mx0); red_max_s32(S.a_box + 16, mx1); red_max_s32(S.a_box + 20, mx2);
+#pragma unroll
+  for (int a = 0; a < kNP; ++a) {
+    const int mn0 = __reduce_min_sync(kFull, bx.mn[a][0]), mn1 = __reduce_min_sync(kFull, bx.mn[a][1]);
+    const int mn2 = __reduce_min_sync(kFull, bx.mn[a][2]), mx0 = __reduce_max_sync(kFull, bx.mx[a][0]);
+    const int mx1 = __reduce_max_sync(kFull, bx.mx[a][1]), mx2 = __reduce_max_sync(kFull, bx.mx[a][2]);
+    if (lane == 0 && !discard && mn0 != INT_MAX) {
+      const uint32_t b = S.a_box + 24u * (uint32_t)a;
+      red_min_s32(b, mn0); red_min_s32(b + 4, mn1); red_min_s32(b + 8, mn2);
+      red_max_s32(b + 12, mx0); red_max_s32(b + 16, mx1); red_max_s32(b + 20, mx2);
+    }
   }
 }
 
 template <int kVW>
-__device__ __forceinline__ void init_smem(const EvalSmem& S, int T, int KK) {
+__device__ __forceinline__ void init_smem(const EvalSmem& S, int T, int KK, int np) {
   const int tid = threadIdx.x;
   for (int i = tid; i < T; i += kThreads) {
     S.tkey[i] = kEmptyKey;
 #pragma unroll
     for (int j = 0; j < kVW; ++j) S.tval[kVW * i + j] = 0u;
   }
-  for (int i = tid; i < KK; i += kThreads) S.hist[i] = 0u;
+  for (int i = tid; i < np * (int)S.hist_stride; i += kThreads) S.hist[i] = 0u;
   if (tid == 0) {
-    S.box[0] = S.box[1] = S.box[2] = INT_MAX;
-    S.box[3] = S.box[4] = S.box[5] = INT_MIN;
+    for (int a = 0; a < np; ++a) {
+      S.box[6 * a + 0] = S.box[6 * a + 1] = S.box[6 * a + 2] = INT_MAX;
+      S.box[6 * a + 3] = S.box[6 * a + 4] = S.box[6 * a + 5] = INT_MIN;
+    }
     S.flags[0] = S.flags[1] = S.flags[2] = S.flags[3] = 0u;
     *S.item = -1;
   }
+  (void)KK;
 }
 
-// Store the pose's partial histogram and bbox, then reset them for the next pose.
-__device__ __forceinline__ void emit_pose(const EvalSmem& S, const EvalItem& I, int lp) {
+// Store the partial histogram and bbox of pose `a` of the sweep as pose lp of item I, then
+// reset them for the next sweep.  Called by all threads.
+__device__ __forceinline__ void emit_pose(const EvalSmem& S, const EvalItem& I, int lp, int a = 0) {
   const int tid = threadIdx.x;
   const int KK = S.gc->K * S.gc->K;
   uint32_t* oc = I.out_c + (size_t)lp * KK;
+  uint32_t* h = S.hist + (size_t)a * S.hist_stride;
+  int32_t* bx = S.box + 6 * a;
   for (int i = tid; i < KK; i += kThreads) {
-    oc[i] = S.hist[i];
-    S.hist[i] = 0u;
+    oc[i] = h[i];
+    h[i] = 0u;
   }
-  if (tid < 6) I.out_box[6 * (size_t)lp + tid] = S.box[tid];
+  if (tid < 6) I.out_box[6 * (size_t)lp + tid] = bx[tid];
   __syncthreads();
-  if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
+  if (tid < 6) bx[tid] = tid < 3 ? INT_MAX : INT_MIN;
   __syncthreads();
 }
 
-__device__ __forceinline__ void reset_pose(const EvalSmem& S) {
+__device__ __forceinline__ void reset_pose(const EvalSmem& S, int a = 0) {
   const int tid = threadIdx.x;
   const int KK = S.gc->K * S.gc->K;
-  for (int i = tid; i < KK; i += kThreads) S.hist[i] = 0u;
-  if (tid < 6) S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
+  uint32_t* h = S.hist + (size_t)a * S.hist_stride;
+  for (int i = tid; i < KK; i += kThreads) h[i] = 0u;
+  if (tid < 6) S.box[6 * a + tid] = tid < 3 ? INT_MAX : INT_MIN;
 }
 
 // Item of global pose gp: the last item whose start is <= gp (binary search).
@@ -760,7 +846,7 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
     point_key<kRot>(vc, P, pts[j], key, dz);
     if (kPart && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != part) key = kEmptyKey;
     const bool done = key != run.key;
-    ring_push<kVW>(S, ring, lane_lt, done, run, fill, a, acc);
+    ring_push<kVW, false>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc);
     if (kVW == 2) {
       run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
     } else {
@@ -774,12 +860,13 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
 
 // The run step of one point whose key and dz are known: append the finished run, extend or
 // restart the run.
-template <int kVW>
+template <int kVW, bool kTwo>
 __device__ __forceinline__ void run_step(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc, uint32_t key,
                                          int dz, Run& run, uint32_t ring, uint32_t lane_lt, uint32_t& fill,
                                          uint32_t& acc) {
   const bool done = key != run.key;
-  ring_push<kVW>(S, ring, lane_lt, done, run, fill, a, acc);
+  // a finished run of points outside the grid (or outside the key partition) is dropped
+  ring_push<kVW, kTwo>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc);
   if (kVW == 2) {
     run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
   } else {
@@ -812,7 +899,7 @@ __device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a,
   int t = 0;
   for (; t + 2 * kDepth <= nt; t += kDepth) {  // every prefetch in range: no guards
     if (t >= next_cut) {  // uniform; only when a stream is longer than nlim points
-      ring_push<kVW>(S, ring, lane_lt, true, run, fill, a, acc);
+      ring_push<kVW, false>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
@@ -833,13 +920,13 @@ __device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a,
 #pragma unroll
     for (int d = 0; d < kDepth; ++d)
 #pragma unroll
-      for (int j = 0; j < kPPT; ++j) run_step<kVW>(S, a, vc, keys[d][j], dzs[d][j], run, ring, lane_lt, fill, acc);
+      for (int j = 0; j < kPPT; ++j) run_step<kVW, false>(S, a, vc, keys[d][j], dzs[d][j], run, ring, lane_lt, fill, acc);
     xy += kDepth * kTileXY;
     zz += kDepth * kTileZ;
   }
   for (; t < nt; t += kDepth) {
     if (t >= next_cut) {
-      ring_push<kVW>(S, ring, lane_lt, true, run, fill, a, acc);
+      ring_push<kVW, false>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
@@ -853,8 +940,113 @@ __device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a,
     xy += kDepth * kTileXY;
     zz += kDepth * kTileZ;
   }
-  ring_push<kVW>(S, ring, lane_lt, true, run, fill, a, acc);
-  while (fill > 0u) ring_drain<kVW, false>(S, ring, fill, min(fill, 32u), a, acc);
+  ring_push<kVW, false>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
+  while (fill > 0u) ring_drain<kVW, false, false>(S, ring, fill, min(fill, 32u), a, acc);
+  if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
+}
+
+// Keys and dz of one pre-rotated point under the two poses of a pair, which differ only in
+// t'_x: the y and z halves of the voxel map (k_y, k_z, the mm rounding and dz) are computed
+// once.  The same FP32 operations as point_key, so each key is bit-identical to a single
+// sweep's; the second pose's keys carry bit 31 (keys are below 2^31).
+__device__ __forceinline__ void pair_key(const VoxelConst& vc, float tx0, float tx1, float ty, float tz,
+                                         const float4& p, uint32_t& k0, uint32_t& k1, int& dz) {
+  const float gy = __fadd_rn(p.y, ty);
+  const float gz = __fadd_rn(p.z, tz);
+  const uint32_t ky = (uint32_t)__float2int_rd(__fmul_rn(gy, vc.inv_res));
+  const uint32_t kz = (uint32_t)__float2int_rd(__fmul_rn(gz, vc.inv_res));
+  const bool in_yz = (ky < (uint32_t)vc.Y) & (kz < (uint32_t)vc.Z);
+  const uint32_t zq = (uint32_t)__float2int_rn(__fmul_rn(gz, 1000.0f));
+  dz = (int)(zq - kz * (uint32_t)vc.res_mm);
+  const uint32_t kyz = (kz * (uint32_t)vc.Y + ky) * (uint32_t)vc.X;
+  const uint32_t kx0 = (uint32_t)__float2int_rd(__fmul_rn(__fadd_rn(p.x, tx0), vc.inv_res));
+  const uint32_t kx1 = (uint32_t)__float2int_rd(__fmul_rn(__fadd_rn(p.x, tx1), vc.inv_res));
+  k0 = (in_yz & (kx0 < (uint32_t)vc.X)) ? kyz + kx0 : kEmptyKey;
+  k1 = (in_yz & (kx1 < (uint32_t)vc.X)) ? (kyz + kx1) | 0x80000000u : kEmptyKey;
+}
+
+// One pass over all tiles for a pose pair (pre-rotated tiles): as sweep_pose, with one run
+// per pose; both poses' runs go to the same ring and table.
+template <int kVW, bool kPart>
+__device__ __forceinline__ void sweep_pair(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc, float tx0,
+                                           float tx1, float ty, float tz, const float4* src, int nt, int lg,
+                                           uint32_t part, uint32_t ring, uint32_t lane_lt, int cut) {
+  Run r0{kEmptyKey, 0u, 0u, 0u}, r1{kEmptyKey, 0u, 0u, 0u};
+  uint32_t fill = 0u, acc = 0u;
+  float4 buf[kPairDepth][kPPT];
+  const float2* xy = reinterpret_cast<const float2*>(src - threadIdx.x) + threadIdx.x;
+  const float* zz = reinterpret_cast<const float*>(src - threadIdx.x) + 2 * kTile + threadIdx.x;
+#pragma unroll
+  for (int d = 0; d < kPairDepth; ++d)
+    if (d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
+  xy += kPairDepth * kTileXY;
+  zz += kPairDepth * kTileZ;
+  int next_cut = cut;
+  int t = 0;
+  for (; t + 2 * kPairDepth <= nt; t += kPairDepth) {
+    if (t >= next_cut) {
+      ring_push<kVW, true>(S, ring, lane_lt, r0.key != kEmptyKey, r0, fill, a, acc);
+      ring_push<kVW, true>(S, ring, lane_lt, r1.key != kEmptyKey, r1, fill, a, acc);
+      r0 = Run{kEmptyKey, 0u, 0u, 0u};
+      r1 = Run{kEmptyKey, 0u, 0u, 0u};
+      next_cut += cut;
+    }
+    uint32_t k0[kPairDepth][kPPT], k1[kPairDepth][kPPT];
+    int dzs[kPairDepth][kPPT];
+#pragma unroll
+    for (int d = 0; d < kPairDepth; ++d)
+#pragma unroll
+      for (int j = 0; j < kPPT; ++j) {
+        pair_key(vc, tx0, tx1, ty, tz, buf[d][j], k0[d][j], k1[d][j], dzs[d][j]);
+        if (kPart) {
+          if (k0[d][j] != kEmptyKey && ((k0[d][j] * 0x85EBCA77u) >> (32 - lg)) != part) k0[d][j] = kEmptyKey;
+          if (k1[d][j] != kEmptyKey && ((k1[d][j] * 0x85EBCA77u) >> (32 - lg)) != part) k1[d][j] = kEmptyKey;
+        }
+      }
+#pragma unroll
+    for (int d = 0; d < kPairDepth; ++d) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
+#pragma unroll
+    for (int d = 0; d < kPairDepth; ++d)
+#pragma unroll
+      for (int j = 0; j < kPPT; ++j) {
+        run_step<kVW, true>(S, a, vc, k0[d][j], dzs[d][j], r0, ring, lane_lt, fill, acc);
+        run_step<kVW, true>(S, a, vc, k1[d][j], dzs[d][j], r1, ring, lane_lt, fill, acc);
+      }
+    xy += kPairDepth * kTileXY;
+    zz += kPairDepth * kTileZ;
+  }
+  for (; t < nt; t += kPairDepth) {
+    if (t >= next_cut) {
+      ring_push<kVW, true>(S, ring, lane_lt, r0.key != kEmptyKey, r0, fill, a, acc);
+      ring_push<kVW, true>(S, ring, lane_lt, r1.key != kEmptyKey, r1, fill, a, acc);
+      r0 = Run{kEmptyKey, 0u, 0u, 0u};
+      r1 = Run{kEmptyKey, 0u, 0u, 0u};
+      next_cut += cut;
+    }
+#pragma unroll
+    for (int d = 0; d < kPairDepth; ++d) {
+      if (t + d < nt) {
+#pragma unroll
+        for (int j = 0; j < kPPT; ++j) {
+          uint32_t q0, q1;
+          int dz;
+          pair_key(vc, tx0, tx1, ty, tz, buf[d][j], q0, q1, dz);
+          if (kPart) {
+            if (q0 != kEmptyKey && ((q0 * 0x85EBCA77u) >> (32 - lg)) != part) q0 = kEmptyKey;
+            if (q1 != kEmptyKey && ((q1 * 0x85EBCA77u) >> (32 - lg)) != part) q1 = kEmptyKey;
+          }
+          run_step<kVW, true>(S, a, vc, q0, dz, r0, ring, lane_lt, fill, acc);
+          run_step<kVW, true>(S, a, vc, q1, dz, r1, ring, lane_lt, fill, acc);
+        }
+        if (t + kPairDepth + d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
+      }
+    }
+    xy += kPairDepth * kTileXY;
+    zz += kPairDepth * kTileZ;
+  }
+  ring_push<kVW, true>(S, ring, lane_lt, r0.key != kEmptyKey, r0, fill, a, acc);
+  ring_push<kVW, true>(S, ring, lane_lt, r1.key != kEmptyKey, r1, fill, a, acc);
+  while (fill > 0u) ring_drain<kVW, false, true>(S, ring, fill, min(fill, 32u), a, acc);
   if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
 }
 
@@ -863,14 +1055,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
   const int T = a.table_slots;
-  eval_smem_layout(a.K, T, kVW, &S, smem_raw);
+  eval_smem_layout(a.K, T, kVW, 1, &S, smem_raw);
   const int tid = threadIdx.x;
   const uint32_t cap = (uint32_t)T - (uint32_t)T / 10u;  // above 90% full the table counts as crowded
   const uint32_t ring = S.a_queue + (uint32_t)(tid >> 5) * kQueue * 16u;
   const uint32_t lane_lt = lane_mask_lt();
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
 
-  init_smem<kVW>(S, T, a.K * a.K);
+  init_smem<kVW>(S, T, a.K * a.K, 1);
   __syncthreads();
   int passes = a.passes0;
   int cur = -1;  // item of the previous pose: key partitions are learned per item
@@ -889,7 +1081,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
     const VoxelConst vc = voxel_const<kVW>(kOne ? a.one.gc : *S.gc);
     const int nt = I.n_tiles;
     // runs are cut every `cut` tiles (a multiple of the prefetch depth, where the sweep checks)
-    const int cut = max(kDepth, (int)min(vc.nlim / (uint32_t)kPPT, (uint32_t)INT_MAX) / kDepth * kDepth);
+    const int cut = max(kPairDepth, (int)min(vc.nlim / (uint32_t)kPPT, (uint32_t)INT_MAX) / kPairDepth * kPairDepth);
     PoseRegs P;
     load_pose(I.poses + 12 * (size_t)lp, P);
     const float4* src = pose_tiles(I, lp) + tid;
@@ -905,12 +1097,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
       }
       __syncthreads();
       if (!full && *(volatile uint32_t*)&S.flags[2] != 0u) {  // runs whose home bucket was full
-        insert_overflow<kVW>(S, a, kOne ? a.one.gc : *S.gc);
+        insert_overflow<kVW, false>(S, a, kOne ? a.one.gc : *S.gc);
         __syncthreads();
       }
       overflowed = overflowed || S.flags[1] != 0u;
       full = full || overflowed;
-      scan_table<kVW, false>(S, kOne ? a.one.gc : *S.gc, I, wide, a.wide_count, T, lp, full);
+      scan_table<kVW, false, 1>(S, kOne ? a.one.gc : *S.gc, I, wide, a.wide_count, T, lp, full);
       __syncthreads();
       max_occupied = max(max_occupied, S.flags[0]);
       full = full || S.flags[3] != 0u;  // a voxel beyond the table sums: wide sums, not partitions
@@ -941,6 +1133,116 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
   }
 }
 
+// One sweep set of the pair kernel: the poses lp0 and, with kNP == 2, lp1 (a pair that shares
+// its tile copy and t'_y, t'_z) swept together over the same table, key partitions as
+// needed; then their histograms and boxes, or both poses to the exact path.
+template <int kVW>
+__device__ __forceinline__ void pair_sweep_set(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc, int lp0,
+                                               int lp1, bool two, int T, int cut, uint32_t cap, uint32_t ring,
+                                               uint32_t lane_lt, unsigned long long* wide, int& passes) {
+  constexpr int kNP = 2;
+  const EvalItem& I = a.one;
+  const int tid = threadIdx.x;
+  PoseRegs P;
+  load_pose(I.poses + 12 * (size_t)lp0, P);
+  // without a second pose, t'_x = +inf puts every point of the second run outside the grid
+  const float tx1 = two ? __ldg(I.poses + 12 * (size_t)lp1 + 9) : __int_as_float(0x7f800000);
+  const float4* src = pose_tiles(I, lp0) + tid;
+  const int nt = I.n_tiles;
+  const int pose_passes = passes;
+  const int lg = __ffs(pose_passes) - 1;
+  uint32_t max_occupied = 0;
+  bool full = false, overflowed = false;
+  for (int pass = 0; pass < pose_passes; ++pass) {
+    if (!full) {
+      if (lg == 0) sweep_pair<kVW, false>(S, a, vc, P.t[0], tx1, P.t[1], P.t[2], src, nt, 0, 0u, ring, lane_lt, cut);
+      else sweep_pair<kVW, true>(S, a, vc, P.t[0], tx1, P.t[1], P.t[2], src, nt, lg, (uint32_t)pass, ring, lane_lt,
+                                 cut);
+    }
+    __syncthreads();
+    if (!full && *(volatile uint32_t*)&S.flags[2] != 0u) {  // runs whose home bucket was full
+      insert_overflow<kVW, true>(S, a, I.gc);
+      __syncthreads();
+    }
+    overflowed = overflowed || S.flags[1] != 0u;
+    full = full || overflowed;
+    scan_table<kVW, false, kNP>(S, I.gc, I, wide, a.wide_count, T, lp0, full);
+    __syncthreads();
+    max_occupied = max(max_occupied, S.flags[0]);
+    full = full || S.flags[3] != 0u;  // a voxel beyond the table sums: wide sums, not partitions
+    __syncthreads();
+    if (tid == 0) {
+      S.flags[0] = 0u;
+      S.flags[2] = 0u;
+      S.flags[3] = 0u;
+    }
+  }
+  if (full) {  // both poses are finished later by the exact path
+    reset_pose(S, 0);
+    reset_pose(S, 1);
+    if (tid == 0) {
+      S.flags[1] = 0u;
+      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)lp0;
+      if (two) a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)lp1;
+    }
+    if (overflowed && passes < kMaxPasses) passes *= 2;
+    __syncthreads();
+    return;
+  }
+  emit_pose(S, I, lp0, 0);
+  if (two) emit_pose(S, I, lp1, 1);
+  else reset_pose(S, 1);
+  if (max_occupied > cap && passes < kMaxPasses) passes *= 2;  // crowded: more partitions next
+}
+
+// Pose pairs (pre-rotated tiles, one item): unit u of a.units is (pose, pose or -1).  Two
+// poses that read the same tile copy and whose t'_y and t'_z are equal bit for bit are swept
+// together (sweep_pair: one point load and one y/z voxel-map half for both); any other unit
+// is swept one pose at a time.  The results are those of the single-pose kernel.
+template <int kVW>
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_pair_kernel(const __grid_constant__ EvalArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  EvalSmem S;
+  const int T = a.table_slots;
+  eval_smem_layout(a.K, T, kVW, 2, &S, smem_raw);
+  const int tid = threadIdx.x;
+  const uint32_t cap = (uint32_t)T - (uint32_t)T / 10u;  // above 90% full the table counts as crowded
+  const uint32_t ring = S.a_queue + (uint32_t)(tid >> 5) * kQueue * 16u;
+  const uint32_t lane_lt = lane_mask_lt();
+  unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
+  init_smem<kVW>(S, T, a.K * a.K, 2);
+  __syncthreads();
+  select_item(S, a, 0);
+  const EvalItem& I = a.one;
+  int passes = I.passes0 > 0 ? I.passes0 : a.passes0;
+  const VoxelConst vc = voxel_const<kVW>(I.gc);
+  // runs are cut every `cut` tiles (a multiple of the prefetch depth, where the sweep checks)
+  const int cut = max(kDepth, (int)min(vc.nlim / (uint32_t)kPPT, (uint32_t)INT_MAX) / kDepth * kDepth);
+  static_assert(kDepth % kPairDepth == 0, "the pair sweep checks cuts at multiples of its depth");
+  for (int u = blockIdx.x; u < a.n_units; u += gridDim.x) {
+    const int p0 = __ldg(a.units + 2 * u), p1 = __ldg(a.units + 2 * u + 1);
+    bool two = false;
+    if (p1 >= 0) {
+      const float* q0 = I.poses + 12 * (size_t)p0;
+      const float* q1 = I.poses + 12 * (size_t)p1;
+      const int s0 = I.pose_src ? __ldg(I.pose_src + p0) : 0, s1 = I.pose_src ? __ldg(I.pose_src + p1) : 0;
+      two = s0 == s1 && __float_as_uint(__ldg(q0 + 10)) == __float_as_uint(__ldg(q1 + 10)) &&
+            __float_as_uint(__ldg(q0 + 11)) == __float_as_uint(__ldg(q1 + 11));
+    }
+    if (two || p1 < 0) {
+      // a single pose is swept as a pair whose second pose has no point inside the grid
+      pair_sweep_set<kVW>(S, a, vc, p0, p1, two, T, cut, cap, ring, lane_lt, wide, passes);
+    } else if (tid == 0) {  // not a pair after all: both poses go to the exact path (single sweeps)
+      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)p0;
+      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)p1;
+    }
+  }
+  if (tid == 0) {
+    atomicMax(a.max_passes, (uint32_t)passes);
+    if (I.item_passes) atomicMax(I.item_passes, (uint32_t)passes);
+  }
+}
+
 // Poses that eval_kernel could not finish: plain sweeps; each run goes straight into the
 // table with 64-bit side sums for voxels beyond the 32-bit bound; a full table restarts
 // the pose with twice the key partitions.
@@ -950,13 +1252,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
   const int T = a.table_slots;
-  eval_smem_layout(a.K, T, kVW, &S, smem_raw);
+  eval_smem_layout(a.K, T, kVW, a.units != nullptr ? 2 : 1, &S, smem_raw);
   const int tid = threadIdx.x;
   const uint32_t nb = (uint32_t)T >> 2;
   unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
   const uint32_t n_redo = *(volatile const uint32_t*)a.redo_count;
   if (blockIdx.x >= n_redo) return;
-  init_smem<kVW>(S, T, a.K * a.K);
+  init_smem<kVW>(S, T, a.K * a.K, 1);
   __syncthreads();
   int passes_used = 1;
   for (uint32_t i = blockIdx.x; i < n_redo; i += gridDim.x) {
@@ -1003,7 +1305,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
       if (rkey != kEmptyKey && rn != 0u) add_run<kVW>(S, wide, rkey, rn, (int)rs1, rs2, nb);
       __syncthreads();
       const bool full = S.flags[1] != 0u;
-      scan_table<kVW, true>(S, *S.gc, I, wide, a.wide_count, T, lp, full);
+      scan_table<kVW, true, 1>(S, *S.gc, I, wide, a.wide_count, T, lp, full);
       __syncthreads();
       if (tid == 0) S.flags[0] = 0u;
       if (full) {
@@ -1218,6 +1520,8 @@ cudaError_t setup_t(int smem) {
     e = cudaFuncSetAttribute(eval_kernel<kVW, kRot, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(redo_kernel<kVW, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess && !kRot)
+    e = cudaFuncSetAttribute(eval_pair_kernel<kVW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
@@ -1235,11 +1539,11 @@ int eval_tile_points() { return kTile; }
 int eval_ovf_cap() { return kOvfCap; }
 int eval_min_tiles() { return kMinTiles; }
 
-size_t eval_smem_bytes(int K, int table_slots, int vw) {
-  return eval_smem_layout(K, table_slots, vw, nullptr, nullptr);
+size_t eval_smem_bytes(int K, int table_slots, int vw, int np) {
+  return eval_smem_layout(K, table_slots, vw, np, nullptr, nullptr);
 }
 
-int eval_table_slots_for(int K, int vw, size_t smem_budget) {
+int eval_table_slots_for(int K, int vw, size_t smem_budget, int np) {
   if (kCtasPerSm > 1) {  // share the SM's shared memory between its resident CTAs
     int dev = 0, per_sm = 0, reserved = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -1248,12 +1552,30 @@ int eval_table_slots_for(int K, int vw, size_t smem_budget) {
       smem_budget = std::min(smem_budget, (size_t)(per_sm / kCtasPerSm - reserved));
   }
   int lo = 32;
-  while (eval_smem_bytes(K, lo + 32, vw) <= smem_budget && lo < (1 << 16)) lo += 32;
+  while (eval_smem_bytes(K, lo + 32, vw, np) <= smem_budget && lo < (1 << 16)) lo += 32;
   return lo;
 }
 
+template <int kVW>
+cudaError_t launch_pair_t(const EvalArgs& a, int n_ctas, size_t smem, cudaStream_t s) {
+  eval_pair_kernel<kVW><<<n_ctas, kThreads, smem, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  redo_kernel<kVW, false><<<n_ctas, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_eval(const EvalArgs& a, int n_ctas, int vw, bool rotate, cudaStream_t s) {
-  const size_t smem = eval_smem_bytes(a.K, a.table_slots, vw);
+  const size_t smem = eval_smem_bytes(a.K, a.table_slots, vw, a.units != nullptr ? 2 : 1);
+  if (a.units != nullptr) {  // pose pairs: pre-rotated tiles of one item only
+    if (rotate || a.item_start != nullptr) return cudaErrorInvalidValue;
+    switch (vw) {
+      case 1: return launch_pair_t<1>(a, n_ctas, smem, s);
+      case 2: return launch_pair_t<2>(a, n_ctas, smem, s);
+      case 3: return launch_pair_t<3>(a, n_ctas, smem, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (vw) {
     case 1: return rotate ? launch_eval_t<1, true>(a, n_ctas, smem, s) : launch_eval_t<1, false>(a, n_ctas, smem, s);
     case 2: return rotate ? launch_eval_t<2, true>(a, n_ctas, smem, s) : launch_eval_t<2, false>(a, n_ctas, smem, s);

@@ -331,11 +331,59 @@ int max_rotation_copies(int64_t P, int32_t n_tiles) {
   return std::min(max_groups, cap_mem);
 }
 
+// Pose pairs for the pair kernel: poses that read the same pre-rotated tile copy (group
+// index `src`) and whose t'_y and t'_z are equal bit for bit, two at a time in order of
+// their first pose; a group's odd pose is a unit of its own.  Two entries per unit (the
+// second -1 for a single pose).  Returns the unit count.
+int pair_units(const float* poses12, const int32_t* src, int64_t P, std::vector<int32_t>& units) {
+  struct Key {
+    int32_t src;
+    uint32_t ty, tz;
+    bool operator==(const Key& o) const { return src == o.src && ty == o.ty && tz == o.tz; }
+  };
+  struct KeyHash {
+    size_t operator()(const Key& k) const {
+      return (size_t)(((uint64_t)(uint32_t)k.src * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)k.ty << 32 | k.tz));
+    }
+  };
+  std::unordered_map<Key, int64_t, KeyHash> open;  // pose waiting for a partner, per key
+  std::vector<int64_t> partner((size_t)P, -2);     // -2: not yet placed
+  units.clear();
+  std::vector<std::pair<int64_t, int64_t>> pairs;
+  for (int64_t p = 0; p < P; ++p) {
+    Key k;
+    k.src = src ? src[p] : 0;
+    std::memcpy(&k.ty, poses12 + 12 * p + 10, 4);
+    std::memcpy(&k.tz, poses12 + 12 * p + 11, 4);
+    auto it = open.find(k);
+    if (it == open.end()) {
+      open.emplace(k, p);
+    } else {
+      pairs.emplace_back(it->second, p);
+      open.erase(it);
+    }
+  }
+  for (const auto& kv : open) pairs.emplace_back(kv.second, -1);
+  std::sort(pairs.begin(), pairs.end());
+  for (const auto& q : pairs) {
+    units.push_back((int32_t)q.first);
+    units.push_back((int32_t)q.second);
+  }
+  return (int)pairs.size();
+}
+
+// Whether the next pre-rotated launch on this grid evaluates pose pairs: while pairs have
+// needed no more key partitions than single poses (both counts are learned per grid and
+// only grow), one pair sweep does the work of two single sweeps.
+bool use_pairs(const align_grid* g) { return g->passes_seed_pair <= g->passes_seed[0]; }
+
 align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_poses, int64_t P, bool rotate,
-                               int n_rot, const EvalOut& out);
+                               int n_rot, const EvalOut& out, const int32_t* d_units = nullptr,
+                               int32_t n_units = 0);
 
 // Enqueue pack + eval + redo + compose + argmax for poses already on the device.
-// h_poses (may be NULL): the same poses on the host, used to find shared rotations.
+// h_poses (may be NULL): the same poses on the host, used to find shared rotations (and
+// pose pairs).
 align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, const float* h_poses, int64_t P,
                           const EvalOut& out) {
   bool rotate = true;
@@ -344,6 +392,23 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
     std::vector<float> rots;
     std::vector<int32_t> idx;
     const int groups = group_rotations(h_poses, P, rots, idx, max_rotation_copies(P, n_tiles));
+    if (groups > 0 && out.dump == nullptr && P >= 2 && use_pairs(g)) {
+      std::vector<int32_t> units;
+      const int n_units = pair_units(h_poses, idx.data(), P, units);
+      if (n_units < P) {  // at least one pair
+        CU(g->rots.ensure(rots.size() * 4), "allocate rotations");
+        CU(cudaMemcpyAsync(g->rots.p, rots.data(), rots.size() * 4, cudaMemcpyHostToDevice, g->stream),
+           "copy rotations");
+        CU(g->pose_src.ensure((size_t)P * 4), "allocate pose sources");
+        CU(cudaMemcpyAsync(g->pose_src.p, idx.data(), (size_t)P * 4, cudaMemcpyHostToDevice, g->stream),
+           "copy pose sources");
+        CU(g->units.ensure(units.size() * 4), "allocate pose pairs");
+        CU(cudaMemcpyAsync(g->units.p, units.data(), units.size() * 4, cudaMemcpyHostToDevice, g->stream),
+           "copy pose pairs");
+        // the copies read pageable host memory: they complete before this call returns
+        return enqueue_eval_core(g, n_tiles, d_poses, P, false, groups, out, g->units.as<int32_t>(), n_units);
+      }
+    }
     if (groups > 0) {
       CU(g->rots.ensure(rots.size() * 4), "allocate rotations");
       CU(cudaMemcpyAsync(g->rots.p, rots.data(), rots.size() * 4, cudaMemcpyHostToDevice, g->stream),
@@ -361,7 +426,7 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
 // The launches of one evaluation.  Unless `rotate`, g->rots holds n_rot rotations and
 // g->pose_src each pose's rotation (on the device, in stream order).
 align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_poses, int64_t P, bool rotate,
-                               int n_rot, const EvalOut& out) {
+                               int n_rot, const EvalOut& out, const int32_t* d_units, int32_t n_units) {
   const int K = g->gc.K;
   const size_t KK = (size_t)K * K;
   CU(g->out_c.ensure((size_t)P * KK * sizeof(uint32_t)), "allocate histograms");
@@ -369,10 +434,12 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   CU(g->best.ensure(sizeof(unsigned long long)), "allocate argmax");
   align_status st0 = ensure_status_words(g);
   if (st0 != ALIGN_OK) return st0;
-  const int n_ctas = (int)std::min<int64_t>(P, g->n_sm);
+  const bool pairs = d_units != nullptr && n_units > 0 && !rotate;
+  const int n_ctas = (int)std::min<int64_t>(pairs ? n_units : P, g->n_sm);
   const bool var = g->gc.feature != ALIGN_FEAT_COUNT || out.dump != nullptr;
   const int vw = eval_layout(g->gc, var);
-  g->table_slots = eval_shape(0).table_slots_for(K, vw, g->smem_optin);
+  g->table_slots = eval_shape(0).table_slots_for(K, vw, g->smem_optin, pairs ? 2 : 1);
+  g->last_pairs = pairs;
   const size_t wide_bytes = (size_t)n_ctas * 2 * g->table_slots * sizeof(unsigned long long);
   if (g->wide.cap < wide_bytes || g->wide.p == nullptr) {
     CU(g->wide.ensure(wide_bytes), "allocate wide sums");
@@ -403,7 +470,7 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   item.n_tiles = n_tiles;
   item.P = (int32_t)P;
   item.pose_base = 0;
-  item.passes0 = g->passes_seed[0];
+  item.passes0 = pairs ? g->passes_seed_pair : g->passes_seed[0];
   item.item_passes = nullptr;
   item.out_c = g->out_c.as<uint32_t>();
   item.out_box = g->out_box.as<int32_t>();
@@ -424,7 +491,9 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   a.K = K;
   a.table_slots = g->table_slots;
   a.n_buckets = g->table_slots / 4;
-  a.passes0 = g->passes_seed[0];
+  a.passes0 = item.passes0;
+  a.units = pairs ? d_units : nullptr;
+  a.n_units = pairs ? n_units : 0;
   a.err = g->err.as<uint32_t>();
   a.max_passes = g->max_passes.as<uint32_t>();
   a.wide_count = g->wide_count.as<uint32_t>();
@@ -474,6 +543,14 @@ align_status drain_events(align_grid* g) {
   return ALIGN_OK;
 }
 
+// Key partitions the last launch's hardest pose needed: the seed of the next launch of the
+// same kind.
+void learn_passes(align_grid* g, uint32_t used) {
+  if (used == 0 || used > (1u << 16) || (used & (used - 1)) != 0) return;
+  int32_t& seed = g->last_pairs ? g->passes_seed_pair : g->passes_seed[0];
+  if (used > (uint32_t)seed) seed = (int32_t)used;
+}
+
 // Read back the kernels' error word and counters (synchronises the stream).
 align_status collect_status(align_grid* g) {
   uint32_t vals[3] = {0, 0, 0};
@@ -488,9 +565,9 @@ align_status collect_status(align_grid* g) {
   CU(cudaMemsetAsync(g->err.p, 0, 4, g->stream), "reset error word");
   CU(cudaMemsetAsync(g->wide_count.p, 0, 4, g->stream), "reset counters");
   CU(cudaMemsetAsync(g->max_passes.p, 0, 4, g->stream), "reset counters");  // a per-launch maximum
-  // seed the next launch with the largest partition count a pose needed (a power of two)
-  if (vals[1] > (uint32_t)g->passes_seed[0] && vals[1] <= (1u << 16) && (vals[1] & (vals[1] - 1)) == 0)
-    g->passes_seed[0] = (int32_t)vals[1];
+  // seed the next launch of the same kind (pairs or single poses) with the largest
+  // partition count a pose needed (a power of two)
+  learn_passes(g, vals[1]);
   g->stats[0] = vals[1];
   g->stats[1] = vals[2];
   if (vals[0] & kErrDzBound) return fail(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");
@@ -554,6 +631,29 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
   // before the buffers change (a search that finished has synchronised the stream)
   if (g->lat_pending) CU(cudaStreamSynchronize(g->stream), "synchronize");
   g->lat_pending = true;
+  // pose pairs of every level (the lattice's index structure: t_x samples 2i and 2i+1 of the
+  // same rotation, t_y and t_z), decided once for the whole search
+  const bool pairs = P >= 2 && m[0] >= 2 && use_pairs(g);
+  int32_t n_units = 0;
+  if (pairs) {
+    if (!std::equal(m, m + 6, g->lattice_units_m) || g->lat_units.p == nullptr) {
+      std::vector<int32_t>& u = g->lattice_units;
+      u.clear();
+      const int64_t n_yz = (int64_t)m[1] * m[2], n_trans = (int64_t)m[0] * n_yz;
+      for (int64_t p = 0; p < P; ++p) {
+        const int64_t itx = (p % n_trans) / n_yz;
+        if (itx % 2 != 0) continue;
+        u.push_back((int32_t)p);
+        u.push_back(itx + 1 < m[0] ? (int32_t)(p + n_yz) : -1);
+      }
+      CU(g->lat_units.ensure(u.size() * 4), "allocate pose pairs");
+      // a pageable source: staged before the call returns
+      CU(cudaMemcpyAsync(g->lat_units.p, u.data(), u.size() * 4, cudaMemcpyHostToDevice, g->stream),
+         "copy pose pairs");
+      std::copy(m, m + 6, g->lattice_units_m);
+    }
+    n_units = (int32_t)(g->lattice_units.size() / 2);
+  }
   Rec* rec = g->lat_rec_h.as<Rec>();
   std::vector<std::array<double, 6>> c((size_t)levels + 1), r((size_t)levels);
   for (int a = 0; a < 6; ++a) c[0][a] = c0[a], r[0][a] = r0[a];
@@ -571,9 +671,7 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
       if (q.am < 0 || q.am >= P) return fail(ALIGN_E_INTERNAL, "argmax out of range");
       lattice_sample(c[(size_t)l - 2].data(), r[(size_t)l - 2].data(), m, q.am, c[(size_t)l - 1].data());
       passes_used = std::max(passes_used, q.max_passes);
-      if (q.max_passes > (uint32_t)g->passes_seed[0] && q.max_passes <= (1u << 16) &&
-          (q.max_passes & (q.max_passes - 1)) == 0)
-        g->passes_seed[0] = (int32_t)q.max_passes;
+      learn_passes(g, q.max_passes);
     }
     // rotation table of level l: options = rotation samples of level l-1 (one at level 0).
     // Per axis the angle of (option sample i, sample j) is centre + offset_i + offset_j; its
@@ -627,7 +725,8 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
     EvalOut o{};
     o.mi = g->mi.as<float>();
     o.argmax = g->argmax.as<int64_t>();
-    align_status st = enqueue_eval_core(g, n_tiles, g->poses.as<float>(), P, false, n_rot, o);
+    align_status st = enqueue_eval_core(g, n_tiles, g->poses.as<float>(), P, false, n_rot, o,
+                                        pairs ? g->lat_units.as<int32_t>() : nullptr, n_units);
     if (st != ALIGN_OK) return st;
     CU(cudaMemcpyAsync(&rec[l].am, g->argmax.p, 8, cudaMemcpyDeviceToHost, g->stream), "read argmax");
     CU(cudaMemcpyAsync(&rec[l].best, g->best.p, 8, cudaMemcpyDeviceToHost, g->stream), "read best");
@@ -693,7 +792,7 @@ align_status align_create_grid(const align_grid_desc* desc, void* cuda_stream, a
   g->device = dev;
   g->n_sm = prop.multiProcessorCount;
   g->smem_optin = prop.sharedMemPerBlockOptin;
-  g->table_slots = eval_shape(0).table_slots_for(gc.K, eval_layout(gc, gc.feature != ALIGN_FEAT_COUNT), g->smem_optin);
+  g->table_slots = eval_shape(0).table_slots_for(gc.K, eval_layout(gc, gc.feature != ALIGN_FEAT_COUNT), g->smem_optin, 1);
   for (int i = 0; i < 6; ++i) g->boxA[i] = i < 3 ? INT_MAX : INT_MIN;
   *out = g;
   return ALIGN_OK;
@@ -706,7 +805,8 @@ align_status align_destroy_grid(align_grid* g) {
   for (DevBuf* b : {&g->symA, &g->sat, &g->xyz, &g->poses, &g->out_c, &g->out_box, &g->mi, &g->hist, &g->best,
                     &g->argmax, &g->err, &g->max_passes, &g->wide_count, &g->wide, &g->dump, &g->pts4,
                     &g->pose_src, &g->rots, &g->redo_list, &g->redo_count, &g->items, &g->ovf, &g->lat_c,
-                    &g->lat_cand, &g->ref_pts, &g->ref_pose, &g->ref_cnt, &g->ref_s1, &g->ref_s2, &g->ref_box})
+                    &g->lat_cand, &g->ref_pts, &g->ref_pose, &g->ref_cnt, &g->ref_s1, &g->ref_s2, &g->ref_box,
+                    &g->units, &g->lat_units})
     b->release();
   for (HostBuf* b : {&g->lat_cand_h, &g->lat_rec_h, &g->lat_c_h, &g->ref_box_h}) b->release();
   for (cudaEvent_t e : g->lat_ev) cudaEventDestroy(e);

@@ -105,8 +105,15 @@ struct align_grid {
   std::vector<cudaEvent_t> lat_ev;
   bool lat_pending = false;  // a search's copies may still be reading the pinned buffers
   int64_t n_points = 0;  // points staged in `xyz`
-  // key partitions the next launch starts with, per kernel shape (its table size)
+  // key partitions the next launch starts with, per kernel shape (its table size), and for
+  // the pose-pair kernel (shape 0)
   int32_t passes_seed[mialign::kEvalShapes] = {1, 1, 1};
+  int32_t passes_seed_pair = 1;
+  bool last_pairs = false;  // the last eval launch evaluated pose pairs
+  mialign::DevBuf units;    // pose pairs of the last pair launch with host poses
+  mialign::DevBuf lat_units;           // pose pairs of a device-built lattice level (by index)
+  std::vector<int32_t> lattice_units;  // ... on the host
+  int32_t lattice_units_m[6] = {0, 0, 0, 0, 0, 0};
   int64_t stats[5] = {0, 0, 0, 0, 0};
   // event timing (align_profile): one (before eval, after eval, after argmax) triple per
   // launch, drained into the totals at the next synchronising call or profile read

@@ -170,3 +170,39 @@ def test_hand_fixture_on_gpu():
         assert bbox.tolist() == hand["boxB"]
         exp = oracle.mi_from_hist(np.array(hand[mode]["hist"]))
         assert abs(mi[0] - exp) <= mi_tolerance()
+
+
+@pytest.mark.parametrize("res,feature", [(0.5, 1), (1.0, 1), (1.0, 0)])
+def test_pose_pairs_match_single_pose_kernel(res, feature):
+    """A lattice given as host poses is evaluated two poses per sweep (poses that share their
+    rotation, t_y and t_z); the same poses given as device poses go through the single-pose
+    kernel.  Histograms and MI must agree bit for bit, for each table layout (three value
+    words at 1 m z-variance, the packed two-word layout at 0.5 m, the count-only layout),
+    and a sample must match the oracle."""
+    import torch
+    from paper_1709_06948_gb300 import align
+    pair = scangen.lidar_pair(seed=scangen.SEED_BASE + 71, n_beams=32)
+    spec = scangen.lidar_grid(res)
+    over = dict(feature=feature, count_levels=7, var_levels=15 if feature == 1 else 1)
+    L = lib_grid(spec, **over)
+    align.align_set_reference(L, pair.xyzA)
+    single_slots = align.align_eval_stats(L)["table_slots"]
+    etas = scangen.pose_grid(pair.T, (0.8, 0.8, 0.1, 0.01, 0.01, 0.04), (8, 4, 2, 1, 1, 2))
+    mi_p, am_p, h_p = align.align_eval_mi(L, pair.xyzB, eta6=etas, with_hist=True)
+    assert align.align_eval_stats(L)["table_slots"] != single_slots  # the pair kernel ran
+    poses = align.align_round_poses(spec.origin, etas)
+    P = len(etas)
+    mi_d = torch.empty(P, device="cuda")
+    am_d = torch.empty(1, dtype=torch.int64, device="cuda")
+    h_d = torch.empty((P, L.K, L.K), dtype=torch.int32, device="cuda")
+    align.align_eval_mi(L, torch.from_numpy(pair.xyzB).cuda(), poses12=torch.from_numpy(poses).cuda(),
+                        out=(mi_d, am_d, h_d))
+    torch.cuda.synchronize()
+    assert np.array_equal(h_p, h_d.cpu().numpy().view(np.uint32))
+    assert np.array_equal(mi_p, mi_d.cpu().numpy()) and am_p == int(am_d.item())
+    G = oracle_grid(spec, **over)
+    symA, boxA = G.reference(pair.xyzA)
+    sample = np.arange(0, P, 5)
+    mo, ho, _ = G.eval_mi(symA, boxA, pair.xyzB, poses[sample], nthreads=NT, with_hist=True)
+    assert np.array_equal(h_p[sample], ho)
+    assert np.max(np.abs(mi_p[sample].astype(np.float64) - mo)) <= mi_tolerance()
