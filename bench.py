@@ -153,7 +153,7 @@ def code_digest(path):
 def committed_traffic():
     """Per-launch DRAM bytes of the eval kernel from the committed ncu summary, if it was
     taken on the current kernel code (else None)."""
-    path = os.path.join(ROOT, "profiles", "eval_kernel_lidar120k.md")
+    path = os.path.join(ROOT, "profiles", "eval_pair_kernel_lidar120k.md")
     src = os.path.join(ROOT, "paper_1709_06948_gb300", "csrc", "eval.cu")
     try:
         text = open(path).read()
@@ -598,7 +598,8 @@ def run_ours(args):
         peak = dev_props.multi_processor_count * 128 * 2070.0e6 / 1e12
         basis = "derived: SMs x 128 lanes x 2,070 MHz (of derived peak; micro-benchmarks skipped)"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "eval_kernel", "eval_kernel_ms": eval_ms,
+                "traffic": traffic, "kernel": "eval_pair_kernel (pose pairs; eval_kernel for single poses)",
+                "eval_kernel_ms": eval_ms,
                 "ops_per_launch": ops_per_launch,
                 "ops_basis": f"{OPS_MAP} lane-ops per (point, pose) x {nB} points x {P} poses",
                 "achieved_amortised": achieved_am, "frac_amortised": achieved_am / peak,
