@@ -57,7 +57,9 @@
 extern "C" {
 #endif
 
-#define ALIGN_API_VERSION 1
+/* 2: align_batch_stats fills 9 counters (poses per CTA added); align_batch_set_poses_per_cta,
+   align_eval_redo_poses and align_microbench added. */
+#define ALIGN_API_VERSION 2
 
 typedef enum {
   ALIGN_OK = 0,
@@ -272,11 +274,20 @@ align_status align_eval_batch(align_batch* b, const align_pair* pairs, int32_t n
 /* Fix the kernel shape (0..2, see align_batch_stats) or return to the default (-1). */
 align_status align_batch_set_shape(align_batch* b, int32_t shape);
 
+/* Fix the poses a CTA sweeps together: 1 (one pose per sweep) or 2 (pose pairs: two poses of
+   a pair with the same rotation, t_y and t_z share one pass over the points and one
+   shared-memory table), or return to the default (-1: pairs where the poses form them).
+   Pairs need pre-rotated tiles (host poses whose rotations repeat); results are the same
+   either way. */
+align_status align_batch_set_poses_per_cta(align_batch* b, int32_t poses_per_cta);
+
 /* Counters: [0] batch launches, [1] graph captures, [2] graph replays, [3] kernel shape of
    the last launch (0: 1024 threads x 1 point per tile, 1: 1024 x 2, 2: 512 x 1 with two
-   CTAs per SM), [4] table slots per CTA, [5] kernels launched by the library, [6] device
-   time of the last launch in microseconds (pack to argmax), [7] tuner trials run. */
-align_status align_batch_stats(const align_batch* b, int64_t out[8]);
+   CTAs per SM), [4] largest table slots per CTA of the last launch, [5] kernels launched by
+   the library, [6] device time of the last launch in microseconds (pack to argmax), [7]
+   tuner trials run, [8] poses per CTA of the last launch (2 when any pair used pose pairs).
+   The tuner (ALIGN_BATCH_TUNE) times every kernel shape x poses-per-CTA candidate. */
+align_status align_batch_stats(const align_batch* b, int64_t out[9]);
 
 /* ---------------------------------------------------------------------------------
    Serving: alignment requests (a lattice search of scan B against a resident reference

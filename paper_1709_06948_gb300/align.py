@@ -29,7 +29,8 @@ _STATUS_NAMES = {0: "ALIGN_OK", 1: "ALIGN_NOT_READY", -1: "ALIGN_E_INVALID", -2:
 EXPORTS = ["align_create_grid", "align_destroy_grid", "align_grid_info", "align_set_reference",
            "align_get_reference", "align_round_poses", "align_eval_mi", "align_accumulate", "align_search",
            "align_search_ex", "align_eval_stats", "align_eval_redo_poses", "align_profile", "align_microbench", "align_reference_noalloc", "align_batch_create",
-           "align_batch_destroy", "align_eval_batch", "align_batch_set_shape", "align_batch_stats",
+           "align_batch_destroy", "align_eval_batch", "align_batch_set_shape", "align_batch_set_poses_per_cta",
+           "align_batch_stats",
            "align_server_create", "align_server_add_reference", "align_submit", "align_poll", "align_wait",
            "align_server_now", "align_server_stats", "align_server_destroy", "align_refine_nm", "align_last_error"]
 
@@ -100,6 +101,7 @@ def load(build_if_missing: bool = True):
         "align_batch_destroy": [P],
         "align_eval_batch": [P, P, i32, C.c_int],
         "align_batch_set_shape": [P, i32],
+        "align_batch_set_poses_per_cta": [P, i32],
         "align_batch_stats": [P, P],
         "align_server_create": [C.c_size_t, i32, P],
         "align_server_add_reference": [P, P, P, i64, P],
@@ -565,11 +567,15 @@ def align_batch_set_shape(batch: Batch, shape: int):
     _check(load().align_batch_set_shape(batch.handle, int(shape)))
 
 
+def align_batch_set_poses_per_cta(batch: Batch, poses_per_cta: int):
+    _check(load().align_batch_set_poses_per_cta(batch.handle, int(poses_per_cta)))
+
+
 def align_batch_stats(batch: Batch):
-    out = np.zeros(8, dtype=np.int64)
+    out = np.zeros(9, dtype=np.int64)
     _check(load().align_batch_stats(batch.handle, out.ctypes.data_as(C.c_void_p)))
     keys = ["launches", "graph_captures", "graph_replays", "shape", "table_slots", "kernel_launches",
-            "last_us", "tuner_trials"]
+            "last_us", "tuner_trials", "poses_per_cta"]
     return {k: int(v) for k, v in zip(keys, out)}
 
 

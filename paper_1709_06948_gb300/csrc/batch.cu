@@ -47,6 +47,9 @@ struct PairPlan {
   std::vector<float> hposes;  // host fp32 poses (when given on the host)
   std::vector<int32_t> idx;   // pose -> rotation copy
   std::vector<float> rots;    // distinct rotations
+  std::vector<int32_t> units; // pose pairs (pair kernel), two local pose indices per unit
+  int32_t n_units = 0;        // 0: one pose per CTA step (eval_kernel)
+  int64_t unit_off = 0;       // units before this pair's (in units)
   int64_t xyz_off = 0;        // floats
   int64_t pose_off = 0;       // poses (global pose index of pose 0)
   int64_t pts_off = 0;        // float4
@@ -56,7 +59,7 @@ struct PairPlan {
 // Workspace sizes of one launch; a change of any of them re-allocates and drops the graph.
 struct Sizes {
   size_t xyz = 0, poses = 0, pts = 0, pose_src = 0, copies = 0, items = 0, starts = 0, outc = 0, box = 0,
-         best = 0, mi = 0, argmax = 0, redo = 0, wide = 0, ipasses = 0, ovf = 0;
+         best = 0, mi = 0, argmax = 0, redo = 0, wide = 0, ipasses = 0, ovf = 0, units = 0;
 };
 
 std::string env_cache_path() {
@@ -64,7 +67,9 @@ std::string env_cache_path() {
   return p ? std::string(p) : std::string();
 }
 
-// Tuner cache: batch class -> shape.  Shared by all batches of the process.
+// Tuner cache: batch class -> choice (kernel shape * 2 + poses per CTA - 1).  Shared by all
+// batches of the process.
+constexpr int kChoices = 2 * kEvalShapes;
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
@@ -79,7 +84,7 @@ void tune_load_locked() {
   char key[512];
   int shape = 0;
   while (std::fscanf(f, "%511s %d", key, &shape) == 2)
-    if (shape >= 0 && shape < kEvalShapes) g_tune[key] = shape;
+    if (shape >= 0 && shape < kChoices) g_tune[key] = shape;
   std::fclose(f);
 }
 
@@ -116,19 +121,21 @@ struct align_batch {
   std::string device_name;
   int shape_fixed = -1;
   DevBuf xyz, poses, pts, pose_src, copies, items, starts, outc, box, best, mi, argmax, redo_list, redo_count, wide,
-      status, ipasses, ovf;
+      status, ipasses, ovf, units;
   // page-locked staging of the poses and their tile copies (asynchronous copies; a call's
   // copies are done when it returns, since every call synchronises its stream)
   mialign::HostBuf h_poses, h_src;
   bool staged = false;  // copies out of the staging buffers may still be queued
   std::vector<align_grid*> last_grids;  // grids of the last launch (per-item partition feedback)
+  std::vector<char> last_pairs;         // whether each item of the last launch used pose pairs
   int last_shape = 0;
+  int pairs_fixed = -1;                 // poses per CTA set by the caller (1, 2), -1: default
   Sizes cap;
   // graph of the last launch sequence
   cudaGraphExec_t exec = nullptr;
   std::vector<int64_t> sig;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t stats[9] = {0, 0, 0, 0, 0, 0, 0, 0, 1};
 };
 
 namespace {
@@ -229,7 +236,7 @@ align_status collect(align_batch* b) {
   // batches on other threads may share the grid (a server's workers): atomic max
   for (size_t i = 0; i < ip.size(); ++i) {
     align_grid* g = b->last_grids[i];
-    int32_t* seed = &g->passes_seed[b->last_shape];
+    int32_t* seed = b->last_pairs[i] ? &g->passes_seed_pair[b->last_shape] : &g->passes_seed[b->last_shape];
     if (ip[i] > (1u << 16) || (ip[i] & (ip[i] - 1)) != 0) continue;
     int32_t cur = __atomic_load_n(seed, __ATOMIC_RELAXED);
     while ((int32_t)ip[i] > cur &&
@@ -294,7 +301,8 @@ align_status align_batch_destroy(align_batch* b) {
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
   for (DevBuf* d : {&b->xyz, &b->poses, &b->pts, &b->pose_src, &b->copies, &b->items, &b->starts, &b->outc, &b->box,
-                    &b->best, &b->mi, &b->argmax, &b->redo_list, &b->redo_count, &b->wide, &b->status, &b->ipasses, &b->ovf})
+                    &b->best, &b->mi, &b->argmax, &b->redo_list, &b->redo_count, &b->wide, &b->status, &b->ipasses, &b->ovf,
+                    &b->units})
     d->release();
   b->h_poses.release();
   b->h_src.release();
@@ -313,9 +321,17 @@ align_status align_batch_set_shape(align_batch* b, int32_t shape) {
   return ALIGN_OK;
 }
 
-align_status align_batch_stats(const align_batch* b, int64_t out[8]) {
+align_status align_batch_set_poses_per_cta(align_batch* b, int32_t poses_per_cta) {
+  if (!b) return report_error(ALIGN_E_INVALID, "batch is NULL");
+  if (poses_per_cta != -1 && poses_per_cta != 1 && poses_per_cta != 2)
+    return report_error(ALIGN_E_INVALID, "poses_per_cta must be 1, 2 or -1");
+  b->pairs_fixed = poses_per_cta;
+  return ALIGN_OK;
+}
+
+align_status align_batch_stats(const align_batch* b, int64_t out[9]) {
   if (!b || !out) return report_error(ALIGN_E_INVALID, "NULL argument");
-  for (int i = 0; i < 8; ++i) out[i] = b->stats[i];
+  for (int i = 0; i < 9; ++i) out[i] = b->stats[i];
   return ALIGN_OK;
 }
 
@@ -326,7 +342,7 @@ namespace {
 // Plan, stage and launch one batch with kernel shape `shape`; outputs stay in the batch's
 // buffers (copied out by the caller).
 align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, const align_pair* pairs,
-                              const std::vector<int32_t>& which, int flags, int shape) {
+                              const std::vector<int32_t>& which, int flags, int shape, bool pose_pairs) {
   const EvalKernels& ek = eval_shape(shape);
   const int n = (int)plans.size();
   const bool xyz_dev = (flags & ALIGN_XYZ_DEVICE) != 0;
@@ -354,9 +370,21 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     prerot_bytes += (size_t)std::max(groups, 1) * (size_t)pp.n_pad * 16;
     if (groups <= 0 || prerot_bytes > kPrerotBudget) rotate = true;
   }
+  int64_t units_n = 0;
   for (PairPlan& pp : plans) {
     pp.prerot = !rotate;
     pp.n_copies = rotate ? 1 : (int)(pp.rots.size() / 9);
+    // pose pairs: a pair's poses with the same rotation, t_y and t_z (pre-rotated tiles only);
+    // a pair whose poses form no pair keeps the single-pose kernel
+    pp.n_units = 0;
+    pp.units.clear();
+    if (pose_pairs && pp.prerot && pp.P >= 2) {
+      const int nu = pair_units(pp.hposes.data(), pp.idx.data(), pp.P, pp.units);
+      if (nu < pp.P) pp.n_units = nu;
+      else pp.units.clear();
+    }
+    pp.unit_off = units_n;
+    units_n += pp.n_units;
     pp.xyz_off = xyz_f;
     pp.pose_off = poses_n;
     pp.pts_off = pts_n;
@@ -375,7 +403,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   int T = 0;  // the largest table of the launches (sizes the 64-bit side sums)
   for (const PairPlan& pp : plans) {
     vws.push_back(eval_layout(pp.g->gc, var));
-    Ts.push_back(ek.table_slots_for(pp.g->gc.K, vws.back(), b->smem_optin, 1));
+    Ts.push_back(ek.table_slots_for(pp.g->gc.K, vws.back(), b->smem_optin, pp.n_units > 0 ? 2 : 1));
     T = std::max(T, Ts.back());
   }
   const int n_ctas = b->n_sm * ek.ctas_per_sm;
@@ -399,6 +427,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   GROW(ipasses, ipasses, (size_t)n * 4, "allocate partition counts", false);
   GROW(wide, wide, (size_t)n_ctas * 2 * T * 8, "allocate wide sums", true);
   GROW(ovf, ovf, (size_t)n_ctas * ek.ovf_cap() * 16, "allocate overflow lists", false);
+  GROW(units, units, (size_t)std::max<int64_t>(1, units_n) * 8, "allocate pose pairs", false);
 #undef GROW
   if (!b->status.p || !b->redo_count.p) {
     drop_graph(b);
@@ -468,7 +497,12 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     it.best = b->best.as<unsigned long long>() + i;
     it.argmax = b->argmax.as<int64_t>() + i;
     it.dump = nullptr;
-    it.passes0 = __atomic_load_n(&g->passes_seed[shape], __ATOMIC_RELAXED);
+    it.passes0 = __atomic_load_n(pp.n_units > 0 ? &g->passes_seed_pair[shape] : &g->passes_seed[shape],
+                                 __ATOMIC_RELAXED);
+    if (pp.n_units > 0)  // a pageable source: staged before the copy call returns
+      BCU(cudaMemcpyAsync(b->units.as<int32_t>() + 2 * pp.unit_off, pp.units.data(), pp.units.size() * 4,
+                          cudaMemcpyHostToDevice, s),
+          "copy pose pairs");
     it.item_passes = b->ipasses.as<uint32_t>() + i;
     hstarts[(size_t)i] = (int32_t)pp.pose_off;
   }
@@ -523,10 +557,16 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     ai.K = plans[(size_t)i].g->gc.K;
     ai.table_slots = Ts[(size_t)i];
     ai.n_buckets = Ts[(size_t)i] / 4;
+    ai.units = plans[(size_t)i].n_units > 0 ? b->units.as<int32_t>() + 2 * plans[(size_t)i].unit_off : nullptr;
+    ai.n_units = plans[(size_t)i].n_units;
     L.evals.push_back(ai);
   }
   b->last_grids.clear();
-  for (const PairPlan& pp : plans) b->last_grids.push_back(pp.g);
+  b->last_pairs.clear();
+  for (const PairPlan& pp : plans) {
+    b->last_grids.push_back(pp.g);
+    b->last_pairs.push_back(pp.n_units > 0 ? 1 : 0);
+  }
   b->last_shape = shape;
   // a graph replays the kernels' parameters as captured, the pairs' items included
   uint64_t h = 1469598103934665603ull;
@@ -535,11 +575,13 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   std::vector<int64_t> sig = {shape,   n,       rotate,     a.passes0, T, n_ctas,
                               poses_n, n_copies, max_out,   maxK,      (int64_t)(uintptr_t)b->pts.p,
                               (int64_t)(uintptr_t)b->items.p, (int64_t)h};
-  for (size_t i = 0; i < vws.size(); ++i) sig.insert(sig.end(), {vws[i], Ts[i]});
+  for (size_t i = 0; i < vws.size(); ++i) sig.insert(sig.end(), {vws[i], Ts[i], plans[i].n_units});
+  sig.push_back((int64_t)(uintptr_t)b->units.p);
   st = run_launch(b, L, (flags & ALIGN_BATCH_GRAPH) != 0, sig);
   if (st != ALIGN_OK) return st;
   b->stats[3] = shape;
   b->stats[4] = T;
+  b->stats[8] = units_n > 0 ? 2 : 1;
   return ALIGN_OK;
 }
 
@@ -597,9 +639,11 @@ extern "C" align_status align_eval_batch(align_batch* b, const align_pair* pairs
     BCU(cudaStreamSynchronize(b->stream), "synchronize");
     return ALIGN_OK;
   }
-  // kernel shape: fixed, tuned (cached per batch class) or the default
+  // kernel shape and poses per CTA: fixed, tuned (cached per batch class) or the default
+  // (shape 0, pose pairs)
   int shape = b->shape_fixed >= 0 ? b->shape_fixed : 0;
-  if (b->shape_fixed < 0 && (flags & ALIGN_BATCH_TUNE)) {
+  bool pose_pairs = b->pairs_fixed != 1;
+  if ((b->shape_fixed < 0 || b->pairs_fixed < 0) && (flags & ALIGN_BATCH_TUNE)) {
     int64_t pts_tot = 0, poses_tot = 0;
     int maxK = 0;
     bool dev_poses = false;
@@ -620,35 +664,42 @@ extern "C" align_status align_eval_batch(align_batch* b, const align_pair* pairs
       tune_load_locked();
       auto it = g_tune.find(key);
       if (it != g_tune.end()) {
-        shape = it->second;
+        shape = it->second / 2;
+        pose_pairs = (it->second % 2) == 1;
         known = true;
       }
     }
     if (!known) {
-      // time every shape on this batch: one warm-up run, then the sum of two timed runs
+      // time every candidate (kernel shape x poses per CTA) on this batch: one warm-up run,
+      // then the sum of three timed runs (device time between events)
       double best_ms = 0.0;
-      int best = 0;
-      for (int c = 0; c < kEvalShapes; ++c) {
+      int best = -1;
+      for (int c = 0; c < kChoices; ++c) {
+        const int cs = c / 2;
+        const bool cp = (c % 2) == 1;
+        if (b->shape_fixed >= 0 && cs != b->shape_fixed) continue;
+        if (b->pairs_fixed >= 1 && cp != (b->pairs_fixed == 2)) continue;
         double total = 0.0;
-        for (int rep = 0; rep < 3; ++rep) {
-          align_status st = eval_batch_shape(b, plans, pairs, which, flags & ~ALIGN_BATCH_GRAPH, c);
+        for (int rep = 0; rep < 4; ++rep) {
+          align_status st = eval_batch_shape(b, plans, pairs, which, flags & ~ALIGN_BATCH_GRAPH, cs, cp);
           if (st != ALIGN_OK) return st;
           st = collect(b);
           if (st != ALIGN_OK) return st;
           if (rep > 0) total += (double)b->stats[6] / 1000.0;
         }
         b->stats[7] += 1;
-        if (c == 0 || total < best_ms) {
+        if (best < 0 || total < best_ms) {
           best_ms = total;
           best = c;
         }
       }
-      shape = best;
+      shape = best / 2;
+      pose_pairs = (best % 2) == 1;
       std::lock_guard<std::mutex> lock(g_tune_mu);
-      tune_store_locked(key, shape);
+      tune_store_locked(key, best);
     }
   }
-  align_status st = eval_batch_shape(b, plans, pairs, which, flags, shape);
+  align_status st = eval_batch_shape(b, plans, pairs, which, flags, shape, pose_pairs);
   if (st != ALIGN_OK) return st;
   // outputs
   const cudaMemcpyKind kind = out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

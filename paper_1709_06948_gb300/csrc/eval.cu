@@ -1180,10 +1180,10 @@ __device__ __forceinline__ void pair_sweep_set(const EvalSmem& S, const EvalArgs
   if (full) {  // both poses are finished later by the exact path
     reset_pose(S, 0);
     reset_pose(S, 1);
-    if (tid == 0) {
+    if (tid == 0) {  // the redo list holds global pose indices (item pose base + local index)
       S.flags[1] = 0u;
-      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)lp0;
-      if (two) a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)lp1;
+      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(I.pose_base + lp0);
+      if (two) a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(I.pose_base + lp1);
     }
     if (overflowed && passes < kMaxPasses) passes *= 2;
     __syncthreads();
@@ -1195,7 +1195,8 @@ __device__ __forceinline__ void pair_sweep_set(const EvalSmem& S, const EvalArgs
   if (max_occupied > cap && passes < kMaxPasses) passes *= 2;  // crowded: more partitions next
 }
 
-// Pose pairs (pre-rotated tiles, one item): unit u of a.units is (pose, pose or -1).  Two
+// Pose pairs (pre-rotated tiles, one item): unit u of a.units is (pose, pose or -1), local
+// pose indices of the item (a.one).  Two
 // poses that read the same tile copy and whose t'_y and t'_z are equal bit for bit are swept
 // together (sweep_pair: one point load and one y/z voxel-map half for both); any other unit
 // is swept one pose at a time.  The results are those of the single-pose kernel.
@@ -1233,8 +1234,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_pair_kernel(const _
       // a single pose is swept as a pair whose second pose has no point inside the grid
       pair_sweep_set<kVW>(S, a, vc, p0, p1, two, T, cut, cap, ring, lane_lt, wide, passes);
     } else if (tid == 0) {  // not a pair after all: both poses go to the exact path (single sweeps)
-      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)p0;
-      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)p1;
+      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(I.pose_base + p0);
+      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(I.pose_base + p1);
     }
   }
   if (tid == 0) {

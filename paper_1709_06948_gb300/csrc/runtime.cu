@@ -335,7 +335,7 @@ int max_rotation_copies(int64_t P, int32_t n_tiles) {
 // index `src`) and whose t'_y and t'_z are equal bit for bit, two at a time in order of
 // their first pose; a group's odd pose is a unit of its own.  Two entries per unit (the
 // second -1 for a single pose).  Returns the unit count.
-int pair_units(const float* poses12, const int32_t* src, int64_t P, std::vector<int32_t>& units) {
+int pair_units_impl(const float* poses12, const int32_t* src, int64_t P, std::vector<int32_t>& units) {
   struct Key {
     int32_t src;
     uint32_t ty, tz;
@@ -375,7 +375,7 @@ int pair_units(const float* poses12, const int32_t* src, int64_t P, std::vector<
 // Whether the next pre-rotated launch on this grid evaluates pose pairs: while pairs have
 // needed no more key partitions than single poses (both counts are learned per grid and
 // only grow), one pair sweep does the work of two single sweeps.
-bool use_pairs(const align_grid* g) { return g->passes_seed_pair <= g->passes_seed[0]; }
+bool use_pairs(const align_grid* g) { return g->passes_seed_pair[0] <= g->passes_seed[0]; }
 
 align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_poses, int64_t P, bool rotate,
                                int n_rot, const EvalOut& out, const int32_t* d_units = nullptr,
@@ -394,7 +394,7 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
     const int groups = group_rotations(h_poses, P, rots, idx, max_rotation_copies(P, n_tiles));
     if (groups > 0 && out.dump == nullptr && P >= 2 && use_pairs(g)) {
       std::vector<int32_t> units;
-      const int n_units = pair_units(h_poses, idx.data(), P, units);
+      const int n_units = pair_units_impl(h_poses, idx.data(), P, units);
       if (n_units < P) {  // at least one pair
         CU(g->rots.ensure(rots.size() * 4), "allocate rotations");
         CU(cudaMemcpyAsync(g->rots.p, rots.data(), rots.size() * 4, cudaMemcpyHostToDevice, g->stream),
@@ -470,7 +470,7 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   item.n_tiles = n_tiles;
   item.P = (int32_t)P;
   item.pose_base = 0;
-  item.passes0 = pairs ? g->passes_seed_pair : g->passes_seed[0];
+  item.passes0 = pairs ? g->passes_seed_pair[0] : g->passes_seed[0];
   item.item_passes = nullptr;
   item.out_c = g->out_c.as<uint32_t>();
   item.out_box = g->out_box.as<int32_t>();
@@ -547,7 +547,7 @@ align_status drain_events(align_grid* g) {
 // same kind.
 void learn_passes(align_grid* g, uint32_t used) {
   if (used == 0 || used > (1u << 16) || (used & (used - 1)) != 0) return;
-  int32_t& seed = g->last_pairs ? g->passes_seed_pair : g->passes_seed[0];
+  int32_t& seed = g->last_pairs ? g->passes_seed_pair[0] : g->passes_seed[0];
   if (used > (uint32_t)seed) seed = (int32_t)used;
 }
 
@@ -1339,6 +1339,9 @@ int group_pose_rotations(const float* poses12, int64_t P, std::vector<float>& ro
   return group_rotations(poses12, P, rots, idx, max_groups);
 }
 align_status check_grid_device(align_grid* g) { return check_grid(g); }
+int pair_units(const float* poses12, const int32_t* src, int64_t P, std::vector<int32_t>& units) {
+  return pair_units_impl(poses12, src, P, units);
+}
 void lattice_poses(const float origin[3], const double c[6], const double r[6], const int32_t m[6],
                    std::vector<double>& eta, std::vector<float>& poses) {
   build_lattice(c, r, m, eta);

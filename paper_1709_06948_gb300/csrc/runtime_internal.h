@@ -70,6 +70,10 @@ align_status report_errorf(align_status st, const char* fmt, ...);
 int group_pose_rotations(const float* poses12, int64_t P, std::vector<float>& rots, std::vector<int32_t>& idx,
                          int max_groups);
 align_status check_grid_device(align_grid* g);
+// Pose pairs of a host pose batch for the pair kernel: poses with the same tile copy
+// (src, or all one copy when NULL) and bitwise equal t'_y, t'_z, two per unit in order of
+// their first pose (local indices; the second -1 for a single pose).  Returns the units.
+int pair_units(const float* poses12, const int32_t* src, int64_t P, std::vector<int32_t>& units);
 // One level of the coarse-to-fine lattice: FP64 poses around centre c (ranges r, m samples
 // per axis; order rx, ry, rz, tx, ty, tz with tz fastest) and their rounded FP32 form.
 void lattice_poses(const float origin[3], const double c[6], const double r[6], const int32_t m[6],
@@ -108,7 +112,7 @@ struct align_grid {
   // key partitions the next launch starts with, per kernel shape (its table size), and for
   // the pose-pair kernel (shape 0)
   int32_t passes_seed[mialign::kEvalShapes] = {1, 1, 1};
-  int32_t passes_seed_pair = 1;
+  int32_t passes_seed_pair[mialign::kEvalShapes] = {1, 1, 1};
   bool last_pairs = false;  // the last eval launch evaluated pose pairs
   mialign::DevBuf units;    // pose pairs of the last pair launch with host poses
   mialign::DevBuf lat_units;           // pose pairs of a device-built lattice level (by index)

@@ -1,7 +1,8 @@
-"""Many pairs in one persistent launch (align_eval_batch) against the oracle and against
-align_eval_mi on each pair alone: grids of different resolutions, features and symbol
-counts in one launch; empty inputs; graph capture and replay; every kernel shape; the
-tuner; device-resident inputs and outputs.
+"""Many pairs in one launch sequence (align_eval_batch: one packing launch, an eval launch per
+pair, one composition and one argmax launch; capturable as one CUDA graph) against the
+oracle and against align_eval_mi on each pair alone: grids of different resolutions,
+features and symbol counts in one batch; empty inputs; graph capture and replay; every
+kernel shape with one and two poses per CTA; the tuner; device-resident inputs and outputs.
 
 Bar: each pair's MI within 1e-5 nats of the oracle's FP64 MI and its argmax equal (or
 within the FP32 band); bit-identical MI and argmax to the same pair evaluated alone."""
@@ -76,15 +77,49 @@ def test_batch_matches_oracle_and_single(cases):
 
 
 def test_every_shape_same_result(cases):
+    """Every kernel shape, one pose or two poses per CTA: identical results."""
     from paper_1709_06948_gb300 import align
     b = align.align_batch_create()
+    align.align_batch_set_poses_per_cta(b, 1)
     ref = align.align_eval_batch(b, _pairs(cases))
+    assert align.align_batch_stats(b)["poses_per_cta"] == 1
     for shape in range(3):
-        align.align_batch_set_shape(b, shape)
-        res = align.align_eval_batch(b, _pairs(cases))
-        assert align.align_batch_stats(b)["shape"] == shape
-        for (mi0, am0), (mi, am) in zip(ref, res):
-            assert np.array_equal(mi0, mi) and am0 == am
+        for ppc in (1, 2):
+            align.align_batch_set_shape(b, shape)
+            align.align_batch_set_poses_per_cta(b, ppc)
+            res = align.align_eval_batch(b, _pairs(cases))
+            st = align.align_batch_stats(b)
+            # pairs need pre-rotated tiles, which one of these pairs' pose sets rules out
+            assert st["shape"] == shape and st["poses_per_cta"] in ((1,) if ppc == 1 else (1, 2))
+            for (mi0, am0), (mi, am) in zip(ref, res):
+                assert np.array_equal(mi0, mi) and am0 == am
+
+
+def test_pose_pairs_in_a_batch():
+    """Lattice pose sets (rotations repeat): with two poses per CTA every pair's lattice is
+    evaluated as pose pairs; results equal one pose per CTA, align_eval_mi alone, and the
+    oracle on a sample."""
+    from paper_1709_06948_gb300 import align
+    cases = []
+    for k, res in enumerate((0.5, 1.0, 0.5)):
+        lp = scangen.lidar_pair(seed=scangen.SEED_BASE + 80 + k, n_beams=32)
+        spec = scangen.lidar_grid(res)
+        etas = scangen.pose_grid(lp.T, (0.8, 0.8, 0.1, 0.01, 0.01, 0.04), (8, 4, 2, 1, 1, 2))
+        cases.append(Case(lp.xyzA, lp.xyzB, spec, etas))
+    b = align.align_batch_create()
+    align.align_batch_set_poses_per_cta(b, 2)
+    res2 = align.align_eval_batch(b, _pairs(cases))
+    assert align.align_batch_stats(b)["poses_per_cta"] == 2
+    align.align_batch_set_poses_per_cta(b, 1)
+    res1 = align.align_eval_batch(b, _pairs(cases))
+    assert align.align_batch_stats(b)["poses_per_cta"] == 1
+    for c, (mi2, am2), (mi1, am1) in zip(cases, res2, res1):
+        assert np.array_equal(mi2, mi1) and am2 == am1
+        mi0, am0, _ = align.align_eval_mi(c.L, c.xyzB, eta6=c.etas)
+        assert np.array_equal(mi2, mi0) and am2 == am0
+        mo = c.oracle_mi()
+        assert np.max(np.abs(mi2.astype(np.float64) - mo)) <= mi_tolerance()
+        check_argmax(am2, mo, mi2)
 
 
 def test_graph_replay(cases):
@@ -111,9 +146,10 @@ def test_tuner_picks_a_shape_and_caches(cases, tmp_path, monkeypatch):
     ref = align.align_eval_batch(b, _pairs(cases))
     res = align.align_eval_batch(b, _pairs(cases), tune=True)
     st = align.align_batch_stats(b)
-    assert st["tuner_trials"] == 3 and 0 <= st["shape"] < 3
+    # every kernel shape x poses per CTA candidate timed once, then cached per batch class
+    assert st["tuner_trials"] == 6 and 0 <= st["shape"] < 3 and st["poses_per_cta"] in (1, 2)
     res2 = align.align_eval_batch(b, _pairs(cases), tune=True)
-    assert align.align_batch_stats(b)["tuner_trials"] == 3  # cached
+    assert align.align_batch_stats(b)["tuner_trials"] == 6  # cached
     for (mi0, am0), (mi1, am1), (mi2, am2) in zip(ref, res, res2):
         assert np.array_equal(mi0, mi1) and np.array_equal(mi0, mi2) and am0 == am1 == am2
 
