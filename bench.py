@@ -261,7 +261,7 @@ SERVE_REQUESTS = 400
 SERVE_RATES_HZ = (80.0, 120.0, 150.0, 200.0)
 SERVE_RANGE = np.array([3.0, 3.0, 0.5, math.radians(2.0), math.radians(2.0), math.radians(10.0)])
 SERVE_RES = (0.25, 0.5, 0.75, 1.0)
-SERVE_SLOTS = 8
+SERVE_SLOTS = 3
 
 
 def run_batched(align, steps):

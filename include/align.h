@@ -291,14 +291,13 @@ align_status align_batch_stats(const align_batch* b, int64_t out[9]);
 
 /* ---------------------------------------------------------------------------------
    Serving: alignment requests (a lattice search of scan B against a resident reference
-   scan A, as align_search_ex) submitted at any time.  Worker threads (two when
-   max_slots > 1), each with its own batch and stream, run continuous batching: at every
-   step a worker admits queued requests (first come, first served) while request slots and
-   the device memory budget allow, evaluates the current lattice level of each of its
-   active requests in one batched launch (align_eval_batch), moves each request to its next
-   level, and retires finished ones, freeing their slot and memory.  While one worker works
-   on the host, the other's launches run.  A request's result is the same as
-   align_search_ex on its grid alone.
+   scan A, as align_search_ex) submitted at any time.  The server has max_slots slots, each
+   a worker thread with its own CUDA stream and evaluation workspace.  A free slot admits the
+   request at the head of the queue (first come, first served) as soon as the device memory
+   budget allows and runs its whole search on the slot's stream, every level built on the
+   device from the previous level's argmax.  Requests arriving while others run are admitted
+   as slots and memory free up, and the launches of all active requests interleave on the
+   device.  A request's result is the same as align_search_ex on its grid alone.
    --------------------------------------------------------------------------------- */
 typedef struct align_server align_server;
 
@@ -319,8 +318,11 @@ typedef struct align_result {
   double t_submit, t_start, t_done;  /* seconds on the server's monotonic clock */
 } align_result;
 
-/* hbm_budget_bytes: device memory the server may hold for references and active requests
-   (estimated per request from its sizes); max_slots: most requests active at once. */
+/* hbm_budget_bytes: device memory the server may hold for the references and the slots'
+   workspaces (a workspace keeps the buffers of the largest request it has run; estimated
+   per request from its sizes, its grid and the device); max_slots (1..256): most requests
+   active at once.  When the request at the head of the queue fits the budget only without
+   them and no request runs, idle slots release their workspaces. */
 align_status align_server_create(size_t hbm_budget_bytes, int32_t max_slots, align_server** out);
 /* Keep scan A (host, nA x 3 fp32) resident as a reference under `desc`; *ref_id names it. */
 align_status align_server_add_reference(align_server* s, const align_grid_desc* desc, const float* xyzA,
@@ -333,12 +335,12 @@ align_status align_poll(align_server* s, uint64_t ticket, align_result* out);
 align_status align_wait(align_server* s, uint64_t ticket, int64_t timeout_ms, align_result* out);
 /* Seconds on the server's monotonic clock (the clock of align_result's times). */
 double align_server_now(const align_server* s);
-/* [0] batched steps (all workers), [1] requests admitted, [2] requests done, [3] most requests active
-   at once, [4] pose evaluations, [5] device bytes held now (estimate), [6] peak of [5],
-   [7] requests waiting in the queue. */
+/* [0] lattice levels evaluated (all slots), [1] requests admitted, [2] requests done, [3] most
+   requests active at once, [4] pose evaluations, [5] device bytes held now (estimate: the
+   references and the slots' workspaces), [6] peak of [5], [7] requests waiting in the queue. */
 align_status align_server_stats(align_server* s, int64_t out[8]);
-/* Stops the worker after its current step; queued and active requests are dropped.  No
-   call on the server (align_wait included) may be in progress or follow. */
+/* Stops the workers after their current requests; queued requests are dropped.  No call on
+   the server (align_wait included) may be in progress or follow. */
 align_status align_server_destroy(align_server* s);
 
 /* Message of the calling thread's last failure ("" if none). */

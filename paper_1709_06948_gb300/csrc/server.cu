@@ -1,15 +1,22 @@
-// server.cu — serving alignment requests with continuous batching.
+// server.cu — serving alignment requests: continuous admission into slots whose work overlaps
+// on the device.
 //
-// Worker threads (two, or one with a single slot) each own a batch (align_eval_batch, with
-// its own stream and workspace) and run steps: admit queued requests while slots and the
-// device memory budget allow (first come, first served; a worker admits only while it
-// holds no more requests than the other), evaluate the current lattice level of each of
-// its active requests in one batched launch, then advance each request to its next level
-// (centre <- best pose, ranges halve, as align_search_ex) and retire the finished ones.
-// Requests therefore join and leave between steps, the work of all of a worker's requests
-// overlaps in the same launches, and while one worker prepares its next step or reads its
-// results back on the host, the other's launches keep the device busy.  Reference scans
-// stay resident as grids owned by the server.
+// A server has max_slots slots.  Each slot is a worker thread with a CUDA stream of its own
+// and a workspace (a grid object holding only evaluation buffers).  A free slot admits the
+// request at the head of the queue (first come, first served) as soon as the device-memory
+// budget allows, binds its workspace to the request's resident reference (the reference's
+// device arrays are shared, not copied) and runs the request's whole coarse-to-fine lattice
+// search on its stream, every level built on the device from the previous level's argmax
+// (the pipeline of align_search_ex, so a request has no host round trip between levels).
+// Requests that arrive while others run are admitted as slots and memory free up; the
+// launches of all active requests interleave on the device (one stream per slot), so each
+// request's host work and the tails of its launches overlap with the others' kernels.  A
+// request's result is bit-identical to align_search_ex on its reference alone.
+//
+// Memory: the budget covers the references and every slot's workspace, which keeps the
+// buffers of the largest request it has run (re-allocating between requests would
+// synchronise the device under the other slots' work).  When the request at the head of
+// the queue fits only without them and nothing runs, idle slots release their workspaces.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,23 +47,25 @@ struct Req {
   int64_t nB = 0;
   double c[6], r[6];
   int32_t counts[6];
-  int32_t levels = 0, level = 0;
-  size_t bytes = 0;        // device memory estimate while active
-  DevBuf dev_xyz;          // resident B while active
-  bool uploaded = false;
+  int32_t levels = 0;
+  size_t bytes = 0;        // device memory estimate of its workspace
+  double T[6] = {0, 0, 0, 0, 0, 0};
   float best_mi = 0.0f;
   int32_t status = ALIGN_OK;
   double t_submit = 0, t_start = 0, t_done = 0;
-  // per-step scratch
-  std::vector<double> eta;
-  std::vector<float> poses;
-  std::vector<float> mi;
-  int64_t am = -1;
 };
 
 struct Ref {
   align_grid* grid = nullptr;
   size_t bytes = 0;
+};
+
+struct Slot {
+  align_grid* ws = nullptr;      // workspace bound to one reference at a time
+  cudaStream_t stream = nullptr;
+  size_t held = 0;               // device bytes its workspace may hold (estimate)
+  bool busy = false;
+  Req* cur = nullptr;
 };
 
 int64_t lattice_size(const int32_t m[6]) {
@@ -69,163 +78,184 @@ int64_t lattice_size(const int32_t m[6]) {
 
 struct align_server {
   int device = 0;
+  int n_sm = 0;
   size_t budget = 0;
   int32_t max_slots = 1;
   std::chrono::steady_clock::time_point t0;
   std::mutex mu;
-  std::condition_variable cv;       // worker: new requests or stop
+  std::condition_variable cv;       // workers: new requests, freed memory or stop
   std::condition_variable cv_done;  // clients: a request finished
   std::deque<Req*> queue;
-  std::vector<std::vector<Req*>> active;  // per worker
-  int32_t n_active = 0;                  // over all workers
   std::unordered_map<uint64_t, Req*> done;
   std::unordered_map<uint64_t, int> pending;  // ticket -> 1 while queued or active
   std::vector<Ref> refs;
-  size_t used = 0, peak = 0;
+  size_t ref_bytes = 0;
+  std::vector<Slot> slots;
+  int32_t n_active = 0;
+  size_t peak = 0;
   uint64_t next_ticket = 1;
   bool stop = false;
-  std::vector<align_batch*> batches;  // per worker
   std::vector<std::thread> workers;
-  // device buffers of retired requests' points, kept for reuse: freeing device memory
-  // synchronises the whole device (the other worker's launches included)
-  std::vector<mialign::DevBuf> spare;
   int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
+  size_t used() const {
+    size_t u = ref_bytes;
+    for (const Slot& sl : slots) u += sl.held;
+    return u;
+  }
 };
 
 namespace {
 
-// Device bytes a request holds while active: its resident points, the batch's staged
-// copy and pre-rotated tiles, and the per-pose buffers of one level.
-size_t request_bytes(int64_t nB, const int32_t m[6], int K) {
+// Device bytes of a workspace running a request of nB points with lattice counts m on a grid
+// whose single-pose table has T slots: the staged points, the pre-rotated tile copies, the
+// per-pose buffers of one level, and the per-CTA 64-bit side sums and overflow lists.
+size_t request_bytes(int64_t nB, const int32_t m[6], int K, int T, int n_sm) {
   const int64_t P = lattice_size(m);
   const int64_t n_pad = std::max<int64_t>(3, (nB + 1023) / 1024) * 1024;
   int64_t n_rot = (int64_t)m[3] * m[4] * m[5];
   if (n_rot > std::max<int64_t>(1, P / 4)) n_rot = 1;
-  return (size_t)(nB * 24 + n_rot * n_pad * 16 + P * ((int64_t)K * K * 4 + 24 + 4 + 48 + 4 + 4 + 4));
+  const int64_t per_pose = (int64_t)K * K * 4 + 24 + 4 + 48 + 4 + 4 + 4;
+  const int64_t per_cta = 2 * (int64_t)T * 8 + (int64_t)eval_shape(0).ovf_cap() * 16;
+  return (size_t)(nB * 12 + n_rot * n_pad * 16 + P * per_pose + (int64_t)n_sm * per_cta);
+}
+
+// A workspace: a grid object that owns only evaluation buffers; the reference arrays it
+// reads are bound from a resident reference grid (and never released through it).
+align_grid* workspace_create(int device, int n_sm, size_t smem_optin, cudaStream_t stream) {
+  align_grid* g = new (std::nothrow) align_grid();
+  if (!g) return nullptr;
+  g->device = device;
+  g->n_sm = n_sm;
+  g->smem_optin = smem_optin;
+  g->stream = stream;
+  return g;
+}
+
+void workspace_bind(align_grid* ws, const align_grid* ref) {
+  ws->gc = ref->gc;
+  std::memcpy(ws->origin, ref->origin, sizeof(ws->origin));
+  ws->res_m = ref->res_m;
+  ws->V = ref->V;
+  std::memcpy(ws->boxA, ref->boxA, sizeof(ws->boxA));
+  ws->symA.p = ref->symA.p;  // borrowed
+  ws->symA.cap = ref->symA.cap;
+  ws->sat.p = ref->sat.p;    // borrowed
+  ws->sat.cap = ref->sat.cap;
+  ws->has_ref = ref->has_ref;
+  ws->table_slots = ref->table_slots;
+  for (int i = 0; i < kEvalShapes; ++i) {
+    ws->passes_seed[i] = ref->passes_seed[i];
+    ws->passes_seed_pair[i] = ref->passes_seed_pair[i];
+  }
+}
+
+// Key partitions learned by a workspace go back to its reference (for the next request).
+void workspace_learn(const align_grid* ws, align_grid* ref) {
+  for (int i = 0; i < kEvalShapes; ++i) {
+    ref->passes_seed[i] = std::max(ref->passes_seed[i], ws->passes_seed[i]);
+    ref->passes_seed_pair[i] = std::max(ref->passes_seed_pair[i], ws->passes_seed_pair[i]);
+  }
+}
+
+void workspace_destroy(align_grid* ws) {
+  if (!ws) return;
+  ws->symA = DevBuf{};  // the reference's arrays: not ours to free
+  ws->sat = DevBuf{};
+  align_destroy_grid(ws);
+}
+
+// Admit the request at the head of the queue into idle slot k if the budget allows it.
+Req* try_admit_locked(align_server* s, size_t k) {
+  if (s->queue.empty()) return nullptr;
+  Req* r = s->queue.front();
+  Slot& me = s->slots[k];
+  auto need = [&]() {
+    size_t others = s->ref_bytes;
+    for (size_t j = 0; j < s->slots.size(); ++j)
+      if (j != k) others += s->slots[j].held;
+    return others + std::max(me.held, r->bytes);
+  };
+  if (need() > s->budget) {
+    if (s->n_active > 0) return nullptr;  // wait until running requests finish
+    // nothing runs: the idle slots' workspaces give way (each fits the budget alone with
+    // the references, as align_submit checked)
+    for (size_t j = 0; j < s->slots.size(); ++j) {
+      Slot& o = s->slots[j];
+      if (j == k || o.held == 0 || o.ws == nullptr) continue;
+      workspace_destroy(o.ws);
+      o.ws = nullptr;
+      o.held = 0;
+    }
+  }
+  s->queue.pop_front();
+  me.held = std::max(me.held, r->bytes);
+  me.busy = true;
+  me.cur = r;
+  r->t_start = s->now();
+  s->n_active += 1;
+  s->peak = std::max(s->peak, s->used());
+  s->stats[1] += 1;
+  s->stats[3] = std::max<int64_t>(s->stats[3], (int64_t)s->n_active);
+  s->stats[5] = (int64_t)s->used();
+  s->stats[6] = (int64_t)s->peak;
+  s->stats[7] = (int64_t)s->queue.size();
+  return r;
 }
 
 void finish_locked(align_server* s, Req* r, int32_t status) {
   r->status = status;
   r->t_done = s->now();
-  s->used -= std::min(s->used, r->bytes);
-  if (r->dev_xyz.p) {  // back to the spare buffers (at most max_slots are kept)
-    if ((int32_t)s->spare.size() < s->max_slots) s->spare.push_back(r->dev_xyz);
-    else r->dev_xyz.release();
-    r->dev_xyz = DevBuf{};
-  }
   s->pending.erase(r->ticket);
   s->done[r->ticket] = r;
   s->stats[2] += 1;
-  s->n_active -= 1;
   s->cv_done.notify_all();
-  s->cv.notify_all();  // a slot and memory are free: any worker may admit
 }
 
-// Admit queued requests into worker w while the slots and the budget allow and w holds no
-// more requests than any other worker.
-void admit_locked(align_server* s, size_t w) {
-  std::vector<Req*>& mine = s->active[w];
-  while (!s->queue.empty() && s->n_active < s->max_slots) {
-    size_t least = mine.size();
-    for (const auto& other : s->active) least = std::min(least, other.size());
-    if (mine.size() > least) break;  // another worker has fewer: it admits next
-    Req* r = s->queue.front();
-    if (s->used + r->bytes > s->budget && s->n_active > 0) break;  // wait for memory
-    s->queue.pop_front();
-    s->used += r->bytes;
-    s->peak = std::max(s->peak, s->used);
-    r->t_start = s->now();
-    mine.push_back(r);
-    s->n_active += 1;
-    s->stats[1] += 1;
-  }
-  s->stats[3] = std::max<int64_t>(s->stats[3], (int64_t)s->n_active);
-  s->stats[5] = (int64_t)s->used;
-  s->stats[6] = (int64_t)s->peak;
-  s->stats[7] = (int64_t)s->queue.size();
-}
-
-void worker_main(align_server* s, size_t w) {
+void worker_main(align_server* s, size_t k) {
   cudaSetDevice(s->device);
-  std::vector<align_pair> pairs;
   for (;;) {
-    std::vector<Req*> act;
+    Req* r = nullptr;
+    align_grid* ref = nullptr;
+    align_grid* ws = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       for (;;) {
         if (s->stop) return;
-        admit_locked(s, w);
-        if (!s->active[w].empty()) break;
+        r = try_admit_locked(s, k);
+        if (r) break;
         s->cv.wait(lk);
       }
-      act = s->active[w];
+      Slot& me = s->slots[k];
+      if (!me.ws) me.ws = workspace_create(s->device, s->n_sm, s->refs[0].grid->smem_optin, me.stream);
+      ws = me.ws;
+      ref = s->refs[(size_t)r->ref].grid;
+      if (ws) workspace_bind(ws, ref);
     }
-    // upload the points of newly admitted requests; build every request's lattice level
-    int32_t step_status = ALIGN_OK;
-    pairs.assign(act.size(), align_pair{});
-    for (size_t i = 0; i < act.size(); ++i) {
-      Req* r = act[i];
-      align_grid* g = s->refs[(size_t)r->ref].grid;
-      if (!r->uploaded) {
-        if (r->nB > 0) {
-          {  // a spare buffer large enough, if there is one
-            std::lock_guard<std::mutex> lk(s->mu);
-            for (size_t k = 0; k < s->spare.size(); ++k)
-              if (s->spare[k].cap >= (size_t)r->nB * 12) {
-                r->dev_xyz = s->spare[k];
-                s->spare.erase(s->spare.begin() + (ptrdiff_t)k);
-                break;
-              }
-          }
-          cudaError_t e = r->dev_xyz.ensure((size_t)r->nB * 12);
-          if (e == cudaSuccess) e = cudaMemcpy(r->dev_xyz.p, r->xyz.data(), (size_t)r->nB * 12, cudaMemcpyHostToDevice);
-          if (e != cudaSuccess) {
-            step_status = report_cuda_error(e, "upload request points");
-            break;
-          }
-        }
-        r->uploaded = true;
-      }
-      lattice_poses(g->origin, r->c, r->r, r->counts, r->eta, r->poses);
-      const int64_t P = (int64_t)(r->eta.size() / 6);
-      r->mi.resize((size_t)P);
-      r->am = -1;
-      align_pair& q = pairs[i];
-      q.grid = g;
-      q.xyzB = r->nB > 0 ? r->dev_xyz.as<float>() : nullptr;
-      q.nB = r->nB;
-      q.poses12 = r->poses.data();
-      q.eta6 = nullptr;
-      q.P = P;
-      q.mi_out = r->mi.data();
-      q.argmax_out = &r->am;
+    int32_t st = ALIGN_OK;
+    float mi = 0.0f;
+    if (!ws) {
+      st = report_error(ALIGN_E_OOM, "host allocation failed");
+    } else {
+      st = align_search_ex(ws, r->nB > 0 ? r->xyz.data() : nullptr, r->nB, 0, r->c, r->r, r->counts, r->levels,
+                           r->T, &mi, nullptr);
     }
-    if (step_status == ALIGN_OK)
-      step_status = align_eval_batch(s->batches[w], pairs.data(), (int32_t)pairs.size(), ALIGN_XYZ_DEVICE);
     std::lock_guard<std::mutex> lk(s->mu);
-    s->stats[0] += 1;
-    std::vector<Req*> still;
-    for (Req* r : act) {
-      if (step_status != ALIGN_OK) {
-        finish_locked(s, r, step_status);
-        continue;
-      }
-      s->stats[4] += (int64_t)r->mi.size();
-      if (r->am < 0 || r->am >= (int64_t)r->mi.size()) {
-        finish_locked(s, r, ALIGN_E_INTERNAL);
-        continue;
-      }
-      r->best_mi = r->mi[(size_t)r->am];
-      std::memcpy(r->c, &r->eta[(size_t)r->am * 6], sizeof(r->c));
-      for (int a = 0; a < 6; ++a) r->r[a] *= 0.5;
-      if (++r->level >= r->levels) finish_locked(s, r, ALIGN_OK);
-      else still.push_back(r);
+    if (ws) workspace_learn(ws, ref);
+    r->best_mi = mi;
+    if (st == ALIGN_OK) {
+      s->stats[0] += r->levels;
+      s->stats[4] += (int64_t)r->levels * lattice_size(r->counts);
     }
-    s->active[w].swap(still);
+    Slot& me = s->slots[k];
+    me.busy = false;
+    me.cur = nullptr;
+    s->n_active -= 1;
+    finish_locked(s, r, st);
+    s->cv.notify_all();  // a slot is free: any waiting worker may admit
   }
 }
 
@@ -236,30 +266,30 @@ extern "C" {
 align_status align_server_create(size_t hbm_budget_bytes, int32_t max_slots, align_server** out) {
   if (!out) return report_error(ALIGN_E_INVALID, "out is NULL");
   *out = nullptr;
-  if (max_slots < 1) return report_error(ALIGN_E_INVALID, "max_slots must be >= 1");
-  int dev = 0;
+  if (max_slots < 1 || max_slots > 256) return report_error(ALIGN_E_INVALID, "max_slots must be in 1..256");
+  int dev = 0, n_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return report_cuda_error(e, "cudaGetDevice");
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return report_cuda_error(e, "device query");
   std::unique_ptr<align_server> s(new (std::nothrow) align_server());
   if (!s) return report_error(ALIGN_E_OOM, "host allocation failed");
   s->device = dev;
+  s->n_sm = n_sm;
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;
   s->t0 = std::chrono::steady_clock::now();
-  const size_t n_workers = max_slots > 1 ? 2 : 1;
-  for (size_t w = 0; w < n_workers; ++w) {
-    align_batch* b = nullptr;
-    align_status st = align_batch_create(nullptr, &b);  // its own stream
-    if (st != ALIGN_OK) {
-      for (align_batch* q : s->batches) align_batch_destroy(q);
-      return st;
+  s->slots.resize((size_t)max_slots);
+  for (Slot& sl : s->slots) {
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      for (Slot& o : s->slots)
+        if (o.stream) cudaStreamDestroy(o.stream);
+      return report_error(ALIGN_E_CUDA, "creating the slots' streams failed");
     }
-    s->batches.push_back(b);
   }
-  s->active.assign(n_workers, {});
   align_server* raw = s.release();
   try {
-    for (size_t w = 0; w < n_workers; ++w) raw->workers.emplace_back(worker_main, raw, w);
+    for (size_t k = 0; k < raw->slots.size(); ++k) raw->workers.emplace_back(worker_main, raw, k);
   } catch (...) {
     {
       std::lock_guard<std::mutex> lk(raw->mu);
@@ -268,7 +298,7 @@ align_status align_server_create(size_t hbm_budget_bytes, int32_t max_slots, ali
     }
     for (std::thread& t : raw->workers)
       if (t.joinable()) t.join();
-    for (align_batch* q : raw->batches) align_batch_destroy(q);
+    for (Slot& o : raw->slots) cudaStreamDestroy(o.stream);
     delete raw;
     return report_error(ALIGN_E_INTERNAL, "could not start the worker threads");
   }
@@ -286,7 +316,7 @@ align_status align_server_add_reference(align_server* s, const align_grid_desc* 
   const size_t bytes = (size_t)V + (size_t)(gc.K - 1) * (gc.X + 1) * (gc.Y + 1) * (gc.Z + 1) * 4;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    if (s->used + bytes > s->budget) return report_error(ALIGN_E_OOM, "reference does not fit the memory budget");
+    if (s->used() + bytes > s->budget) return report_error(ALIGN_E_OOM, "reference does not fit the memory budget");
   }
   cudaError_t e = cudaSetDevice(s->device);
   if (e != cudaSuccess) return report_cuda_error(e, "cudaSetDevice");
@@ -294,14 +324,18 @@ align_status align_server_add_reference(align_server* s, const align_grid_desc* 
   st = align_create_grid(desc, nullptr, &g);
   if (st != ALIGN_OK) return st;
   st = align_set_reference(g, xyzA, nA, 0);
+  if (st == ALIGN_OK) {
+    e = cudaStreamSynchronize(g->stream);  // every slot's stream reads the arrays from now on
+    if (e != cudaSuccess) st = report_cuda_error(e, "synchronize");
+  }
   if (st != ALIGN_OK) {
     align_destroy_grid(g);
     return st;
   }
   std::lock_guard<std::mutex> lk(s->mu);
   s->refs.push_back(Ref{g, bytes});
-  s->used += bytes;
-  s->peak = std::max(s->peak, s->used);
+  s->ref_bytes += bytes;
+  s->peak = std::max(s->peak, s->used());
   *ref_id = (int32_t)s->refs.size() - 1;
   return ALIGN_OK;
 }
@@ -331,15 +365,15 @@ align_status align_submit(align_server* s, const align_request* req, uint64_t* t
   std::lock_guard<std::mutex> lk(s->mu);
   if (req->ref_id < 0 || req->ref_id >= (int32_t)s->refs.size()) return report_error(ALIGN_E_INVALID, "unknown ref_id");
   r->ref = req->ref_id;
-  r->bytes = request_bytes(r->nB, r->counts, s->refs[(size_t)r->ref].grid->gc.K);
-  size_t ref_bytes = 0;
-  for (const Ref& f : s->refs) ref_bytes += f.bytes;
-  if (ref_bytes + r->bytes > s->budget) return report_error(ALIGN_E_OOM, "request can never fit the memory budget");
+  const align_grid* g = s->refs[(size_t)r->ref].grid;
+  r->bytes = request_bytes(r->nB, r->counts, g->gc.K, g->table_slots, s->n_sm);
+  if (s->ref_bytes + r->bytes > s->budget) return report_error(ALIGN_E_OOM, "request can never fit the memory budget");
   r->ticket = s->next_ticket++;
   r->t_submit = s->now();
   *ticket = r->ticket;
   Req* raw = r.release();
   if (raw->levels == 0) {  // nothing to evaluate: the centre is the answer
+    std::memcpy(raw->T, raw->c, sizeof(raw->T));
     raw->t_start = raw->t_submit;
     raw->t_done = raw->t_submit;
     s->done[raw->ticket] = raw;
@@ -355,7 +389,7 @@ align_status align_submit(align_server* s, const align_request* req, uint64_t* t
 }
 
 static void fill_result(const Req* r, align_result* out) {
-  std::memcpy(out->T, r->c, sizeof(out->T));
+  std::memcpy(out->T, r->T, sizeof(out->T));
   out->mi = r->best_mi;
   out->status = r->status;
   out->t_submit = r->t_submit;
@@ -399,7 +433,7 @@ double align_server_now(const align_server* s) { return s ? s->now() : 0.0; }
 align_status align_server_stats(align_server* s, int64_t out[8]) {
   if (!s || !out) return report_error(ALIGN_E_INVALID, "NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
-  s->stats[5] = (int64_t)s->used;
+  s->stats[5] = (int64_t)s->used();
   s->stats[6] = (int64_t)s->peak;
   s->stats[7] = (int64_t)s->queue.size();
   for (int i = 0; i < 8; ++i) out[i] = s->stats[i];
@@ -417,15 +451,12 @@ align_status align_server_destroy(align_server* s) {
     if (t.joinable()) t.join();
   cudaSetDevice(s->device);
   for (Req* r : s->queue) delete r;
-  for (auto& act : s->active)
-    for (Req* r : act) {
-      r->dev_xyz.release();
-      delete r;
-    }
   for (auto& kv : s->done) delete kv.second;
-  for (DevBuf& b : s->spare) b.release();
+  for (Slot& sl : s->slots) {
+    workspace_destroy(sl.ws);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+  }
   for (Ref& f : s->refs) align_destroy_grid(f.grid);
-  for (align_batch* b : s->batches) align_batch_destroy(b);
   delete s;
   return ALIGN_OK;
 }

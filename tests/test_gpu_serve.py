@@ -1,7 +1,8 @@
-"""Serving with continuous batching (align_server_*): each request's result is the same
-alone and in a mix of concurrent requests, and the same as align_search_ex on its own
-grid (itself pinned to the oracle's search); the tiny request also against the oracle
-directly.  Admission by slots and by the device memory budget; polling semantics."""
+"""Serving (align_server_*): requests admitted into slots as they free up, each slot running
+its request's device-pipelined search on its own stream.  Each request's result is the same
+alone and in a mix of concurrent requests, and the same as align_search_ex on its own grid
+(itself pinned to the oracle's search); the tiny request also against the oracle directly.
+Admission by slots and by the device memory budget; polling semantics."""
 import math
 import time
 
@@ -93,10 +94,10 @@ def test_tiny_request_matches_oracle(world):
     s.close()
 
 
-def test_mix_is_batched_and_results_unchanged(world):
-    """All requests submitted at once: they run concurrently in shared launches (fewer
-    steps than levels in total, several active at a time) and each result is bit-identical
-    to the request run alone."""
+def test_mix_runs_concurrently_and_results_unchanged(world):
+    """All requests submitted at once: several run at the same time (their intervals from
+    admission to completion overlap) and each result is bit-identical to the request run
+    alone."""
     from paper_1709_06948_gb300 import align
     s, ids = world.make_server()
     tickets = [_submit(align, s, ids, req) for req in world.reqs]
@@ -106,7 +107,9 @@ def test_mix_is_batched_and_results_unchanged(world):
         assert r["status"] == 0
         assert r["T"].tolist() == T.tolist() and r["mi"] == mi
     total_levels = sum(req[4] for req in world.reqs)
-    assert st["max_active"] > 1 and st["steps"] < total_levels
+    assert st["max_active"] > 1 and st["steps"] == total_levels
+    overlaps = sum(1 for a in res for b in res if a is not b and a["t_start"] < b["t_done"] and b["t_start"] < a["t_done"])
+    assert overlaps > 0
     assert st["admitted"] == len(world.reqs) and st["queued"] == 0
     s.close()
 
@@ -128,17 +131,18 @@ def test_staggered_arrivals_join_running_batches(world):
 
 def test_memory_budget_limits_admission(world):
     from paper_1709_06948_gb300 import align
-    probe, ids = world.make_server()
+    probe, ids = world.make_server(slots=1)
     base = align.align_server_stats(probe)["bytes_held"]  # the references
     probe.close()
-    # room for the references and the largest of three requests, not for two of them
-    # (per-request bytes as the server estimates them: points, tiles, per-pose buffers)
+
+    # room for the references and the largest of three requests, not for two of them (a
+    # request's bytes as the server estimates them: what its slot holds after running it alone)
     def est(req):
-        n = req[1].shape[0]
-        P = int(np.prod(COUNTS))
-        n_pad = max(3, -(-n // 1024)) * 1024
-        n_rot = COUNTS[3] * COUNTS[4] * COUNTS[5]
-        return n * 24 + n_rot * n_pad * 16 + P * (16 * 16 * 4 + 24 + 4 + 48 + 12)
+        p, pid = world.make_server(slots=1)
+        align.align_wait(p, _submit(align, p, pid, req), 60000)
+        held = align.align_server_stats(p)["bytes_held"] - base
+        p.close()
+        return held
     sizes = sorted(est(r) for r in world.reqs[1:4])
     assert sizes[0] + sizes[1] > sizes[2]
     s, ids = world.make_server(budget=base + sizes[2], slots=64)
