@@ -362,7 +362,17 @@ def run_large(align, steps):
     etas = scangen.large_poses()
     P = len(etas)
     B = torch.from_numpy(pair.xyzB).cuda()
-    align.align_eval_mi(L, B, eta6=etas)  # warm-up (learns the key partitions)
+    # warm-up: the grid learns its key partitions and which way of sweeping fits (pose pairs,
+    # one pose per CTA, one pose per 2-CTA cluster); stop once that stays the same
+    prev, learned = None, []
+    for _ in range(8):
+        align.align_eval_mi(L, B, eta6=etas)
+        st = align.align_eval_stats(L)
+        cur = (st["sweep"], st["passes"])
+        learned.append(cur)
+        if cur == prev:
+            break
+        prev = cur
     torch.cuda.synchronize()
     align.align_profile(L, 1)
     wall = []
@@ -378,6 +388,8 @@ def run_large(align, steps):
            "pose_evals_per_s_wall": P / statistics.median(wall),
            "ms_per_launch_wall": statistics.median(wall) * 1e3,
            "eval_kernel_ms": ev_ms / max(n, 1), "key_partitions": st["passes"],
+           "sweep": align.SWEEP_KINDS.get(st["sweep"], st["sweep"]),
+           "warmup_sweep_and_partitions": [[align.SWEEP_KINDS.get(k, k), p] for k, p in learned],
            "argmax_eta": [float(x) for x in etas[am]], "T_true": [float(x) for x in pair.T], "mi_max": float(mi[am])}
     L.close()
     return out

@@ -57,8 +57,9 @@
 extern "C" {
 #endif
 
-/* 2: align_batch_stats fills 9 counters (poses per CTA added); align_batch_set_poses_per_cta,
-   align_eval_redo_poses and align_microbench added. */
+/* 2: align_batch_stats fills 9 counters (poses per CTA added), align_eval_stats 6 (sweep
+   kind added); align_batch_set_poses_per_cta, align_eval_redo_poses and align_microbench
+   added. */
 #define ALIGN_API_VERSION 2
 
 typedef enum {
@@ -171,8 +172,12 @@ align_status align_refine_nm(align_grid* grid, const float* xyzB, int64_t nB, in
 /* Counters of the last synchronising evaluation on this grid (host ints):
    [0] key-partition passes of the hardest pose so far, [1] voxels that needed the
    wide (64-bit) side sums, [2] hash-table slots per CTA, [3] CTAs of the last eval
-   launch, [4] kernels launched by this grid since creation. */
-align_status align_eval_stats(align_grid* grid, int64_t out[5]);
+   launch, [4] kernels launched by this grid since creation, [5] how the last eval launch
+   swept its poses: 0 one pose per CTA, 1 pose pairs (two poses per CTA that share their
+   rotation, t_y and t_z), 2 one pose per 2-CTA cluster sharing a table split between the
+   two CTAs' shared memories (grids whose poses need key partitions).  Each way learns its
+   own key-partition count; results are the same whichever runs. */
+align_status align_eval_stats(align_grid* grid, int64_t out[6]);
 
 /* Poses of the last evaluation on this grid (align_eval_mi, align_accumulate or the last
    level of a search) that the exact path finished: poses whose voxels did not fit the

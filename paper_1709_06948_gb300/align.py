@@ -364,11 +364,14 @@ def align_refine_nm(grid: Grid, xyzB, starts, step=(8.0, 8.0, 1.0, 0.1, 0.1, 0.8
     return T, mi, it
 
 
+SWEEP_KINDS = {0: "one pose per CTA", 1: "pose pairs", 2: "2-CTA cluster"}
+
+
 def align_eval_stats(grid: Grid):
-    out = np.zeros(5, dtype=np.int64)
+    out = np.zeros(6, dtype=np.int64)
     _check(load().align_eval_stats(grid.handle, out.ctypes.data_as(C.c_void_p)))
     return {"passes": int(out[0]), "wide_voxels": int(out[1]), "table_slots": int(out[2]), "ctas": int(out[3]),
-            "kernel_launches": int(out[4])}
+            "kernel_launches": int(out[4]), "sweep": int(out[5])}
 
 
 def align_eval_redo_poses(grid: Grid) -> np.ndarray:

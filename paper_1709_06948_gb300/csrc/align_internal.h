@@ -93,6 +93,9 @@ struct EvalArgs {
   // second -1 for a single pose.  nullptr: one pose per CTA step (eval_kernel).
   const int32_t* units;
   int32_t n_units;
+  // One item, one pose per 2-CTA cluster sharing a table split between the pair's shared
+  // memories (eval_cluster_kernel; an even number of CTAs).
+  int32_t cluster;
 };
 
 // One point-tile PackCopy of a batch: scan xyz (n points) -> out (n_out float4), raw

@@ -171,6 +171,85 @@ __device__ __forceinline__ uint32_t lane_mask_lt() {
   return m;
 }
 
+// ---------------------------------------------------------------------------------
+// Thread-block clusters (the cluster kernel): rank, the distributed shared-memory window
+// (.shared::cluster addresses of either CTA's shared memory) and the cluster barrier.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// All threads of every CTA of the cluster; release/acquire: shared-memory writes before it
+// are visible to the other CTA after it.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// The .shared::cluster address of shared-window address `a` of CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_cluster(uint32_t a, uint32_t rank) {
+  uint32_t d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(rank));
+  return d;
+}
+__device__ __forceinline__ uint32_t ldc32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint4 ldc128(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t atomc_cas(uint32_t a, uint32_t cmp, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared::cluster.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "r"(a), "r"(cmp), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ uint32_t atomc_add(uint32_t a, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void redc_add(uint32_t a, uint32_t v) {
+  asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void redc_min_s32(uint32_t a, int v) {
+  asm volatile("red.shared::cluster.min.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void redc_max_s32(uint32_t a, int v) {
+  asm volatile("red.shared::cluster.max.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atomc_cas_if(bool p, uint32_t a, uint32_t cmp, uint32_t v) {
+  uint32_t old;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\tmov.u32 %0, %3;\n\t@q atom.shared::cluster.cas.b32 %0, [%2], "
+      "%3, %4;\n\t}"
+      : "=r"(old)
+      : "r"((uint32_t)p), "r"(a), "r"(cmp), "r"(v)
+      : "memory");
+  return old;
+}
+__device__ __forceinline__ uint32_t atomc_add_if(bool p, uint32_t a, uint32_t v) {
+  uint32_t old;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\tmov.u32 %0, 0;\n\t@q atom.shared::cluster.add.u32 %0, [%2], "
+      "%3;\n\t}"
+      : "=r"(old)
+      : "r"((uint32_t)p), "r"(a), "r"(v)
+      : "memory");
+  return old;
+}
+__device__ __forceinline__ void redc_add_if(bool p, uint32_t a, uint32_t v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q red.shared::cluster.add.u32 [%1], %2;\n\t}" ::"r"(
+                   (uint32_t)p),
+               "r"(a), "r"(v)
+               : "memory");
+}
+
 // Layout: per-warp rings | flags (16 B) | table keys (T x 4 B) | table values (T x kVW
 // words) | histogram | grid constants | bbox | current item.  The flags sit just below the
 // keys so that the hot loop reaches them at a fixed offset from the key base.
@@ -197,7 +276,12 @@ struct EvalSmem {
   uint32_t hist_stride;
   // shared-window addresses
   uint32_t a_queue, a_key, a_vals, a_hist, a_box;
+  // the cluster kernel: this CTA's rank and the .shared::cluster address of a_key in each
+  // CTA of the pair (both CTAs have the same layout, so any table address maps by offset)
+  uint32_t rank, c_key[2];
 };
+// The CTA of a 2-CTA cluster whose half of the distributed table holds `key`.
+__device__ __forceinline__ uint32_t key_owner(uint32_t key) { return (key * 0xD6E8FEB9u) >> 31; }
 constexpr uint32_t kFlagOccupied = 16u;  // byte offsets of the flags below a_key
 constexpr uint32_t kFlagFull = 12u;
 constexpr uint32_t kFlagOvf = 8u;        // entries in the CTA's overflow list
@@ -370,6 +454,73 @@ __device__ __forceinline__ void insert_overflow(const EvalSmem& S, const EvalArg
   }
 }
 
+// The same find-or-insert for the cluster kernel's distributed table (two-choice buckets in
+// the owning CTA's half, addressed through the cluster window).  tb: the owner's key base.
+__device__ __noinline__ int table_slot_slow_cl(uint32_t tb, uint32_t key, uint32_t nb, uint32_t b) {
+#pragma unroll 1
+  for (int i = 0; i < kProbeBuckets; ++i) {
+    const uint4 k4 = ldc128(tb + 16u * b);
+    const int h = bucket_hit(k4, key);
+    if (h >= 0) return (int)(4 * b) + h;
+    const uint32_t f = bucket_fill(k4);
+    if (f < 4u) {
+      const uint32_t s = 4 * b + f;
+      const uint32_t old = atomc_cas(tb + 4u * s, kEmptyKey, key);
+      if (old == kEmptyKey || old == key) return (int)s;
+      continue;  // another thread took that slot: read the bucket again
+    }
+    b = (b + 1 == nb) ? 0u : b + 1;
+  }
+  return -1;
+}
+__device__ __forceinline__ int table_slot_cl(uint32_t tb, uint32_t key, uint32_t nb) {
+  uint32_t b1, b2;
+  table_buckets(key, nb, b1, b2);
+#pragma unroll 1
+  for (int tries = 0; tries < 9; ++tries) {  // each lost race means one more key in b1 or b2
+    const uint4 ka = ldc128(tb + 16u * b1);
+    const uint4 kb = ldc128(tb + 16u * b2);
+    const int ha = bucket_hit(ka, key), hb = bucket_hit(kb, key);
+    if (ha >= 0) return (int)(4 * b1) + ha;
+    if (hb >= 0) return (int)(4 * b2) + hb;
+    const uint32_t fa = bucket_fill(ka), fb = bucket_fill(kb);
+    if (fa == 4u && fb == 4u) break;  // both full: the key can never enter b1 or b2
+    const uint32_t s = fa <= fb ? 4 * b1 + fa : 4 * b2 + fb;
+    const uint32_t old = atomc_cas(tb + 4u * s, kEmptyKey, key);
+    if (old == kEmptyKey || old == key) return (int)s;
+  }
+  return table_slot_slow_cl(tb, key, nb, b2 + 1 == nb ? 0u : b2 + 1);
+}
+
+// Cluster kernel, after a sweep: insert this CTA's overflow list into the distributed table.
+template <int kVW>
+__device__ __forceinline__ void insert_overflow_cl(const EvalSmem& S, const EvalArgs& a, const GridConst& gc) {
+  const uint32_t n = min(*(volatile uint32_t*)&S.flags[2], (uint32_t)kOvfCap);
+  const uint4* ovf = a.ovf + (size_t)blockIdx.x * kOvfCap;
+  for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
+    const uint4 e = ovf[i];
+    const uint32_t tb = S.c_key[key_owner(e.x)];
+    const int slot = table_slot_cl(tb, e.x, (uint32_t)a.n_buckets);
+    if (slot < 0) {
+      sts32(S.a_key - kFlagFull, 1u);
+      continue;
+    }
+    const uint32_t v = tb + (S.a_vals - S.a_key) + 4u * kVW * (uint32_t)slot;
+    if (kVW == 2) {
+      const uint32_t ns = (uint32_t)gc.ns_shift;
+      const uint32_t old = atomc_add(v, e.y);
+      if ((old >> ns) + (e.y >> ns) > gc.nlim_pack) sts32(S.a_key - kFlagWide, 1u);
+      redc_add(v + 4u, e.z);
+    } else {
+      redc_add(v, e.y);
+      if (kVW == 3) {
+        redc_add(v + 4u, e.z);
+        redc_add(v + 8u, e.w);
+      }
+    }
+  }
+}
+
 // Exact path (redo_kernel): add one run; the table keeps the plain count, S1 and S2 go to
 // the CTA's 64-bit sums in global memory.
 template <int kVW>
@@ -414,7 +565,7 @@ __device__ __forceinline__ uint4 run_entry(const Run& r) {
 // While no n field in it reaches 2^b (2^(b+1) - 2 <= nlim), every add kept the voxel at or
 // below nlim; the sweep's end tests acc once (the exact path takes the pose otherwise).
 // kCount32: a drain of 32 entries (during the sweep); otherwise `count` (the last drain).
-template <int kVW, bool kCount32, bool kTwo>
+template <int kVW, bool kCount32, bool kTwo, bool kCl = false>
 __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count_arg,
                                            const EvalArgs& a, uint32_t& acc) {
   const uint32_t count = kCount32 ? 32u : count_arg;
@@ -423,14 +574,18 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
   uint4 e = lds128(ring + 16u * lane);  // the ring holds 64 entries: always in bounds
   if (!kCount32 && lane >= count) e.x = kEmptyKey;
   const bool valid = e.x != kEmptyKey;
+  // the table holding e.x: this CTA's, or (cluster kernel) the owning CTA's half of the
+  // distributed table, addressed through the cluster window
+  const uint32_t tb = kCl ? S.c_key[key_owner(e.x)] : S.a_key;  // keys
+  const uint32_t vb = tb + (S.a_vals - S.a_key);                 // values
   int slot;
   uint32_t s_new;
   bool ins;
   if constexpr (kTwo) {
     uint32_t b1, b2;
     table_buckets(e.x, (uint32_t)a.n_buckets, b1, b2);
-    const uint4 ka = lds128(S.a_key + 16u * b1);
-    const uint4 kb = lds128(S.a_key + 16u * b2);
+    const uint4 ka = kCl ? ldc128(tb + 16u * b1) : lds128(tb + 16u * b1);
+    const uint4 kb = kCl ? ldc128(tb + 16u * b2) : lds128(tb + 16u * b2);
     const int ha = bucket_hit(ka, e.x), hb = bucket_hit(kb, e.x);
     const uint32_t fa = bucket_fill(ka), fb = bucket_fill(kb);
     slot = ha >= 0 ? (int)(4 * b1) + ha : hb >= 0 ? (int)(4 * b2) + hb : -1;
@@ -439,21 +594,29 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
     ins = valid && slot < 0 && (fa < 4u || fb < 4u);
   } else {
     const uint32_t b = __umulhi(e.x * 0x9E3779B1u, (uint32_t)a.n_buckets);
-    const uint4 k4 = lds128(S.a_key + 16u * b);
+    const uint4 k4 = kCl ? ldc128(tb + 16u * b) : lds128(tb + 16u * b);
     const int h = bucket_hit(k4, e.x);
     const uint32_t f = bucket_fill(k4);
     slot = h >= 0 ? (int)(4 * b) + h : -1;
     s_new = 4 * b + f;
     ins = valid && slot < 0 && f < 4u;
   }
-  const uint32_t old = atom_cas_if(ins, S.a_key + 4u * s_new, kEmptyKey, e.x);
+  const uint32_t old = kCl ? atomc_cas_if(ins, tb + 4u * s_new, kEmptyKey, e.x)
+                           : atom_cas_if(ins, tb + 4u * s_new, kEmptyKey, e.x);
   if (ins && (old == kEmptyKey || old == e.x)) slot = (int)s_new;
   const bool ok = valid && slot >= 0;
-  const uint32_t v = S.a_vals + 4u * kVW * (uint32_t)slot;
+  const uint32_t v = vb + 4u * kVW * (uint32_t)slot;
   if (kVW == 2) {
-    const uint32_t old = atom_add_if(ok, v, e.y);
+    const uint32_t old = kCl ? atomc_add_if(ok, v, e.y) : atom_add_if(ok, v, e.y);
     acc |= ok ? (old | e.y) : 0u;
-    red_add_if(ok, v + 4u, e.z);
+    if (kCl) redc_add_if(ok, v + 4u, e.z);
+    else red_add_if(ok, v + 4u, e.z);
+  } else if (kCl) {
+    redc_add_if(ok, v, e.y);
+    if (kVW == 3) {
+      redc_add_if(ok, v + 4u, e.z);
+      redc_add_if(ok, v + 8u, e.w);
+    }
   } else {
     red_add_if(ok, v, e.y);
     if (kVW == 3) {
@@ -461,8 +624,8 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
       red_add_if(ok, v + 8u, e.w);
     }
   }
-  // both buckets full (or insert race lost): the run goes to the overflow list (rare at
-  // the table's load: the warp skips this unless one of its lanes needs it)
+  // both buckets full (or insert race lost): the run goes to this CTA's overflow list (rare
+  // at the table's load: the warp skips this unless one of its lanes needs it)
   const bool ov = valid && slot < 0;
   if (__any_sync(kFull, ov)) {
     const uint32_t i = atom_add_if(ov, S.a_key - kFlagOvf, 1u);
@@ -481,14 +644,14 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
 }
 
 // Append the finished runs of the lanes with `done` set, then drain if 32 are waiting.
-template <int kVW, bool kTwo>
+template <int kVW, bool kTwo, bool kCl = false>
 __device__ __forceinline__ void ring_push(const EvalSmem& S, uint32_t ring, uint32_t lane_lt, bool done,
                                           const Run& r, uint32_t& fill, const EvalArgs& a, uint32_t& acc) {
   const uint32_t m = __ballot_sync(kFull, done);
   sts128_if(done, ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), run_entry<kVW>(r));
   fill += (uint32_t)__popc(m);
   // fill is the same in every lane; the vote lets the compiler know the branch is uniform
-  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVW, true, kTwo>(S, ring, fill, 32u, a, acc);
+  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVW, true, kTwo, kCl>(S, ring, fill, 32u, a, acc);
 }
 
 struct PoseRegs {
@@ -835,7 +998,7 @@ __device__ __forceinline__ const float4* pose_tiles(const EvalItem& I, int lp) {
 // One tile of this thread's stream: key, run step, ring append of the finished run.  No
 // per-point check of dz: the grid constants guarantee 0 <= dz <= res_mm for every point
 // inside the grid (validate_desc).
-template <int kVW, bool kRot, bool kPart>
+template <int kVW, bool kRot, bool kPart, bool kTwo = false, bool kCl = false>
 __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                            const PoseRegs& P, const float4* pts, int lg, uint32_t part, Run& run,
                                            uint32_t ring, uint32_t lane_lt, uint32_t& fill, uint32_t& acc) {
@@ -846,7 +1009,7 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
     point_key<kRot>(vc, P, pts[j], key, dz);
     if (kPart && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != part) key = kEmptyKey;
     const bool done = key != run.key;
-    ring_push<kVW, false>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc);
+    ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc);
     if (kVW == 2) {
       run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
     } else {
@@ -860,13 +1023,13 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
 
 // The run step of one point whose key and dz are known: append the finished run, extend or
 // restart the run.
-template <int kVW, bool kTwo>
+template <int kVW, bool kTwo, bool kCl = false>
 __device__ __forceinline__ void run_step(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc, uint32_t key,
                                          int dz, Run& run, uint32_t ring, uint32_t lane_lt, uint32_t& fill,
                                          uint32_t& acc) {
   const bool done = key != run.key;
   // a finished run of points outside the grid (or outside the key partition) is dropped
-  ring_push<kVW, kTwo>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc);
+  ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc);
   if (kVW == 2) {
     run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
   } else {
@@ -880,35 +1043,35 @@ __device__ __forceinline__ void run_step(const EvalSmem& S, const EvalArgs& a, c
 // One pass over all tiles of the pose: every thread streams its own points straight from
 // L2, kDepth tiles ahead.  A run is cut every `cut` tiles so that its 32-bit sums stay
 // below nlim points.
-template <int kVW, bool kRot, bool kPart>
+template <int kVW, bool kRot, bool kPart, bool kTwo = false, bool kCl = false, int kD = kDepth>
 __device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                                const PoseRegs& P, const float4* src, int nt, int lg, uint32_t part,
                                                uint32_t ring, uint32_t lane_lt, int cut) {
   Run run{kEmptyKey, 0u, 0u, 0u};
   uint32_t fill = 0u, acc = 0u;
-  float4 buf[kDepth][kPPT];  // register ring of the next kDepth tiles
+  float4 buf[kD][kPPT];  // register ring of the next kD tiles
   // this thread's slot of tile 0 (x,y and z); tile t is kTileXY / kTileZ further on
   const float2* xy = reinterpret_cast<const float2*>(src - threadIdx.x) + threadIdx.x;
   const float* zz = reinterpret_cast<const float*>(src - threadIdx.x) + 2 * kTile + threadIdx.x;
 #pragma unroll
-  for (int d = 0; d < kDepth; ++d)
+  for (int d = 0; d < kD; ++d)
     if (d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
-  xy += kDepth * kTileXY;  // the next tile to load: t + kDepth
-  zz += kDepth * kTileZ;
+  xy += kD * kTileXY;  // the next tile to load: t + kD
+  zz += kD * kTileZ;
   int next_cut = cut;
   int t = 0;
-  for (; t + 2 * kDepth <= nt; t += kDepth) {  // every prefetch in range: no guards
+  for (; t + 2 * kD <= nt; t += kD) {  // every prefetch in range: no guards
     if (t >= next_cut) {  // uniform; only when a stream is longer than nlim points
-      ring_push<kVW, false>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
+      ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
-    // the keys of the kDepth buffered tiles first (independent of one another), then the
+    // the keys of the kD buffered tiles first (independent of one another), then the
     // next loads into the freed buffers, then the run steps in stream order
-    uint32_t keys[kDepth][kPPT];
-    int dzs[kDepth][kPPT];
+    uint32_t keys[kD][kPPT];
+    int dzs[kD][kPPT];
 #pragma unroll
-    for (int d = 0; d < kDepth; ++d)
+    for (int d = 0; d < kD; ++d)
 #pragma unroll
       for (int j = 0; j < kPPT; ++j) {
         point_key<kRot>(vc, P, buf[d][j], keys[d][j], dzs[d][j]);
@@ -916,32 +1079,32 @@ __device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a,
           keys[d][j] = kEmptyKey;
       }
 #pragma unroll
-    for (int d = 0; d < kDepth; ++d) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
+    for (int d = 0; d < kD; ++d) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
 #pragma unroll
-    for (int d = 0; d < kDepth; ++d)
+    for (int d = 0; d < kD; ++d)
 #pragma unroll
-      for (int j = 0; j < kPPT; ++j) run_step<kVW, false>(S, a, vc, keys[d][j], dzs[d][j], run, ring, lane_lt, fill, acc);
-    xy += kDepth * kTileXY;
-    zz += kDepth * kTileZ;
+      for (int j = 0; j < kPPT; ++j) run_step<kVW, kTwo, kCl>(S, a, vc, keys[d][j], dzs[d][j], run, ring, lane_lt, fill, acc);
+    xy += kD * kTileXY;
+    zz += kD * kTileZ;
   }
-  for (; t < nt; t += kDepth) {
+  for (; t < nt; t += kD) {
     if (t >= next_cut) {
-      ring_push<kVW, false>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
+      ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
 #pragma unroll
-    for (int d = 0; d < kDepth; ++d) {
+    for (int d = 0; d < kD; ++d) {
       if (t + d < nt) {
-        sweep_tile<kVW, kRot, kPart>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, acc);
-        if (t + kDepth + d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
+        sweep_tile<kVW, kRot, kPart, kTwo, kCl>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, acc);
+        if (t + kD + d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
       }
     }
-    xy += kDepth * kTileXY;
-    zz += kDepth * kTileZ;
+    xy += kD * kTileXY;
+    zz += kD * kTileZ;
   }
-  ring_push<kVW, false>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
-  while (fill > 0u) ring_drain<kVW, false, false>(S, ring, fill, min(fill, 32u), a, acc);
+  ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
+  while (fill > 0u) ring_drain<kVW, false, kTwo, kCl>(S, ring, fill, min(fill, 32u), a, acc);
   if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
 }
 
@@ -1244,6 +1407,115 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_pair_kernel(const _
   }
 }
 
+// One pose at a time per 2-CTA cluster, for grids whose single-pose table needs key
+// partitions (the large grid).  The two CTAs sweep the two halves of every thread's stream
+// of points and share one table split between their shared memories: a key lives in the
+// half its owner bit names (key_owner), reached through the cluster window, so the pair
+// holds twice the keys of one CTA's table (half the key partitions) and every point is swept
+// once per pass, by one of the two CTAs.  Each CTA then scans its own half; the second CTA
+// adds its partial histogram and box into the first's, which emits them.  Every cluster
+// barrier is reached by both CTAs with the same decisions, taken from both halves' flags,
+// and neither CTA leaves while the other may still address its shared memory.
+template <int kVW, bool kRot>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    eval_cluster_kernel(const __grid_constant__ EvalArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  EvalSmem S;
+  const int T = a.table_slots;
+  eval_smem_layout(a.K, T, kVW, 1, &S, smem_raw);
+  const int tid = threadIdx.x;
+  const uint32_t rank = cluster_rank();
+  const uint32_t peer = rank ^ 1u;
+  S.rank = rank;
+  S.c_key[0] = map_cluster(S.a_key, 0u);
+  S.c_key[1] = map_cluster(S.a_key, 1u);
+  const uint32_t cap = (uint32_t)T - (uint32_t)T / 10u;  // above 90% full a half counts as crowded
+  const uint32_t ring = S.a_queue + (uint32_t)(tid >> 5) * kQueue * 16u;
+  const uint32_t lane_lt = lane_mask_lt();
+  unsigned long long* wide = a.wide + (size_t)blockIdx.x * 2u * (size_t)T;
+  init_smem<kVW>(S, T, a.K * a.K, 1);
+  __syncthreads();
+  select_item(S, a, 0);
+  cluster_sync();  // both halves are empty before any insert crosses over
+  const EvalItem& I = a.one;
+  int passes = I.passes0 > 0 ? I.passes0 : a.passes0;
+  const VoxelConst vc = voxel_const<kVW>(I.gc);
+  const int cut = max(kDepth, (int)min(vc.nlim / (uint32_t)kPPT, (uint32_t)INT_MAX) / kDepth * kDepth);
+  const int nt = I.n_tiles;
+  const int half = (nt + 1) / 2;  // tiles [0, half) for rank 0, [half, nt) for rank 1
+  const int t0 = rank == 0u ? 0 : half;
+  const int nt_mine = rank == 0u ? half : nt - half;
+  const int n_cl = (int)(gridDim.x / 2), cid = (int)(blockIdx.x / 2);
+  const uint32_t c_peer = S.c_key[peer];
+  for (int gp = cid; gp < a.P; gp += n_cl) {
+    const int lp = gp - I.pose_base;
+    PoseRegs P;
+    load_pose(I.poses + 12 * (size_t)lp, P);
+    const float4* src = pose_tiles(I, lp) + tid + (size_t)t0 * kTile;
+    const int pose_passes = passes;
+    const int lg = __ffs(pose_passes) - 1;
+    uint32_t max_occupied = 0;
+    bool full = false, overflowed = false;
+    for (int pass = 0; pass < pose_passes; ++pass) {
+      if (!full && nt_mine > 0) {
+        if (lg == 0) sweep_pose<kVW, kRot, false, true, true, 2>(S, a, vc, P, src, nt_mine, 0, 0u, ring, lane_lt, cut);
+        else sweep_pose<kVW, kRot, true, true, true, 2>(S, a, vc, P, src, nt_mine, lg, (uint32_t)pass, ring, lane_lt, cut);
+      }
+      cluster_sync();  // every run of both CTAs is in the table or in an overflow list
+      if (!full && *(volatile uint32_t*)&S.flags[2] != 0u) insert_overflow_cl<kVW>(S, a, I.gc);
+      cluster_sync();  // the overflow inserts of both CTAs are done
+      overflowed = overflowed || S.flags[1] != 0u || ldc32(c_peer - kFlagFull) != 0u;
+      full = full || overflowed;
+      scan_table<kVW, false, 1>(S, I.gc, I, wide, a.wide_count, T, lp, full);  // this CTA's half
+      __syncthreads();
+      cluster_sync();  // both scans are done: the occupied counts and wide flags are final
+      max_occupied = max(max_occupied, max(S.flags[0], ldc32(c_peer - kFlagOccupied)));
+      full = full || S.flags[3] != 0u || ldc32(c_peer - kFlagWide) != 0u;
+      cluster_sync();  // both have read the other's flags before they are reset
+      if (tid == 0) {
+        S.flags[0] = 0u;
+        S.flags[2] = 0u;
+        S.flags[3] = 0u;
+      }
+    }
+    if (full) {  // finished later by the exact path
+      reset_pose(S);
+      if (tid == 0) {
+        S.flags[1] = 0u;
+        if (rank == 0u) a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)gp;
+      }
+      if (overflowed && passes < kMaxPasses) passes *= 2;
+      __syncthreads();
+      cluster_sync();  // the full flags are reset before either CTA sweeps the next pose
+      continue;
+    }
+    // the pose's histogram and box: the second CTA adds its partial ones into the first's
+    if (rank == 1u) {
+      const int KK = S.gc->K * S.gc->K;
+      const uint32_t h0 = c_peer + (S.a_hist - S.a_key);
+      for (int i = tid; i < KK; i += kThreads) {
+        const uint32_t v = S.hist[i];
+        if (v != 0u) redc_add(h0 + 4u * (uint32_t)i, v);
+        S.hist[i] = 0u;
+      }
+      if (tid < 6) {
+        const uint32_t b0 = c_peer + (S.a_box - S.a_key) + 4u * (uint32_t)tid;
+        if (tid < 3) redc_min_s32(b0, S.box[tid]);
+        else redc_max_s32(b0, S.box[tid]);
+        S.box[tid] = tid < 3 ? INT_MAX : INT_MIN;
+      }
+    }
+    cluster_sync();  // the first CTA holds the pose's histogram and box
+    if (rank == 0u) emit_pose(S, I, lp);
+    if (max_occupied > cap && passes < kMaxPasses) passes *= 2;  // crowded: more partitions next
+  }
+  if (tid == 0 && rank == 0u) {
+    atomicMax(a.max_passes, (uint32_t)passes);
+    if (I.item_passes) atomicMax(I.item_passes, (uint32_t)passes);
+  }
+  cluster_sync();  // neither CTA leaves while the other may still address its shared memory
+}
+
 // Poses that eval_kernel could not finish: plain sweeps; each run goes straight into the
 // table with 64-bit side sums for voxels beyond the 32-bit bound; a full table restarts
 // the pose with twice the key partitions.
@@ -1523,13 +1795,20 @@ cudaError_t setup_t(int smem) {
     e = cudaFuncSetAttribute(redo_kernel<kVW, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess && !kRot)
     e = cudaFuncSetAttribute(eval_pair_kernel<kVW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(eval_cluster_kernel<kVW, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
 template <int kVW, bool kRot>
 cudaError_t launch_eval_t(const EvalArgs& a, int n_ctas, size_t smem, cudaStream_t s) {
-  auto* k = a.item_start == nullptr ? eval_kernel<kVW, kRot, true> : eval_kernel<kVW, kRot, false>;
-  k<<<n_ctas, kThreads, smem, s>>>(a);
+  if (a.cluster) {  // 2-CTA clusters: an even grid, one item
+    if (a.item_start != nullptr || n_ctas < 2 || (n_ctas & 1)) return cudaErrorInvalidValue;
+    eval_cluster_kernel<kVW, kRot><<<n_ctas, kThreads, smem, s>>>(a);
+  } else {
+    auto* k = a.item_start == nullptr ? eval_kernel<kVW, kRot, true> : eval_kernel<kVW, kRot, false>;
+    k<<<n_ctas, kThreads, smem, s>>>(a);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   redo_kernel<kVW, kRot><<<n_ctas, kThreads, smem, s>>>(a);

@@ -377,9 +377,15 @@ int pair_units_impl(const float* poses12, const int32_t* src, int64_t P, std::ve
 // only grow), one pair sweep does the work of two single sweeps.
 bool use_pairs(const align_grid* g) { return g->passes_seed_pair[0] <= g->passes_seed[0]; }
 
+// Whether a launch of single poses runs one pose per 2-CTA cluster: while the grid's single
+// poses need key partitions and the cluster's twice-as-large table has needed fewer.
+bool use_cluster(const align_grid* g) {
+  return g->n_sm >= 2 && g->passes_seed[0] >= 2 && g->passes_seed_cluster < g->passes_seed[0];
+}
+
 align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_poses, int64_t P, bool rotate,
                                int n_rot, const EvalOut& out, const int32_t* d_units = nullptr,
-                               int32_t n_units = 0);
+                               int32_t n_units = 0, bool cluster = false);
 
 // Enqueue pack + eval + redo + compose + argmax for poses already on the device.
 // h_poses (may be NULL): the same poses on the host, used to find shared rotations (and
@@ -420,13 +426,15 @@ align_status enqueue_eval(align_grid* g, int32_t n_tiles, const float* d_poses, 
       n_rot = groups;
     }
   }
-  return enqueue_eval_core(g, n_tiles, d_poses, P, rotate, n_rot, out);
+  return enqueue_eval_core(g, n_tiles, d_poses, P, rotate, n_rot, out, nullptr, 0,
+                           out.dump == nullptr && use_cluster(g));
 }
 
 // The launches of one evaluation.  Unless `rotate`, g->rots holds n_rot rotations and
 // g->pose_src each pose's rotation (on the device, in stream order).
 align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_poses, int64_t P, bool rotate,
-                               int n_rot, const EvalOut& out, const int32_t* d_units, int32_t n_units) {
+                               int n_rot, const EvalOut& out, const int32_t* d_units, int32_t n_units,
+                               bool cluster) {
   const int K = g->gc.K;
   const size_t KK = (size_t)K * K;
   CU(g->out_c.ensure((size_t)P * KK * sizeof(uint32_t)), "allocate histograms");
@@ -435,11 +443,14 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   align_status st0 = ensure_status_words(g);
   if (st0 != ALIGN_OK) return st0;
   const bool pairs = d_units != nullptr && n_units > 0 && !rotate;
-  const int n_ctas = (int)std::min<int64_t>(pairs ? n_units : P, g->n_sm);
+  cluster = cluster && !pairs;
+  const int n_ctas = cluster ? 2 * (int)std::min<int64_t>(P, g->n_sm / 2)
+                             : (int)std::min<int64_t>(pairs ? n_units : P, g->n_sm);
   const bool var = g->gc.feature != ALIGN_FEAT_COUNT || out.dump != nullptr;
   const int vw = eval_layout(g->gc, var);
   g->table_slots = eval_shape(0).table_slots_for(K, vw, g->smem_optin, pairs ? 2 : 1);
   g->last_pairs = pairs;
+  g->last_cluster = cluster;
   const size_t wide_bytes = (size_t)n_ctas * 2 * g->table_slots * sizeof(unsigned long long);
   if (g->wide.cap < wide_bytes || g->wide.p == nullptr) {
     CU(g->wide.ensure(wide_bytes), "allocate wide sums");
@@ -470,7 +481,10 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   item.n_tiles = n_tiles;
   item.P = (int32_t)P;
   item.pose_base = 0;
-  item.passes0 = pairs ? g->passes_seed_pair[0] : g->passes_seed[0];
+  // a cluster's table holds twice a CTA's keys: it starts from half the single-pose count
+  item.passes0 = pairs     ? g->passes_seed_pair[0]
+                 : cluster ? std::max(g->passes_seed_cluster, g->passes_seed[0] / 2)
+                           : g->passes_seed[0];
   item.item_passes = nullptr;
   item.out_c = g->out_c.as<uint32_t>();
   item.out_box = g->out_box.as<int32_t>();
@@ -494,6 +508,7 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   a.passes0 = item.passes0;
   a.units = pairs ? d_units : nullptr;
   a.n_units = pairs ? n_units : 0;
+  a.cluster = cluster ? 1 : 0;
   a.err = g->err.as<uint32_t>();
   a.max_passes = g->max_passes.as<uint32_t>();
   a.wide_count = g->wide_count.as<uint32_t>();
@@ -523,6 +538,7 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   }
   g->stats[2] = g->table_slots;
   g->stats[3] = n_ctas;
+  g->stats[5] = pairs ? 1 : cluster ? 2 : 0;
   g->stats[4] += 5;  // pack, eval, redo, compose, argmax
   return ALIGN_OK;
 }
@@ -547,7 +563,7 @@ align_status drain_events(align_grid* g) {
 // same kind.
 void learn_passes(align_grid* g, uint32_t used) {
   if (used == 0 || used > (1u << 16) || (used & (used - 1)) != 0) return;
-  int32_t& seed = g->last_pairs ? g->passes_seed_pair[0] : g->passes_seed[0];
+  int32_t& seed = g->last_pairs ? g->passes_seed_pair[0] : g->last_cluster ? g->passes_seed_cluster : g->passes_seed[0];
   if (used > (uint32_t)seed) seed = (int32_t)used;
 }
 
@@ -634,6 +650,7 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
   // pose pairs of every level (the lattice's index structure: t_x samples 2i and 2i+1 of the
   // same rotation, t_y and t_z), decided once for the whole search
   const bool pairs = P >= 2 && m[0] >= 2 && use_pairs(g);
+  const bool cluster = !pairs && use_cluster(g);  // likewise decided once for the search
   int32_t n_units = 0;
   if (pairs) {
     if (!std::equal(m, m + 6, g->lattice_units_m) || g->lat_units.p == nullptr) {
@@ -726,7 +743,8 @@ align_status search_pipelined(align_grid* g, int32_t n_tiles, const double c0[6]
     o.mi = g->mi.as<float>();
     o.argmax = g->argmax.as<int64_t>();
     align_status st = enqueue_eval_core(g, n_tiles, g->poses.as<float>(), P, false, n_rot, o,
-                                        pairs ? g->lat_units.as<int32_t>() : nullptr, n_units);
+                                        pairs ? g->lat_units.as<int32_t>() : nullptr, n_units,
+                                        !pairs && cluster);
     if (st != ALIGN_OK) return st;
     CU(cudaMemcpyAsync(&rec[l].am, g->argmax.p, 8, cudaMemcpyDeviceToHost, g->stream), "read argmax");
     CU(cudaMemcpyAsync(&rec[l].best, g->best.p, 8, cudaMemcpyDeviceToHost, g->stream), "read best");
@@ -1265,10 +1283,13 @@ align_status align_search(align_grid* g, const float* xyzB, int64_t nB, int flag
   return align_search_ex(g, xyzB, nB, flags, init, range, counts, levels, T_out, mi_out, nullptr);
 }
 
-align_status align_eval_stats(align_grid* g, int64_t out[5]) {
+align_status align_eval_stats(align_grid* g, int64_t out[6]) {
   if (!g || !out) return fail(ALIGN_E_INVALID, "NULL argument");
-  for (int i = 0; i < 5; ++i) out[i] = g->stats[i];
-  out[0] = std::max<int64_t>(out[0], g->passes_seed[0]);  // batched launches feed back through the seed
+  for (int i = 0; i < 6; ++i) out[i] = g->stats[i];
+  // batched launches feed back through the seed of the way the last launch swept its poses
+  const int32_t seed = g->last_pairs ? g->passes_seed_pair[0] : g->last_cluster ? g->passes_seed_cluster
+                                                                                 : g->passes_seed[0];
+  out[0] = std::max<int64_t>(out[0], seed);
   return ALIGN_OK;
 }
 

@@ -113,12 +113,14 @@ struct align_grid {
   // the pose-pair kernel (shape 0)
   int32_t passes_seed[mialign::kEvalShapes] = {1, 1, 1};
   int32_t passes_seed_pair[mialign::kEvalShapes] = {1, 1, 1};
-  bool last_pairs = false;  // the last eval launch evaluated pose pairs
+  int32_t passes_seed_cluster = 1;  // the 2-CTA cluster kernel (shape 0)
+  bool last_pairs = false;    // the last eval launch evaluated pose pairs
+  bool last_cluster = false;  // ... or ran one pose per 2-CTA cluster
   mialign::DevBuf units;    // pose pairs of the last pair launch with host poses
   mialign::DevBuf lat_units;           // pose pairs of a device-built lattice level (by index)
   std::vector<int32_t> lattice_units;  // ... on the host
   int32_t lattice_units_m[6] = {0, 0, 0, 0, 0, 0};
-  int64_t stats[5] = {0, 0, 0, 0, 0};
+  int64_t stats[6] = {0, 0, 0, 0, 0, 0};
   // event timing (align_profile): one (before eval, after eval, after argmax) triple per
   // launch, drained into the totals at the next synchronising call or profile read
   bool profiling = false;

@@ -151,6 +151,7 @@ void workspace_bind(align_grid* ws, const align_grid* ref) {
     ws->passes_seed[i] = ref->passes_seed[i];
     ws->passes_seed_pair[i] = ref->passes_seed_pair[i];
   }
+  ws->passes_seed_cluster = ref->passes_seed_cluster;
 }
 
 // Key partitions learned by a workspace go back to its reference (for the next request).
@@ -159,6 +160,7 @@ void workspace_learn(const align_grid* ws, align_grid* ref) {
     ref->passes_seed[i] = std::max(ref->passes_seed[i], ws->passes_seed[i]);
     ref->passes_seed_pair[i] = std::max(ref->passes_seed_pair[i], ws->passes_seed_pair[i]);
   }
+  ref->passes_seed_cluster = std::max(ref->passes_seed_cluster, ws->passes_seed_cluster);
 }
 
 void workspace_destroy(align_grid* ws) {

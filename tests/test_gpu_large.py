@@ -56,3 +56,38 @@ def test_large_lattice_matches_oracle(large):
     # the oracle's maximum over the compared poses is the GPU's argmax (within the FP32 band)
     o = int(sample[oracle.argmax(mo)])
     assert o == am_h or abs(mo[np.searchsorted(sample, am_h)] - mo.max()) <= 2e-5
+
+
+def test_large_every_sweep_kind_agrees(large):
+    """The same 4,096 large-grid poses evaluated repeatedly on one grid: the library first
+    tries pose pairs, learns that their table needs more key partitions than single poses,
+    evaluates single poses, then one pose per 2-CTA cluster (a table split between two CTAs'
+    shared memories, half the partitions).  Every call's MI and histograms are identical,
+    and a sample (with each call's argmax and exact-path poses) matches the oracle."""
+    from paper_1709_06948_gb300 import align
+    spec = large.grid
+    L = lib_grid(spec)
+    align.align_set_reference(L, large.xyzA)
+    etas = scangen.large_poses()[::8]
+    P = len(etas)
+    kinds, runs, must = [], [], set()
+    for _ in range(5):
+        mi, am, hist = align.align_eval_mi(L, large.xyzB, eta6=etas, with_hist=True)
+        st = align.align_eval_stats(L)
+        kinds.append((st["sweep"], st["passes"]))
+        runs.append((mi, am, hist))
+        must.update(align.align_eval_redo_poses(L).tolist())
+        must.add(am)
+    assert 2 in [k for k, _ in kinds], kinds  # the cluster kernel ran
+    for mi, am, hist in runs[1:]:
+        assert np.array_equal(mi, runs[0][0]) and am == runs[0][1] and np.array_equal(hist, runs[0][2])
+    rng = np.random.default_rng(82)
+    must = np.array(sorted(must), dtype=np.int64)
+    rest = np.setdiff1d(np.arange(P), must)
+    sample = np.sort(np.concatenate([must, rng.choice(rest, max(0, 256 - len(must)), replace=False)]))
+    G = oracle_grid(spec)
+    symA, boxA = G.reference(large.xyzA)
+    poses = align.align_round_poses(spec.origin, etas)
+    mo, ho, _ = G.eval_mi(symA, boxA, large.xyzB, poses[sample], nthreads=NT, with_hist=True)
+    assert np.array_equal(runs[0][2][sample], ho)
+    assert np.max(np.abs(runs[0][0][sample].astype(np.float64) - mo)) <= mi_tolerance()
