@@ -797,6 +797,67 @@ def run_surface(args):
     return 0
 
 
+SWEEP_WORKLOADS = ("lidar0.5", "lidar0.25", "large")
+
+
+def run_sweeps(args):
+    """Each way of sweeping poses (align_set_sweep kinds 0-2, and the automatic choice) on
+    4,096 lattice poses of three grids: the 120k-point LiDAR pair at 0.5 m and 0.25 m
+    (z-variance) and the large pair (260k points, 0.2 m, joint feature; every 8th pose of its
+    32,768-pose lattice).  Per kind: key partitions learned, eval-kernel time per launch
+    (CUDA events, median over --steps launches after the partitions settle).  One JSON line."""
+    import torch
+    from paper_1709_06948_gb300 import align
+    torch.cuda.set_device(0)
+    names = [w for w in args.sweep_workloads.split(",") if w]
+    bad = [w for w in names if w not in SWEEP_WORKLOADS]
+    if bad:
+        raise SystemExit(f"unknown workloads {bad}; choose from {SWEEP_WORKLOADS}")
+    kinds = [int(k) for k in args.sweep_kinds.split(",") if k]
+    res = []
+    for name in names:
+        if name == "large":
+            pair = scangen.large_pair()
+            spec, etas = pair.grid, scangen.large_poses()[::8]
+        else:
+            pair = scangen.lidar_pair()
+            spec, etas = scangen.lidar_grid(float(name[5:])), scangen.lidar_poses()
+        B = torch.from_numpy(pair.xyzB).cuda()
+        row = {"workload": name, "points": int(pair.xyzB.shape[0]), "dims": list(spec.dims), "poses": len(etas)}
+        ref_mi = None
+        for kind in kinds:
+            L = align.align_create_grid(spec.origin, spec.res_m, spec.dims, spec.feature, spec.count_levels,
+                                        spec.var_levels)
+            align.align_set_reference(L, pair.xyzA)
+            align.align_set_sweep(L, kind)
+            prev = None
+            for _ in range(8):  # until the kind and its partition count stay the same
+                mi, am, _ = align.align_eval_mi(L, B, eta6=etas)
+                st = align.align_eval_stats(L)
+                cur = (st["sweep"], st["passes"])
+                if cur == prev:
+                    break
+                prev = cur
+            if ref_mi is None:
+                ref_mi = mi
+            times = []
+            for _ in range(max(1, args.steps)):
+                align.align_profile(L, 1)
+                align.align_eval_mi(L, B, eta6=etas)
+                ev_ms, _, n = align.align_profile(L, 2)
+                times.append(ev_ms / max(n, 1))
+            align.align_profile(L, 0)
+            st = align.align_eval_stats(L)
+            row[f"kind{kind}"] = {"sweep": align.SWEEP_KINDS.get(st["sweep"], st["sweep"]),
+                                  "key_partitions": st["passes"],
+                                  "eval_kernel_ms": round(statistics.median(times), 4),
+                                  "same_mi_as_first_kind": bool(np.array_equal(mi, ref_mi))}
+            L.close()
+        res.append(row)
+    print(json.dumps({"mode": "sweeps", "gpu": torch.cuda.get_device_name(0), "results": res}))
+    return 0
+
+
 def run_peaks(args):
     """The measured peaks alone (one JSON line)."""
     import torch
@@ -817,12 +878,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="search", choices=["search", "eval", "accuracy", "surface", "peaks"],
+    ap.add_argument("--mode", default="search", choices=["search", "eval", "accuracy", "surface", "peaks", "sweeps"],
                     help="search: reference build + 6-level search per step (default); "
                          "eval: reference build + one align_eval_mi of --poses poses per step; "
                          "accuracy: final error vs initial error (synthetic Figs. 4-5); "
                          "surface: MI cost surfaces around the truth (synthetic Fig. 6); "
-                         "peaks: the throughput micro-benchmarks alone")
+                         "peaks: the throughput micro-benchmarks alone; "
+                         "sweeps: eval-kernel time of each way of sweeping poses on three grids")
+    ap.add_argument("--sweep-workloads", default=",".join(SWEEP_WORKLOADS), help="sweeps mode: workloads")
+    ap.add_argument("--sweep-kinds", default="-1,0,1,2", help="sweeps mode: align_set_sweep kinds")
     ap.add_argument("--pairs", type=int, default=4, help="accuracy mode: pairs per initial error")
     ap.add_argument("--surface-out", default=None, help="surface mode: prefix of .npy files for the surfaces")
     ap.add_argument("--poses", type=int, default=4096)
@@ -843,6 +907,8 @@ def main():
         return run_surface(args)
     if args.mode == "peaks":
         return run_peaks(args)
+    if args.mode == "sweeps":
+        return run_sweeps(args)
     return run_ours(args)
 
 

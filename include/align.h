@@ -58,8 +58,8 @@ extern "C" {
 #endif
 
 /* 2: align_batch_stats fills 9 counters (poses per CTA added), align_eval_stats 6 (sweep
-   kind added); align_batch_set_poses_per_cta, align_eval_redo_poses and align_microbench
-   added. */
+   kind added); align_batch_set_poses_per_cta, align_eval_redo_poses, align_set_sweep and
+   align_microbench added. */
 #define ALIGN_API_VERSION 2
 
 typedef enum {
@@ -175,9 +175,18 @@ align_status align_refine_nm(align_grid* grid, const float* xyzB, int64_t nB, in
    launch, [4] kernels launched by this grid since creation, [5] how the last eval launch
    swept its poses: 0 one pose per CTA, 1 pose pairs (two poses per CTA that share their
    rotation, t_y and t_z), 2 one pose per 2-CTA cluster sharing a table split between the
-   two CTAs' shared memories (grids whose poses need key partitions).  Each way learns its
-   own key-partition count; results are the same whichever runs. */
+   two CTAs' shared memories (grids whose single poses need 8 or more key partitions).
+   Each way learns its own key-partition count; results are the same whichever runs. */
 align_status align_eval_stats(align_grid* grid, int64_t out[6]);
+
+/* How this grid's launches sweep their poses (the kinds of align_eval_stats [5]): -1
+   automatic (the default: pairs while their tables fit as well as single poses', the
+   cluster while single poses need 8 or more key partitions), 0 one pose per CTA, 1 pose
+   pairs wherever the poses form pairs (single poses elsewhere), 2 one pose per 2-CTA
+   cluster for single-pose launches (never for align_accumulate's dumps nor inside a batch,
+   which sweeps pairs or single poses).  Results are the same for every kind; the choice
+   serves measurement and tests.  Errors: ALIGN_E_INVALID for another value. */
+align_status align_set_sweep(align_grid* grid, int32_t kind);
 
 /* Poses of the last evaluation on this grid (align_eval_mi, align_accumulate or the last
    level of a search) that the exact path finished: poses whose voxels did not fit the

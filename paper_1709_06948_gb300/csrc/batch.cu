@@ -380,8 +380,11 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     pp.units.clear();
     // (and only while the grid's pairs have needed no more key partitions than its single
     // poses: a pair table holds two poses' voxels)
-    const bool fits = __atomic_load_n(&pp.g->passes_seed_pair[shape], __ATOMIC_RELAXED) <=
-                      __atomic_load_n(&pp.g->passes_seed[shape], __ATOMIC_RELAXED);
+    // (a grid's align_set_sweep choice of single poses or pairs holds here too)
+    const bool fits = pp.g->sweep_mode >= 0
+                          ? pp.g->sweep_mode == 1
+                          : __atomic_load_n(&pp.g->passes_seed_pair[shape], __ATOMIC_RELAXED) <=
+                                __atomic_load_n(&pp.g->passes_seed[shape], __ATOMIC_RELAXED);
     if (pose_pairs && fits && pp.prerot && pp.P >= 2) {
       const int nu = pair_units(pp.hposes.data(), pp.idx.data(), pp.P, pp.units);
       if (nu < pp.P) pp.n_units = nu;

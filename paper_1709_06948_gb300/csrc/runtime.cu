@@ -375,12 +375,19 @@ int pair_units_impl(const float* poses12, const int32_t* src, int64_t P, std::ve
 // Whether the next pre-rotated launch on this grid evaluates pose pairs: while pairs have
 // needed no more key partitions than single poses (both counts are learned per grid and
 // only grow), one pair sweep does the work of two single sweeps.
-bool use_pairs(const align_grid* g) { return g->passes_seed_pair[0] <= g->passes_seed[0]; }
+bool use_pairs(const align_grid* g) {
+  return g->sweep_mode < 0 ? g->passes_seed_pair[0] <= g->passes_seed[0] : g->sweep_mode == 1;
+}
 
 // Whether a launch of single poses runs one pose per 2-CTA cluster: while the grid's single
-// poses need key partitions and the cluster's twice-as-large table has needed fewer.
+// poses need at least 8 key partitions and the cluster's twice-as-large table has needed
+// fewer.  Half of a cluster's table inserts go to the peer CTA's shared memory and wait
+// several times as long as a local insert; measured per 4,096 poses, halving 2 partitions
+// to 1 loses (4.01 against 2.81 ms, 0.25 m LiDAR grid) and halving 4 to 2 breaks even
+// (10.14 against 10.04 ms, 0.2 m 6.4M-voxel grid).
 bool use_cluster(const align_grid* g) {
-  return g->n_sm >= 2 && g->passes_seed[0] >= 2 && g->passes_seed_cluster < g->passes_seed[0];
+  if (g->sweep_mode >= 0) return g->sweep_mode == 2 && g->n_sm >= 2;
+  return g->n_sm >= 2 && g->passes_seed[0] >= 8 && g->passes_seed_cluster < g->passes_seed[0];
 }
 
 align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_poses, int64_t P, bool rotate,
@@ -1290,6 +1297,13 @@ align_status align_eval_stats(align_grid* g, int64_t out[6]) {
   const int32_t seed = g->last_pairs ? g->passes_seed_pair[0] : g->last_cluster ? g->passes_seed_cluster
                                                                                  : g->passes_seed[0];
   out[0] = std::max<int64_t>(out[0], seed);
+  return ALIGN_OK;
+}
+
+align_status align_set_sweep(align_grid* g, int32_t kind) {
+  if (!g) return fail(ALIGN_E_INVALID, "NULL grid");
+  if (kind < -1 || kind > 2) return fail(ALIGN_E_INVALID, "sweep kind must be -1, 0, 1 or 2");
+  g->sweep_mode = kind;
   return ALIGN_OK;
 }
 

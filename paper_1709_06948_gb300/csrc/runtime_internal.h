@@ -114,6 +114,7 @@ struct align_grid {
   int32_t passes_seed[mialign::kEvalShapes] = {1, 1, 1};
   int32_t passes_seed_pair[mialign::kEvalShapes] = {1, 1, 1};
   int32_t passes_seed_cluster = 1;  // the 2-CTA cluster kernel (shape 0)
+  int32_t sweep_mode = -1;  // -1 automatic, else the sweep kind every launch takes (align_set_sweep)
   bool last_pairs = false;    // the last eval launch evaluated pose pairs
   bool last_cluster = false;  // ... or ran one pose per 2-CTA cluster
   mialign::DevBuf units;    // pose pairs of the last pair launch with host poses

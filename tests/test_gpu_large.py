@@ -60,10 +60,11 @@ def test_large_lattice_matches_oracle(large):
 
 def test_large_every_sweep_kind_agrees(large):
     """The same 4,096 large-grid poses evaluated repeatedly on one grid: the library first
-    tries pose pairs, learns that their table needs more key partitions than single poses,
-    evaluates single poses, then one pose per 2-CTA cluster (a table split between two CTAs'
-    shared memories, half the partitions).  Every call's MI and histograms are identical,
-    and a sample (with each call's argmax and exact-path poses) matches the oracle."""
+    tries pose pairs, learns that their table needs more key partitions than single poses
+    and evaluates single poses; then the grid is set to one pose per 2-CTA cluster (a table
+    split between two CTAs' shared memories, starting from half the single-pose partitions).
+    Every call's MI and histograms are identical, and a sample (with each call's argmax and
+    exact-path poses) matches the oracle."""
     from paper_1709_06948_gb300 import align
     spec = large.grid
     L = lib_grid(spec)
@@ -71,14 +72,17 @@ def test_large_every_sweep_kind_agrees(large):
     etas = scangen.large_poses()[::8]
     P = len(etas)
     kinds, runs, must = [], [], set()
-    for _ in range(5):
+    for i in range(5):
+        if i == 3:
+            align.align_set_sweep(L, 2)
         mi, am, hist = align.align_eval_mi(L, large.xyzB, eta6=etas, with_hist=True)
         st = align.align_eval_stats(L)
         kinds.append((st["sweep"], st["passes"]))
         runs.append((mi, am, hist))
         must.update(align.align_eval_redo_poses(L).tolist())
         must.add(am)
-    assert 2 in [k for k, _ in kinds], kinds  # the cluster kernel ran
+    assert [k for k, _ in kinds][:4] == [1, 0, 0, 2], kinds
+    assert kinds[3][1] < kinds[2][1], kinds  # the cluster's table needs fewer partitions
     for mi, am, hist in runs[1:]:
         assert np.array_equal(mi, runs[0][0]) and am == runs[0][1] and np.array_equal(hist, runs[0][2])
     rng = np.random.default_rng(82)
