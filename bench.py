@@ -801,10 +801,10 @@ SWEEP_WORKLOADS = ("lidar0.5", "lidar0.25", "large")
 
 
 def run_sweeps(args):
-    """Each way of sweeping poses (align_set_sweep kinds 0-2, and the automatic choice) on
-    4,096 lattice poses of three grids: the 120k-point LiDAR pair at 0.5 m and 0.25 m
-    (z-variance) and the large pair (260k points, 0.2 m, joint feature; every 8th pose of its
-    32,768-pose lattice).  Per kind: key partitions learned, eval-kernel time per launch
+    """Each way of sweeping poses (align_set_sweep kinds 0-2, kind 0 with the spill queues
+    off, and the automatic choice) on 4,096 lattice poses of three grids: the 120k-point
+    LiDAR pair at 0.5 m and 0.25 m (z-variance) and the large pair (260k points, 0.2 m, joint
+    feature; every 8th pose of its 32,768-pose lattice).  Per kind: key partitions learned, eval-kernel time per launch
     (CUDA events, median over --steps launches after the partitions settle).  One JSON line."""
     import torch
     from paper_1709_06948_gb300 import align
@@ -813,7 +813,8 @@ def run_sweeps(args):
     bad = [w for w in names if w not in SWEEP_WORKLOADS]
     if bad:
         raise SystemExit(f"unknown workloads {bad}; choose from {SWEEP_WORKLOADS}")
-    kinds = [int(k) for k in args.sweep_kinds.split(",") if k]
+    kinds = [k for k in args.sweep_kinds.split(",") if k]  # a kind, or "0nospill": one pose per CTA
+    # sweeping B once per key partition instead of queueing the later partitions' runs
     res = []
     for name in names:
         if name == "large":
@@ -825,11 +826,13 @@ def run_sweeps(args):
         B = torch.from_numpy(pair.xyzB).cuda()
         row = {"workload": name, "points": int(pair.xyzB.shape[0]), "dims": list(spec.dims), "poses": len(etas)}
         ref_mi = None
-        for kind in kinds:
+        for kname in kinds:
+            kind = int(kname.replace("nospill", ""))
             L = align.align_create_grid(spec.origin, spec.res_m, spec.dims, spec.feature, spec.count_levels,
                                         spec.var_levels)
             align.align_set_reference(L, pair.xyzA)
             align.align_set_sweep(L, kind)
+            align.align_set_spill(L, "nospill" not in kname)
             prev = None
             for _ in range(8):  # until the kind and its partition count stay the same
                 mi, am, _ = align.align_eval_mi(L, B, eta6=etas)
@@ -848,7 +851,7 @@ def run_sweeps(args):
                 times.append(ev_ms / max(n, 1))
             align.align_profile(L, 0)
             st = align.align_eval_stats(L)
-            row[f"kind{kind}"] = {"sweep": align.SWEEP_KINDS.get(st["sweep"], st["sweep"]),
+            row[f"kind{kname}"] = {"sweep": align.SWEEP_KINDS.get(st["sweep"], st["sweep"]),
                                   "key_partitions": st["passes"],
                                   "eval_kernel_ms": round(statistics.median(times), 4),
                                   "same_mi_as_first_kind": bool(np.array_equal(mi, ref_mi))}
@@ -886,7 +889,8 @@ def main():
                          "peaks: the throughput micro-benchmarks alone; "
                          "sweeps: eval-kernel time of each way of sweeping poses on three grids")
     ap.add_argument("--sweep-workloads", default=",".join(SWEEP_WORKLOADS), help="sweeps mode: workloads")
-    ap.add_argument("--sweep-kinds", default="-1,0,1,2", help="sweeps mode: align_set_sweep kinds")
+    ap.add_argument("--sweep-kinds", default="-1,0,0nospill,1,2",
+                    help="sweeps mode: align_set_sweep kinds (0nospill: kind 0 with align_set_spill off)")
     ap.add_argument("--pairs", type=int, default=4, help="accuracy mode: pairs per initial error")
     ap.add_argument("--surface-out", default=None, help="surface mode: prefix of .npy files for the surfaces")
     ap.add_argument("--poses", type=int, default=4096)

@@ -58,8 +58,8 @@ extern "C" {
 #endif
 
 /* 2: align_batch_stats fills 9 counters (poses per CTA added), align_eval_stats 6 (sweep
-   kind added); align_batch_set_poses_per_cta, align_eval_redo_poses, align_set_sweep and
-   align_microbench added. */
+   kind added); align_batch_set_poses_per_cta, align_eval_redo_poses, align_set_sweep,
+   align_set_spill and align_microbench added. */
 #define ALIGN_API_VERSION 2
 
 typedef enum {
@@ -187,6 +187,14 @@ align_status align_eval_stats(align_grid* grid, int64_t out[6]);
    which sweeps pairs or single poses).  Results are the same for every kind; the choice
    serves measurement and tests.  Errors: ALIGN_E_INVALID for another value. */
 align_status align_set_sweep(align_grid* grid, int32_t kind);
+
+/* Whether single poses that need key partitions sweep B once (1, the default) or once per
+   partition (0).  Swept once, the first pass inserts the runs of partition 0 into the
+   shared-memory table and appends the runs of the other partitions to per-CTA queues in
+   device memory, which the later passes insert (the grid holds the queues: about
+   CTAs x 7 x n_B / 2 x 16 bytes at 8 partitions).  Results are the same either way.
+   Errors: ALIGN_E_INVALID for another value. */
+align_status align_set_spill(align_grid* grid, int32_t on);
 
 /* Poses of the last evaluation on this grid (align_eval_mi, align_accumulate or the last
    level of a search) that the exact path finished: poses whose voxels did not fit the

@@ -28,7 +28,7 @@ _STATUS_NAMES = {0: "ALIGN_OK", 1: "ALIGN_NOT_READY", -1: "ALIGN_E_INVALID", -2:
 # Every entry point include/align.h declares (checked by the tests against the .so).
 EXPORTS = ["align_create_grid", "align_destroy_grid", "align_grid_info", "align_set_reference",
            "align_get_reference", "align_round_poses", "align_eval_mi", "align_accumulate", "align_search",
-           "align_search_ex", "align_eval_stats", "align_set_sweep", "align_eval_redo_poses", "align_profile", "align_microbench", "align_reference_noalloc", "align_batch_create",
+           "align_search_ex", "align_eval_stats", "align_set_sweep", "align_set_spill", "align_eval_redo_poses", "align_profile", "align_microbench", "align_reference_noalloc", "align_batch_create",
            "align_batch_destroy", "align_eval_batch", "align_batch_set_shape", "align_batch_set_poses_per_cta",
            "align_batch_stats",
            "align_server_create", "align_server_add_reference", "align_submit", "align_poll", "align_wait",
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
         "align_search_ex": [P, P, i64, C.c_int, P, P, P, i32, P, P, P],
         "align_eval_stats": [P, P],
         "align_set_sweep": [P, i32],
+        "align_set_spill": [P, i32],
         "align_eval_redo_poses": [P, P, i64, P],
         "align_profile": [P, i32, P],
         "align_reference_noalloc": [P, P, i64, P, P, P],
@@ -378,6 +379,11 @@ def align_eval_stats(grid: Grid):
 def align_set_sweep(grid: Grid, kind: int):
     """-1 automatic (default), or a kind of SWEEP_KINDS that every launch on the grid takes."""
     _check(load().align_set_sweep(grid.handle, int(kind)))
+
+
+def align_set_spill(grid: Grid, on: bool):
+    """Sweep B once per pose (queueing the later key partitions' runs) or once per partition."""
+    _check(load().align_set_spill(grid.handle, 1 if on else 0))
 
 
 def align_eval_redo_poses(grid: Grid) -> np.ndarray:

@@ -267,6 +267,7 @@ __device__ __forceinline__ void redc_add_if(bool p, uint32_t a, uint32_t v) {
 struct EvalSmem {
   uint4* queue;       // per warp: kQueue finished runs (key, and the run's value words), a ring
   uint32_t* flags;    // occupied count, table full, overflow entries, sums need the exact path
+  uint32_t* spill_cnt;  // runs spilled to each key partition's queue (eval_kernel, 8 words)
   uint32_t* tkey;
   uint32_t* tval;     // kVW words per slot
   uint32_t* hist;     // np partial histograms of hist_stride words
@@ -275,7 +276,7 @@ struct EvalSmem {
   int32_t* item;      // the item whose constants are loaded
   uint32_t hist_stride;
   // shared-window addresses
-  uint32_t a_queue, a_key, a_vals, a_hist, a_box;
+  uint32_t a_queue, a_key, a_vals, a_hist, a_box, a_spill;
   // the cluster kernel: this CTA's rank and the .shared::cluster address of a_key in each
   // CTA of the pair (both CTAs have the same layout, so any table address maps by offset)
   uint32_t rank, c_key[2];
@@ -297,7 +298,8 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, int vw, int np,
     return o;
   };
   size_t o_queue = take((size_t)kWarps * kQueue * 16, 16);
-  size_t o_flags = take(16, 16);
+  size_t o_spill = take(32, 16);
+  size_t o_flags = take(16, 16);  // directly below the keys: addressed as a_key - kFlag*
   size_t o_key = take((size_t)T * 4, 16);
   size_t o_vals = take((size_t)T * 4 * vw, 16);
   size_t o_hist = take((size_t)np * round4(K * K) * 4, 16);
@@ -307,6 +309,7 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, int vw, int np,
   if (s) {
     s->queue = (uint4*)(base + o_queue);
     s->flags = (uint32_t*)(base + o_flags);
+    s->spill_cnt = (uint32_t*)(base + o_spill);
     s->tkey = (uint32_t*)(base + o_key);
     s->tval = (uint32_t*)(base + o_vals);
     s->hist = (uint32_t*)(base + o_hist);
@@ -321,6 +324,7 @@ __host__ __device__ inline size_t eval_smem_layout(int K, int T, int vw, int np,
     s->a_vals = a0 + (uint32_t)o_vals;
     s->a_hist = a0 + (uint32_t)o_hist;
     s->a_box = a0 + (uint32_t)o_box;
+    s->a_spill = a0 + (uint32_t)o_spill;
 #endif
   }
   return off;
@@ -565,14 +569,9 @@ __device__ __forceinline__ uint4 run_entry(const Run& r) {
 // While no n field in it reaches 2^b (2^(b+1) - 2 <= nlim), every add kept the voxel at or
 // below nlim; the sweep's end tests acc once (the exact path takes the pose otherwise).
 // kCount32: a drain of 32 entries (during the sweep); otherwise `count` (the last drain).
-template <int kVW, bool kCount32, bool kTwo, bool kCl = false>
-__device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count_arg,
-                                           const EvalArgs& a, uint32_t& acc) {
-  const uint32_t count = kCount32 ? 32u : count_arg;
-  const uint32_t lane = threadIdx.x & 31u;
-  __syncwarp();
-  uint4 e = lds128(ring + 16u * lane);  // the ring holds 64 entries: always in bounds
-  if (!kCount32 && lane >= count) e.x = kEmptyKey;
+// One entry per lane (e.x == kEmptyKey: none) into the table; all 32 lanes take part.
+template <int kVW, bool kTwo, bool kCl = false>
+__device__ __forceinline__ void insert_entry(const EvalSmem& S, const EvalArgs& a, const uint4& e, uint32_t& acc) {
   const bool valid = e.x != kEmptyKey;
   // the table holding e.x: this CTA's, or (cluster kernel) the owning CTA's half of the
   // distributed table, addressed through the cluster window
@@ -633,6 +632,41 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
     stg128_if(ov_ok, a.ovf + ((size_t)blockIdx.x * kOvfCap + (ov_ok ? i : 0u)), e);
     sts32_if(ov && !ov_ok, S.a_key - kFlagFull, 1u);
   }
+}
+
+// A pose swept once for all its key partitions (eval_kernel): an entry whose key belongs to
+// partition p >= 1 (of 2^lg) is appended to this CTA's queue of partition p in global
+// memory instead of the table; the later passes insert the queues.  Lanes of one partition
+// take consecutive queue places (one shared atomic per partition and warp).  A full queue
+// sends the pose to the exact path.
+__device__ __forceinline__ void spill_entry(const EvalSmem& S, const EvalArgs& a, uint4& e, uint32_t lg) {
+  const uint32_t part = e.x != kEmptyKey ? (e.x * 0x85EBCA77u) >> (32 - lg) : 0u;
+  const bool sp = part != 0u;
+  if (!__any_sync(kFull, sp)) return;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t grp = __match_any_sync(kFull, part);
+  const uint32_t leader = (uint32_t)__ffs(grp) - 1u;
+  uint32_t base = 0u;
+  if (sp && lane == leader) base = atom_add(S.a_spill + 4u * part, (uint32_t)__popc(grp));
+  base = __shfl_sync(kFull, base, (int)leader);
+  const uint32_t idx = base + (uint32_t)__popc(grp & lane_mask_lt());
+  const bool ok = sp && idx < (uint32_t)a.spill_cap;
+  uint4* q = a.spill + ((size_t)blockIdx.x * (size_t)(a.spill_np - 1) + (sp ? part - 1u : 0u)) * (size_t)a.spill_cap;
+  stg128_if(ok, q + (ok ? idx : 0u), e);
+  sts32_if(sp && !ok, S.a_key - kFlagFull, 1u);
+  if (sp) e.x = kEmptyKey;
+}
+
+template <int kVW, bool kCount32, bool kTwo, bool kCl = false, bool kSpill = false>
+__device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uint32_t& fill, uint32_t count_arg,
+                                           const EvalArgs& a, uint32_t& acc, uint32_t lg = 0u) {
+  const uint32_t count = kCount32 ? 32u : count_arg;
+  const uint32_t lane = threadIdx.x & 31u;
+  __syncwarp();
+  uint4 e = lds128(ring + 16u * lane);  // the ring holds 64 entries: always in bounds
+  if (!kCount32 && lane >= count) e.x = kEmptyKey;
+  if constexpr (kSpill) spill_entry(S, a, e, lg);
+  insert_entry<kVW, kTwo, kCl>(S, a, e, acc);
   // move the entries beyond `count` down (lane l reads entry l + count and writes entry l,
   // which only it has read; entry l + count < 64 for count <= 32)
   const bool mv = lane + count < fill;
@@ -644,14 +678,15 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
 }
 
 // Append the finished runs of the lanes with `done` set, then drain if 32 are waiting.
-template <int kVW, bool kTwo, bool kCl = false>
+template <int kVW, bool kTwo, bool kCl = false, bool kSpill = false>
 __device__ __forceinline__ void ring_push(const EvalSmem& S, uint32_t ring, uint32_t lane_lt, bool done,
-                                          const Run& r, uint32_t& fill, const EvalArgs& a, uint32_t& acc) {
+                                          const Run& r, uint32_t& fill, const EvalArgs& a, uint32_t& acc,
+                                          uint32_t lg = 0u) {
   const uint32_t m = __ballot_sync(kFull, done);
   sts128_if(done, ring + 16u * (fill + (uint32_t)__popc(m & lane_lt)), run_entry<kVW>(r));
   fill += (uint32_t)__popc(m);
   // fill is the same in every lane; the vote lets the compiler know the branch is uniform
-  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVW, true, kTwo, kCl>(S, ring, fill, 32u, a, acc);
+  if (__any_sync(kFull, fill >= 32u)) ring_drain<kVW, true, kTwo, kCl, kSpill>(S, ring, fill, 32u, a, acc, lg);
 }
 
 struct PoseRegs {
@@ -936,6 +971,7 @@ __device__ __forceinline__ void init_smem(const EvalSmem& S, int T, int KK, int 
       S.box[6 * a + 3] = S.box[6 * a + 4] = S.box[6 * a + 5] = INT_MIN;
     }
     S.flags[0] = S.flags[1] = S.flags[2] = S.flags[3] = 0u;
+    for (int q = 0; q < 8; ++q) S.spill_cnt[q] = 0u;
     *S.item = -1;
   }
   (void)KK;
@@ -998,7 +1034,7 @@ __device__ __forceinline__ const float4* pose_tiles(const EvalItem& I, int lp) {
 // One tile of this thread's stream: key, run step, ring append of the finished run.  No
 // per-point check of dz: the grid constants guarantee 0 <= dz <= res_mm for every point
 // inside the grid (validate_desc).
-template <int kVW, bool kRot, bool kPart, bool kTwo = false, bool kCl = false>
+template <int kVW, bool kRot, bool kPart, bool kTwo = false, bool kCl = false, bool kSpill = false>
 __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                            const PoseRegs& P, const float4* pts, int lg, uint32_t part, Run& run,
                                            uint32_t ring, uint32_t lane_lt, uint32_t& fill, uint32_t& acc) {
@@ -1009,7 +1045,8 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
     point_key<kRot>(vc, P, pts[j], key, dz);
     if (kPart && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != part) key = kEmptyKey;
     const bool done = key != run.key;
-    ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc);
+    ring_push<kVW, kTwo, kCl, kSpill>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc,
+                                      (uint32_t)lg);
     if (kVW == 2) {
       run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
     } else {
@@ -1023,13 +1060,13 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
 
 // The run step of one point whose key and dz are known: append the finished run, extend or
 // restart the run.
-template <int kVW, bool kTwo, bool kCl = false>
+template <int kVW, bool kTwo, bool kCl = false, bool kSpill = false>
 __device__ __forceinline__ void run_step(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc, uint32_t key,
                                          int dz, Run& run, uint32_t ring, uint32_t lane_lt, uint32_t& fill,
-                                         uint32_t& acc) {
+                                         uint32_t& acc, uint32_t lg = 0u) {
   const bool done = key != run.key;
   // a finished run of points outside the grid (or outside the key partition) is dropped
-  ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc);
+  ring_push<kVW, kTwo, kCl, kSpill>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc, lg);
   if (kVW == 2) {
     run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
   } else {
@@ -1043,7 +1080,8 @@ __device__ __forceinline__ void run_step(const EvalSmem& S, const EvalArgs& a, c
 // One pass over all tiles of the pose: every thread streams its own points straight from
 // L2, kDepth tiles ahead.  A run is cut every `cut` tiles so that its 32-bit sums stay
 // below nlim points.
-template <int kVW, bool kRot, bool kPart, bool kTwo = false, bool kCl = false, int kD = kDepth>
+template <int kVW, bool kRot, bool kPart, bool kTwo = false, bool kCl = false, int kD = kDepth,
+          bool kSpill = false>
 __device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                                const PoseRegs& P, const float4* src, int nt, int lg, uint32_t part,
                                                uint32_t ring, uint32_t lane_lt, int cut) {
@@ -1062,7 +1100,7 @@ __device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a,
   int t = 0;
   for (; t + 2 * kD <= nt; t += kD) {  // every prefetch in range: no guards
     if (t >= next_cut) {  // uniform; only when a stream is longer than nlim points
-      ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
+      ring_push<kVW, kTwo, kCl, kSpill>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc, (uint32_t)lg);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
@@ -1083,28 +1121,63 @@ __device__ __forceinline__ void sweep_pose(const EvalSmem& S, const EvalArgs& a,
 #pragma unroll
     for (int d = 0; d < kD; ++d)
 #pragma unroll
-      for (int j = 0; j < kPPT; ++j) run_step<kVW, kTwo, kCl>(S, a, vc, keys[d][j], dzs[d][j], run, ring, lane_lt, fill, acc);
+      for (int j = 0; j < kPPT; ++j)
+        run_step<kVW, kTwo, kCl, kSpill>(S, a, vc, keys[d][j], dzs[d][j], run, ring, lane_lt, fill, acc,
+                                         (uint32_t)lg);
     xy += kD * kTileXY;
     zz += kD * kTileZ;
   }
   for (; t < nt; t += kD) {
     if (t >= next_cut) {
-      ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
+      ring_push<kVW, kTwo, kCl, kSpill>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc, (uint32_t)lg);
       run = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
     }
 #pragma unroll
     for (int d = 0; d < kD; ++d) {
       if (t + d < nt) {
-        sweep_tile<kVW, kRot, kPart, kTwo, kCl>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, acc);
+        sweep_tile<kVW, kRot, kPart, kTwo, kCl, kSpill>(S, a, vc, P, buf[d], lg, part, run, ring, lane_lt, fill, acc);
         if (t + kD + d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
       }
     }
     xy += kD * kTileXY;
     zz += kD * kTileZ;
   }
-  ring_push<kVW, kTwo, kCl>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc);
-  while (fill > 0u) ring_drain<kVW, false, kTwo, kCl>(S, ring, fill, min(fill, 32u), a, acc);
+  ring_push<kVW, kTwo, kCl, kSpill>(S, ring, lane_lt, run.key != kEmptyKey, run, fill, a, acc, (uint32_t)lg);
+  while (fill > 0u)
+    ring_drain<kVW, false, kTwo, kCl, kSpill>(S, ring, fill, min(fill, 32u), a, acc, (uint32_t)lg);
+  if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
+}
+
+// Plain 16-byte global load (not the read-only path: the data were written in this launch).
+__device__ __forceinline__ uint4 ldg128_plain(const uint4* g) {
+  uint4 v;
+  asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(g)
+               : "memory");
+  return v;
+}
+
+// Pass `part` >= 1 of a pose swept once (eval_kernel): insert the runs that the first pass
+// spilled to this partition's queue; each warp takes 32 entries at a time, the next 32
+// loading while it inserts.
+template <int kVW>
+__device__ __forceinline__ void drain_spilled(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
+                                              uint32_t part) {
+  const uint32_t n = min(*(volatile uint32_t*)&S.spill_cnt[part], (uint32_t)a.spill_cap);
+  const uint4* q = a.spill + ((size_t)blockIdx.x * (size_t)(a.spill_np - 1) + (part - 1u)) * (size_t)a.spill_cap;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint4 none = make_uint4(kEmptyKey, 0u, 0u, 0u);
+  uint32_t acc = 0u;
+  uint32_t i = (threadIdx.x >> 5) * 32u;
+  uint4 e = i + lane < n ? ldg128_plain(q + i + lane) : none;
+  for (; i < n; i += 32u * kWarps) {  // the same trip count in every lane of a warp
+    const uint32_t j = i + 32u * kWarps;
+    const uint4 nx = j + lane < n ? ldg128_plain(q + j + lane) : none;
+    insert_entry<kVW, false>(S, a, e, acc);
+    e = nx;
+  }
   if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
 }
 
@@ -1213,7 +1286,10 @@ __device__ __forceinline__ void sweep_pair(const EvalSmem& S, const EvalArgs& a,
   if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
 }
 
-template <int kVW, bool kRot, bool kOne>
+// kSp (one item, a.spill set): every pose in 2 .. a.spill_np key partitions with B swept once
+// (the first pass queues the runs of the later partitions, which the later passes insert); a
+// pose whose table overflows at a.spill_np partitions goes to the exact path.
+template <int kVW, bool kRot, bool kOne, bool kSp = false>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid_constant__ EvalArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
@@ -1239,6 +1315,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
         atomicMax(item_at<kOne>(a, cur).item_passes, (uint32_t)passes);
       cur = it;
       if (I.passes0 > 0) passes = I.passes0;
+      if (kSp) passes = min(max(passes, 2), a.spill_np);
     }
     const int lp = gp - I.pose_base;
     const VoxelConst vc = voxel_const<kVW>(kOne ? a.one.gc : *S.gc);
@@ -1255,8 +1332,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
     bool overflowed = false;  // ... because its keys did not fit: more partitions help
     for (int pass = 0; pass < pose_passes; ++pass) {
       if (!full) {
-        if (lg == 0) sweep_pose<kVW, kRot, false>(S, a, vc, P, src, nt, 0, 0u, ring, lane_lt, cut);
-        else sweep_pose<kVW, kRot, true>(S, a, vc, P, src, nt, lg, (uint32_t)pass, ring, lane_lt, cut);
+        if constexpr (kSp) {
+          // B swept once: the first pass inserts the runs of partition 0 and queues the
+          // others; each later pass inserts its queue
+          if (pass == 0)
+            sweep_pose<kVW, kRot, false, false, false, kDepth, true>(S, a, vc, P, src, nt, lg, 0u, ring, lane_lt,
+                                                                     cut);
+          else drain_spilled<kVW>(S, a, vc, (uint32_t)pass);
+        } else if (lg == 0) {
+          sweep_pose<kVW, kRot, false>(S, a, vc, P, src, nt, 0, 0u, ring, lane_lt, cut);
+        } else {
+          sweep_pose<kVW, kRot, true>(S, a, vc, P, src, nt, lg, (uint32_t)pass, ring, lane_lt, cut);
+        }
       }
       __syncthreads();
       if (!full && *(volatile uint32_t*)&S.flags[2] != 0u) {  // runs whose home bucket was full
@@ -1274,7 +1361,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
         S.flags[0] = 0u;
         S.flags[2] = 0u;
         S.flags[3] = 0u;
+        if (kSp && pass == pose_passes - 1)
+          for (int q = 0; q < 8; ++q) S.spill_cnt[q] = 0u;
       }
+      __syncthreads();  // the resets before the next pass's drains count again
     }
     if (full) {
       // finished later by the exact path
@@ -1283,12 +1373,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
         S.flags[1] = 0u;
         a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)gp;
       }
-      if (overflowed && passes < kMaxPasses) passes *= 2;
+      if (overflowed && passes < (kSp ? a.spill_np : kMaxPasses)) passes *= 2;
       __syncthreads();
       continue;
     }
     emit_pose(S, I, lp);
-    if (max_occupied > cap && passes < kMaxPasses) passes *= 2;  // crowded: more partitions next
+    if (max_occupied > cap && passes < (kSp ? a.spill_np : kMaxPasses)) passes *= 2;  // crowded: more next
   }
   if (tid == 0) {
     atomicMax(a.max_passes, (uint32_t)passes);
@@ -1790,6 +1880,8 @@ template <int kVW, bool kRot>
 cudaError_t setup_t(int smem) {
   cudaError_t e = cudaFuncSetAttribute(eval_kernel<kVW, kRot, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(eval_kernel<kVW, kRot, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(eval_kernel<kVW, kRot, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(redo_kernel<kVW, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1806,7 +1898,9 @@ cudaError_t launch_eval_t(const EvalArgs& a, int n_ctas, size_t smem, cudaStream
     if (a.item_start != nullptr || n_ctas < 2 || (n_ctas & 1)) return cudaErrorInvalidValue;
     eval_cluster_kernel<kVW, kRot><<<n_ctas, kThreads, smem, s>>>(a);
   } else {
-    auto* k = a.item_start == nullptr ? eval_kernel<kVW, kRot, true> : eval_kernel<kVW, kRot, false>;
+    auto* k = a.item_start != nullptr ? eval_kernel<kVW, kRot, false>
+              : a.spill != nullptr      ? eval_kernel<kVW, kRot, true, true>
+                                        : eval_kernel<kVW, kRot, true>;
     k<<<n_ctas, kThreads, smem, s>>>(a);
   }
   cudaError_t e = cudaGetLastError();

@@ -525,6 +525,17 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   CU(g->ovf.ensure((size_t)n_ctas * ek.ovf_cap() * 16), "allocate overflow lists");
   a.ovf = g->ovf.as<uint4>();
   a.ovf_cap = ek.ovf_cap();
+  // single poses that need key partitions: B swept once, the later partitions' runs queued
+  // (room for one doubling of the seed, at most 8 partitions; half a run per padded point
+  // and queue: a queue that fills sends its pose to the exact path)
+  if (g->spill_on && !pairs && !cluster && out.dump == nullptr && item.passes0 >= 2 && item.passes0 <= 8) {
+    const int32_t np = std::min(8, 2 * item.passes0);
+    const int64_t cap = (n_pad / 2 + 31) / 32 * 32;
+    CU(g->spill.ensure((size_t)n_ctas * (size_t)(np - 1) * (size_t)cap * 16), "allocate spill queues");
+    a.spill = g->spill.as<uint4>();
+    a.spill_cap = cap;
+    a.spill_np = np;
+  }
   std::array<cudaEvent_t, 3> evs{};
   if (g->profiling) {
     if (g->ev_pool.empty()) {
@@ -1304,6 +1315,13 @@ align_status align_set_sweep(align_grid* g, int32_t kind) {
   if (!g) return fail(ALIGN_E_INVALID, "NULL grid");
   if (kind < -1 || kind > 2) return fail(ALIGN_E_INVALID, "sweep kind must be -1, 0, 1 or 2");
   g->sweep_mode = kind;
+  return ALIGN_OK;
+}
+
+align_status align_set_spill(align_grid* g, int32_t on) {
+  if (!g) return fail(ALIGN_E_INVALID, "NULL grid");
+  if (on != 0 && on != 1) return fail(ALIGN_E_INVALID, "spill must be 0 or 1");
+  g->spill_on = on;
   return ALIGN_OK;
 }
 

@@ -118,6 +118,8 @@ struct align_grid {
   bool last_pairs = false;    // the last eval launch evaluated pose pairs
   bool last_cluster = false;  // ... or ran one pose per 2-CTA cluster
   mialign::DevBuf units;    // pose pairs of the last pair launch with host poses
+  mialign::DevBuf spill;    // runs queued for the later key partitions (EvalArgs::spill)
+  int32_t spill_on = 1;     // align_set_spill
   mialign::DevBuf lat_units;           // pose pairs of a device-built lattice level (by index)
   std::vector<int32_t> lattice_units;  // ... on the host
   int32_t lattice_units_m[6] = {0, 0, 0, 0, 0, 0};

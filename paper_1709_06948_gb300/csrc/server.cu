@@ -153,6 +153,7 @@ void workspace_bind(align_grid* ws, const align_grid* ref) {
   }
   ws->passes_seed_cluster = ref->passes_seed_cluster;
   ws->sweep_mode = ref->sweep_mode;
+  ws->spill_on = ref->spill_on;
 }
 
 // Key partitions learned by a workspace go back to its reference (for the next request).

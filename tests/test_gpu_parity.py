@@ -210,8 +210,9 @@ def test_pose_pairs_match_single_pose_kernel(res, feature):
 
 def test_every_sweep_kind_agrees_on_a_fine_grid():
     """The 120k-point LiDAR pair on a 0.25 m grid (320x320x32, z-variance), 4,096 lattice
-    poses swept each way the library has (one pose per CTA, pose pairs, one pose per 2-CTA
-    cluster with its table split between two shared memories, and the automatic choice),
+    poses swept each way the library has (one pose per CTA, with its key partitions' runs
+    queued after one sweep of B or with one sweep per partition; pose pairs; one pose per
+    2-CTA cluster with its table split between two shared memories; the automatic choice),
     each on a fresh grid: MI, argmax and every histogram are identical across the kinds, and
     a sample holding the argmax and every exact-path pose matches the oracle."""
     from paper_1709_06948_gb300 import align
@@ -219,25 +220,25 @@ def test_every_sweep_kind_agrees_on_a_fine_grid():
     spec = scangen.lidar_grid(0.25)
     etas = scangen.lidar_poses()
     P = len(etas)
-    runs, must = {}, set()
-    for kind in (0, 1, 2, -1):
+    runs, must = [], set()
+    for kind, spill in ((0, True), (0, False), (1, True), (2, True), (-1, True)):
         L = lib_grid(spec)
         align.align_set_reference(L, pair.xyzA)
         align.align_set_sweep(L, kind)
+        align.align_set_spill(L, spill)
         for _ in range(2):  # the second launch starts from the partitions the first learned
             mi, am, hist = align.align_eval_mi(L, pair.xyzB, eta6=etas, with_hist=True)
             st = align.align_eval_stats(L)
             if kind >= 0:
                 assert st["sweep"] == kind, (kind, st)
             must.update(align.align_eval_redo_poses(L).tolist())
-            runs.setdefault(kind, []).append((mi, am, hist))
+            runs.append((kind, spill, mi, am, hist))
         assert am == lowest_argmax(mi)
         must.add(am)
         L.close()
-    mi0, am0, h0 = runs[0][0]
-    for kind, rs in runs.items():
-        for mi, am, hist in rs:
-            assert np.array_equal(mi, mi0) and am == am0 and np.array_equal(hist, h0), kind
+    _, _, mi0, am0, h0 = runs[0]
+    for kind, spill, mi, am, hist in runs:
+        assert np.array_equal(mi, mi0) and am == am0 and np.array_equal(hist, h0), (kind, spill)
     rng = np.random.default_rng(83)
     must = np.array(sorted(must), dtype=np.int64)
     rest = np.setdiff1d(np.arange(P), must)
