@@ -54,12 +54,15 @@ struct PairPlan {
   int64_t pose_off = 0;       // poses (global pose index of pose 0)
   int64_t pts_off = 0;        // float4
   int64_t outc_off = 0;       // uint32
+  int32_t passes0 = 1;        // the grid's key-partition seed for this launch's kind
+  int32_t spill_np = 0;       // single poses with 2-8 partitions: EvalArgs::spill_np (0: no queues)
+  int64_t spill_cap = 0;      // ... and the runs per queue
 };
 
 // Workspace sizes of one launch; a change of any of them re-allocates and drops the graph.
 struct Sizes {
   size_t xyz = 0, poses = 0, pts = 0, pose_src = 0, copies = 0, items = 0, starts = 0, outc = 0, box = 0,
-         best = 0, mi = 0, argmax = 0, redo = 0, wide = 0, ipasses = 0, ovf = 0, units = 0;
+         best = 0, mi = 0, argmax = 0, redo = 0, wide = 0, ipasses = 0, ovf = 0, units = 0, spill = 0;
 };
 
 std::string env_cache_path() {
@@ -121,7 +124,7 @@ struct align_batch {
   std::string device_name;
   int shape_fixed = -1;
   DevBuf xyz, poses, pts, pose_src, copies, items, starts, outc, box, best, mi, argmax, redo_list, redo_count, wide,
-      status, ipasses, ovf, units;
+      status, ipasses, ovf, units, spill;
   // page-locked staging of the poses and their tile copies (asynchronous copies; a call's
   // copies are done when it returns, since every call synchronises its stream)
   mialign::HostBuf h_poses, h_src;
@@ -302,7 +305,7 @@ align_status align_batch_destroy(align_batch* b) {
   drop_graph(b);
   for (DevBuf* d : {&b->xyz, &b->poses, &b->pts, &b->pose_src, &b->copies, &b->items, &b->starts, &b->outc, &b->box,
                     &b->best, &b->mi, &b->argmax, &b->redo_list, &b->redo_count, &b->wide, &b->status, &b->ipasses, &b->ovf,
-                    &b->units})
+                    &b->units, &b->spill})
     d->release();
   b->h_poses.release();
   b->h_src.release();
@@ -371,6 +374,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     if (groups <= 0 || prerot_bytes > kPrerotBudget) rotate = true;
   }
   int64_t units_n = 0;
+  int64_t spill_words = 0;  // largest (queues x runs per queue) of a pair with spill queues
   for (PairPlan& pp : plans) {
     pp.prerot = !rotate;
     pp.n_copies = rotate ? 1 : (int)(pp.rots.size() / 9);
@@ -389,6 +393,17 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
       const int nu = pair_units(pp.hposes.data(), pp.idx.data(), pp.P, pp.units);
       if (nu < pp.P) pp.n_units = nu;
       else pp.units.clear();
+    }
+    // the seed of the kind this pair runs; single poses with key partitions sweep B once and
+    // queue the later partitions' runs (as the single-pair path does)
+    pp.passes0 = __atomic_load_n(pp.n_units > 0 ? &pp.g->passes_seed_pair[shape] : &pp.g->passes_seed[shape],
+                                 __ATOMIC_RELAXED);
+    pp.spill_np = 0;
+    pp.spill_cap = 0;
+    if (pp.n_units == 0 && pp.g->spill_on && pp.passes0 >= 2 && pp.passes0 <= 8) {
+      pp.spill_np = std::min(8, 2 * pp.passes0);
+      pp.spill_cap = (pp.n_pad / 2 + 31) / 32 * 32;
+      spill_words = std::max(spill_words, (int64_t)(pp.spill_np - 1) * pp.spill_cap);
     }
     pp.unit_off = units_n;
     units_n += pp.n_units;
@@ -435,6 +450,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   GROW(wide, wide, (size_t)n_ctas * 2 * T * 8, "allocate wide sums", true);
   GROW(ovf, ovf, (size_t)n_ctas * ek.ovf_cap() * 16, "allocate overflow lists", false);
   GROW(units, units, (size_t)std::max<int64_t>(1, units_n) * 8, "allocate pose pairs", false);
+  GROW(spill, spill, (size_t)n_ctas * (size_t)std::max<int64_t>(1, spill_words) * 16, "allocate spill queues", false);
 #undef GROW
   if (!b->status.p || !b->redo_count.p) {
     drop_graph(b);
@@ -504,8 +520,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     it.best = b->best.as<unsigned long long>() + i;
     it.argmax = b->argmax.as<int64_t>() + i;
     it.dump = nullptr;
-    it.passes0 = __atomic_load_n(pp.n_units > 0 ? &g->passes_seed_pair[shape] : &g->passes_seed[shape],
-                                 __ATOMIC_RELAXED);
+    it.passes0 = pp.passes0;
     if (pp.n_units > 0)  // a pageable source: staged before the copy call returns
       BCU(cudaMemcpyAsync(b->units.as<int32_t>() + 2 * pp.unit_off, pp.units.data(), pp.units.size() * 4,
                           cudaMemcpyHostToDevice, s),
@@ -566,6 +581,11 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     ai.n_buckets = Ts[(size_t)i] / 4;
     ai.units = plans[(size_t)i].n_units > 0 ? b->units.as<int32_t>() + 2 * plans[(size_t)i].unit_off : nullptr;
     ai.n_units = plans[(size_t)i].n_units;
+    if (plans[(size_t)i].spill_np > 0) {
+      ai.spill = b->spill.as<uint4>();
+      ai.spill_cap = plans[(size_t)i].spill_cap;
+      ai.spill_np = plans[(size_t)i].spill_np;
+    }
     L.evals.push_back(ai);
   }
   b->last_grids.clear();
@@ -582,8 +602,10 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   std::vector<int64_t> sig = {shape,   n,       rotate,     a.passes0, T, n_ctas,
                               poses_n, n_copies, max_out,   maxK,      (int64_t)(uintptr_t)b->pts.p,
                               (int64_t)(uintptr_t)b->items.p, (int64_t)h};
-  for (size_t i = 0; i < vws.size(); ++i) sig.insert(sig.end(), {vws[i], Ts[i], plans[i].n_units});
+  for (size_t i = 0; i < vws.size(); ++i)
+    sig.insert(sig.end(), {vws[i], Ts[i], plans[i].n_units, plans[i].spill_np, plans[i].spill_cap});
   sig.push_back((int64_t)(uintptr_t)b->units.p);
+  sig.push_back((int64_t)(uintptr_t)b->spill.p);
   st = run_launch(b, L, (flags & ALIGN_BATCH_GRAPH) != 0, sig);
   if (st != ALIGN_OK) return st;
   b->stats[3] = shape;

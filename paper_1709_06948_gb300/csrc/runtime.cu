@@ -528,8 +528,9 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   // single poses that need key partitions: B swept once, the later partitions' runs queued
   // (room for one doubling of the seed, at most 8 partitions; half a run per padded point
   // and queue: a queue that fills sends its pose to the exact path)
-  if (g->spill_on && !pairs && !cluster && out.dump == nullptr && item.passes0 >= 2 && item.passes0 <= 8) {
-    const int32_t np = std::min(8, 2 * item.passes0);
+  if (g->spill_on && !pairs && !cluster && out.dump == nullptr && item.passes0 >= 2 &&
+      item.passes0 <= g->spill_np_max) {
+    const int32_t np = std::min(g->spill_np_max, 2 * item.passes0);
     const int64_t cap = (n_pad / 2 + 31) / 32 * 32;
     CU(g->spill.ensure((size_t)n_ctas * (size_t)(np - 1) * (size_t)cap * 16), "allocate spill queues");
     a.spill = g->spill.as<uint4>();

@@ -49,6 +49,7 @@ struct Req {
   int32_t counts[6];
   int32_t levels = 0;
   size_t bytes = 0;        // device memory estimate of its workspace
+  int32_t spill_np = 0;    // key partitions its spill queues serve (0: none; counted in bytes)
   double T[6] = {0, 0, 0, 0, 0, 0};
   float best_mi = 0.0f;
   int32_t status = ALIGN_OK;
@@ -113,14 +114,16 @@ namespace {
 // Device bytes of a workspace running a request of nB points with lattice counts m on a grid
 // whose single-pose table has T slots: the staged points, the pre-rotated tile copies, the
 // per-pose buffers of one level, and the per-CTA 64-bit side sums and overflow lists.
-size_t request_bytes(int64_t nB, const int32_t m[6], int K, int T, int n_sm) {
+size_t request_bytes(int64_t nB, const int32_t m[6], int K, int T, int n_sm, int spill_np) {
   const int64_t P = lattice_size(m);
   const int64_t n_pad = std::max<int64_t>(3, (nB + 1023) / 1024) * 1024;
   int64_t n_rot = (int64_t)m[3] * m[4] * m[5];
   if (n_rot > std::max<int64_t>(1, P / 4)) n_rot = 1;
   const int64_t per_pose = (int64_t)K * K * 4 + 24 + 4 + 48 + 4 + 4 + 4;
   const int64_t per_cta = 2 * (int64_t)T * 8 + (int64_t)eval_shape(0).ovf_cap() * 16;
-  return (size_t)(nB * 12 + n_rot * n_pad * 16 + P * per_pose + (int64_t)n_sm * per_cta);
+  // spill queues: spill_np - 1 of n_pad / 2 runs per CTA
+  const int64_t spill = spill_np > 1 ? (int64_t)(spill_np - 1) * ((n_pad / 2 + 31) / 32 * 32) * 16 : 0;
+  return (size_t)(nB * 12 + n_rot * n_pad * 16 + P * per_pose + (int64_t)n_sm * (per_cta + spill));
 }
 
 // A workspace: a grid object that owns only evaluation buffers; the reference arrays it
@@ -237,7 +240,11 @@ void worker_main(align_server* s, size_t k) {
       if (!me.ws) me.ws = workspace_create(s->device, s->n_sm, s->refs[0].grid->smem_optin, me.stream);
       ws = me.ws;
       ref = s->refs[(size_t)r->ref].grid;
-      if (ws) workspace_bind(ws, ref);
+      if (ws) {
+        workspace_bind(ws, ref);
+        ws->spill_on = r->spill_np > 0 ? 1 : 0;  // within the request's memory estimate
+        ws->spill_np_max = std::max(2, r->spill_np);
+      }
     }
     int32_t st = ALIGN_OK;
     float mi = 0.0f;
@@ -370,7 +377,11 @@ align_status align_submit(align_server* s, const align_request* req, uint64_t* t
   if (req->ref_id < 0 || req->ref_id >= (int32_t)s->refs.size()) return report_error(ALIGN_E_INVALID, "unknown ref_id");
   r->ref = req->ref_id;
   const align_grid* g = s->refs[(size_t)r->ref].grid;
-  r->bytes = request_bytes(r->nB, r->counts, g->gc.K, g->table_slots, s->n_sm);
+  // a grid whose single poses already needed key partitions gets spill queues for up to twice
+  // as many (a request on a grid that has not needed them sweeps B once per partition)
+  const int32_t seed = g->passes_seed[0];
+  r->spill_np = g->spill_on && seed >= 2 && seed <= 8 ? std::min(8, 2 * seed) : 0;
+  r->bytes = request_bytes(r->nB, r->counts, g->gc.K, g->table_slots, s->n_sm, r->spill_np);
   if (s->ref_bytes + r->bytes > s->budget) return report_error(ALIGN_E_OOM, "request can never fit the memory budget");
   r->ticket = s->next_ticket++;
   r->t_submit = s->now();
