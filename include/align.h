@@ -342,7 +342,9 @@ typedef struct align_result {
 
 /* hbm_budget_bytes: device memory the server may hold for the references and the slots'
    workspaces (a workspace keeps the buffers of the largest request it has run; estimated
-   per request from its sizes, its grid and the device); max_slots (1..256): most requests
+   per request from its sizes, its grid and the device, including the spill queues of
+   align_set_spill when the request's grid has already needed key partitions; a request
+   on a grid that has not sweeps B once per partition); max_slots (1..256): most requests
    active at once.  When the request at the head of the queue fits the budget only without
    them and no request runs, idle slots release their workspaces. */
 align_status align_server_create(size_t hbm_budget_bytes, int32_t max_slots, align_server** out);
