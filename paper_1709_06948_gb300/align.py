@@ -94,7 +94,7 @@ def load(build_if_missing: bool = True):
         "align_search_ex": [P, P, i64, C.c_int, P, P, P, i32, P, P, P],
         "align_eval_stats": [P, P],
         "align_set_sweep": [P, i32],
-        "align_set_spill": [P, i32],
+        "align_set_spill": [P, i32, i64],
         "align_eval_redo_poses": [P, P, i64, P],
         "align_profile": [P, i32, P],
         "align_reference_noalloc": [P, P, i64, P, P, P],
@@ -381,9 +381,10 @@ def align_set_sweep(grid: Grid, kind: int):
     _check(load().align_set_sweep(grid.handle, int(kind)))
 
 
-def align_set_spill(grid: Grid, on: bool):
-    """Sweep B once per pose (queueing the later key partitions' runs) or once per partition."""
-    _check(load().align_set_spill(grid.handle, 1 if on else 0))
+def align_set_spill(grid: Grid, on: bool, queue_runs: int = 0):
+    """Sweep B once per pose (queueing the later key partitions' runs) or once per partition;
+    queue_runs: runs per queue and CTA (0: half the points of B)."""
+    _check(load().align_set_spill(grid.handle, 1 if on else 0, int(queue_runs)))
 
 
 def align_eval_redo_poses(grid: Grid) -> np.ndarray:

@@ -531,7 +531,7 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   if (g->spill_on && !pairs && !cluster && out.dump == nullptr && item.passes0 >= 2 &&
       item.passes0 <= g->spill_np_max) {
     const int32_t np = std::min(g->spill_np_max, 2 * item.passes0);
-    const int64_t cap = (n_pad / 2 + 31) / 32 * 32;
+    const int64_t cap = ((g->spill_runs > 0 ? g->spill_runs : n_pad / 2) + 31) / 32 * 32;
     CU(g->spill.ensure((size_t)n_ctas * (size_t)(np - 1) * (size_t)cap * 16), "allocate spill queues");
     a.spill = g->spill.as<uint4>();
     a.spill_cap = cap;
@@ -1319,10 +1319,12 @@ align_status align_set_sweep(align_grid* g, int32_t kind) {
   return ALIGN_OK;
 }
 
-align_status align_set_spill(align_grid* g, int32_t on) {
+align_status align_set_spill(align_grid* g, int32_t on, int64_t queue_runs) {
   if (!g) return fail(ALIGN_E_INVALID, "NULL grid");
   if (on != 0 && on != 1) return fail(ALIGN_E_INVALID, "spill must be 0 or 1");
+  if (queue_runs < 0 || queue_runs > (int64_t)1 << 31) return fail(ALIGN_E_INVALID, "queue_runs out of range");
   g->spill_on = on;
+  g->spill_runs = queue_runs;
   return ALIGN_OK;
 }
 

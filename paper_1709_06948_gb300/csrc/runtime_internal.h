@@ -120,6 +120,7 @@ struct align_grid {
   mialign::DevBuf units;    // pose pairs of the last pair launch with host poses
   mialign::DevBuf spill;    // runs queued for the later key partitions (EvalArgs::spill)
   int32_t spill_on = 1;     // align_set_spill
+  int64_t spill_runs = 0;   // runs per queue and CTA (0: half the padded points of B)
   int32_t spill_np_max = 8; // most key partitions the spill queues serve (a server's workspace: its request's)
   mialign::DevBuf lat_units;           // pose pairs of a device-built lattice level (by index)
   std::vector<int32_t> lattice_units;  // ... on the host

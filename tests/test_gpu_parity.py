@@ -211,8 +211,9 @@ def test_pose_pairs_match_single_pose_kernel(res, feature):
 def test_every_sweep_kind_agrees_on_a_fine_grid():
     """The 120k-point LiDAR pair on a 0.25 m grid (320x320x32, z-variance), 4,096 lattice
     poses swept each way the library has (one pose per CTA, with its key partitions' runs
-    queued after one sweep of B or with one sweep per partition; pose pairs; one pose per
-    2-CTA cluster with its table split between two shared memories; the automatic choice),
+    queued after one sweep of B, with queues of 64 runs that overflow and send the poses to
+    the exact path, or with one sweep per partition; pose pairs; one pose per 2-CTA cluster
+    with its table split between two shared memories; the automatic choice),
     each on a fresh grid: MI, argmax and every histogram are identical across the kinds, and
     a sample holding the argmax and every exact-path pose matches the oracle."""
     from paper_1709_06948_gb300 import align
@@ -221,17 +222,22 @@ def test_every_sweep_kind_agrees_on_a_fine_grid():
     etas = scangen.lidar_poses()
     P = len(etas)
     runs, must = [], set()
-    for kind, spill in ((0, True), (0, False), (1, True), (2, True), (-1, True)):
+    for kind, spill, queue_runs in ((0, True, 0), (0, True, 64), (0, False, 0), (1, True, 0), (2, True, 0),
+                                    (-1, True, 0)):
         L = lib_grid(spec)
         align.align_set_reference(L, pair.xyzA)
         align.align_set_sweep(L, kind)
-        align.align_set_spill(L, spill)
-        for _ in range(2):  # the second launch starts from the partitions the first learned
+        align.align_set_spill(L, spill, queue_runs)
+        for i in range(2):  # the second launch starts from the partitions the first learned
             mi, am, hist = align.align_eval_mi(L, pair.xyzB, eta6=etas, with_hist=True)
             st = align.align_eval_stats(L)
             if kind >= 0:
                 assert st["sweep"] == kind, (kind, st)
-            must.update(align.align_eval_redo_poses(L).tolist())
+            redo = align.align_eval_redo_poses(L)
+            if queue_runs and i == 1:  # the queues overflowed: the exact path took the poses
+                assert len(redo) > P // 2, len(redo)
+            else:
+                must.update(redo.tolist())
             runs.append((kind, spill, mi, am, hist))
         assert am == lowest_argmax(mi)
         must.add(am)
