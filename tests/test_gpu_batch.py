@@ -122,6 +122,39 @@ def test_pose_pairs_in_a_batch():
         check_argmax(am2, mo, mi2)
 
 
+def test_key_partitions_in_a_batch():
+    """Pairs on a 0.25 m grid whose single poses need key partitions: after the grid has
+    learned them, the batch sweeps B once per pose and queues the later partitions' runs
+    (spill queues, as align_eval_mi does); with the queues switched off on the grid it sweeps
+    B once per partition.  Both batches, align_eval_mi alone and the oracle on a sample
+    agree (MI and argmax bit-identical between the library's paths)."""
+    from paper_1709_06948_gb300 import align
+    pair = scangen.lidar_pair()
+    spec = scangen.lidar_grid(0.25)
+    etas = scangen.lidar_poses()[::8]
+    c = Case(pair.xyzA, pair.xyzB, spec, etas)
+    small = Case(pair.xyzA, scangen.subsample(pair.xyzB, 20000, np.random.default_rng(84)), spec, etas[::4])
+    for _ in range(2):  # the grid learns its partitions (and that pose pairs need more)
+        align.align_eval_mi(c.L, c.xyzB, eta6=c.etas)
+    assert align.align_eval_stats(c.L)["passes"] >= 2
+    b = align.align_batch_create()
+    align.align_batch_set_shape(b, 0)  # the shape whose partitions the grid learned
+    align.align_batch_set_poses_per_cta(b, 1)
+    res_q = align.align_eval_batch(b, _pairs([c, small]))
+    align.align_set_spill(c.L, False)
+    res_p = align.align_eval_batch(b, _pairs([c, small]))
+    align.align_set_spill(c.L, True)
+    for cc, (mi_q, am_q), (mi_p, am_p) in zip((c, small), res_q, res_p):
+        assert np.array_equal(mi_q, mi_p) and am_q == am_p
+        mi0, am0, _ = align.align_eval_mi(cc.L, cc.xyzB, eta6=cc.etas)
+        assert np.array_equal(mi_q, mi0) and am_q == am0
+    G = oracle_grid(spec)
+    symA, boxA = G.reference(c.xyzA)
+    sample = np.unique(np.concatenate([[res_q[0][1]], np.arange(0, len(etas), 16)]))
+    mo, _, _ = G.eval_mi(symA, boxA, c.xyzB, G.round_pose(etas[sample]), nthreads=NT)
+    assert np.max(np.abs(res_q[0][0][sample].astype(np.float64) - mo)) <= mi_tolerance()
+
+
 def test_graph_replay(cases):
     """Same shape, new poses: the graph is captured once and replayed; results equal the
     non-graph launch."""
