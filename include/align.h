@@ -189,11 +189,11 @@ align_status align_eval_stats(align_grid* grid, int64_t out[6]);
 align_status align_set_sweep(align_grid* grid, int32_t kind);
 
 /* Whether single poses that need key partitions sweep B once (on = 1, the default) or once
-   per partition (0).  Swept once, the first pass inserts the runs of partition 0 into the
-   shared-memory table and appends the runs of the other partitions to per-CTA queues in
-   device memory, which the later passes insert.  queue_runs: runs each queue holds (16 bytes
-   each, rounded up to a multiple of 32); 0 (the default) sizes them for half the points of
-   B, so that the grid holds about CTAs x 7 x n_B / 2 x 16 bytes at 8 partitions.  A pose
+   per partition (0).  Swept once, the sweep appends every run of B's points to a per-CTA
+   queue of its key partition in device memory, and each pass inserts one queue into the
+   shared-memory table.  queue_runs: runs each queue holds (16 bytes each, rounded up to a
+   multiple of 32); 0 (the default) sizes them for half the points of B, so that the grid
+   holds about CTAs x 8 x n_B / 2 x 16 bytes at 8 partitions.  A pose
    whose runs overflow a queue is finished by the exact path.  Results are the same either
    way.  Errors: ALIGN_E_INVALID for another on, or queue_runs outside 0 .. 2^31. */
 align_status align_set_spill(align_grid* grid, int32_t on, int64_t queue_runs);

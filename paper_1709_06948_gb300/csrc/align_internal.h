@@ -96,9 +96,9 @@ struct EvalArgs {
   // One item, one pose per 2-CTA cluster sharing a table split between the pair's shared
   // memories (eval_cluster_kernel; an even number of CTAs).
   int32_t cluster;
-  // eval_kernel, poses with 2 .. spill_np key partitions: B is swept once and the runs of
-  // partitions 1 .. np-1 are queued here (per CTA: spill_np - 1 queues of spill_cap runs),
-  // each later pass inserting one queue.  nullptr: every pass sweeps B.
+  // eval_kernel, poses with 2 .. spill_np key partitions: B is swept once and its runs are
+  // queued here by key partition (per CTA: spill_np queues of spill_cap runs), each pass
+  // inserting one queue.  nullptr: every pass sweeps B.
   uint4* spill;
   int64_t spill_cap;
   int32_t spill_np;

@@ -403,7 +403,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     if (pp.n_units == 0 && pp.g->spill_on && pp.passes0 >= 2 && pp.passes0 <= 8) {
       pp.spill_np = std::min(8, 2 * pp.passes0);
       pp.spill_cap = ((pp.g->spill_runs > 0 ? pp.g->spill_runs : pp.n_pad / 2) + 31) / 32 * 32;
-      spill_words = std::max(spill_words, (int64_t)(pp.spill_np - 1) * pp.spill_cap);
+      spill_words = std::max(spill_words, (int64_t)pp.spill_np * pp.spill_cap);
     }
     pp.unit_off = units_n;
     units_n += pp.n_units;

@@ -634,27 +634,80 @@ __device__ __forceinline__ void insert_entry(const EvalSmem& S, const EvalArgs& 
   }
 }
 
-// A pose swept once for all its key partitions (eval_kernel): an entry whose key belongs to
-// partition p >= 1 (of 2^lg) is appended to this CTA's queue of partition p in global
-// memory instead of the table; the later passes insert the queues.  Lanes of one partition
-// take consecutive queue places (one shared atomic per partition and warp).  A full queue
-// sends the pose to the exact path.
-__device__ __forceinline__ void spill_entry(const EvalSmem& S, const EvalArgs& a, uint4& e, uint32_t lg) {
-  const uint32_t part = e.x != kEmptyKey ? (e.x * 0x85EBCA77u) >> (32 - lg) : 0u;
-  const bool sp = part != 0u;
-  if (!__any_sync(kFull, sp)) return;
+// Two entries per lane into this CTA's single-bucket table, the steps of the two inserts
+// interleaved so that their shared-memory round trips overlap (insert_entry's steps, twice).
+// Two entries of one lane compete for a slot like entries of two lanes: the same new key
+// aimed at one free slot is placed by the first CAS and found by the second; a different
+// key loses the slot and goes to the overflow list.
+template <int kVW>
+__device__ __forceinline__ void insert_entry2(const EvalSmem& S, const EvalArgs& a, const uint4& e0, const uint4& e1,
+                                              uint32_t& acc) {
+  const bool v0 = e0.x != kEmptyKey, v1 = e1.x != kEmptyKey;
+  const uint32_t nb = (uint32_t)a.n_buckets;
+  const uint32_t b0 = __umulhi(e0.x * 0x9E3779B1u, nb), b1 = __umulhi(e1.x * 0x9E3779B1u, nb);
+  const uint4 k0 = lds128(S.a_key + 16u * b0);
+  const uint4 k1 = lds128(S.a_key + 16u * b1);
+  const int h0 = bucket_hit(k0, e0.x), h1 = bucket_hit(k1, e1.x);
+  const uint32_t f0 = bucket_fill(k0), f1 = bucket_fill(k1);
+  int slot0 = h0 >= 0 ? (int)(4 * b0) + h0 : -1;
+  int slot1 = h1 >= 0 ? (int)(4 * b1) + h1 : -1;
+  const uint32_t s0 = 4 * b0 + f0, s1 = 4 * b1 + f1;
+  const bool ins0 = v0 && slot0 < 0 && f0 < 4u, ins1 = v1 && slot1 < 0 && f1 < 4u;
+  const uint32_t o0 = atom_cas_if(ins0, S.a_key + 4u * s0, kEmptyKey, e0.x);
+  const uint32_t o1 = atom_cas_if(ins1, S.a_key + 4u * s1, kEmptyKey, e1.x);
+  if (ins0 && (o0 == kEmptyKey || o0 == e0.x)) slot0 = (int)s0;
+  if (ins1 && (o1 == kEmptyKey || o1 == e1.x)) slot1 = (int)s1;
+  const bool ok0 = v0 && slot0 >= 0, ok1 = v1 && slot1 >= 0;
+  const uint32_t w0 = S.a_vals + 4u * kVW * (uint32_t)slot0, w1 = S.a_vals + 4u * kVW * (uint32_t)slot1;
+  if (kVW == 2) {
+    const uint32_t old0 = atom_add_if(ok0, w0, e0.y);
+    const uint32_t old1 = atom_add_if(ok1, w1, e1.y);
+    red_add_if(ok0, w0 + 4u, e0.z);
+    red_add_if(ok1, w1 + 4u, e1.z);
+    acc |= (ok0 ? (old0 | e0.y) : 0u) | (ok1 ? (old1 | e1.y) : 0u);
+  } else {
+    red_add_if(ok0, w0, e0.y);
+    red_add_if(ok1, w1, e1.y);
+    if (kVW == 3) {
+      red_add_if(ok0, w0 + 4u, e0.z);
+      red_add_if(ok1, w1 + 4u, e1.z);
+      red_add_if(ok0, w0 + 8u, e0.w);
+      red_add_if(ok1, w1 + 8u, e1.w);
+    }
+  }
+  const bool ov0 = v0 && slot0 < 0, ov1 = v1 && slot1 < 0;
+  if (__any_sync(kFull, ov0 || ov1)) {
+    uint4* ovf = a.ovf + (size_t)blockIdx.x * kOvfCap;
+    const uint32_t i0 = atom_add_if(ov0, S.a_key - kFlagOvf, 1u);
+    const uint32_t i1 = atom_add_if(ov1, S.a_key - kFlagOvf, 1u);
+    const bool ok_i0 = ov0 && i0 < (uint32_t)kOvfCap, ok_i1 = ov1 && i1 < (uint32_t)kOvfCap;
+    stg128_if(ok_i0, ovf + (ok_i0 ? i0 : 0u), e0);
+    stg128_if(ok_i1, ovf + (ok_i1 ? i1 : 0u), e1);
+    sts32_if((ov0 && !ok_i0) || (ov1 && !ok_i1), S.a_key - kFlagFull, 1u);
+  }
+}
+
+// A pose swept once for all its key partitions (eval_kernel<..., kSp>): every entry is
+// appended to this CTA's queue of its key partition p (of 2^lg) in global memory, and each
+// pass then inserts one queue into the table, 32 entries per warp at a time (inserting
+// partition 0's entries during the sweep would run the insert for every lane of a drain
+// with only a 2^-lg share of them valid).  Lanes of one partition take consecutive queue
+// places (one shared atomic per partition and warp).  A full queue sends the pose to the
+// exact path.
+__device__ __forceinline__ void spill_entry(const EvalSmem& S, const EvalArgs& a, const uint4& e, uint32_t lg) {
+  const bool sp = e.x != kEmptyKey;
+  const uint32_t part = sp ? (e.x * 0x85EBCA77u) >> (32 - lg) : 0u;
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t grp = __match_any_sync(kFull, part);
+  const uint32_t grp = __match_any_sync(kFull, sp ? part : 0xFFFFFFFFu);
   const uint32_t leader = (uint32_t)__ffs(grp) - 1u;
   uint32_t base = 0u;
   if (sp && lane == leader) base = atom_add(S.a_spill + 4u * part, (uint32_t)__popc(grp));
   base = __shfl_sync(kFull, base, (int)leader);
   const uint32_t idx = base + (uint32_t)__popc(grp & lane_mask_lt());
   const bool ok = sp && idx < (uint32_t)a.spill_cap;
-  uint4* q = a.spill + ((size_t)blockIdx.x * (size_t)(a.spill_np - 1) + (sp ? part - 1u : 0u)) * (size_t)a.spill_cap;
+  uint4* q = a.spill + ((size_t)blockIdx.x * (size_t)a.spill_np + part) * (size_t)a.spill_cap;
   stg128_if(ok, q + (ok ? idx : 0u), e);
   sts32_if(sp && !ok, S.a_key - kFlagFull, 1u);
-  if (sp) e.x = kEmptyKey;
 }
 
 template <int kVW, bool kCount32, bool kTwo, bool kCl = false, bool kSpill = false>
@@ -666,7 +719,7 @@ __device__ __forceinline__ void ring_drain(const EvalSmem& S, uint32_t ring, uin
   uint4 e = lds128(ring + 16u * lane);  // the ring holds 64 entries: always in bounds
   if (!kCount32 && lane >= count) e.x = kEmptyKey;
   if constexpr (kSpill) spill_entry(S, a, e, lg);
-  insert_entry<kVW, kTwo, kCl>(S, a, e, acc);
+  else insert_entry<kVW, kTwo, kCl>(S, a, e, acc);
   // move the entries beyond `count` down (lane l reads entry l + count and writes entry l,
   // which only it has read; entry l + count < 64 for count <= 32)
   const bool mv = lane + count < fill;
@@ -1159,24 +1212,29 @@ __device__ __forceinline__ uint4 ldg128_plain(const uint4* g) {
   return v;
 }
 
-// Pass `part` >= 1 of a pose swept once (eval_kernel): insert the runs that the first pass
-// spilled to this partition's queue; each warp takes 32 entries at a time, the next 32
-// loading while it inserts.
+// Pass `part` of a pose swept once (eval_kernel<..., kSp>): insert the runs that the sweep
+// queued for this partition.
 template <int kVW>
 __device__ __forceinline__ void drain_spilled(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                               uint32_t part) {
   const uint32_t n = min(*(volatile uint32_t*)&S.spill_cnt[part], (uint32_t)a.spill_cap);
-  const uint4* q = a.spill + ((size_t)blockIdx.x * (size_t)(a.spill_np - 1) + (part - 1u)) * (size_t)a.spill_cap;
+  const uint4* q = a.spill + ((size_t)blockIdx.x * (size_t)a.spill_np + part) * (size_t)a.spill_cap;
   const uint32_t lane = threadIdx.x & 31u;
   const uint4 none = make_uint4(kEmptyKey, 0u, 0u, 0u);
   uint32_t acc = 0u;
+  // each warp takes two batches of 32 at a time (the two inserts interleaved), the next two
+  // loading meanwhile
+  constexpr uint32_t kStep = 32u * kWarps;
   uint32_t i = (threadIdx.x >> 5) * 32u;
-  uint4 e = i + lane < n ? ldg128_plain(q + i + lane) : none;
-  for (; i < n; i += 32u * kWarps) {  // the same trip count in every lane of a warp
-    const uint32_t j = i + 32u * kWarps;
-    const uint4 nx = j + lane < n ? ldg128_plain(q + j + lane) : none;
-    insert_entry<kVW, false>(S, a, e, acc);
-    e = nx;
+  uint4 e0 = i + lane < n ? ldg128_plain(q + i + lane) : none;
+  uint4 e1 = i + kStep + lane < n ? ldg128_plain(q + i + kStep + lane) : none;
+  for (; i < n; i += 2u * kStep) {  // the same trip count in every lane of a warp
+    const uint32_t j = i + 2u * kStep;
+    const uint4 n0 = j + lane < n ? ldg128_plain(q + j + lane) : none;
+    const uint4 n1 = j + kStep + lane < n ? ldg128_plain(q + j + kStep + lane) : none;
+    insert_entry2<kVW>(S, a, e0, e1, acc);
+    e0 = n0;
+    e1 = n1;
   }
   if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
 }
@@ -1333,12 +1391,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
     for (int pass = 0; pass < pose_passes; ++pass) {
       if (!full) {
         if constexpr (kSp) {
-          // B swept once: the first pass inserts the runs of partition 0 and queues the
-          // others; each later pass inserts its queue
-          if (pass == 0)
+          // B swept once in the first pass, every run queued by key partition; each pass
+          // inserts its partition's queue
+          if (pass == 0) {
             sweep_pose<kVW, kRot, false, false, false, kDepth, true>(S, a, vc, P, src, nt, lg, 0u, ring, lane_lt,
                                                                      cut);
-          else drain_spilled<kVW>(S, a, vc, (uint32_t)pass);
+            __syncthreads();  // every queue complete (full is the same in every thread)
+          }
+          drain_spilled<kVW>(S, a, vc, (uint32_t)pass);
         } else if (lg == 0) {
           sweep_pose<kVW, kRot, false>(S, a, vc, P, src, nt, 0, 0u, ring, lane_lt, cut);
         } else {

@@ -525,14 +525,14 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   CU(g->ovf.ensure((size_t)n_ctas * ek.ovf_cap() * 16), "allocate overflow lists");
   a.ovf = g->ovf.as<uint4>();
   a.ovf_cap = ek.ovf_cap();
-  // single poses that need key partitions: B swept once, the later partitions' runs queued
-  // (room for one doubling of the seed, at most 8 partitions; half a run per padded point
-  // and queue: a queue that fills sends its pose to the exact path)
+  // single poses that need key partitions: B swept once, its runs queued by partition (room
+  // for one doubling of the seed, at most 8 partitions; half a run per padded point and
+  // queue: a queue that fills sends its pose to the exact path)
   if (g->spill_on && !pairs && !cluster && out.dump == nullptr && item.passes0 >= 2 &&
       item.passes0 <= g->spill_np_max) {
     const int32_t np = std::min(g->spill_np_max, 2 * item.passes0);
     const int64_t cap = ((g->spill_runs > 0 ? g->spill_runs : n_pad / 2) + 31) / 32 * 32;
-    CU(g->spill.ensure((size_t)n_ctas * (size_t)(np - 1) * (size_t)cap * 16), "allocate spill queues");
+    CU(g->spill.ensure((size_t)n_ctas * (size_t)np * (size_t)cap * 16), "allocate spill queues");
     a.spill = g->spill.as<uint4>();
     a.spill_cap = cap;
     a.spill_np = np;
