@@ -95,3 +95,45 @@ def test_large_every_sweep_kind_agrees(large):
     mo, ho, _ = G.eval_mi(symA, boxA, large.xyzB, poses[sample], nthreads=NT, with_hist=True)
     assert np.array_equal(runs[0][2][sample], ho)
     assert np.max(np.abs(runs[0][0][sample].astype(np.float64) - mo)) <= mi_tolerance()
+
+
+@pytest.mark.parametrize("layout", ["count", "three_words"])
+def test_spill_queues_every_table_layout(large, layout):
+    """Key partitions with B swept once and its runs queued per partition, for the table
+    layouts the LiDAR and large-grid tests do not partition: the count feature (one value
+    word) on the 0.2 m large grid, and the z-variance feature on a 0.6 m grid, whose packed
+    word would hold too few points per voxel (three value words), with B subsampled to 60k
+    points.  After the grid has learned its partitions, MI, argmax and histograms equal those
+    of one sweep of B per partition, no pose needs the exact path, and a sample matches the
+    oracle."""
+    from paper_1709_06948_gb300 import align
+    if layout == "count":
+        spec = scangen.GridSpec(origin=large.grid.origin, res_m=0.2, dims=(400, 400, 40), feature=0,
+                                count_levels=7, var_levels=1)
+        B = large.xyzB
+    else:
+        spec = scangen.GridSpec(origin=(-120.0, -120.0, -5.0), res_m=0.6, dims=(400, 400, 33), feature=1,
+                                count_levels=1, var_levels=15)
+        B = scangen.subsample(large.xyzB, 60000, np.random.default_rng(85))
+    etas = scangen.large_poses()[::64]
+    res = []
+    for spill in (True, False):
+        L = lib_grid(spec)
+        align.align_set_reference(L, large.xyzA)
+        align.align_set_sweep(L, 0)
+        align.align_set_spill(L, spill)
+        align.align_eval_mi(L, B, eta6=etas)  # learns the partitions
+        res.append(align.align_eval_mi(L, B, eta6=etas, with_hist=True))
+        assert align.align_eval_stats(L)["passes"] >= 2
+        assert len(align.align_eval_redo_poses(L)) == 0
+        L.close()
+    (mi, am, hist), (mi_p, am_p, hist_p) = res
+    assert np.array_equal(mi, mi_p) and am == am_p and np.array_equal(hist, hist_p)
+    assert am == lowest_argmax(mi)
+    sample = np.unique(np.concatenate([[am], np.arange(0, len(etas), 16)]))
+    G = oracle_grid(spec)
+    symA, boxA = G.reference(large.xyzA)
+    poses = align.align_round_poses(spec.origin, etas[sample])
+    mo, ho, _ = G.eval_mi(symA, boxA, B, poses, nthreads=NT, with_hist=True)
+    assert np.array_equal(hist[sample], ho)
+    assert np.max(np.abs(mi[sample].astype(np.float64) - mo)) <= mi_tolerance()
