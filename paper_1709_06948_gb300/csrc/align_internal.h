@@ -32,6 +32,8 @@ struct GridConst {
   int32_t dz_shift;       // smallest m with 2^m > 2 * dz_bound (the sweep checks dz + dz_bound < 2^m)
   uint32_t nlim;          // largest n whose S1, S2 fit the 32-bit table sums for |dz| < 2^m - dz_bound
   uint32_t nlim_pack;     // largest n of the packed word n * 2^ns + sum(dz + dz_bound) (and of S2)
+  uint32_t nlim3c;        // three-word layout: largest n whose sums of dz - res_mm / 2 and of its
+                          // square fit 32 bits (below 2^16 when sym32)
   int32_t ns_shift;       // ns, the shift of n in the packed word
   int32_t wide_shift;     // ns + b, b the largest with 2^(b+1) - 2 <= nlim_pack: two n fields
                           // below 2^b sum to at most nlim_pack
@@ -83,6 +85,8 @@ struct EvalArgs {
   uint32_t* err;              // error bits
   uint32_t* max_passes;       // running max of key-partition passes (seed for the next launch)
   uint32_t* wide_count;       // voxels that needed the 64-bit side sums
+  uint32_t* wide_poses;       // passes of packed-layout poses sent to the exact path by a wide
+                              // voxel (nullptr: not counted)
   unsigned long long* wide;   // per CTA: table_slots x 2 (S1 as two's complement, S2)
   uint32_t* redo_list;        // P: poses whose table overflowed, finished by the redo kernel
   uint32_t* redo_count;       // entries in redo_list (zeroed before every launch)

@@ -131,6 +131,7 @@ struct align_batch {
   bool staged = false;  // copies out of the staging buffers may still be queued
   std::vector<align_grid*> last_grids;  // grids of the last launch (per-item partition feedback)
   std::vector<char> last_pairs;         // whether each item of the last launch used pose pairs
+  std::vector<int> last_vws;            // each item's table layout in the last launch
   int last_shape = 0;
   int pairs_fixed = -1;                 // poses per CTA set by the caller (1, 2), -1: default
   Sizes cap;
@@ -227,9 +228,9 @@ align_status run_launch(align_batch* b, const Launch& L, bool use_graph, const s
 
 // Read the kernels' status words (synchronises the stream).
 align_status collect(align_batch* b) {
-  uint32_t v[3] = {0, 0, 0};
+  uint32_t v[4] = {0, 0, 0, 0};
   std::vector<uint32_t> ip(b->last_grids.size(), 0);
-  BCU(cudaMemcpyAsync(v, b->status.p, 12, cudaMemcpyDeviceToHost, b->stream), "read status");
+  BCU(cudaMemcpyAsync(v, b->status.p, 16, cudaMemcpyDeviceToHost, b->stream), "read status");
   if (!ip.empty())
     BCU(cudaMemcpyAsync(ip.data(), b->ipasses.p, ip.size() * 4, cudaMemcpyDeviceToHost, b->stream),
         "read partition counts");
@@ -246,10 +247,15 @@ align_status collect(align_batch* b) {
            !__atomic_compare_exchange_n(seed, &cur, (int32_t)ip[i], false, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
     }
   }
+  // packed-layout poses sent to the exact path by a wide voxel: the grids of the launch that
+  // used the packed layout take the three-word layout from now on (one counter for the launch)
+  if (v[3] > 0)
+    for (size_t i = 0; i < b->last_grids.size() && i < b->last_vws.size(); ++i)
+      if (b->last_vws[i] == 2) __atomic_store_n(&b->last_grids[i]->layout_min, 3, __ATOMIC_RELAXED);
   float ms = 0.0f;
   if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->stats[6] = (int64_t)std::llround(ms * 1000.0);
-  // reset the error word, the partition maximum and the wide-voxel count (per launch)
-  BCU(cudaMemsetAsync(b->status.p, 0, 12, b->stream), "reset status");
+  // reset the error word, the partition maximum and the wide counters (per launch)
+  BCU(cudaMemsetAsync(b->status.p, 0, 16, b->stream), "reset status");
   if (v[0] & kErrDzBound) return report_error(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");
   if (v[0] & kErrPassLimit) return report_error(ALIGN_E_INTERNAL, "key partitioning limit reached");
   return ALIGN_OK;
@@ -424,7 +430,9 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   std::vector<int> vws, Ts;
   int T = 0;  // the largest table of the launches (sizes the 64-bit side sums)
   for (const PairPlan& pp : plans) {
-    vws.push_back(eval_layout(pp.g->gc, var));
+    int vw = eval_layout(pp.g->gc, var);  // at least the layout the grid has learned to need
+    if (var) vw = std::max(vw, (int)__atomic_load_n(&pp.g->layout_min, __ATOMIC_RELAXED));
+    vws.push_back(vw);
     Ts.push_back(ek.table_slots_for(pp.g->gc.K, vws.back(), b->smem_optin, pp.n_units > 0 ? 2 : 1));
     T = std::max(T, Ts.back());
   }
@@ -563,6 +571,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   a.err = status;
   a.max_passes = status + 1;
   a.wide_count = status + 2;
+  a.wide_poses = status + 3;
   a.wide = b->wide.as<unsigned long long>();
   a.redo_list = b->redo_list.as<uint32_t>();
   a.redo_count = b->redo_count.as<uint32_t>();
@@ -590,6 +599,7 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
   }
   b->last_grids.clear();
   b->last_pairs.clear();
+  b->last_vws = vws;
   for (const PairPlan& pp : plans) {
     b->last_grids.push_back(pp.g);
     b->last_pairs.push_back(pp.n_units > 0 ? 1 : 0);

@@ -337,13 +337,15 @@ struct VoxelConst {
   uint32_t nlim;        // largest n per voxel of the layout's table sums
   uint32_t winc;        // layout 2, per point: 2^ns + dz_bound (plus dz)
   uint32_t wide_shift;  // layout 2: ns + b with 2^(b+1) - 2 <= nlim_pack (the drains' bound)
+  int zc;               // layout 3 sums dz - zc (zc = res_mm / 2; 0 in the other layouts)
 };
 
 template <int kVW>
 __device__ __forceinline__ VoxelConst voxel_const(const GridConst& g) {
-  const uint32_t nlim = kVW == 2 ? g.nlim_pack : kVW == 3 ? g.nlim : 0x7FFFFFFFu;
+  const uint32_t nlim = kVW == 2 ? g.nlim_pack : kVW == 3 ? g.nlim3c : 0x7FFFFFFFu;
   return VoxelConst{g.inv_res, g.X, g.Y, g.Z, g.res_mm, g.dz_bound, nlim,
-                    (1u << g.ns_shift) + (uint32_t)g.dz_bound, (uint32_t)g.wide_shift};
+                    (1u << g.ns_shift) + (uint32_t)g.dz_bound, (uint32_t)g.wide_shift,
+                    kVW == 3 ? g.res_mm / 2 : 0};
 }
 
 // The table: buckets of 4 key slots (one 16-byte load each).  With kTwo (the pair kernel,
@@ -931,10 +933,10 @@ __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& g
     n = w >> gc.ns_shift;
     s1 = (int64_t)(w & ((1u << gc.ns_shift) - 1u)) - (int64_t)n * gc.dz_bound;
     s2 = lds32(v + 4u);
-  } else if (kVW == 3) {
+  } else if (kVW == 3) {  // sums of dz - res_mm / 2 (the feature symbols are shift-invariant)
     s1 = (int32_t)lds32(v + 4u);
     s2 = lds32(v + 8u);
-    if (n > gc.nlim) sts32(S.a_key - kFlagWide, 1u);  // the sums may have wrapped: exact path
+    if (n > gc.nlim3c) sts32(S.a_key - kFlagWide, 1u);  // the sums may have wrapped: exact path
   }
   sts32(S.a_key + 4u * s, kEmptyKey);
 #pragma unroll
@@ -955,6 +957,11 @@ __device__ __forceinline__ void scan_entry(const EvalSmem& S, const GridConst& g
       kz <= gc.boxA[5])
     red_add(S.a_hist + 4u * (pa * S.hist_stride + (uint32_t)(sA * gc.K + sB)), 1u);
   if (I.dump != nullptr && lp == 0 && pa == 0u) {
+    if (kVW == 3 && !kExact) {  // back to sums of dz: S1 + n c and S2 + 2 c S1 + n c^2
+      const int64_t c = gc.res_mm / 2;
+      s2 = (uint64_t)((int64_t)s2 + 2 * c * s1 + (int64_t)n * c * c);
+      s1 += (int64_t)n * c;
+    }
     I.dump[3 * (size_t)k] = (int64_t)n;
     I.dump[3 * (size_t)k + 1] = s1;
     I.dump[3 * (size_t)k + 2] = (int64_t)s2;
@@ -1030,6 +1037,15 @@ __device__ __forceinline__ void init_smem(const EvalSmem& S, int T, int KK, int 
   (void)KK;
 }
 
+// After a pass's table scan (flags final): in the packed layout a set wide flag means that a
+// voxel may have passed nlim_pack, which sends the pose to the exact path; such passes are
+// counted for the host, which then gives the grid the three-word layout (a larger limit).
+template <int kVW>
+__device__ __forceinline__ void note_wide(const EvalSmem& S, const EvalArgs& a) {
+  if (kVW == 2 && threadIdx.x == 0 && a.wide_poses != nullptr && *(volatile uint32_t*)&S.flags[3] != 0u)
+    atomicAdd(a.wide_poses, 1u);
+}
+
 // Store the partial histogram and bbox of pose `a` of the sweep as pose lp of item I, then
 // reset them for the next sweep.  Called by all threads.
 __device__ __forceinline__ void emit_pose(const EvalSmem& S, const EvalItem& I, int lp, int a = 0) {
@@ -1100,13 +1116,14 @@ __device__ __forceinline__ void sweep_tile(const EvalSmem& S, const EvalArgs& a,
     const bool done = key != run.key;
     ring_push<kVW, kTwo, kCl, kSpill>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc,
                                       (uint32_t)lg);
+    const int dzr = kVW == 3 ? dz - vc.zc : dz;  // layout 3 sums offsets from the voxel's middle
     if (kVW == 2) {
       run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
     } else {
       run.w = (done ? 0u : run.w) + 1u;
-      if (kVW == 3) run.s1 = (done ? 0u : run.s1) + (uint32_t)dz;
+      if (kVW == 3) run.s1 = (done ? 0u : run.s1) + (uint32_t)dzr;
     }
-    if (kVW > 1) run.s2 = (done ? 0u : run.s2) + (uint32_t)(dz * dz);
+    if (kVW > 1) run.s2 = (done ? 0u : run.s2) + (uint32_t)(dzr * dzr);
     run.key = key;
   }
 }
@@ -1120,13 +1137,14 @@ __device__ __forceinline__ void run_step(const EvalSmem& S, const EvalArgs& a, c
   const bool done = key != run.key;
   // a finished run of points outside the grid (or outside the key partition) is dropped
   ring_push<kVW, kTwo, kCl, kSpill>(S, ring, lane_lt, done && run.key != kEmptyKey, run, fill, a, acc, lg);
+  const int dzr = kVW == 3 ? dz - vc.zc : dz;  // layout 3 sums offsets from the voxel's middle
   if (kVW == 2) {
     run.w = (done ? 0u : run.w) + ((uint32_t)dz + vc.winc);
   } else {
     run.w = (done ? 0u : run.w) + 1u;
-    if (kVW == 3) run.s1 = (done ? 0u : run.s1) + (uint32_t)dz;
+    if (kVW == 3) run.s1 = (done ? 0u : run.s1) + (uint32_t)dzr;
   }
-  if (kVW > 1) run.s2 = (done ? 0u : run.s2) + (uint32_t)(dz * dz);
+  if (kVW > 1) run.s2 = (done ? 0u : run.s2) + (uint32_t)(dzr * dzr);
   run.key = key;
 }
 
@@ -1415,6 +1433,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
       scan_table<kVW, false, 1>(S, kOne ? a.one.gc : *S.gc, I, wide, a.wide_count, T, lp, full);
       __syncthreads();
       max_occupied = max(max_occupied, S.flags[0]);
+      note_wide<kVW>(S, a);
       full = full || S.flags[3] != 0u;  // a voxel beyond the table sums: wide sums, not partitions
       __syncthreads();
       if (tid == 0) {
@@ -1482,6 +1501,7 @@ __device__ __forceinline__ void pair_sweep_set(const EvalSmem& S, const EvalArgs
     scan_table<kVW, false, kNP>(S, I.gc, I, wide, a.wide_count, T, lp0, full);
     __syncthreads();
     max_occupied = max(max_occupied, S.flags[0]);
+    note_wide<kVW>(S, a);
     full = full || S.flags[3] != 0u;  // a voxel beyond the table sums: wide sums, not partitions
     __syncthreads();
     if (tid == 0) {
@@ -1620,6 +1640,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       __syncthreads();
       cluster_sync();  // both scans are done: the occupied counts and wide flags are final
       max_occupied = max(max_occupied, max(S.flags[0], ldc32(c_peer - kFlagOccupied)));
+      note_wide<kVW>(S, a);
       full = full || S.flags[3] != 0u || ldc32(c_peer - kFlagWide) != 0u;
       cluster_sync();  // both have read the other's flags before they are reset
       if (tid == 0) {
@@ -1690,7 +1711,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
     select_item(S, a, it);
     const EvalItem& I = a.items[it];
     const int lp = gp - I.pose_base;
-    const VoxelConst vc = voxel_const<3>(*S.gc);  // runs with 32-bit sums, cut at nlim
+    const VoxelConst vc = voxel_const<3>(*S.gc);
+    const uint32_t run_lim = S.gc->nlim;  // runs with 32-bit sums of dz and dz^2, cut at nlim
     PoseRegs P;
     load_pose(I.poses + 12 * (size_t)lp, P);
     const float4* src = pose_tiles(I, lp) + tid;
@@ -1714,7 +1736,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) redo_kernel(const __grid
           if (lg > 0 && key != kEmptyKey && ((key * 0x85EBCA77u) >> (32 - lg)) != (uint32_t)pass) key = kEmptyKey;
           // dz is meaningful inside the grid only (the bound holds there; a cheap assertion)
           bad |= (uint32_t)(key != kEmptyKey && (uint32_t)(dz + vc.dz_bound) > (uint32_t)(2 * vc.dz_bound));
-          if (key != rkey || (kVar && rn >= vc.nlim)) {
+          if (key != rkey || (kVar && rn >= run_lim)) {
             if (rkey != kEmptyKey && rn != 0u) add_run<kVW>(S, wide, rkey, rn, (int)rs1, rs2, nb);
             rkey = key;
             rn = rs1 = rs2 = 0u;

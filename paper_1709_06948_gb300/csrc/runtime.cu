@@ -226,12 +226,20 @@ align_status validate_desc(const align_grid_desc* d, GridConst* gc) {
   gc->ns_shift = best_ns;
   gc->nlim = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull / (D * D), 0x7FFFFFFFull / D);
   gc->nlim_pack = (uint32_t)std::min<uint64_t>(best, gc->nlim);
+  // The three-word table layout sums dz - c with c = res_mm / 2: shifting every dz of a voxel
+  // by c leaves n * S2 - S1^2 (all the feature symbols read) unchanged, and |dz - c| is at
+  // most res_mm - c for in-grid points (0 <= dz <= res_mm, above), a quarter of the squares
+  // (plus the same margin as dz_bound).
+  const uint64_t Dc = (uint64_t)(res_mm - res_mm / 2 + 4 + (int64_t)std::ceil(drift));
+  gc->nlim3c = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull / (Dc * Dc), 0x7FFFFFFFull / Dc);
   int b = 0;
   while (b < 30 && (2ull << (b + 1)) - 2ull <= (uint64_t)gc->nlim_pack) ++b;
   gc->wide_shift = std::min(31, best_ns + b);
   gc->sym32 = gc->nlim < 65536u ? 1 : 0;
   for (int j = 0; j + 1 < Lv; ++j)
     if (gc->var_thresh[j] >= (int64_t(1) << 32)) gc->sym32 = 0;
+  // the 32-bit symbol test needs n < 2^16 (nlim3c >= nlim either way: |dz - c| <= |dz|)
+  if (gc->sym32) gc->nlim3c = std::min(gc->nlim3c, 65535u);
   for (int i = 0; i < 3; ++i) gc->boxA[i] = INT_MAX, gc->boxA[3 + i] = INT_MIN;
   // division of 32-bit keys by X and Y as a 64-bit multiply-high (Lemire, Kaser and Kurz,
   // "Faster remainder by direct computation", 2019: exact for every 32-bit dividend)
@@ -454,7 +462,8 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   const int n_ctas = cluster ? 2 * (int)std::min<int64_t>(P, g->n_sm / 2)
                              : (int)std::min<int64_t>(pairs ? n_units : P, g->n_sm);
   const bool var = g->gc.feature != ALIGN_FEAT_COUNT || out.dump != nullptr;
-  const int vw = eval_layout(g->gc, var);
+  const int vw = var ? std::max(eval_layout(g->gc, var), g->layout_min) : eval_layout(g->gc, var);
+  g->last_vw = vw;
   g->table_slots = eval_shape(0).table_slots_for(K, vw, g->smem_optin, pairs ? 2 : 1);
   g->last_pairs = pairs;
   g->last_cluster = cluster;
@@ -519,6 +528,7 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   a.err = g->err.as<uint32_t>();
   a.max_passes = g->max_passes.as<uint32_t>();
   a.wide_count = g->wide_count.as<uint32_t>();
+  a.wide_poses = g->wide_count.as<uint32_t>() + 1;  // the counter buffer's second word
   a.wide = g->wide.as<unsigned long long>();
   a.redo_list = g->redo_list.as<uint32_t>();
   a.redo_count = g->redo_count.as<uint32_t>();
@@ -588,21 +598,24 @@ void learn_passes(align_grid* g, uint32_t used) {
 
 // Read back the kernels' error word and counters (synchronises the stream).
 align_status collect_status(align_grid* g) {
-  uint32_t vals[3] = {0, 0, 0};
+  uint32_t vals[4] = {0, 0, 0, 0};
   CU(cudaMemcpyAsync(&vals[0], g->err.p, 4, cudaMemcpyDeviceToHost, g->stream), "read error word");
   CU(cudaMemcpyAsync(&vals[1], g->max_passes.p, 4, cudaMemcpyDeviceToHost, g->stream), "read counters");
-  CU(cudaMemcpyAsync(&vals[2], g->wide_count.p, 4, cudaMemcpyDeviceToHost, g->stream), "read counters");
+  CU(cudaMemcpyAsync(&vals[2], g->wide_count.p, 8, cudaMemcpyDeviceToHost, g->stream), "read counters");
   CU(cudaStreamSynchronize(g->stream), "synchronize");
   {
     align_status stp = drain_events(g);
     if (stp != ALIGN_OK) return stp;
   }
   CU(cudaMemsetAsync(g->err.p, 0, 4, g->stream), "reset error word");
-  CU(cudaMemsetAsync(g->wide_count.p, 0, 4, g->stream), "reset counters");
+  CU(cudaMemsetAsync(g->wide_count.p, 0, 8, g->stream), "reset counters");
   CU(cudaMemsetAsync(g->max_passes.p, 0, 4, g->stream), "reset counters");  // a per-launch maximum
   // seed the next launch of the same kind (pairs or single poses) with the largest
   // partition count a pose needed (a power of two)
   learn_passes(g, vals[1]);
+  // packed-layout poses that a voxel past nlim_pack sent to the exact path: the grid's scans
+  // are dense enough for the three-word layout (a limit several times larger, fewer slots)
+  if (vals[3] > 0 && g->last_vw == 2) g->layout_min = 3;
   g->stats[0] = vals[1];
   g->stats[1] = vals[2];
   if (vals[0] & kErrDzBound) return fail(ALIGN_E_INTERNAL, "a z offset exceeded its proven bound");

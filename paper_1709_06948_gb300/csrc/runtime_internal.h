@@ -120,6 +120,9 @@ struct align_grid {
   mialign::DevBuf units;    // pose pairs of the last pair launch with host poses
   mialign::DevBuf spill;    // runs queued for the later key partitions (EvalArgs::spill)
   int32_t spill_on = 1;     // align_set_spill
+  int32_t layout_min = 1;   // smallest table layout (value words) of this grid's z-sum launches:
+                            // 3 once packed-layout poses went to the exact path for a wide voxel
+  int32_t last_vw = 0;      // the layout of the last eval launch
   int64_t spill_runs = 0;   // runs per queue and CTA (0: half the padded points of B)
   int32_t spill_np_max = 8; // most key partitions the spill queues serve (a server's workspace: its request's)
   mialign::DevBuf lat_units;           // pose pairs of a device-built lattice level (by index)

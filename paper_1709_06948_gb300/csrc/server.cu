@@ -156,6 +156,7 @@ void workspace_bind(align_grid* ws, const align_grid* ref) {
   }
   ws->passes_seed_cluster = ref->passes_seed_cluster;
   ws->sweep_mode = ref->sweep_mode;
+  ws->layout_min = ref->layout_min;
   ws->spill_on = ref->spill_on;
 }
 
@@ -166,6 +167,7 @@ void workspace_learn(const align_grid* ws, align_grid* ref) {
     ref->passes_seed_pair[i] = std::max(ref->passes_seed_pair[i], ws->passes_seed_pair[i]);
   }
   ref->passes_seed_cluster = std::max(ref->passes_seed_cluster, ws->passes_seed_cluster);
+  ref->layout_min = std::max(ref->layout_min, ws->layout_min);
 }
 
 void workspace_destroy(align_grid* ws) {

@@ -189,21 +189,27 @@ def test_non_finite_pose_rejected(tiny):
 
 
 def test_exact_path_does_not_escalate_partitions():
-    """Poses finished on the exact path (wide sums) many times over: the partition count the
-    next launches start with must stay where the data put it (no growth per launch)."""
+    """Poses finished on the exact path (wide sums) many times over: a voxel of 70,000 points,
+    past the per-voxel limit of the packed layout (which the first launch uses) and of the
+    three-word layout (which the grid takes after it).  The layout changes once; the
+    partition count the next launches start with stays where the data put it (no growth per
+    launch), and the results never change."""
     from paper_1709_06948_gb300 import align
     rng = np.random.default_rng(38)
     spec = scangen.lidar_grid(0.5)
-    dense = np.stack([rng.uniform(1.01, 1.49, 25000), rng.uniform(2.01, 2.49, 25000), rng.uniform(0.01, 0.49, 25000)], 1)
+    n = 70000
+    dense = np.stack([rng.uniform(1.01, 1.49, n), rng.uniform(2.01, 2.49, n), rng.uniform(0.01, 0.49, n)], 1)
     xyz = dense.astype(np.float32)
     L = lib_grid(spec)
     align.align_set_reference(L, xyz)
     etas = np.zeros((3, 6))
     first, _, _ = align.align_eval_mi(L, xyz, eta6=etas)
+    slots_packed = align.align_eval_stats(L)["table_slots"]
     for _ in range(20):
         mi, _, _ = align.align_eval_mi(L, xyz, eta6=etas)
         assert np.array_equal(mi, first)
     st = align.align_eval_stats(L)
+    assert st["table_slots"] < slots_packed  # the three-word layout (fewer, larger slots)
     assert st["wide_voxels"] >= 1 and st["passes"] <= 2
 
 

@@ -137,3 +137,38 @@ def test_spill_queues_every_table_layout(large, layout):
     mo, ho, _ = G.eval_mi(symA, boxA, B, poses, nthreads=NT, with_hist=True)
     assert np.array_equal(hist[sample], ho)
     assert np.max(np.abs(mi[sample].astype(np.float64) - mo)) <= mi_tolerance()
+
+
+@pytest.mark.parametrize("res", [1.0, 0.5])
+def test_dense_scan_keeps_the_fast_path(large, res):
+    """The 128-beam large scan on coarse z-variance grids (240 m square): voxels near the
+    sensor hold thousands of points, past the packed layout's per-voxel limit at 0.5 m and
+    past the uncentred three-word limit at 1 m.  The three-word layout sums z offsets from the
+    voxel's middle (a quarter of the squares), and a grid whose packed-layout poses went to the
+    exact path takes that layout from its next launch on (where its first poses may still
+    overflow the smaller table until the partitions are learned): by the third launch no more
+    than 2% of the poses need the exact path, every launch gives the same results, and a
+    sample matches the oracle."""
+    from paper_1709_06948_gb300 import align
+    n = int(round(240 / res))
+    spec = scangen.GridSpec(origin=(-120.0, -120.0, -5.0), res_m=res, dims=(n, n, int(round(20 / res))), feature=1,
+                            count_levels=1, var_levels=15)
+    L = lib_grid(spec)
+    align.align_set_reference(L, large.xyzA)
+    etas = scangen.large_poses()[::64]
+    runs, exact = [], []
+    for _ in range(3):
+        runs.append(align.align_eval_mi(L, large.xyzB, eta6=etas, with_hist=True))
+        exact.append(len(align.align_eval_redo_poses(L)))
+    assert exact[-1] <= len(etas) // 50, exact
+    for mi, am, hist in runs[1:]:
+        assert np.array_equal(mi, runs[0][0]) and am == runs[0][1] and np.array_equal(hist, runs[0][2])
+    mi, am, hist = runs[-1]
+    assert am == lowest_argmax(mi)
+    sample = np.unique(np.concatenate([[am], np.arange(0, len(etas), 32)]))
+    G = oracle_grid(spec)
+    symA, boxA = G.reference(large.xyzA)
+    poses = align.align_round_poses(spec.origin, etas[sample])
+    mo, ho, _ = G.eval_mi(symA, boxA, large.xyzB, poses, nthreads=NT, with_hist=True)
+    assert np.array_equal(hist[sample], ho)
+    assert np.max(np.abs(mi[sample].astype(np.float64) - mo)) <= mi_tolerance()
