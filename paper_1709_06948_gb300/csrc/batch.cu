@@ -55,7 +55,7 @@ struct PairPlan {
   int64_t pts_off = 0;        // float4
   int64_t outc_off = 0;       // uint32
   int32_t passes0 = 1;        // the grid's key-partition seed for this launch's kind
-  int32_t spill_np = 0;       // single poses with 2-8 partitions: EvalArgs::spill_np (0: no queues)
+  int32_t spill_np = 0;       // 2-8 key partitions: EvalArgs::spill_np (0: no queues)
   int64_t spill_cap = 0;      // ... and the runs per queue
 };
 
@@ -393,22 +393,23 @@ align_status eval_batch_shape(align_batch* b, std::vector<PairPlan>& plans, cons
     // (a grid's align_set_sweep choice of single poses or pairs holds here too)
     const bool fits = pp.g->sweep_mode >= 0
                           ? pp.g->sweep_mode == 1
-                          : __atomic_load_n(&pp.g->passes_seed_pair[shape], __ATOMIC_RELAXED) <=
-                                __atomic_load_n(&pp.g->passes_seed[shape], __ATOMIC_RELAXED);
+                          : pairs_fit(pp.g, __atomic_load_n(&pp.g->passes_seed_pair[shape], __ATOMIC_RELAXED),
+                                      __atomic_load_n(&pp.g->passes_seed[shape], __ATOMIC_RELAXED));
     if (pose_pairs && fits && pp.prerot && pp.P >= 2) {
       const int nu = pair_units(pp.hposes.data(), pp.idx.data(), pp.P, pp.units);
       if (nu < pp.P) pp.n_units = nu;
       else pp.units.clear();
     }
-    // the seed of the kind this pair runs; single poses with key partitions sweep B once and
-    // queue the later partitions' runs (as the single-pair path does)
+    // the seed of the kind this pair runs; poses (or pose pairs) with key partitions sweep B
+    // once and queue its runs by partition (as the single-pair path does)
     pp.passes0 = __atomic_load_n(pp.n_units > 0 ? &pp.g->passes_seed_pair[shape] : &pp.g->passes_seed[shape],
                                  __ATOMIC_RELAXED);
     pp.spill_np = 0;
     pp.spill_cap = 0;
-    if (pp.n_units == 0 && pp.g->spill_on && pp.passes0 >= 2 && pp.passes0 <= 8) {
+    if (pp.g->spill_on && pp.passes0 >= 2 && pp.passes0 <= 8) {
       pp.spill_np = std::min(8, 2 * pp.passes0);
-      pp.spill_cap = ((pp.g->spill_runs > 0 ? pp.g->spill_runs : pp.n_pad / 2) + 31) / 32 * 32;
+      const int64_t runs = pp.g->spill_runs > 0 ? pp.g->spill_runs : pp.n_units > 0 ? pp.n_pad : pp.n_pad / 2;
+      pp.spill_cap = (runs + 31) / 32 * 32;
       spill_words = std::max(spill_words, (int64_t)pp.spill_np * pp.spill_cap);
     }
     pp.unit_off = units_n;

@@ -1230,9 +1230,10 @@ __device__ __forceinline__ uint4 ldg128_plain(const uint4* g) {
   return v;
 }
 
-// Pass `part` of a pose swept once (eval_kernel<..., kSp>): insert the runs that the sweep
-// queued for this partition.
-template <int kVW>
+// Pass `part` of a pose (or pose pair) swept once (eval_kernel<..., kSp>, eval_pair_kernel<...,
+// kSp>): insert the runs that the sweep queued for this partition.  kTwo: the pair kernel's
+// two-choice table, one batch per warp at a time with the next loading meanwhile.
+template <int kVW, bool kTwo = false>
 __device__ __forceinline__ void drain_spilled(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc,
                                               uint32_t part) {
   const uint32_t n = min(*(volatile uint32_t*)&S.spill_cnt[part], (uint32_t)a.spill_cap);
@@ -1240,10 +1241,21 @@ __device__ __forceinline__ void drain_spilled(const EvalSmem& S, const EvalArgs&
   const uint32_t lane = threadIdx.x & 31u;
   const uint4 none = make_uint4(kEmptyKey, 0u, 0u, 0u);
   uint32_t acc = 0u;
-  // each warp takes two batches of 32 at a time (the two inserts interleaved), the next two
-  // loading meanwhile
   constexpr uint32_t kStep = 32u * kWarps;
   uint32_t i = (threadIdx.x >> 5) * 32u;
+  if constexpr (kTwo) {
+    uint4 e = i + lane < n ? ldg128_plain(q + i + lane) : none;
+    for (; i < n; i += kStep) {  // the same trip count in every lane of a warp
+      const uint32_t j = i + kStep;
+      const uint4 nx = j + lane < n ? ldg128_plain(q + j + lane) : none;
+      insert_entry<kVW, true>(S, a, e, acc);
+      e = nx;
+    }
+    if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
+    return;
+  }
+  // each warp takes two batches of 32 at a time (the two inserts interleaved), the next two
+  // loading meanwhile
   uint4 e0 = i + lane < n ? ldg128_plain(q + i + lane) : none;
   uint4 e1 = i + kStep + lane < n ? ldg128_plain(q + i + kStep + lane) : none;
   for (; i < n; i += 2u * kStep) {  // the same trip count in every lane of a warp
@@ -1279,7 +1291,7 @@ __device__ __forceinline__ void pair_key(const VoxelConst& vc, float tx0, float 
 
 // One pass over all tiles for a pose pair (pre-rotated tiles): as sweep_pose, with one run
 // per pose; both poses' runs go to the same ring and table.
-template <int kVW, bool kPart>
+template <int kVW, bool kPart, bool kSpill = false>
 __device__ __forceinline__ void sweep_pair(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc, float tx0,
                                            float tx1, float ty, float tz, const float4* src, int nt, int lg,
                                            uint32_t part, uint32_t ring, uint32_t lane_lt, int cut) {
@@ -1297,8 +1309,8 @@ __device__ __forceinline__ void sweep_pair(const EvalSmem& S, const EvalArgs& a,
   int t = 0;
   for (; t + 2 * kPairDepth <= nt; t += kPairDepth) {
     if (t >= next_cut) {
-      ring_push<kVW, true>(S, ring, lane_lt, r0.key != kEmptyKey, r0, fill, a, acc);
-      ring_push<kVW, true>(S, ring, lane_lt, r1.key != kEmptyKey, r1, fill, a, acc);
+      ring_push<kVW, true, false, kSpill>(S, ring, lane_lt, r0.key != kEmptyKey, r0, fill, a, acc, (uint32_t)lg);
+      ring_push<kVW, true, false, kSpill>(S, ring, lane_lt, r1.key != kEmptyKey, r1, fill, a, acc, (uint32_t)lg);
       r0 = Run{kEmptyKey, 0u, 0u, 0u};
       r1 = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
@@ -1321,16 +1333,16 @@ __device__ __forceinline__ void sweep_pair(const EvalSmem& S, const EvalArgs& a,
     for (int d = 0; d < kPairDepth; ++d)
 #pragma unroll
       for (int j = 0; j < kPPT; ++j) {
-        run_step<kVW, true>(S, a, vc, k0[d][j], dzs[d][j], r0, ring, lane_lt, fill, acc);
-        run_step<kVW, true>(S, a, vc, k1[d][j], dzs[d][j], r1, ring, lane_lt, fill, acc);
+        run_step<kVW, true, false, kSpill>(S, a, vc, k0[d][j], dzs[d][j], r0, ring, lane_lt, fill, acc, (uint32_t)lg);
+        run_step<kVW, true, false, kSpill>(S, a, vc, k1[d][j], dzs[d][j], r1, ring, lane_lt, fill, acc, (uint32_t)lg);
       }
     xy += kPairDepth * kTileXY;
     zz += kPairDepth * kTileZ;
   }
   for (; t < nt; t += kPairDepth) {
     if (t >= next_cut) {
-      ring_push<kVW, true>(S, ring, lane_lt, r0.key != kEmptyKey, r0, fill, a, acc);
-      ring_push<kVW, true>(S, ring, lane_lt, r1.key != kEmptyKey, r1, fill, a, acc);
+      ring_push<kVW, true, false, kSpill>(S, ring, lane_lt, r0.key != kEmptyKey, r0, fill, a, acc, (uint32_t)lg);
+      ring_push<kVW, true, false, kSpill>(S, ring, lane_lt, r1.key != kEmptyKey, r1, fill, a, acc, (uint32_t)lg);
       r0 = Run{kEmptyKey, 0u, 0u, 0u};
       r1 = Run{kEmptyKey, 0u, 0u, 0u};
       next_cut += cut;
@@ -1347,8 +1359,8 @@ __device__ __forceinline__ void sweep_pair(const EvalSmem& S, const EvalArgs& a,
             if (q0 != kEmptyKey && ((q0 * 0x85EBCA77u) >> (32 - lg)) != part) q0 = kEmptyKey;
             if (q1 != kEmptyKey && ((q1 * 0x85EBCA77u) >> (32 - lg)) != part) q1 = kEmptyKey;
           }
-          run_step<kVW, true>(S, a, vc, q0, dz, r0, ring, lane_lt, fill, acc);
-          run_step<kVW, true>(S, a, vc, q1, dz, r1, ring, lane_lt, fill, acc);
+          run_step<kVW, true, false, kSpill>(S, a, vc, q0, dz, r0, ring, lane_lt, fill, acc, (uint32_t)lg);
+          run_step<kVW, true, false, kSpill>(S, a, vc, q1, dz, r1, ring, lane_lt, fill, acc, (uint32_t)lg);
         }
         if (t + kPairDepth + d < nt) load_tile_at(xy + d * kTileXY, zz + d * kTileZ, buf[d]);
       }
@@ -1356,9 +1368,9 @@ __device__ __forceinline__ void sweep_pair(const EvalSmem& S, const EvalArgs& a,
     xy += kPairDepth * kTileXY;
     zz += kPairDepth * kTileZ;
   }
-  ring_push<kVW, true>(S, ring, lane_lt, r0.key != kEmptyKey, r0, fill, a, acc);
-  ring_push<kVW, true>(S, ring, lane_lt, r1.key != kEmptyKey, r1, fill, a, acc);
-  while (fill > 0u) ring_drain<kVW, false, true>(S, ring, fill, min(fill, 32u), a, acc);
+  ring_push<kVW, true, false, kSpill>(S, ring, lane_lt, r0.key != kEmptyKey, r0, fill, a, acc, (uint32_t)lg);
+  ring_push<kVW, true, false, kSpill>(S, ring, lane_lt, r1.key != kEmptyKey, r1, fill, a, acc, (uint32_t)lg);
+  while (fill > 0u) ring_drain<kVW, false, true, false, kSpill>(S, ring, fill, min(fill, 32u), a, acc, (uint32_t)lg);
   if (kVW == 2 && (acc >> vc.wide_shift) != 0u) sts32(S.a_key - kFlagWide, 1u);  // may pass nlim_pack
 }
 
@@ -1468,7 +1480,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_kernel(const __grid
 // One sweep set of the pair kernel: the poses lp0 and, with kNP == 2, lp1 (a pair that shares
 // its tile copy and t'_y, t'_z) swept together over the same table, key partitions as
 // needed; then their histograms and boxes, or both poses to the exact path.
-template <int kVW>
+template <int kVW, bool kSp = false>
 __device__ __forceinline__ void pair_sweep_set(const EvalSmem& S, const EvalArgs& a, const VoxelConst& vc, int lp0,
                                                int lp1, bool two, int T, int cut, uint32_t cap, uint32_t ring,
                                                uint32_t lane_lt, unsigned long long* wide, int& passes) {
@@ -1487,9 +1499,19 @@ __device__ __forceinline__ void pair_sweep_set(const EvalSmem& S, const EvalArgs
   bool full = false, overflowed = false;
   for (int pass = 0; pass < pose_passes; ++pass) {
     if (!full) {
-      if (lg == 0) sweep_pair<kVW, false>(S, a, vc, P.t[0], tx1, P.t[1], P.t[2], src, nt, 0, 0u, ring, lane_lt, cut);
-      else sweep_pair<kVW, true>(S, a, vc, P.t[0], tx1, P.t[1], P.t[2], src, nt, lg, (uint32_t)pass, ring, lane_lt,
-                                 cut);
+      if constexpr (kSp) {
+        // the pair's points swept once in the first pass, every run queued by key partition;
+        // each pass inserts its partition's queue
+        if (pass == 0) {
+          sweep_pair<kVW, false, true>(S, a, vc, P.t[0], tx1, P.t[1], P.t[2], src, nt, lg, 0u, ring, lane_lt, cut);
+          __syncthreads();  // every queue complete (full is the same in every thread)
+        }
+        drain_spilled<kVW, true>(S, a, vc, (uint32_t)pass);
+      } else if (lg == 0) {
+        sweep_pair<kVW, false>(S, a, vc, P.t[0], tx1, P.t[1], P.t[2], src, nt, 0, 0u, ring, lane_lt, cut);
+      } else {
+        sweep_pair<kVW, true>(S, a, vc, P.t[0], tx1, P.t[1], P.t[2], src, nt, lg, (uint32_t)pass, ring, lane_lt, cut);
+      }
     }
     __syncthreads();
     if (!full && *(volatile uint32_t*)&S.flags[2] != 0u) {  // runs whose home bucket was full
@@ -1508,7 +1530,10 @@ __device__ __forceinline__ void pair_sweep_set(const EvalSmem& S, const EvalArgs
       S.flags[0] = 0u;
       S.flags[2] = 0u;
       S.flags[3] = 0u;
+      if (kSp && pass == pose_passes - 1)
+        for (int q = 0; q < 8; ++q) S.spill_cnt[q] = 0u;
     }
+    __syncthreads();  // the resets before the next pass's drains count again
   }
   if (full) {  // both poses are finished later by the exact path
     reset_pose(S, 0);
@@ -1518,14 +1543,14 @@ __device__ __forceinline__ void pair_sweep_set(const EvalSmem& S, const EvalArgs
       a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(I.pose_base + lp0);
       if (two) a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(I.pose_base + lp1);
     }
-    if (overflowed && passes < kMaxPasses) passes *= 2;
+    if (overflowed && passes < (kSp ? a.spill_np : kMaxPasses)) passes *= 2;
     __syncthreads();
     return;
   }
   emit_pose(S, I, lp0, 0);
   if (two) emit_pose(S, I, lp1, 1);
   else reset_pose(S, 1);
-  if (max_occupied > cap && passes < kMaxPasses) passes *= 2;  // crowded: more partitions next
+  if (max_occupied > cap && passes < (kSp ? a.spill_np : kMaxPasses)) passes *= 2;  // crowded: more next
 }
 
 // Pose pairs (pre-rotated tiles, one item): unit u of a.units is (pose, pose or -1), local
@@ -1533,7 +1558,9 @@ __device__ __forceinline__ void pair_sweep_set(const EvalSmem& S, const EvalArgs
 // poses that read the same tile copy and whose t'_y and t'_z are equal bit for bit are swept
 // together (sweep_pair: one point load and one y/z voxel-map half for both); any other unit
 // is swept one pose at a time.  The results are those of the single-pose kernel.
-template <int kVW>
+// kSp (a.spill set): every pair in 2 .. a.spill_np key partitions with its points swept once
+// and the runs queued by partition (as eval_kernel<..., kSp>).
+template <int kVW, bool kSp = false>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_pair_kernel(const __grid_constant__ EvalArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EvalSmem S;
@@ -1549,6 +1576,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_pair_kernel(const _
   select_item(S, a, 0);
   const EvalItem& I = a.one;
   int passes = I.passes0 > 0 ? I.passes0 : a.passes0;
+  if (kSp) passes = min(max(passes, 2), a.spill_np);
   const VoxelConst vc = voxel_const<kVW>(I.gc);
   // runs are cut every `cut` tiles (a multiple of the prefetch depth, where the sweep checks)
   const int cut = max(kDepth, (int)min(vc.nlim / (uint32_t)kPPT, (uint32_t)INT_MAX) / kDepth * kDepth);
@@ -1565,7 +1593,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) eval_pair_kernel(const _
     }
     if (two || p1 < 0) {
       // a single pose is swept as a pair whose second pose has no point inside the grid
-      pair_sweep_set<kVW>(S, a, vc, p0, p1, two, T, cut, cap, ring, lane_lt, wide, passes);
+      pair_sweep_set<kVW, kSp>(S, a, vc, p0, p1, two, T, cut, cap, ring, lane_lt, wide, passes);
     } else if (tid == 0) {  // not a pair after all: both poses go to the exact path (single sweeps)
       a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(I.pose_base + p0);
       a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(I.pose_base + p1);
@@ -1648,6 +1676,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         S.flags[2] = 0u;
         S.flags[3] = 0u;
       }
+      __syncthreads();  // the resets before the next pass's drains count again
     }
     if (full) {  // finished later by the exact path
       reset_pose(S);
@@ -1969,6 +1998,8 @@ cudaError_t setup_t(int smem) {
     e = cudaFuncSetAttribute(redo_kernel<kVW, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess && !kRot)
     e = cudaFuncSetAttribute(eval_pair_kernel<kVW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess && !kRot)
+    e = cudaFuncSetAttribute(eval_pair_kernel<kVW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(eval_cluster_kernel<kVW, kRot>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
@@ -2014,7 +2045,8 @@ int eval_table_slots_for(int K, int vw, size_t smem_budget, int np) {
 
 template <int kVW>
 cudaError_t launch_pair_t(const EvalArgs& a, int n_ctas, size_t smem, cudaStream_t s) {
-  eval_pair_kernel<kVW><<<n_ctas, kThreads, smem, s>>>(a);
+  if (a.spill != nullptr) eval_pair_kernel<kVW, true><<<n_ctas, kThreads, smem, s>>>(a);
+  else eval_pair_kernel<kVW><<<n_ctas, kThreads, smem, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   redo_kernel<kVW, false><<<n_ctas, kThreads, smem, s>>>(a);

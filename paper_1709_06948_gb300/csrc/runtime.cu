@@ -380,11 +380,21 @@ int pair_units_impl(const float* poses12, const int32_t* src, int64_t P, std::ve
   return (int)pairs.size();
 }
 
-// Whether the next pre-rotated launch on this grid evaluates pose pairs: while pairs have
-// needed no more key partitions than single poses (both counts are learned per grid and
-// only grow), one pair sweep does the work of two single sweeps.
+// Whether the next pre-rotated launch on this grid evaluates pose pairs (automatic choice,
+// from the key-partition counts learned per grid, which only grow): while pairs have needed
+// no more partitions than single poses, one pair sweep does the work of two single sweeps;
+// and where both need partitions, the spill queues sweep the points once whatever the count,
+// so pairs pay only their extra passes' table scans: measured per 4,096 poses 2.44 against
+// 2.51 ms (0.25 m LiDAR grid, 4 against 2 partitions), and even on the 6.4M-voxel grid (8
+// against 4; 6.6-6.8 against 6.6-7.0 ms over three runs).
+}  // namespace
+bool mialign::pairs_fit(const align_grid* g, int32_t seed_pair, int32_t seed_single) {
+  if (seed_pair <= seed_single) return true;
+  return g->spill_on && seed_single >= 2 && seed_pair <= 2 * seed_single && seed_pair <= g->spill_np_max;
+}
+namespace {
 bool use_pairs(const align_grid* g) {
-  return g->sweep_mode < 0 ? g->passes_seed_pair[0] <= g->passes_seed[0] : g->sweep_mode == 1;
+  return g->sweep_mode < 0 ? pairs_fit(g, g->passes_seed_pair[0], g->passes_seed[0]) : g->sweep_mode == 1;
 }
 
 // Whether a launch of single poses runs one pose per 2-CTA cluster: while the grid's single
@@ -535,13 +545,13 @@ align_status enqueue_eval_core(align_grid* g, int32_t n_tiles, const float* d_po
   CU(g->ovf.ensure((size_t)n_ctas * ek.ovf_cap() * 16), "allocate overflow lists");
   a.ovf = g->ovf.as<uint4>();
   a.ovf_cap = ek.ovf_cap();
-  // single poses that need key partitions: B swept once, its runs queued by partition (room
-  // for one doubling of the seed, at most 8 partitions; half a run per padded point and
-  // queue: a queue that fills sends its pose to the exact path)
-  if (g->spill_on && !pairs && !cluster && out.dump == nullptr && item.passes0 >= 2 &&
-      item.passes0 <= g->spill_np_max) {
+  // single poses or pose pairs that need key partitions: B swept once, its runs queued by
+  // partition (room for one doubling of the seed, at most 8 partitions; half a run per padded
+  // point and queue, a whole one for pairs: a queue that fills sends its pose to the exact
+  // path)
+  if (g->spill_on && !cluster && out.dump == nullptr && item.passes0 >= 2 && item.passes0 <= g->spill_np_max) {
     const int32_t np = std::min(g->spill_np_max, 2 * item.passes0);
-    const int64_t cap = ((g->spill_runs > 0 ? g->spill_runs : n_pad / 2) + 31) / 32 * 32;
+    const int64_t cap = ((g->spill_runs > 0 ? g->spill_runs : pairs ? n_pad : n_pad / 2) + 31) / 32 * 32;
     CU(g->spill.ensure((size_t)n_ctas * (size_t)np * (size_t)cap * 16), "allocate spill queues");
     a.spill = g->spill.as<uint4>();
     a.spill_cap = cap;

@@ -74,6 +74,9 @@ align_status check_grid_device(align_grid* g);
 // (src, or all one copy when NULL) and bitwise equal t'_y, t'_z, two per unit in order of
 // their first pose (local indices; the second -1 for a single pose).  Returns the units.
 int pair_units(const float* poses12, const int32_t* src, int64_t P, std::vector<int32_t>& units);
+// Whether pose pairs are the automatic choice for a grid with these learned key-partition
+// counts (pairs, single poses).
+bool pairs_fit(const align_grid* g, int32_t seed_pair, int32_t seed_single);
 // One level of the coarse-to-fine lattice: FP64 poses around centre c (ranges r, m samples
 // per axis; order rx, ry, rz, tx, ty, tz with tz fastest) and their rounded FP32 form.
 void lattice_poses(const float origin[3], const double c[6], const double r[6], const int32_t m[6],

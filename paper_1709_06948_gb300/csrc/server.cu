@@ -121,8 +121,8 @@ size_t request_bytes(int64_t nB, const int32_t m[6], int K, int T, int n_sm, int
   if (n_rot > std::max<int64_t>(1, P / 4)) n_rot = 1;
   const int64_t per_pose = (int64_t)K * K * 4 + 24 + 4 + 48 + 4 + 4 + 4;
   const int64_t per_cta = 2 * (int64_t)T * 8 + (int64_t)eval_shape(0).ovf_cap() * 16;
-  // spill queues: spill_np of n_pad / 2 runs per CTA
-  const int64_t spill = spill_np > 1 ? (int64_t)spill_np * ((n_pad / 2 + 31) / 32 * 32) * 16 : 0;
+  // spill queues: spill_np of n_pad runs per CTA (pose pairs'; single poses use half)
+  const int64_t spill = spill_np > 1 ? (int64_t)spill_np * ((n_pad + 31) / 32 * 32) * 16 : 0;
   return (size_t)(nB * 12 + n_rot * n_pad * 16 + P * per_pose + (int64_t)n_sm * (per_cta + spill));
 }
 

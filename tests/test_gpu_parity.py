@@ -210,10 +210,10 @@ def test_pose_pairs_match_single_pose_kernel(res, feature):
 
 def test_every_sweep_kind_agrees_on_a_fine_grid():
     """The 120k-point LiDAR pair on a 0.25 m grid (320x320x32, z-variance), 4,096 lattice
-    poses swept each way the library has (one pose per CTA, with its key partitions' runs
-    queued after one sweep of B, with queues of 64 runs that overflow and send the poses to
-    the exact path, or with one sweep per partition; pose pairs; one pose per 2-CTA cluster
-    with its table split between two shared memories; the automatic choice),
+    poses swept each way the library has (one pose per CTA and pose pairs, each with its key
+    partitions' runs queued after one sweep of B, with queues of 64 runs that overflow and
+    send the poses to the exact path, or with one sweep per partition; one pose per 2-CTA
+    cluster with its table split between two shared memories; the automatic choice),
     each on a fresh grid: MI, argmax and every histogram are identical across the kinds, and
     a sample holding the argmax and every exact-path pose matches the oracle."""
     from paper_1709_06948_gb300 import align
@@ -222,8 +222,8 @@ def test_every_sweep_kind_agrees_on_a_fine_grid():
     etas = scangen.lidar_poses()
     P = len(etas)
     runs, must = [], set()
-    for kind, spill, queue_runs in ((0, True, 0), (0, True, 64), (0, False, 0), (1, True, 0), (2, True, 0),
-                                    (-1, True, 0)):
+    for kind, spill, queue_runs in ((0, True, 0), (0, True, 64), (0, False, 0), (1, True, 0), (1, True, 64),
+                                    (1, False, 0), (2, True, 0), (-1, True, 0)):
         L = lib_grid(spec)
         align.align_set_reference(L, pair.xyzA)
         align.align_set_sweep(L, kind)
@@ -255,3 +255,36 @@ def test_every_sweep_kind_agrees_on_a_fine_grid():
     mo, ho, _ = G.eval_mi(symA, boxA, pair.xyzB, poses[sample], nthreads=NT, with_hist=True)
     assert np.array_equal(h0[sample], ho)
     assert np.max(np.abs(mi0[sample].astype(np.float64) - mo)) <= mi_tolerance()
+
+
+def test_spill_queues_with_raw_tiles():
+    """Poses whose rotations do not repeat (random, as a Nelder-Mead simplex gives) use raw
+    tiles that the kernel rotates itself; on the 0.25 m grid they need key partitions.  With
+    the spill queues and with one sweep of B per partition the results are identical, and a
+    sample matches the oracle."""
+    from paper_1709_06948_gb300 import align
+    pair = scangen.lidar_pair()
+    spec = scangen.lidar_grid(0.25)
+    rng = np.random.default_rng(86)
+    etas = np.concatenate([rng.uniform(-2, 2, (600, 2)), rng.uniform(-0.2, 0.2, (600, 1)),
+                           rng.uniform(-0.02, 0.02, (600, 2)), rng.uniform(-0.1, 0.1, (600, 1))], 1)
+    res = []
+    for spill in (True, False):
+        L = lib_grid(spec)
+        align.align_set_reference(L, pair.xyzA)
+        align.align_set_sweep(L, 0)
+        align.align_set_spill(L, spill)
+        align.align_eval_mi(L, pair.xyzB, eta6=etas)  # learns the partitions
+        res.append(align.align_eval_mi(L, pair.xyzB, eta6=etas, with_hist=True))
+        assert align.align_eval_stats(L)["passes"] >= 2
+        L.close()
+    (mi, am, hist), (mi_p, am_p, hist_p) = res
+    assert np.array_equal(mi, mi_p) and am == am_p and np.array_equal(hist, hist_p)
+    assert am == lowest_argmax(mi)
+    sample = np.unique(np.concatenate([[am], np.arange(0, len(etas), 40)]))
+    G = oracle_grid(spec)
+    symA, boxA = G.reference(pair.xyzA)
+    poses = align.align_round_poses(spec.origin, etas[sample])
+    mo, ho, _ = G.eval_mi(symA, boxA, pair.xyzB, poses, nthreads=NT, with_hist=True)
+    assert np.array_equal(hist[sample], ho)
+    assert np.max(np.abs(mi[sample].astype(np.float64) - mo)) <= mi_tolerance()
