@@ -861,6 +861,44 @@ def run_sweeps(args):
     return 0
 
 
+def run_dense(args):
+    """The 128-beam large scan (258k points; every 8th pose of its lattice: 4,096) on coarse
+    240 m square z-variance grids at 1 m and 0.5 m, whose near-sensor voxels hold thousands of
+    points: per call of align_eval_mi on one grid, the eval-kernel time (CUDA events, exact
+    path included), the sweep kind, key partitions, table slots (the layout) and the poses
+    the exact path finished, for the automatic choice and single poses.  One JSON line."""
+    import torch
+    from paper_1709_06948_gb300 import align
+    torch.cuda.set_device(0)
+    big = scangen.large_pair()
+    etas = scangen.large_poses()[::8]
+    B = torch.from_numpy(big.xyzB).cuda()
+    out = []
+    for res in (1.0, 0.5):
+        n = int(round(240 / res))
+        kw = dict(origin=(-120.0, -120.0, -5.0), res_m=res, dims=(n, n, int(round(20 / res))), feature=1,
+                  count_levels=1, var_levels=15)
+        for kind in (-1, 0):
+            L = align.align_create_grid(**kw)
+            align.align_set_reference(L, big.xyzA)
+            align.align_set_sweep(L, kind)
+            calls = []
+            for _ in range(max(5, args.steps)):
+                align.align_profile(L, 1)
+                align.align_eval_mi(L, B, eta6=etas)
+                ev, _, cnt = align.align_profile(L, 2)
+                st = align.align_eval_stats(L)
+                calls.append({"eval_ms": round(ev / max(cnt, 1), 3), "sweep": align.SWEEP_KINDS.get(st["sweep"]),
+                              "key_partitions": st["passes"], "table_slots": st["table_slots"],
+                              "exact_path_poses": int(len(align.align_eval_redo_poses(L)))})
+            align.align_profile(L, 0)
+            out.append({"res_m": res, "dims": kw["dims"], "kind": kind, "calls": calls})
+            L.close()
+    print(json.dumps({"mode": "dense", "gpu": torch.cuda.get_device_name(0), "points": int(big.xyzB.shape[0]),
+                      "poses": len(etas), "results": out}))
+    return 0
+
+
 def run_peaks(args):
     """The measured peaks alone (one JSON line)."""
     import torch
@@ -881,13 +919,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="search", choices=["search", "eval", "accuracy", "surface", "peaks", "sweeps"],
+    ap.add_argument("--mode", default="search",
+                    choices=["search", "eval", "accuracy", "surface", "peaks", "sweeps", "dense"],
                     help="search: reference build + 6-level search per step (default); "
                          "eval: reference build + one align_eval_mi of --poses poses per step; "
                          "accuracy: final error vs initial error (synthetic Figs. 4-5); "
                          "surface: MI cost surfaces around the truth (synthetic Fig. 6); "
                          "peaks: the throughput micro-benchmarks alone; "
-                         "sweeps: eval-kernel time of each way of sweeping poses on three grids")
+                         "sweeps: eval-kernel time of each way of sweeping poses on three grids; "
+                         "dense: a dense 128-beam scan on coarse grids, per call (layout and partitions learned)")
     ap.add_argument("--sweep-workloads", default=",".join(SWEEP_WORKLOADS), help="sweeps mode: workloads")
     ap.add_argument("--sweep-kinds", default="-1,0,0nospill,1,2",
                     help="sweeps mode: align_set_sweep kinds (0nospill: kind 0 with align_set_spill off)")
@@ -913,6 +953,8 @@ def main():
         return run_peaks(args)
     if args.mode == "sweeps":
         return run_sweeps(args)
+    if args.mode == "dense":
+        return run_dense(args)
     return run_ours(args)
 
 
