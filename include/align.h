@@ -180,20 +180,22 @@ align_status align_refine_nm(align_grid* grid, const float* xyzB, int64_t nB, in
 align_status align_eval_stats(align_grid* grid, int64_t out[6]);
 
 /* How this grid's launches sweep their poses (the kinds of align_eval_stats [5]): -1
-   automatic (the default: pairs while their tables fit as well as single poses', the
-   cluster while single poses need 8 or more key partitions), 0 one pose per CTA, 1 pose
+   automatic (the default: pairs while their tables need no more key partitions than
+   single poses', or, with spill queues and both partitioned, no more than twice as many up
+   to 8; the cluster while single poses need 8 or more key partitions), 0 one pose per CTA, 1 pose
    pairs wherever the poses form pairs (single poses elsewhere), 2 one pose per 2-CTA
    cluster for single-pose launches (never for align_accumulate's dumps nor inside a batch,
    which sweeps pairs or single poses).  Results are the same for every kind; the choice
    serves measurement and tests.  Errors: ALIGN_E_INVALID for another value. */
 align_status align_set_sweep(align_grid* grid, int32_t kind);
 
-/* Whether single poses that need key partitions sweep B once (on = 1, the default) or once
-   per partition (0).  Swept once, the sweep appends every run of B's points to a per-CTA
-   queue of its key partition in device memory, and each pass inserts one queue into the
-   shared-memory table.  queue_runs: runs each queue holds (16 bytes each, rounded up to a
-   multiple of 32); 0 (the default) sizes them for half the points of B, so that the grid
-   holds about CTAs x 8 x n_B / 2 x 16 bytes at 8 partitions.  A pose
+/* Whether poses (or pose pairs) that need key partitions sweep B once (on = 1, the default)
+   or once per partition (0).  Swept once, the sweep appends every run of B's points to a
+   per-CTA queue of its key partition in device memory, and each pass inserts one queue into
+   the shared-memory table.  queue_runs: runs each queue holds (16 bytes each, rounded up to
+   a multiple of 32); 0 (the default) sizes them for half the points of B (all of them for
+   pose pairs), so that the grid holds about CTAs x 8 x n_B / 2 x 16 bytes at 8 partitions
+   of single poses.  A pose
    whose runs overflow a queue is finished by the exact path.  Results are the same either
    way.  Errors: ALIGN_E_INVALID for another on, or queue_runs outside 0 .. 2^31. */
 align_status align_set_spill(align_grid* grid, int32_t on, int64_t queue_runs);
