@@ -23,6 +23,15 @@
 //    keys split into 2, 4, ... hash partitions, each run added at once, the plain count in
 //    the table and S1, S2 in 64-bit sums in global memory.  A crowded table makes the CTA
 //    sweep its following poses in twice as many partitions.
+//  - Key partitions: a pose whose voxels do not fit the table keeps the keys of one hash
+//    partition per pass.  With spill queues (eval_kernel<..., kSp>) B is swept once, every
+//    run is appended to its partition's queue in device memory, and each pass inserts one
+//    queue; otherwise every pass sweeps B and drops the other partitions' keys.
+//
+// eval_pair_kernel: two poses that read the same tile copy and differ only in t'_x, swept
+// together over one table (one point load and one y/z half of the voxel map for both).
+// eval_cluster_kernel: one pose per 2-CTA cluster, its table split between the two CTAs'
+// shared memories (distributed shared memory).
 //
 // compose_kernel: per pose, the overlap box (Algorithm 1), A's symbol counts over it from
 // per-symbol prefix sums, the phi column h[a][0], then Eqs. 2-5 in FP32 with a fixed
