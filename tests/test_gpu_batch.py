@@ -126,8 +126,9 @@ def test_key_partitions_in_a_batch():
     """Pairs on a 0.25 m grid whose single poses need key partitions: after the grid has
     learned them, the batch sweeps B once per pose and queues the later partitions' runs
     (spill queues, as align_eval_mi does); with the queues switched off on the grid it sweeps
-    B once per partition.  Both batches, align_eval_mi alone and the oracle on a sample
-    agree (MI and argmax bit-identical between the library's paths)."""
+    B once per partition; with two poses per CTA it sweeps pose pairs, queued as well.  All
+    batches, align_eval_mi alone and the oracle on a sample agree (MI and argmax
+    bit-identical between the library's paths)."""
     from paper_1709_06948_gb300 import align
     pair = scangen.lidar_pair()
     spec = scangen.lidar_grid(0.25)
@@ -144,8 +145,13 @@ def test_key_partitions_in_a_batch():
     align.align_set_spill(c.L, False)
     res_p = align.align_eval_batch(b, _pairs([c, small]))
     align.align_set_spill(c.L, True)
-    for cc, (mi_q, am_q), (mi_p, am_p) in zip((c, small), res_q, res_p):
+    # pose pairs (their own partitions, queued as well) give the same results
+    align.align_batch_set_poses_per_cta(b, 2)
+    res_2 = align.align_eval_batch(b, _pairs([c, small]))
+    assert align.align_batch_stats(b)["poses_per_cta"] == 2
+    for cc, (mi_q, am_q), (mi_p, am_p), (mi_2, am_2) in zip((c, small), res_q, res_p, res_2):
         assert np.array_equal(mi_q, mi_p) and am_q == am_p
+        assert np.array_equal(mi_q, mi_2) and am_q == am_2
         mi0, am0, _ = align.align_eval_mi(cc.L, cc.xyzB, eta6=cc.etas)
         assert np.array_equal(mi_q, mi0) and am_q == am0
     G = oracle_grid(spec)
